@@ -1,0 +1,160 @@
+"""Seeded synthetic inputs (SplitMix64), shared by the tests, the bench and the oracle runs.
+
+This module holds data generation only -- none of the method's arithmetic.  Every
+array is a numpy ``uint64`` array produced from a counter-based SplitMix64 stream
+(value i of stream ``seed`` is ``mix(seed + (i + 1) * GAMMA)``), so the same seed
+gives the same column on any machine.
+
+Shapes and distributions follow the paper's synthetic columns (Sec. 5.1, Table 1)
+and the workloads this project measures:
+  * ``table1_column``   -- C1..C4 of Table 1 (C1 uniform in [0,63]; C2 with 0.01%
+    outliers 2^63-1; C3 uniform in [2^62, 2^62+63]; C4 sorted in [2^47, 2^47+100K]),
+  * ``tiny_fragment``   -- two 2^20-row columns: A ~ U[0,2^12), B ~ U[0,2^20),
+  * ``skewed_widths``   -- per-512-block bit width drawn from {3,8,16,27,40},
+  * ``sorted_gaps``     -- sorted keys with geometric gaps of mean 4,
+  * ``star_fact`` / ``star_dims`` -- a star-schema-shaped fact table and dimensions.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+BLOCK = 512
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Values offset .. offset+n-1 of the counter-based SplitMix64 stream ``seed``."""
+    with np.errstate(over="ignore"):
+        i = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform(seed: int, n: int, lo: int, hi: int) -> np.ndarray:
+    """Integers in [lo, hi) (hi - lo >= 1).  Power-of-two spans take the top bits."""
+    span = hi - lo
+    if span <= 0:
+        raise ValueError("empty range")
+    z = splitmix64(seed, n)
+    if span & (span - 1) == 0:
+        k = span.bit_length() - 1
+        r = (z >> np.uint64(64 - k)) if k > 0 else np.zeros(n, dtype=np.uint64)
+    else:
+        r = z % np.uint64(span)
+    with np.errstate(over="ignore"):
+        return r + np.uint64(lo)
+
+
+def geometric_gaps(seed: int, n: int) -> np.ndarray:
+    """Gaps in {1, 2, ...} with P(g = k) = (3/4)^(k-1) / 4 (mean 4), capped at 33.
+
+    Trial t succeeds when bits 2t, 2t+1 of the draw are both zero (probability 1/4).
+    """
+    z = splitmix64(seed, n)
+    gap = np.full(n, 33, dtype=np.uint64)
+    open_ = np.ones(n, dtype=bool)
+    for t in range(32):
+        hit = open_ & (((z >> np.uint64(2 * t)) & np.uint64(3)) == 0)
+        gap[hit] = t + 1
+        open_ &= ~hit
+    return gap
+
+
+# --------------------------------------------------------------- Table 1 columns
+
+def table1_column(which: str, n: int, seed: int = 1) -> np.ndarray:
+    """Synthetic columns C1-C4 (Sec. 5.1, Table 1), length n."""
+    if which == "C1":
+        return uniform(seed, n, 0, 64)
+    if which == "C2":
+        x = uniform(seed, n, 0, 64)
+        out = splitmix64(seed + 7, n) % np.uint64(10000) == 0  # 0.01 % outliers
+        x[out] = np.uint64(2**63 - 1)
+        return x
+    if which == "C3":
+        return uniform(seed, n, 2**62, 2**62 + 64)
+    if which == "C4":
+        return np.sort(uniform(seed, n, 2**47, 2**47 + 100_000 + 1))
+    raise ValueError(which)
+
+
+def table1_point_select_variant(which: str, n: int, seed: int = 1) -> np.ndarray:
+    """Sec. 5.1 single-operator input: 90% of values equal the column's lowest value."""
+    x = table1_column(which, n, seed)
+    lowest = {"C1": 0, "C2": 0, "C3": 2**62, "C4": 2**47}[which]
+    pick = splitmix64(seed + 11, n) % np.uint64(10) != 0
+    x = x.copy()
+    x[pick] = np.uint64(lowest)
+    if which == "C4":
+        x = np.sort(x)
+    return x
+
+
+# ------------------------------------------------------------ measured workloads
+
+def tiny_fragment(seed: int = 42, n: int = 1 << 20):
+    """Two columns: A ~ U[0, 2^12) (static BP at 12 bits), B ~ U[0, 2^20)."""
+    return uniform(seed, n, 0, 1 << 12), uniform(seed + 1, n, 0, 1 << 20)
+
+
+WIDTH_CHOICES = (3, 8, 16, 27, 40)
+
+
+def skewed_widths(seed: int, n: int, widths=WIDTH_CHOICES) -> np.ndarray:
+    """Per 512-block width b drawn uniformly from ``widths``; values U[0, 2^b) with
+    one value per block forced to have bit b-1 set, so the block's width is exactly b."""
+    nblk = (n + BLOCK - 1) // BLOCK
+    choice = np.asarray(widths, dtype=np.uint64)[splitmix64(seed, nblk) % np.uint64(len(widths))]
+    b = np.repeat(choice, BLOCK)[:n]
+    z = splitmix64(seed + 1, n)
+    x = z >> (np.uint64(64) - b)
+    first = np.arange(0, n, BLOCK)
+    forced_at = first + (splitmix64(seed + 2, nblk) % np.uint64(BLOCK)).astype(np.int64)
+    forced_at = np.minimum(forced_at, n - 1)
+    x[forced_at] |= np.uint64(1) << (b[forced_at] - np.uint64(1))
+    return x
+
+
+def sorted_gaps(seed: int, n: int) -> np.ndarray:
+    """Sorted keys: K_0 = 0 and K_i - K_{i-1} ~ Geometric(1/4) (mean 4)."""
+    if n == 0:
+        return np.zeros(0, dtype=np.uint64)
+    g = geometric_gaps(seed, n)
+    g[0] = 0
+    return np.cumsum(g, dtype=np.uint64)
+
+
+def value_at_rank(x: np.ndarray, s: float) -> int:
+    """Value at rank floor(s*n) of x sorted ascending (threshold for `x < c` at selectivity ~s)."""
+    k = min(int(s * x.size), x.size - 1)
+    return int(np.partition(x, k)[k])
+
+
+# ---------------------------------------------------------------- star schema
+
+DIM_SIZES = (2_500_000, 200_000, 30_000, 2556)
+
+
+def star_dims(seed: int = 7):
+    """Dimension attributes: D1.c5 ~ U[0,5) over 2.5e6 keys, D2.c25 ~ U[0,25) over 2e5 keys."""
+    return uniform(seed, DIM_SIZES[0], 0, 5), uniform(seed + 1, DIM_SIZES[1], 0, 25)
+
+
+def star_fact(seed: int, n: int) -> dict:
+    """Fact columns: fk1..fk3 uniform over the dimension sizes, fk_date sorted over
+    [0, 2556) with equal counts per day, quantity U[1,50], discount U[0,10],
+    revenue U[0, 2^23)."""
+    day = (np.arange(n, dtype=np.uint64) * np.uint64(DIM_SIZES[3])) // np.uint64(max(n, 1))
+    return {
+        "fk1": uniform(seed + 10, n, 0, DIM_SIZES[0]),
+        "fk2": uniform(seed + 11, n, 0, DIM_SIZES[1]),
+        "fk3": uniform(seed + 12, n, 0, DIM_SIZES[2]),
+        "fk_date": day,
+        "quantity": uniform(seed + 13, n, 1, 51),
+        "discount": uniform(seed + 14, n, 0, 11),
+        "revenue": uniform(seed + 15, n, 0, 1 << 23),
+    }
