@@ -1,0 +1,226 @@
+/*
+ * morphstore.h -- C ABI of libms, a GB300 (sm_103a) implementation of the
+ * compression-enabled processing model of MorphStore (Damme et al., VLDB 2020,
+ * arXiv 2004.09350).
+ *
+ * Model (Sec. 3, Sec. 4).  Base data, intermediates and results are columns of
+ * unsigned 64-bit integers.  Every column is stored in exactly one format
+ * ("Foundations", Sec. 3.1; "Column Storage", Sec. 4.1).  Operators follow the
+ * operator-at-a-time model: each runs to completion and materialises its output
+ * column.  Each operator takes the formats of its inputs from the columns and a
+ * caller-chosen output format.  It decompresses input blocks on the fly, runs its
+ * core on the uncompressed values in registers, and recompresses the output
+ * block by block.  This is the "on-the-fly de/re-compression" degree of Sec. 3.2,
+ * fused into one kernel per operator.  No uncompressed intermediate is written
+ * to device memory.
+ *
+ * Formats and byte layout (Sec. 2.1 techniques; Sec. 4.1 main part of 512-value
+ * blocks plus an uncompressed remainder behind it):
+ *   bw(x)        number of significant bits of x; bw(0) = 0.
+ *   block        512 consecutive values.  Value i of a block is value k = i%16 of
+ *                lane j = i/16.  Lane j's 16 values are packed LSB-first at b bits:
+ *                value k sits at stream bits [k*b, k*b+b).  Stream halfword q of
+ *                lane j is stored at payload halfword 32*q + j.  A block of width b
+ *                therefore takes 64*b bytes.
+ *   MS_UNCOMPR   n raw little-endian uint64 values; size 8n.
+ *   MS_STATIC_BP every full 512-value chunk is packed as a block at the fixed
+ *                width b (chunk c at byte 64*b*c).  The n%512 tail values follow,
+ *                packed LSB-first one after the other, padded to whole words.
+ *                size = ceil(n*b/64)*8.  Random access needs no directory.
+ *   MS_DYN_BP    header of n/512 entries {(payload word offset << 8) | b_k, ref_k},
+ *                then the block payloads, then the n%512 remainder values as raw
+ *                uint64.  b_k = bw(max residual), residual = value, ref = 0
+ *                (SIMD-BP512, Sec. 4.1).
+ *   MS_DELTA_BP  as DYN_BP with residual_0 = 0, residual_i = x_i - x_{i-1}
+ *                (mod 2^64), ref = the block's first value.  DELTA is the
+ *                difference to the predecessor, restarted at every block.
+ *   MS_FOR_BP    as DYN_BP with residual = x - ref, ref = the block minimum.  FOR
+ *                is the difference to a reference value.
+ *   A column buffer starts on a 256-byte boundary.  The header is 16 bytes per
+ *   block, so every block payload starts on a 64-byte boundary.
+ *
+ * Memory and ownership.  A context owns an arena of device memory.  Operator
+ * outputs are carved from it at a device-side top-of-arena offset.  The
+ * output's size is therefore decided on the GPU and the host never waits for
+ * it.  Column metadata (length, size, ...) lives in device memory.
+ * ms_column_info() is the one call that copies it to the host, and it
+ * synchronises the stream.  Arena columns are released in LIFO order: freeing a
+ * column that is not the most recent one only marks it, and its space comes
+ * back when every column allocated after it is freed too.  Imported columns are
+ * allocated with the context's allocator callbacks (cudaMalloc when none are
+ * given).
+ *
+ * Streams and errors.  Operators are asynchronous on the given stream.
+ * `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ * stream.  Operators on one context must be ordered on one stream.
+ * Host-detectable errors (NULL pointers, unknown formats, static_bw outside
+ * 1..64) return immediately with nothing enqueued.  Device-detected errors are
+ * stored in a sticky device error word: a value too wide for static BP, a
+ * position >= n, a group id >= G, a corrupt header, a length mismatch, arena
+ * exhaustion, or a bounded spin running out.  The next ms_get_error() returns
+ * that word and clears it.  After a device error the outputs are unspecified
+ * but every write stayed in bounds.  No exception crosses this interface.
+ *
+ * Final query results are uncompressed (Sec. 3.3).  They come out through
+ * ms_decompress, ms_agg_sum or ms_group_sum into caller-owned device memory.
+ */
+#ifndef MORPHSTORE_H
+#define MORPHSTORE_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MS_UNCOMPR = 0,
+  MS_STATIC_BP = 1,
+  MS_DYN_BP = 2,
+  MS_DELTA_BP = 3,
+  MS_FOR_BP = 4
+} ms_fmt;
+
+typedef enum {
+  MS_OK = 0,
+  MS_ERR_INVALID_ARG = 1,
+  MS_ERR_FORMAT = 2,
+  MS_ERR_VALUE_TOO_WIDE = 3,
+  MS_ERR_OUT_OF_RANGE = 4,
+  MS_ERR_NOMEM = 5,
+  MS_ERR_TIMEOUT = 6,
+  MS_ERR_CUDA = 7
+} ms_status;
+
+/* select predicates against constants (Sec. 5.1 uses a point predicate) */
+typedef enum {
+  MS_EQ = 0, MS_NE = 1, MS_LT = 2, MS_LE = 3, MS_GT = 4, MS_GE = 5,
+  MS_BETWEEN = 6 /* c1 <= x <= c2 */
+} ms_cmp;
+
+typedef enum { MS_ADD = 0, MS_SUB = 1, MS_MUL = 2 } ms_arith;
+
+typedef struct ms_ctx ms_ctx;
+typedef struct ms_column ms_column;
+
+/* Allocator callbacks.  Must return device memory that is at least 256-byte
+   aligned, or NULL on failure. */
+typedef void *(*ms_alloc_fn)(size_t bytes, void *user);
+typedef void (*ms_free_fn)(void *ptr, void *user);
+
+/* Host copy of a column's metadata (filled by ms_column_info). */
+typedef struct {
+  uint64_t n;             /* logical values */
+  int32_t fmt;            /* ms_fmt */
+  int32_t static_bw;      /* width of MS_STATIC_BP, else 0 */
+  uint64_t size_bytes;    /* physical size (the paper's footprint measure, Sec. 5) */
+  uint64_t n_blocks;      /* 512-value blocks in the main part (block formats) */
+  uint64_t payload_words; /* packed payload size in uint64 words (block formats) */
+  uint64_t device_ptr;    /* device address of the column buffer */
+} ms_column_meta;
+
+/* ---------------------------------------------------------------- context */
+
+/* Creates a context on `device`.  The context owns an arena of `arena_bytes`
+   for operator outputs and scratch space for columns of up to `max_rows`
+   values.  Scratch grows on demand for longer columns; growing synchronises the
+   device.  alloc/free may be NULL, which means cudaMalloc/cudaFree.
+   Errors: MS_ERR_INVALID_ARG, MS_ERR_NOMEM, MS_ERR_CUDA. */
+ms_status ms_ctx_create(ms_ctx **out, int device, uint64_t arena_bytes,
+                        uint64_t max_rows, ms_alloc_fn alloc, ms_free_fn free_fn,
+                        void *user);
+/* Synchronises the device, frees every column and the context's memory. */
+ms_status ms_ctx_destroy(ms_ctx *ctx);
+
+/* Reads and clears the sticky device error word; synchronises `stream`. */
+ms_status ms_get_error(ms_ctx *ctx, void *stream);
+/* Details of the last device error (an offending index or value), 0 if none;
+   valid after ms_get_error returned an error. */
+uint64_t ms_last_error_info(ms_ctx *ctx);
+
+/* Arena bytes in use (current) and the high-water mark since the last reset;
+   both synchronise `stream`.  The high-water mark is the peak footprint of the
+   operator outputs. */
+ms_status ms_arena_usage(ms_ctx *ctx, uint64_t *in_use, uint64_t *high_water,
+                         void *stream);
+ms_status ms_arena_reset_high_water(ms_ctx *ctx, void *stream);
+
+/* ---------------------------------------------------------------- columns */
+
+/* Copies n values' worth of bytes in `fmt` (layout above) from `src` (host or
+   device memory, `size` bytes) into a new column allocated with the allocator
+   callbacks.  The header chain of block formats is checked on the device
+   (MS_ERR_FORMAT).  `static_bw` is used by MS_STATIC_BP only. */
+ms_status ms_column_import(ms_ctx *ctx, int fmt, int static_bw, uint64_t n,
+                           const void *src, uint64_t size, ms_column **out,
+                           void *stream);
+/* Copies the column's bytes to `dst` (host or device, `cap` bytes) and returns
+   the size; synchronises `stream`.  MS_ERR_INVALID_ARG if cap is too small. */
+ms_status ms_column_export(ms_ctx *ctx, const ms_column *col, void *dst, uint64_t cap,
+                           uint64_t *size_out, void *stream);
+/* Copies the column's metadata to the host; synchronises `stream`. */
+ms_status ms_column_info(ms_ctx *ctx, const ms_column *col, ms_column_meta *out,
+                         void *stream);
+/* Upper bound on the column's length known on the host without a sync. */
+uint64_t ms_column_max_rows(const ms_column *col);
+/* Releases a column (LIFO for arena columns, see above).  Enqueued on `stream`. */
+ms_status ms_column_free(ms_ctx *ctx, ms_column *col, void *stream);
+
+/* -------------------------------------------------------------- operators */
+
+/* compress (Sec. 4.1): n uncompressed values at device address d_in (16-byte
+   aligned) -> new column in `fmt`.  MS_ERR_VALUE_TOO_WIDE (device) if a value
+   needs more than static_bw bits under MS_STATIC_BP. */
+ms_status ms_compress(ms_ctx *ctx, const uint64_t *d_in, uint64_t n, int fmt,
+                      int static_bw, ms_column **out, void *stream);
+
+/* decompress: column -> uncompressed values at d_out (16-byte aligned, room for
+   `cap` values).  MS_ERR_INVALID_ARG (device) if the column holds more than cap
+   values; nothing past cap is written. */
+ms_status ms_decompress(ms_ctx *ctx, const ms_column *col, uint64_t *d_out,
+                        uint64_t cap, void *stream);
+
+/* select (Sec. 5.1 "Single Operator"): ascending 0-based positions i with
+   x_i <cmp> c1 (MS_BETWEEN: c1 <= x_i <= c2), as a new column in out_fmt. */
+ms_status ms_select(ms_ctx *ctx, const ms_column *in, int cmp, uint64_t c1,
+                    uint64_t c2, int out_fmt, int out_static_bw, ms_column **out,
+                    void *stream);
+
+/* project (Sec. 4.2, random read access): out_j = data[pos_j].  Any data format
+   is accepted; random access into the block formats goes through the block
+   header, which doubles as a directory.  MS_ERR_OUT_OF_RANGE (device) for
+   pos_j >= n(data). */
+ms_status ms_project(ms_ctx *ctx, const ms_column *data, const ms_column *pos,
+                     int out_fmt, int out_static_bw, ms_column **out, void *stream);
+
+/* calc: out_i = a_i <op> b_i modulo 2^64, or a_i <op> c when b is NULL.
+   MS_ERR_INVALID_ARG (device) if n(a) != n(b); the output then has min(n(a),
+   n(b)) values. */
+ms_status ms_calc(ms_ctx *ctx, int op, const ms_column *a, const ms_column *b,
+                  uint64_t c, int out_fmt, int out_static_bw, ms_column **out,
+                  void *stream);
+
+/* sum (Sec. 5.1 "Simple Query"): *d_result = sum of all values modulo 2^64
+   (0 for an empty column).  d_result is caller-owned device memory. */
+ms_status ms_agg_sum(ms_ctx *ctx, const ms_column *in, uint64_t *d_result,
+                     void *stream);
+
+/* grouped sum (Sec. 4.2: random writes go to an uncompressed result):
+   d_sums[k] = sum of val_i over gid_i == k, for k < n_groups, modulo 2^64.
+   d_sums (n_groups values) is caller-owned and is overwritten.
+   MS_ERR_OUT_OF_RANGE (device) for gid_i >= n_groups. */
+ms_status ms_group_sum(ms_ctx *ctx, const ms_column *gid, const ms_column *val,
+                       uint64_t n_groups, uint64_t *d_sums, void *stream);
+
+/* semi-join: ascending positions i with probe_i in the set of build_keys, as a
+   new column in out_fmt.  Keys index a dimension of `key_domain` rows;
+   MS_ERR_OUT_OF_RANGE (device) for a key >= key_domain.  Probe values >=
+   key_domain simply do not match.  Duplicate keys are allowed. */
+ms_status ms_semijoin(ms_ctx *ctx, const ms_column *probe, const ms_column *build_keys,
+                      uint64_t key_domain, int out_fmt, int out_static_bw,
+                      ms_column **out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MORPHSTORE_H */

@@ -1,0 +1,54 @@
+// ms_host.h -- host-side context and column structures of libms.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "morphstore.h"
+#include "ms_device.cuh"
+
+struct ms_column {
+  ms_ctx* ctx;
+  int slot;         // metadata slot on the device
+  int fmt, bw;      // format (host-known)
+  uint64_t n_max;   // host-known upper bound on the length
+  bool arena;       // carved from the arena (else allocated by the callbacks)
+  bool freed;       // released by the caller, waiting for LIFO reclamation
+  void* ext;        // external buffer (non-arena columns)
+};
+
+struct ms_ctx {
+  int device = 0, sms = 0;
+  ms_alloc_fn alloc = nullptr;
+  ms_free_fn free_fn = nullptr;
+  void* user = nullptr;
+  uint8_t* arena = nullptr;
+  uint64_t arena_cap = 0;
+  ms::DevCtl* ctl = nullptr;
+  ms::DevMeta* metas = nullptr;
+  std::vector<int> free_slots;
+  std::vector<ms_column*> stack;  // arena columns in allocation order
+  std::vector<ms_column*> live;
+  uint8_t* work = nullptr;
+  uint64_t work_cap = 0;
+  uint64_t* pin = nullptr;  // pinned host scratch
+  uint64_t last_err_info = 0;
+};
+
+namespace ms {
+
+inline uint64_t cdiv(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+inline uint64_t align_up(uint64_t a, uint64_t b) { return cdiv(a, b) * b; }
+
+void* dev_alloc(ms_ctx* c, size_t bytes);
+void dev_free(ms_ctx* c, void* p);
+ms_status cuda_status(cudaError_t e);
+bool valid_format(int fmt, int bw);
+int take_slot(ms_ctx* c);
+ms_column* new_arena_column(ms_ctx* c, int fmt, int bw, uint64_t n_max);
+void drop_new_column(ms_ctx* c, ms_column* col);
+// Makes sure the scratch area holds at least `bytes`; synchronises when it grows.
+ms_status ensure_work(ms_ctx* c, uint64_t bytes);
+
+}  // namespace ms

@@ -1,0 +1,313 @@
+"""Thin Python binding of libms (include/morphstore.h) over ctypes.
+
+Argument marshalling only: every step of every operator runs in libms's CUDA
+kernels.  PyTorch supplies device memory (the caching allocator backs the
+library's allocator callbacks), tensors for caller-owned buffers and the current
+stream.  The binding refuses to load without the compiled library: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libms.so")
+_HEADER = os.path.join(os.path.dirname(_PKG), "include", "morphstore.h")
+
+UNCOMPR, STATIC_BP, DYN_BP, DELTA_BP, FOR_BP = range(5)
+FORMAT_NAMES = ("uncompr", "static_bp", "dyn_bp", "delta_bp", "for_bp")
+EQ, NE, LT, LE, GT, GE, BETWEEN = range(7)
+ADD, SUB, MUL = range(3)
+STATUS = ("MS_OK", "MS_ERR_INVALID_ARG", "MS_ERR_FORMAT", "MS_ERR_VALUE_TOO_WIDE",
+          "MS_ERR_OUT_OF_RANGE", "MS_ERR_NOMEM", "MS_ERR_TIMEOUT", "MS_ERR_CUDA")
+(MS_OK, MS_ERR_INVALID_ARG, MS_ERR_FORMAT, MS_ERR_VALUE_TOO_WIDE, MS_ERR_OUT_OF_RANGE,
+ MS_ERR_NOMEM, MS_ERR_TIMEOUT, MS_ERR_CUDA) = range(8)
+
+
+class MSError(RuntimeError):
+    def __init__(self, code: int, what: str, info: int = 0):
+        name = STATUS[code] if 0 <= code < len(STATUS) else str(code)
+        super().__init__(f"{what}: {name} (info {info})")
+        self.code = code
+        self.info = info
+
+
+class ColumnMeta(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("fmt", ctypes.c_int32), ("static_bw", ctypes.c_int32),
+                ("size_bytes", ctypes.c_uint64), ("n_blocks", ctypes.c_uint64),
+                ("payload_words", ctypes.c_uint64), ("device_ptr", ctypes.c_uint64)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load() -> ctypes.CDLL:
+    """Loads libms.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"libms.so is missing at {_LIB_PATH}; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(_LIB_PATH)
+    p, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sigs = {
+        "ms_ctx_create": [pp, i32, u64, u64, _ALLOC_FN, _FREE_FN, p],
+        "ms_ctx_destroy": [p],
+        "ms_get_error": [p, p],
+        "ms_arena_usage": [p, ctypes.POINTER(u64), ctypes.POINTER(u64), p],
+        "ms_arena_reset_high_water": [p, p],
+        "ms_column_import": [p, i32, i32, u64, p, u64, pp, p],
+        "ms_column_export": [p, p, p, u64, ctypes.POINTER(u64), p],
+        "ms_column_info": [p, p, ctypes.POINTER(ColumnMeta), p],
+        "ms_column_free": [p, p, p],
+        "ms_compress": [p, p, u64, i32, i32, pp, p],
+        "ms_decompress": [p, p, p, u64, p],
+        "ms_select": [p, p, i32, u64, u64, i32, i32, pp, p],
+        "ms_project": [p, p, p, i32, i32, pp, p],
+        "ms_calc": [p, i32, p, p, u64, i32, i32, pp, p],
+        "ms_agg_sum": [p, p, p, p],
+        "ms_group_sum": [p, p, p, u64, p, p],
+        "ms_semijoin": [p, p, p, u64, i32, i32, pp, p],
+    }
+    for name, args in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.ms_last_error_info.argtypes = [p]
+    lib.ms_last_error_info.restype = u64
+    lib.ms_column_max_rows.argtypes = [p]
+    lib.ms_column_max_rows.restype = u64
+    _lib = lib
+    return lib
+
+
+def header_symbols() -> list[str]:
+    """Names of the functions include/morphstore.h declares."""
+    with open(_HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:ms_status|uint64_t)\s+(ms_\w+)\s*\(", text, re.M)))
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(code: int, what: str, ctx=None):
+    if code != MS_OK:
+        info = 0
+        if ctx is not None:
+            info = load().ms_last_error_info(ctx)
+        raise MSError(code, what, info)
+
+
+def as_device_u64(x, device) -> torch.Tensor:
+    """uint64 numpy array (or int64 tensor) -> int64 CUDA tensor holding the same bits."""
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=torch.int64).contiguous()
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.uint64))
+    return torch.from_numpy(a.view(np.int64)).to(device)
+
+
+class Column:
+    """Handle of a column owned by a context (opaque ms_column*)."""
+
+    __slots__ = ("ctx", "ptr", "fmt", "bw")
+
+    def __init__(self, ctx: "Ctx", ptr: int, fmt: int, bw: int):
+        self.ctx, self.ptr, self.fmt, self.bw = ctx, ptr, fmt, bw
+
+    @property
+    def max_rows(self) -> int:
+        return int(load().ms_column_max_rows(self.ptr))
+
+    def info(self, stream=None) -> dict:
+        return self.ctx.info(self, stream)
+
+    def __repr__(self):
+        return f"Column(fmt={FORMAT_NAMES[self.fmt]}, bw={self.bw}, max_rows={self.max_rows})"
+
+
+class Ctx:
+    """A libms context on one device (see ms_ctx_create)."""
+
+    def __init__(self, device: int = 0, arena_bytes: int = 1 << 30, max_rows: int = 1 << 20,
+                 torch_allocator: bool = True):
+        lib = load()
+        self.device = torch.device("cuda", device)
+        self._blocks = {}
+        if torch_allocator:
+            def _alloc(size, user):
+                try:
+                    t = torch.empty(int(size), dtype=torch.uint8, device=self.device)
+                except RuntimeError:
+                    return None
+                self._blocks[t.data_ptr()] = t
+                return t.data_ptr()
+
+            def _free(ptr, user):
+                self._blocks.pop(int(ptr), None)
+
+            self._alloc_cb, self._free_cb = _ALLOC_FN(_alloc), _FREE_FN(_free)
+        else:
+            self._alloc_cb, self._free_cb = _ALLOC_FN(0), _FREE_FN(0)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.ms_ctx_create(ctypes.byref(h), device, arena_bytes, max_rows,
+                                     self._alloc_cb, self._free_cb, None), "ms_ctx_create")
+        self.h = h
+        self.arena_bytes = arena_bytes
+
+    # -------------------------------------------------------------- lifecycle
+    def close(self):
+        if getattr(self, "h", None):
+            load().ms_ctx_destroy(self.h)
+            self.h = None
+            self._blocks.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---------------------------------------------------------------- errors
+    def get_error(self, stream=None) -> int:
+        return load().ms_get_error(self.h, _stream_handle(stream))
+
+    def last_error_info(self) -> int:
+        return int(load().ms_last_error_info(self.h))
+
+    def check(self, stream=None, what="device"):
+        code = self.get_error(stream)
+        if code != MS_OK:
+            raise MSError(code, what, self.last_error_info())
+
+    def arena_usage(self, stream=None):
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().ms_arena_usage(self.h, ctypes.byref(a), ctypes.byref(b), _stream_handle(stream)),
+               "ms_arena_usage")
+        return a.value, b.value
+
+    def reset_high_water(self, stream=None):
+        _check(load().ms_arena_reset_high_water(self.h, _stream_handle(stream)), "reset_high_water")
+
+    # --------------------------------------------------------------- columns
+    def _new(self, out: ctypes.c_void_p, fmt: int, bw: int) -> Column:
+        return Column(self, out.value, fmt, bw if fmt == STATIC_BP else 0)
+
+    def import_bytes(self, fmt: int, n: int, data, bw: int = 0, stream=None) -> Column:
+        """Column from bytes in the documented layout (numpy uint8 or a uint8 tensor, host or device)."""
+        if isinstance(data, torch.Tensor):
+            src, size, keep = data.data_ptr(), data.numel() * data.element_size(), data
+        else:
+            keep = np.ascontiguousarray(np.asarray(data, dtype=np.uint8))
+            src, size = keep.ctypes.data, keep.size
+        out = ctypes.c_void_p()
+        _check(load().ms_column_import(self.h, fmt, bw, n, ctypes.c_void_p(src), size, ctypes.byref(out),
+                                       _stream_handle(stream)), "ms_column_import", self.h)
+        if not isinstance(data, torch.Tensor):
+            torch.cuda.current_stream(self.device).synchronize() if stream is None else stream.synchronize()
+        del keep
+        return self._new(out, fmt, bw)
+
+    def export_bytes(self, col: Column, stream=None) -> np.ndarray:
+        meta = self.info(col, stream)
+        buf = np.zeros(max(meta["size_bytes"], 1), dtype=np.uint8)
+        got = ctypes.c_uint64()
+        _check(load().ms_column_export(self.h, col.ptr, ctypes.c_void_p(buf.ctypes.data), buf.size,
+                                       ctypes.byref(got), _stream_handle(stream)), "ms_column_export")
+        return buf[: got.value]
+
+    def info(self, col: Column, stream=None) -> dict:
+        m = ColumnMeta()
+        _check(load().ms_column_info(self.h, col.ptr, ctypes.byref(m), _stream_handle(stream)),
+               "ms_column_info")
+        return {k: getattr(m, k) for k, _ in ColumnMeta._fields_}
+
+    def free(self, col: Column, stream=None):
+        _check(load().ms_column_free(self.h, col.ptr, _stream_handle(stream)), "ms_column_free")
+        col.ptr = None
+
+    # ------------------------------------------------------------- operators
+    def compress(self, d_in: torch.Tensor, fmt: int, bw: int = 0, stream=None) -> Column:
+        assert d_in.is_cuda and d_in.element_size() == 8 and d_in.is_contiguous()
+        out = ctypes.c_void_p()
+        _check(load().ms_compress(self.h, ctypes.c_void_p(d_in.data_ptr()), d_in.numel(), fmt, bw,
+                                  ctypes.byref(out), _stream_handle(stream)), "ms_compress")
+        return self._new(out, fmt, bw)
+
+    def decompress(self, col: Column, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            n = self.info(col, stream)["n"]
+            out = torch.empty(max(n, 1), dtype=torch.int64, device=self.device)[:n]
+        _check(load().ms_decompress(self.h, col.ptr, ctypes.c_void_p(out.data_ptr()), out.numel(),
+                                    _stream_handle(stream)), "ms_decompress")
+        return out
+
+    def select(self, col: Column, cmp: int, c1: int, c2: int = 0, fmt: int = UNCOMPR, bw: int = 0,
+               stream=None) -> Column:
+        out = ctypes.c_void_p()
+        _check(load().ms_select(self.h, col.ptr, cmp, c1, c2, fmt, bw, ctypes.byref(out),
+                                _stream_handle(stream)), "ms_select")
+        return self._new(out, fmt, bw)
+
+    def project(self, data: Column, pos: Column, fmt: int = UNCOMPR, bw: int = 0, stream=None) -> Column:
+        out = ctypes.c_void_p()
+        _check(load().ms_project(self.h, data.ptr, pos.ptr, fmt, bw, ctypes.byref(out),
+                                 _stream_handle(stream)), "ms_project")
+        return self._new(out, fmt, bw)
+
+    def calc(self, op: int, a: Column, b: Column | None = None, c: int = 0, fmt: int = UNCOMPR,
+             bw: int = 0, stream=None) -> Column:
+        out = ctypes.c_void_p()
+        _check(load().ms_calc(self.h, op, a.ptr, None if b is None else b.ptr, c, fmt, bw,
+                              ctypes.byref(out), _stream_handle(stream)), "ms_calc")
+        return self._new(out, fmt, bw)
+
+    def agg_sum(self, col: Column, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(1, dtype=torch.int64, device=self.device)
+        _check(load().ms_agg_sum(self.h, col.ptr, ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+               "ms_agg_sum")
+        return out
+
+    def group_sum(self, gid: Column, val: Column, n_groups: int, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(max(n_groups, 1), dtype=torch.int64, device=self.device)[:n_groups]
+        _check(load().ms_group_sum(self.h, gid.ptr, val.ptr, n_groups, ctypes.c_void_p(out.data_ptr()),
+                                   _stream_handle(stream)), "ms_group_sum")
+        return out
+
+    def semijoin(self, probe: Column, keys: Column, key_domain: int, fmt: int = UNCOMPR, bw: int = 0,
+                 stream=None) -> Column:
+        out = ctypes.c_void_p()
+        _check(load().ms_semijoin(self.h, probe.ptr, keys.ptr, key_domain, fmt, bw, ctypes.byref(out),
+                                  _stream_handle(stream)), "ms_semijoin")
+        return self._new(out, fmt, bw)
+
+
+def to_numpy_u64(t: torch.Tensor) -> np.ndarray:
+    """int64 tensor holding uint64 bits -> numpy uint64."""
+    return t.detach().cpu().numpy().view(np.uint64)

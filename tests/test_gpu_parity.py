@@ -1,0 +1,317 @@
+"""GPU parity: every operator through the C ABI against the CPU oracle.
+
+Integer work, so the bar is bit-exact: decompressed values, compressed bytes (both
+sides implement the same written layout) and aggregates.  Sizes span several
+4096-value tiles plus ragged tails; every input/output format pair is covered.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2004_09350_gb300 import morphstore as ms
+from paper_2004_09350_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FMTS = [ms.UNCOMPR, ms.STATIC_BP, ms.DYN_BP, ms.DELTA_BP, ms.FOR_BP]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = ms.Ctx(0, arena_bytes=3 << 30, max_rows=1 << 22)
+    yield c
+    c.close()
+
+
+def static_bw(x):
+    return max(1, int(x.max()).bit_length()) if x.size else 1
+
+
+def gpu_col(ctx, x, fmt, bw=None):
+    bw = static_bw(x) if bw is None else bw
+    d = ms.as_device_u64(x, ctx.device)
+    col = ctx.compress(d, fmt, bw if fmt == ms.STATIC_BP else 0)
+    return col, (bw if fmt == ms.STATIC_BP else 0)
+
+
+def values(ctx, col):
+    return ms.to_numpy_u64(ctx.decompress(col))
+
+
+def assert_column(ctx, col, want, fmt, bw=0):
+    ctx.check(what="device error")
+    got = values(ctx, col)
+    np.testing.assert_array_equal(got, want)
+    ref = oracle.compress(fmt, want, bw=bw)
+    assert ctx.export_bytes(col).tobytes() == ref.tobytes()
+
+
+def edge_column(n, b, seed=1):
+    if b == 0:
+        return np.zeros(n, dtype=np.uint64)
+    x = synth.splitmix64(seed, n) >> np.uint64(64 - b)
+    if n:
+        x[n // 2] |= np.uint64(1) << np.uint64(b - 1)
+    return x
+
+
+NS = [0, 1, 15, 511, 512, 513, 4096, 4097, 3 * 4096 + 777]
+
+
+# ------------------------------------------------------------------- codecs
+
+@pytest.mark.parametrize("fmt", FMTS)
+@pytest.mark.parametrize("n", NS)
+@pytest.mark.parametrize("b", [0, 1, 7, 31, 32, 33, 63, 64])
+def test_compress_matches_oracle_bytes(ctx, fmt, n, b):
+    x = edge_column(n, b, seed=n + b)
+    col, bw = gpu_col(ctx, x, fmt)
+    assert_column(ctx, col, x, fmt, bw)
+    ctx.free(col)
+
+
+@pytest.mark.parametrize("fmt", FMTS)
+@pytest.mark.parametrize("kind", ["skewed", "sorted", "C2", "C3", "C4"])
+def test_compress_workload_shapes(ctx, fmt, kind):
+    n = 5 * 4096 + 333
+    x = {"skewed": lambda: synth.skewed_widths(3, n), "sorted": lambda: synth.sorted_gaps(4, n),
+         "C2": lambda: synth.table1_column("C2", n), "C3": lambda: synth.table1_column("C3", n),
+         "C4": lambda: synth.table1_column("C4", n)}[kind]()
+    col, bw = gpu_col(ctx, x, fmt)
+    assert_column(ctx, col, x, fmt, bw)
+    info = ctx.info(col)
+    assert info["n"] == n and info["size_bytes"] == oracle.size(fmt, x, bw)
+    ctx.free(col)
+
+
+@pytest.mark.parametrize("fmt", FMTS)
+@pytest.mark.parametrize("n", [0, 700, 4096 * 2 + 5])
+def test_decode_of_oracle_bytes(ctx, fmt, n):
+    x = synth.skewed_widths(n + 11, n)
+    bw = static_bw(x)
+    buf = oracle.compress(fmt, x, bw=bw)
+    col = ctx.import_bytes(fmt, n, buf, bw=bw)
+    ctx.check()
+    np.testing.assert_array_equal(values(ctx, col), x)
+    ctx.free(col)
+
+
+# ------------------------------------------------------------------ select
+
+@pytest.mark.parametrize("in_fmt", FMTS)
+@pytest.mark.parametrize("out_fmt", FMTS)
+def test_select_every_format_pair(ctx, in_fmt, out_fmt):
+    n = 6 * 4096 + 321
+    x = synth.skewed_widths(7, n, widths=(3, 8, 16))
+    col, _ = gpu_col(ctx, x, in_fmt)
+    for sel in (0.001, 0.1, 0.9):
+        c = synth.value_at_rank(x, sel)
+        want = oracle.select(x, oracle.LT, c)
+        bw = static_bw(np.array([n], dtype=np.uint64)) if out_fmt == ms.STATIC_BP else 0
+        pos = ctx.select(col, ms.LT, c, fmt=out_fmt, bw=bw)
+        assert_column(ctx, pos, want, out_fmt, bw)
+        ctx.free(pos)
+    ctx.free(col)
+
+
+@pytest.mark.parametrize("cmp", [ms.EQ, ms.NE, ms.LE, ms.GT, ms.GE, ms.BETWEEN])
+def test_select_predicates(ctx, cmp):
+    n = 3 * 4096 + 99
+    x = synth.uniform(3, n, 0, 50)
+    col, _ = gpu_col(ctx, x, ms.DYN_BP)
+    pos = ctx.select(col, cmp, 17, 31, fmt=ms.DELTA_BP)
+    assert_column(ctx, pos, oracle.select(x, cmp, 17, 31), ms.DELTA_BP)
+    ctx.free(pos)
+    ctx.free(col)
+
+
+def test_select_none_and_all(ctx):
+    x = synth.uniform(5, 4096 * 4 + 17, 10, 20)
+    col, _ = gpu_col(ctx, x, ms.FOR_BP)
+    for c, want_n in ((10, 0), (20, x.size)):
+        pos = ctx.select(col, ms.LT, c, fmt=ms.DELTA_BP)
+        assert ctx.info(pos)["n"] == want_n
+        assert_column(ctx, pos, oracle.select(x, oracle.LT, c), ms.DELTA_BP)
+        ctx.free(pos)
+    ctx.free(col)
+
+
+# ----------------------------------------------------------------- project
+
+@pytest.mark.parametrize("data_fmt", FMTS)
+@pytest.mark.parametrize("out_fmt", FMTS)
+def test_project_every_format_pair(ctx, data_fmt, out_fmt):
+    n = 5 * 4096 + 123
+    d = synth.sorted_gaps(9, n) if data_fmt == ms.DELTA_BP else synth.skewed_widths(9, n)
+    dcol, _ = gpu_col(ctx, d, data_fmt)
+    pos = np.sort(synth.uniform(10, 3000, 0, n))
+    pcol, _ = gpu_col(ctx, pos, ms.DELTA_BP)
+    want = oracle.project(d, pos)
+    bw = static_bw(want)
+    out = ctx.project(dcol, pcol, fmt=out_fmt, bw=bw)
+    assert_column(ctx, out, want, out_fmt, bw if out_fmt == ms.STATIC_BP else 0)
+    ctx.free(out)
+    ctx.free(pcol)
+    ctx.free(dcol)
+
+
+@pytest.mark.parametrize("data_fmt", FMTS)
+@pytest.mark.parametrize("pos_fmt", FMTS)
+def test_project_position_formats_and_unsorted(ctx, data_fmt, pos_fmt):
+    n = 3 * 4096 + 1000
+    d = synth.splitmix64(21, n) >> np.uint64(20)
+    dcol, _ = gpu_col(ctx, d, data_fmt)
+    pos = synth.uniform(22, 5000, 0, n)  # unsorted, with repeats
+    pcol, _ = gpu_col(ctx, pos, pos_fmt)
+    out = ctx.project(dcol, pcol, fmt=ms.UNCOMPR)
+    assert_column(ctx, out, oracle.project(d, pos), ms.UNCOMPR)
+    ctx.free(out)
+    ctx.free(pcol)
+    ctx.free(dcol)
+
+
+# -------------------------------------------------------------------- calc
+
+@pytest.mark.parametrize("fa,fb", [(f, f) for f in FMTS] + [(ms.DYN_BP, ms.DELTA_BP), (ms.UNCOMPR, ms.FOR_BP),
+                                                           (ms.STATIC_BP, ms.DYN_BP)])
+@pytest.mark.parametrize("op", [ms.ADD, ms.SUB, ms.MUL])
+def test_calc_pairs(ctx, fa, fb, op):
+    n = 4 * 4096 + 55
+    a = synth.skewed_widths(31, n)
+    b = synth.sorted_gaps(32, n)
+    ca, _ = gpu_col(ctx, a, fa)
+    cb, _ = gpu_col(ctx, b, fb)
+    want = oracle.calc(op, a, b)
+    for out_fmt in (ms.UNCOMPR, ms.DYN_BP, ms.FOR_BP):
+        out = ctx.calc(op, ca, cb, fmt=out_fmt)
+        assert_column(ctx, out, want, out_fmt)
+        ctx.free(out)
+    out = ctx.calc(op, ca, None, c=12345, fmt=ms.DELTA_BP)
+    assert_column(ctx, out, oracle.calc(op, a, c=12345), ms.DELTA_BP)
+    ctx.free(out)
+    ctx.free(cb)
+    ctx.free(ca)
+
+
+# --------------------------------------------------------------- aggregates
+
+@pytest.mark.parametrize("fmt", FMTS)
+@pytest.mark.parametrize("n", [0, 1, 513, 7 * 4096 + 3])
+def test_agg_sum(ctx, fmt, n):
+    x = synth.table1_column("C3", n) if fmt != ms.STATIC_BP else synth.skewed_widths(4, n)
+    col, _ = gpu_col(ctx, x, fmt)
+    got = int(ms.to_numpy_u64(ctx.agg_sum(col))[0])
+    ctx.check()
+    assert got == oracle.agg_sum(x)
+    ctx.free(col)
+
+
+@pytest.mark.parametrize("fg,fv", [(ms.UNCOMPR, ms.UNCOMPR), (ms.STATIC_BP, ms.DYN_BP), (ms.DYN_BP, ms.FOR_BP),
+                                   (ms.FOR_BP, ms.DELTA_BP)])
+@pytest.mark.parametrize("G", [1, 105, 5000])
+def test_group_sum(ctx, fg, fv, G):
+    n = 5 * 4096 + 77
+    g = synth.uniform(41, n, 0, G)
+    v = synth.splitmix64(42, n)
+    cg, _ = gpu_col(ctx, g, fg)
+    cv, _ = gpu_col(ctx, v, fv)
+    got = ms.to_numpy_u64(ctx.group_sum(cg, cv, G))
+    ctx.check()
+    np.testing.assert_array_equal(got, oracle.group_sum(g, v, G))
+    ctx.free(cv)
+    ctx.free(cg)
+
+
+@pytest.mark.parametrize("probe_fmt", FMTS)
+@pytest.mark.parametrize("out_fmt", [ms.UNCOMPR, ms.DELTA_BP, ms.DYN_BP])
+def test_semijoin(ctx, probe_fmt, out_fmt):
+    n, dom = 6 * 4096 + 999, 30_000
+    probe = synth.uniform(51, n, 0, dom)
+    keys = np.sort(synth.uniform(52, 4000, 0, dom))
+    cp, _ = gpu_col(ctx, probe, probe_fmt)
+    ck, _ = gpu_col(ctx, keys, ms.DELTA_BP)
+    out = ctx.semijoin(cp, ck, dom, fmt=out_fmt)
+    assert_column(ctx, out, oracle.semijoin(probe, keys, dom), out_fmt)
+    ctx.free(out)
+    ctx.free(ck)
+    ctx.free(cp)
+
+
+# ------------------------------------------------------------------ plans
+
+def test_tiny_fragment_plan_bit_exact(ctx):
+    """Two 2^20-row columns: A static BP 12 bits, B dynamic BP; select A < 410 ->
+    DELTA+BP positions -> project B -> dynamic BP -> sum; and all-uncompressed."""
+    a, b = synth.tiny_fragment()
+    want_pos = oracle.select(a, oracle.LT, 410)
+    want_y = oracle.project(b, want_pos)
+    want_sum = oracle.agg_sum(want_y)
+    assert abs(want_pos.size - 104_960) < 6 * 307  # Binomial(2^20, 410/4096)
+    for fa, fb, fp, fy in ((ms.STATIC_BP, ms.DYN_BP, ms.DELTA_BP, ms.DYN_BP),
+                           (ms.UNCOMPR, ms.UNCOMPR, ms.UNCOMPR, ms.UNCOMPR)):
+        ca, _ = gpu_col(ctx, a, fa, bw=12)
+        cb, _ = gpu_col(ctx, b, fb)
+        pos = ctx.select(ca, ms.LT, 410, fmt=fp)
+        y = ctx.project(cb, pos, fmt=fy)
+        s = int(ms.to_numpy_u64(ctx.agg_sum(y))[0])
+        assert_column(ctx, pos, want_pos, fp)
+        assert_column(ctx, y, want_y, fy)
+        assert s == want_sum
+        for col in (y, pos, cb, ca):
+            ctx.free(col)
+
+
+# ------------------------------------------------------------------- errors
+
+def test_errors_are_reported_not_trapped(ctx):
+    assert ctx.get_error() == ms.MS_OK
+    x = np.array([1, 2, 300], dtype=np.uint64)
+    col, _ = gpu_col(ctx, x, ms.STATIC_BP, bw=8)
+    assert ctx.get_error() == ms.MS_ERR_VALUE_TOO_WIDE
+    ctx.free(col)
+
+    d, _ = gpu_col(ctx, np.arange(100, dtype=np.uint64), ms.DYN_BP)
+    p, _ = gpu_col(ctx, np.array([5, 100], dtype=np.uint64), ms.UNCOMPR)
+    out = ctx.project(d, p)
+    assert ctx.get_error() == ms.MS_ERR_OUT_OF_RANGE and ctx.last_error_info() == 100
+    ctx.free(out)
+
+    g, _ = gpu_col(ctx, np.array([0, 7], dtype=np.uint64), ms.UNCOMPR)
+    v, _ = gpu_col(ctx, np.array([1, 1], dtype=np.uint64), ms.UNCOMPR)
+    ctx.group_sum(g, v, 7)
+    assert ctx.get_error() == ms.MS_ERR_OUT_OF_RANGE
+    out = ctx.semijoin(v, g, 7)
+    assert ctx.get_error() == ms.MS_ERR_OUT_OF_RANGE
+    ctx.free(out)
+    small = torch.empty(1, dtype=torch.int64, device=ctx.device)
+    ctx.decompress(p, out=small)
+    assert ctx.get_error() == ms.MS_ERR_INVALID_ARG
+    for col in (v, g, p, d):
+        ctx.free(col)
+
+    x = synth.skewed_widths(3, 2048)
+    buf = oracle.compress(oracle.DYN_BP, x).copy()
+    buf[16] ^= 1
+    bad = ctx.import_bytes(ms.DYN_BP, 2048, buf)
+    assert ctx.get_error() == ms.MS_ERR_FORMAT
+    ctx.free(bad)
+    with pytest.raises(ms.MSError):
+        ctx.compress(ms.as_device_u64(x, ctx.device), ms.STATIC_BP, 65)
+    assert ctx.get_error() == ms.MS_OK
+
+
+def test_arena_is_lifo_and_tracks_high_water(ctx):
+    base, _ = ctx.arena_usage()
+    ctx.reset_high_water()
+    x = synth.skewed_widths(1, 10_000)
+    a, _ = gpu_col(ctx, x, ms.DYN_BP)
+    b, _ = gpu_col(ctx, x, ms.UNCOMPR)
+    used, high = ctx.arena_usage()
+    sa, sb = ctx.info(a)["size_bytes"], ctx.info(b)["size_bytes"]
+    assert used - base >= sa + sb and high == used
+    ctx.free(a)  # not the top: only marked
+    assert ctx.arena_usage()[0] == used
+    ctx.free(b)  # pops both
+    assert ctx.arena_usage()[0] == base
+    assert ctx.arena_usage()[1] == high
