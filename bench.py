@@ -1,0 +1,483 @@
+#!/usr/bin/env python
+"""Throughput of the on-the-fly morphing pipeline on one GB300 (or N replicas).
+
+Workload: two 2^28-row uint64 columns.  X has a bit width drawn per 512-value block
+from {3, 8, 16, 27, 40}.  K is sorted with geometric gaps of mean 4.  One step is
+the plan select(X < c) -> P; project(X, P) -> X'; project(K, P) -> K';
+calc(X' * K') -> Y; agg_sum(Y).  c is picked for about 10% selectivity.
+Compressed pipeline: X dynamic BP, K DELTA+BP, P DELTA+BP, X' dynamic BP,
+K' DELTA+BP, Y dynamic BP.  The same plan with every column uncompressed is
+timed beside it.
+
+value = logical input rows per second of the compressed pipeline (whole job).
+roofline = the dominant kernel's algorithmic bytes per launch / its mean launch
+time, against the measured HBM copy peak.  e2e = the same plan through the C
+ABI with the compressed base columns copied from pinned host memory every step
+and the sum read back.  cpu_baseline = the CPU oracle on a bounded sample of the
+same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "logical rows/s and achieved HBM GB/s (% of peak), compressed vs uncompressed"
+FALLBACK_HBM = 6800.0
+BLOCK = 512
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rows", type=int, default=1 << 28)
+    ap.add_argument("--selectivity", type=float, default=0.1)
+    ap.add_argument("--seed", type=int, default=2020)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    a = ap.parse_args()
+    a.warmup = max(a.warmup, 3)
+    return a
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+# ----------------------------------------------------------------- workload
+
+def make_inputs(rows, seed, sel):
+    from paper_2004_09350_gb300 import synth
+    x = synth.skewed_widths(seed, rows)
+    k = synth.sorted_gaps(seed + 1, rows)
+    c = synth.value_at_rank(x, sel)
+    return x, k, c
+
+
+COMPRESSED = {"X": "dyn_bp", "K": "delta_bp", "P": "delta_bp", "X'": "dyn_bp", "K'": "delta_bp", "Y": "dyn_bp"}
+UNCOMPRESSED = {k: "uncompr" for k in COMPRESSED}
+
+
+def fmt_id(name):
+    from paper_2004_09350_gb300 import morphstore as ms
+    return ms.FORMAT_NAMES.index(name)
+
+
+def run_plan(ctx, cx, ck, c, fm, res):
+    """One step of the plan; frees its intermediates (LIFO) before returning."""
+    from paper_2004_09350_gb300 import morphstore as ms
+    pos = ctx.select(cx, ms.LT, c, fmt=fmt_id(fm["P"]))
+    xp = ctx.project(cx, pos, fmt=fmt_id(fm["X'"]))
+    kp = ctx.project(ck, pos, fmt=fmt_id(fm["K'"]))
+    y = ctx.calc(ms.MUL, xp, kp, fmt=fmt_id(fm["Y"]))
+    ctx.agg_sum(y, out=res)
+    return [y, kp, xp, pos]
+
+
+def free_all(ctx, cols):
+    for col in cols:
+        ctx.free(col)
+
+
+# ------------------------------------------------------ algorithmic bytes
+
+def block_widths(x, delta=False):
+    nb = x.size // BLOCK
+    blk = x[: nb * BLOCK].reshape(nb, BLOCK)
+    if delta:
+        d = np.diff(blk, axis=1)
+        m = d.max(axis=1) if nb else np.zeros(0, np.uint64)
+    else:
+        m = blk.max(axis=1)
+    w = np.zeros(nb, dtype=np.int64)
+    v = m.copy()
+    while np.any(v):
+        nz = v != 0
+        w[nz] += 1
+        v >>= np.uint64(1)
+    return w
+
+
+def touched_bytes_dyn(x_widths, n, pos):
+    """32-byte sectors of a dynamic-BP column that random reads at `pos` touch
+    (block header + the halfwords of each value's lane stream)."""
+    nb = x_widths.size
+    pay_off = 16 * nb + 8 * np.concatenate([[0], np.cumsum(8 * x_widths)])[:-1]
+    total_bytes = 16 * nb + 64 * int(x_widths.sum()) + 8 * (n % BLOCK)
+    touched = np.zeros(total_bytes // 32 + 2, dtype=bool)
+    p = pos.astype(np.int64)
+    inblk = p < nb * BLOCK
+    pm, pr = p[inblk], p[~inblk]
+    g = pm >> 9
+    r = pm & 511
+    j, kk = r >> 4, r & 15
+    b = x_widths[g]
+    touched[(16 * g) >> 5] = True
+    q0 = (kk * b) >> 4
+    q1 = np.where(b > 0, (kk * b + b - 1) >> 4, q0 - 1)
+    for t in range(6):
+        q = q0 + t
+        ok = q <= q1
+        addr = pay_off[g[ok]] + 2 * (32 * q[ok] + j[ok])
+        touched[addr >> 5] = True
+    if pr.size:
+        rem_off = 16 * nb + 64 * int(x_widths.sum())
+        touched[(rem_off + 8 * (pr - nb * BLOCK)) >> 5] = True
+    return int(touched.sum()) * 32
+
+
+def touched_bytes_delta(k_widths, pos):
+    g = np.unique(pos.astype(np.int64) >> 9)
+    g = g[g < k_widths.size]
+    return int((64 * k_widths[g] + 16).sum())
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def oracle_plan(x, k, c):
+    """The same plan on the CPU oracle: every column passes through the oracle's
+    codec in the pipeline's formats (decode inputs, encode each intermediate)."""
+    import oracle
+    f = {n: oracle.FORMAT_NAMES.index(v) for n, v in COMPRESSED.items()}
+    bx, bk = oracle.compress(f["X"], x), oracle.compress(f["K"], k)
+    t0 = time.perf_counter()
+    xd = oracle.decompress(f["X"], x.size, bx)
+    kd = oracle.decompress(f["K"], k.size, bk)
+    pos = oracle.select(xd, oracle.LT, c)
+    pd = oracle.decompress(f["P"], pos.size, oracle.compress(f["P"], pos))
+    xp = oracle.project(xd, pd)
+    kp = oracle.project(kd, pd)
+    xpd = oracle.decompress(f["X'"], xp.size, oracle.compress(f["X'"], xp))
+    kpd = oracle.decompress(f["K'"], kp.size, oracle.compress(f["K'"], kp))
+    y = oracle.calc(oracle.MUL, xpd, kpd)
+    yd = oracle.decompress(f["Y"], y.size, oracle.compress(f["Y"], y))
+    s = oracle.agg_sum(yd)
+    return time.perf_counter() - t0, s
+
+
+def cpu_baseline(x, k, c, target_s=15.0):
+    """Oracle on a bounded prefix sample sized for ~target_s seconds of CPU work."""
+    probe = min(x.size, 1 << 15)
+    t, _ = oracle_plan(x[:probe], k[:probe], c)
+    rows = int(min(x.size, max(probe, probe * target_s / max(t, 1e-6))))
+    rows -= rows % BLOCK
+    t, _ = oracle_plan(x[:rows], k[:rows], c)
+    return {"value": rows / t, "unit": "rows/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {rows} rows of X and K, same plan and formats, single thread ({t:.1f} s)"}
+
+
+# ---------------------------------------------------------------- helpers
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2004_09350_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """dram bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        t = json.load(f)
+    e = t.get(kernel)
+    if not e or e.get("source_digest") != source_digest():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# -------------------------------------------------------------- our arm
+
+def bench_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2004_09350_gb300 import morphstore as ms
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n = args.rows
+    x, k, c = make_inputs(n, args.seed, args.selectivity)
+    dev = torch.device("cuda", local)
+    ctx = ms.Ctx(local, arena_bytes=int(2.5 * 8 * n) + (1 << 30), max_rows=n)
+    res = torch.zeros(1, dtype=torch.int64, device=dev)
+    dx, dk = ms.as_device_u64(x, dev), ms.as_device_u64(k, dev)
+    out = {}
+    for label, fm in (("compressed", COMPRESSED), ("uncompressed", UNCOMPRESSED)):
+        cx = ctx.compress(dx, fmt_id(fm["X"]))
+        ck = ctx.compress(dk, fmt_id(fm["K"]))
+        ctx.check(what="base columns")
+        # warm-up, sizes of every column of the plan and the peak footprint
+        for _ in range(args.warmup):
+            free_all(ctx, run_plan(ctx, cx, ck, c, fm, res))
+        ctx.reset_high_water()
+        cols = run_plan(ctx, cx, ck, c, fm, res)
+        sizes = {"X": ctx.info(cx)["size_bytes"], "K": ctx.info(ck)["size_bytes"]}
+        for name, col in zip(("Y", "K'", "X'", "P"), cols):
+            sizes[name] = ctx.info(col)["size_bytes"]
+        m = ctx.info(cols[3])["n"]
+        free_all(ctx, cols)
+        base_use, high = ctx.arena_usage()
+        ctx.check(what=f"{label} warm-up")
+        want = None
+        barrier()
+        ctx.profile(True)
+        clocks = Clocks(local) if label == "compressed" else None
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(args.steps):
+            free_all(ctx, run_plan(ctx, cx, ck, c, fm, res))
+        t1.record()
+        barrier()
+        ck_info = clocks.stop() if clocks else None
+        prof = ctx.profile_collect()
+        ctx.profile(False)
+        ctx.check(what=f"{label} timed steps")
+        ms_step = t0.elapsed_time(t1) / args.steps
+        if world > 1:
+            tt = torch.tensor([ms_step], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms_step = float(tt.item())
+        got = int(ms.to_numpy_u64(res)[0])
+        out[label] = dict(ms_step=ms_step, sizes=sizes, m=m, prof=prof, clocks=ck_info, sum=got,
+                          footprint=int(sum(sizes.values())), arena_peak=int(high - (base_use - 0)))
+        ctx.free(ck)
+        ctx.free(cx)
+    assert out["compressed"]["sum"] == out["uncompressed"]["sum"], "pipelines disagree"
+
+    # ---- algorithmic bytes of each kernel of the compressed plan (per launch)
+    comp = out["compressed"]
+    s, m = comp["sizes"], comp["m"]
+    pos = np.flatnonzero(x < np.uint64(c))
+    xw, kw = block_widths(x), block_widths(k, delta=True)
+    nch = -(-n // BLOCK)
+    alg = {
+        "mark": s["X"] + n // 8 + 8 * nch,
+        "emit": n // 8 + 8 * nch + s["P"],
+        "project": (s["P"] + touched_bytes_dyn(xw, n, pos) + s["X'"]
+                    + s["P"] + touched_bytes_delta(kw, pos) + s["K'"]) / 2,
+        "calc": s["X'"] + s["K'"] + s["Y"],
+        "agg_sum": s["Y"] + 8,
+    }
+    per_kernel = {}
+    for kname, (launches, total) in comp["prof"].items():
+        avg = total / max(launches, 1)
+        gbs = alg.get(kname, 0) / (avg * 1e-3) / 1e9 if kname in alg else None
+        per_kernel[kname] = {"launches": launches, "avg_ms": round(avg, 4),
+                             "alg_bytes": int(alg.get(kname, 0)), "alg_GBps": None if gbs is None else round(gbs, 1)}
+    dom = max(per_kernel, key=lambda kk: per_kernel[kk]["avg_ms"] * per_kernel[kk]["launches"])
+    peak, peak_kind = peaks()
+    ach = per_kernel[dom]["alg_GBps"]
+    plan_bytes = sum(v * per_kernel.get(kk, {"launches": 0})["launches"] / args.steps for kk, v in alg.items())
+
+    # ---- end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        fm = COMPRESSED
+        cx = ctx.compress(dx, fmt_id(fm["X"]))
+        ck = ctx.compress(dk, fmt_id(fm["K"]))
+        hx = torch.from_numpy(ctx.export_bytes(cx)).pin_memory()
+        hk = torch.from_numpy(ctx.export_bytes(ck)).pin_memory()
+        ctx.free(ck)
+        ctx.free(cx)
+        hres = torch.zeros(1, dtype=torch.int64).pin_memory()
+
+        def e2e_step():
+            ix = ctx.import_bytes(fmt_id(fm["X"]), n, hx)
+            ik = ctx.import_bytes(fmt_id(fm["K"]), n, hk)
+            free_all(ctx, run_plan(ctx, ix, ik, c, fm, res))
+            hres.copy_(res, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            ctx.free(ik)
+            ctx.free(ix)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        barrier()
+        e2e_ms = (time.perf_counter() - t) * 1e3 / args.steps
+        if world > 1:
+            tt = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tt.item())
+        assert int(hres.numpy().view(np.uint64)[0]) == comp["sum"]
+        e2e = {"value": world * n / (e2e_ms * 1e-3), "unit": "rows/s",
+               "h2d_bytes_per_step": int(hx.numel() + hk.numel()), "d2h_bytes_per_step": 8,
+               "ms_per_step": round(e2e_ms, 3)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(x, k, c)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+
+    unc = out["uncompressed"]
+    line = {
+        "metric": METRIC,
+        "value": world * n / (comp["ms_step"] * 1e-3),
+        "unit": "rows/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(comp["ms_step"], 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic (seeded SplitMix64)",
+        "config": {
+            "workload": "select(X<c)->project(X,K)->calc(X'*K')->agg_sum on 2^28-row columns, "
+                        "X widths {3,8,16,27,40} per 512-block, K sorted gaps mean 4",
+            "rows": n, "selectivity": round(comp["m"] / n, 5), "formats": COMPRESSED,
+            "l2": "inputs larger than L2 (compressed X %.2f GB, K %.2f GB; uncompressed 2.1 GB each)"
+                  % (comp["sizes"]["X"] / 1e9, comp["sizes"]["K"] / 1e9),
+            "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": None if ach is None else round(ach / peak, 4), "peak_kind": peak_kind,
+                     "traffic": measured_traffic(dom),
+                     "alg_bytes_per_launch": per_kernel[dom]["alg_bytes"]},
+        "per_kernel": per_kernel,
+        "plan_GBps": round(plan_bytes / (comp["ms_step"] * 1e-3) / 1e9, 1),
+        "uncompressed": {"value": world * n / (unc["ms_step"] * 1e-3), "ms_per_step": round(unc["ms_step"], 4),
+                         "footprint_bytes": unc["footprint"], "arena_peak_bytes": unc["arena_peak"]},
+        "compressed": {"footprint_bytes": comp["footprint"], "arena_peak_bytes": comp["arena_peak"],
+                       "sizes": comp["sizes"]},
+        "speedup_vs_uncompressed": round(unc["ms_step"] / comp["ms_step"], 3),
+        "gpu_launches": int(sum(v[0] for v in comp["prof"].values())),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": comp["clocks"],
+    }
+    return line
+
+
+# ------------------------------------------------------------ reference arm
+
+def bench_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return None
+    x, k, c = make_inputs(args.rows, args.seed, args.selectivity)
+    # each step runs the oracle on a bounded prefix so the whole run stays within minutes
+    per_step_s = max(2.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
+    probe = min(x.size, 1 << 15)
+    t, _ = oracle_plan(x[:probe], k[:probe], c)
+    rows = int(min(x.size, max(probe, probe * per_step_s / max(t, 1e-6))))
+    rows -= rows % BLOCK
+    for _ in range(args.warmup):
+        oracle_plan(x[: min(rows, 1 << 15)], k[: min(rows, 1 << 15)], c)
+    times = [oracle_plan(x[:rows], k[:rows], c)[0] for _ in range(args.steps)]
+    tot = sum(times)
+    value = rows * args.steps / tot
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (seeded SplitMix64)",
+            "config": {"workload": "same plan as the GPU arm on a prefix sample", "rows": rows},
+            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {rows} rows per step of the 2^28-row workload"},
+            "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    line = bench_reference(args) if args.impl == "reference" else bench_ours(args)
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -220,6 +220,37 @@ ms_status ms_semijoin(ms_ctx *ctx, const ms_column *probe, const ms_column *buil
                       uint64_t key_domain, int out_fmt, int out_static_bw,
                       ms_column **out, void *stream);
 
+/* ------------------------------------------------------------ profiling */
+
+/* Kernels of the library, as reported by ms_profile_collect. */
+typedef enum {
+  MS_K_MARK = 0,       /* select / semi-join: decode + predicate -> match bitmap */
+  MS_K_EMIT = 1,       /* select / semi-join: match bitmap -> positions column */
+  MS_K_COMPRESS = 2,
+  MS_K_DECOMPRESS = 3,
+  MS_K_PROJECT = 4,
+  MS_K_CALC = 5,
+  MS_K_AGG_SUM = 6,
+  MS_K_GROUP_SUM = 7,
+  MS_K_BUILD_KEYS = 8, /* semi-join build side */
+  MS_K_VALIDATE = 9,   /* header check of imported columns */
+  MS_K_COUNT = 10
+} ms_kernel;
+
+typedef struct {
+  int32_t kernel;    /* ms_kernel */
+  uint32_t launches; /* launches recorded since the last collect */
+  double total_ms;   /* summed device time between the events around each launch */
+} ms_kernel_time;
+
+/* When on, every kernel launch is bracketed by two CUDA events on its stream. */
+ms_status ms_profile_enable(ms_ctx *ctx, int on);
+/* Synchronises the device, sums the recorded launches per kernel into out[0..*n_out)
+   (at most `max` entries, kernels without launches omitted) and clears the record. */
+ms_status ms_profile_collect(ms_ctx *ctx, ms_kernel_time *out, int max, int *n_out);
+/* Static name of a kernel id ("mark", "emit", ...), "?" when unknown. */
+const char *ms_kernel_name(int kernel);
+
 #ifdef __cplusplus
 }
 #endif

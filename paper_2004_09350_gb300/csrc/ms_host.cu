@@ -84,6 +84,30 @@ ms_status ensure_work(ms_ctx* c, uint64_t bytes) {
   return MS_OK;
 }
 
+static cudaEvent_t pooled_event(ms_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+ProfScope::ProfScope(ms_ctx* c, int kernel, cudaStream_t s) : c_(c), s_(s) {
+  if (!c->prof_on) return;
+  ms_prof_rec r{kernel, pooled_event(c), pooled_event(c)};
+  if (!r.start || !r.stop) return;
+  cudaEventRecord(r.start, s);
+  c->prof.push_back(r);
+  idx_ = (int)c->prof.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (idx_ >= 0) cudaEventRecord(c_->prof[idx_].stop, s_);
+}
+
 __global__ void k_write_meta(DevMeta* m, DevMeta v) { *m = v; }
 
 __global__ void k_set_top(DevCtl* ctl, const DevMeta* m) {
@@ -174,6 +198,11 @@ ms_status ms_ctx_destroy(ms_ctx* c) {
   dev_free(c, c->ctl);
   dev_free(c, c->metas);
   if (c->pin) cudaFreeHost(c->pin);
+  for (auto& r : c->prof) {
+    cudaEventDestroy(r.start);
+    cudaEventDestroy(r.stop);
+  }
+  for (auto e : c->event_pool) cudaEventDestroy(e);
   delete c;
   return MS_OK;
 }
@@ -244,6 +273,7 @@ ms_status ms_column_import(ms_ctx* c, int fmt, int bw, uint64_t n, const void* s
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && fmt >= MS_DYN_BP) {
+    ProfScope ps(c, MS_K_VALIDATE, s);
     k_validate<<<(unsigned)std::min<uint64_t>(cdiv(std::max<uint64_t>(nb, 1), 256), 1024), 256, 0, s>>>(
         c->metas + slot, c->ctl);
     e = cudaGetLastError();
@@ -339,6 +369,40 @@ ms_status ms_column_free(ms_ctx* c, ms_column* col, void* stream) {
     if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
   }
   return MS_OK;
+}
+
+ms_status ms_profile_enable(ms_ctx* c, int on) {
+  if (!c) return MS_ERR_INVALID_ARG;
+  c->prof_on = on != 0;
+  return MS_OK;
+}
+
+ms_status ms_profile_collect(ms_ctx* c, ms_kernel_time* out, int max, int* n_out) {
+  if (!c || (!out && max > 0)) return MS_ERR_INVALID_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return MS_ERR_CUDA;
+  ms_kernel_time acc[MS_K_COUNT];
+  for (int k = 0; k < MS_K_COUNT; k++) acc[k] = ms_kernel_time{k, 0, 0.0};
+  for (auto& r : c->prof) {
+    float ms = 0.f;
+    if (r.kernel >= 0 && r.kernel < MS_K_COUNT && cudaEventElapsedTime(&ms, r.start, r.stop) == cudaSuccess) {
+      acc[r.kernel].launches++;
+      acc[r.kernel].total_ms += ms;
+    }
+    c->event_pool.push_back(r.start);
+    c->event_pool.push_back(r.stop);
+  }
+  c->prof.clear();
+  int n = 0;
+  for (int k = 0; k < MS_K_COUNT && n < max; k++)
+    if (acc[k].launches) out[n++] = acc[k];
+  if (n_out) *n_out = n;
+  return MS_OK;
+}
+
+const char* ms_kernel_name(int k) {
+  static const char* names[MS_K_COUNT] = {"mark", "emit", "compress", "decompress", "project",
+                                          "calc", "agg_sum", "group_sum", "build_keys", "validate"};
+  return (k >= 0 && k < MS_K_COUNT) ? names[k] : "?";
 }
 
 }  // extern "C"

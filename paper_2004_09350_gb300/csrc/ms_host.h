@@ -18,6 +18,11 @@ struct ms_column {
   void* ext;        // external buffer (non-arena columns)
 };
 
+struct ms_prof_rec {
+  int kernel;
+  cudaEvent_t start, stop;
+};
+
 struct ms_ctx {
   int device = 0, sms = 0;
   ms_alloc_fn alloc = nullptr;
@@ -34,6 +39,9 @@ struct ms_ctx {
   uint64_t work_cap = 0;
   uint64_t* pin = nullptr;  // pinned host scratch
   uint64_t last_err_info = 0;
+  bool prof_on = false;
+  std::vector<ms_prof_rec> prof;
+  std::vector<cudaEvent_t> event_pool;
 };
 
 namespace ms {
@@ -50,5 +58,17 @@ ms_column* new_arena_column(ms_ctx* c, int fmt, int bw, uint64_t n_max);
 void drop_new_column(ms_ctx* c, ms_column* col);
 // Makes sure the scratch area holds at least `bytes`; synchronises when it grows.
 ms_status ensure_work(ms_ctx* c, uint64_t bytes);
+
+// Brackets one kernel launch with profiling events when profiling is on.
+class ProfScope {
+ public:
+  ProfScope(ms_ctx* c, int kernel, cudaStream_t s);
+  ~ProfScope();
+
+ private:
+  ms_ctx* c_;
+  cudaStream_t s_;
+  int idx_ = -1;
+};
 
 }  // namespace ms

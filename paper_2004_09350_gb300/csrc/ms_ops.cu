@@ -50,11 +50,14 @@ int grid_for(ms_ctx* c, K kernel, size_t smem, uint64_t tiles) {
 
 bool owned(ms_ctx* c, const ms_column* col) { return col && col->ctx == c && !col->freed; }
 
+constexpr int kProduceKernel[5] = {MS_K_COMPRESS, MS_K_DECOMPRESS, MS_K_PROJECT, MS_K_CALC, MS_K_EMIT};
+
 template <int OP>
 ms_status launch_produce(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
   const size_t smem = (size_t)SmemPlan<OP>::kPerWarp * kWarps;
   const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
   const int grid = grid_for(c, k_produce<OP>, smem, tiles);
+  ProfScope ps(c, kProduceKernel[OP], s);
   k_produce<OP><<<grid, kThreads, smem, s>>>(a);
   return cuda_status(cudaGetLastError());
 }
@@ -63,6 +66,7 @@ ms_status launch_mark(ms_ctx* c, MarkArgs& a, uint64_t n_max, cudaStream_t s) {
   const size_t smem = 4096 * kWarps;
   const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
   const int grid = grid_for(c, k_mark, smem, tiles);
+  ProfScope ps(c, MS_K_MARK, s);
   k_mark<<<grid, kThreads, smem, s>>>(a);
   return cuda_status(cudaGetLastError());
 }
@@ -229,6 +233,7 @@ ms_status ms_agg_sum(ms_ctx* c, const ms_column* in, uint64_t* d_result, void* s
   const size_t smem = 4096 * kWarps;
   const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(in->n_max, 1), kBlock), kWarps);
   const int grid = grid_for(c, k_agg_sum, smem, tiles);
+  ProfScope ps(c, MS_K_AGG_SUM, s);
   k_agg_sum<<<grid, kThreads, smem, s>>>(c->metas + in->slot, d_result, c->ctl);
   return cuda_status(cudaGetLastError());
 }
@@ -242,6 +247,7 @@ ms_status ms_group_sum(ms_ctx* c, const ms_column* gid, const ms_column* val, ui
   const uint64_t n_max = std::min(gid->n_max, val->n_max);
   const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
   const int grid = grid_for(c, k_group_sum, 4096 * kWarps + 8 * kSmemGroups, tiles);
+  ProfScope ps(c, MS_K_GROUP_SUM, s);
   k_group_sum<<<grid, kThreads, smem, s>>>(c->metas + gid->slot, c->metas + val->slot, G, d_sums, c->ctl);
   return cuda_status(cudaGetLastError());
 }
@@ -260,6 +266,7 @@ ms_status ms_semijoin(ms_ctx* c, const ms_column* probe, const ms_column* keys, 
     const size_t smem = 4096 * kWarps;
     const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(keys->n_max, 1), kBlock), kWarps);
     const int grid = grid_for(c, k_build_keys, smem, tiles);
+    ProfScope ps(c, MS_K_BUILD_KEYS, s);
     k_build_keys<<<grid, kThreads, smem, s>>>(c->metas + keys->slot, domain, w.keybits, c->ctl);
     if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
   }

@@ -37,6 +37,10 @@ class MSError(RuntimeError):
         self.info = info
 
 
+class KernelTime(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("launches", ctypes.c_uint32), ("total_ms", ctypes.c_double)]
+
+
 class ColumnMeta(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("fmt", ctypes.c_int32), ("static_bw", ctypes.c_int32),
                 ("size_bytes", ctypes.c_uint64), ("n_blocks", ctypes.c_uint64),
@@ -86,6 +90,12 @@ def load() -> ctypes.CDLL:
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
+    lib.ms_profile_enable.argtypes = [p, i32]
+    lib.ms_profile_enable.restype = ctypes.c_int
+    lib.ms_profile_collect.argtypes = [p, ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
+    lib.ms_profile_collect.restype = ctypes.c_int
+    lib.ms_kernel_name.argtypes = [i32]
+    lib.ms_kernel_name.restype = ctypes.c_char_p
     lib.ms_last_error_info.argtypes = [p]
     lib.ms_last_error_info.restype = u64
     lib.ms_column_max_rows.argtypes = [p]
@@ -98,7 +108,7 @@ def header_symbols() -> list[str]:
     """Names of the functions include/morphstore.h declares."""
     with open(_HEADER) as f:
         text = f.read()
-    return sorted(set(re.findall(r"^\s*(?:ms_status|uint64_t)\s+(ms_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:ms_status|uint64_t|const char \*)\s*(ms_\w+)\s*\(", text, re.M)))
 
 
 def _stream_handle(stream) -> ctypes.c_void_p:
@@ -211,6 +221,19 @@ class Ctx:
 
     def reset_high_water(self, stream=None):
         _check(load().ms_arena_reset_high_water(self.h, _stream_handle(stream)), "reset_high_water")
+
+    # ------------------------------------------------------------- profiling
+    def profile(self, on: bool = True):
+        _check(load().ms_profile_enable(self.h, 1 if on else 0), "ms_profile_enable")
+
+    def profile_collect(self) -> dict:
+        """{kernel name: (launches, total device ms)} since the last collect (synchronises)."""
+        arr = (KernelTime * 16)()
+        n = ctypes.c_int()
+        _check(load().ms_profile_collect(self.h, arr, 16, ctypes.byref(n)), "ms_profile_collect")
+        lib = load()
+        return {lib.ms_kernel_name(arr[i].kernel).decode(): (arr[i].launches, arr[i].total_ms)
+                for i in range(n.value)}
 
     # --------------------------------------------------------------- columns
     def _new(self, out: ctypes.c_void_p, fmt: int, bw: int) -> Column:

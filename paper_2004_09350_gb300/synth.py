@@ -52,16 +52,18 @@ def uniform(seed: int, n: int, lo: int, hi: int) -> np.ndarray:
 def geometric_gaps(seed: int, n: int) -> np.ndarray:
     """Gaps in {1, 2, ...} with P(g = k) = (3/4)^(k-1) / 4 (mean 4), capped at 33.
 
-    Trial t succeeds when bits 2t, 2t+1 of the draw are both zero (probability 1/4).
+    Trial t succeeds when bits 2t, 2t+1 of the draw are both zero (probability 1/4);
+    the gap is one plus the index of the first success.  The index comes from the
+    lowest set bit of the "pair is 00" mask, located exactly with frexp.
     """
     z = splitmix64(seed, n)
-    gap = np.full(n, 33, dtype=np.uint64)
-    open_ = np.ones(n, dtype=bool)
-    for t in range(32):
-        hit = open_ & (((z >> np.uint64(2 * t)) & np.uint64(3)) == 0)
-        gap[hit] = t + 1
-        open_ &= ~hit
-    return gap
+    with np.errstate(over="ignore"):
+        m = ~(z | (z >> np.uint64(1))) & np.uint64(0x5555555555555555)
+        low = m & (~m + np.uint64(1))
+    _, e = np.frexp(low.astype(np.float64))
+    gap = (e.astype(np.int64) - 1) // 2 + 1
+    gap[m == 0] = 33
+    return gap.astype(np.uint64)
 
 
 # --------------------------------------------------------------- Table 1 columns
