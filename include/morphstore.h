@@ -220,6 +220,35 @@ ms_status ms_semijoin(ms_ctx *ctx, const ms_column *probe, const ms_column *buil
                       uint64_t key_domain, int out_fmt, int out_static_bw,
                       ms_column **out, void *stream);
 
+/* ------------------------------------------------------- no-allocation use */
+
+/* Largest column ms_compress_noalloc accepts (16 Mi values). */
+#define MS_NOALLOC_MAX_ROWS (1ull << 24)
+
+/* Compression for callers that cannot allocate device memory.  The paper has no
+   counterpart: this serves embedding hosts.  Some callers cannot call cudaMalloc:
+   a memory manager compressing a buffer while it serves an allocation request
+   (it must not re-enter the allocator), a host whose device memory is all handed
+   out by its own pool, or a latency-critical path that cannot take the implicit
+   synchronisation a driver allocation may cause.
+   It does what ms_compress does for the n uncompressed values at d_in (16-byte
+   aligned).  It writes the column's bytes, in the layout above, to d_out
+   (16-byte aligned, out_cap bytes) instead of a context's arena.  d_result
+   (device, 2 uint64 words) receives the column's size in bytes and the device
+   status (an ms_status: MS_ERR_NOMEM if out_cap is too small,
+   MS_ERR_VALUE_TOO_WIDE for static BP).  Neither this call nor anything it
+   starts allocates: its scratch (look-back status words and a control block,
+   about 33 KB) is a fixed device array in the library.  n above
+   MS_NOALLOC_MAX_ROWS is rejected with MS_ERR_INVALID_ARG.
+   The first call on a device (with that device current) looks the array's
+   device address up and caches it; make that first call before any stream
+   capture.  Every call shares the array: calls that
+   overlap on the GPU (different streams or host threads) race and must be
+   serialised by the caller.  No context is needed.  Asynchronous on `stream`. */
+ms_status ms_compress_noalloc(const uint64_t *d_in, uint64_t n, int fmt, int static_bw,
+                              void *d_out, uint64_t out_cap, uint64_t *d_result,
+                              void *stream);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Kernels of the library, as reported by ms_profile_collect. */

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libms.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ms_host.cu", "ms_ops.cu"]
+SOURCES = ["ms_host.cu", "ms_ops.cu", "ms_noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -43,6 +43,7 @@ struct MarkArgs {
   uint64_t* status;
 };
 
+#ifndef MS_PRODUCE_ONLY  // translation units that only instantiate k_produce
 __global__ void __launch_bounds__(kThreads) k_mark(MarkArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ uint64_t s_cnt[kWarps];
@@ -96,6 +97,8 @@ __global__ void __launch_bounds__(kThreads) k_mark(MarkArgs a) {
     __syncthreads();
   }
 }
+
+#endif  // MS_PRODUCE_ONLY
 
 // ------------------------------------------------------- produce (map) kernel
 
@@ -501,6 +504,7 @@ __global__ void __launch_bounds__(kThreads) k_produce(ProduceArgs a) {
   }
 }
 
+#ifndef MS_PRODUCE_ONLY
 // ----------------------------------------------------------------- aggregates
 
 __global__ void __launch_bounds__(kThreads) k_agg_sum(const DevMeta* in, uint64_t* result, DevCtl* ctl) {
@@ -586,5 +590,7 @@ __global__ void __launch_bounds__(kThreads) k_build_keys(const DevMeta* keys, ui
     }
   }
 }
+
+#endif  // MS_PRODUCE_ONLY
 
 }  // namespace ms

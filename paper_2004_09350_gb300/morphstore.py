@@ -85,6 +85,7 @@ def load() -> ctypes.CDLL:
         "ms_agg_sum": [p, p, p, p],
         "ms_group_sum": [p, p, p, u64, p, p],
         "ms_semijoin": [p, p, p, u64, i32, i32, pp, p],
+        "ms_compress_noalloc": [p, u64, i32, i32, p, u64, p, p],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -329,6 +330,23 @@ class Ctx:
         _check(load().ms_semijoin(self.h, probe.ptr, keys.ptr, key_domain, fmt, bw, ctypes.byref(out),
                                   _stream_handle(stream)), "ms_semijoin")
         return self._new(out, fmt, bw)
+
+
+NOALLOC_MAX_ROWS = 1 << 24
+
+
+def compress_noalloc(d_in: torch.Tensor, fmt: int, d_out: torch.Tensor, d_result: torch.Tensor,
+                     bw: int = 0, stream=None) -> None:
+    """ms_compress_noalloc: compress into caller memory without any device allocation.
+
+    d_out receives the column bytes; d_result (2 int64 words on the device) the size
+    in bytes and the device status.  Calls that overlap on the GPU race on the
+    library's fixed scratch array."""
+    assert d_in.is_cuda and d_in.element_size() == 8 and d_in.is_contiguous()
+    _check(load().ms_compress_noalloc(ctypes.c_void_p(d_in.data_ptr()), d_in.numel(), fmt, bw,
+                                      ctypes.c_void_p(d_out.data_ptr()), d_out.numel() * d_out.element_size(),
+                                      ctypes.c_void_p(d_result.data_ptr()), _stream_handle(stream)),
+           "ms_compress_noalloc")
 
 
 def to_numpy_u64(t: torch.Tensor) -> np.ndarray:
