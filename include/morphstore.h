@@ -263,7 +263,10 @@ typedef enum {
   MS_K_GROUP_SUM = 7,
   MS_K_BUILD_KEYS = 8, /* semi-join build side */
   MS_K_VALIDATE = 9,   /* header check of imported columns */
-  MS_K_COUNT = 10
+  MS_K_SCAN = 10,      /* select / semi-join: exclusive scan of per-chunk match counts */
+  MS_K_PLACE_SCAN = 11, /* block-format outputs: payload offsets and headers */
+  MS_K_PLACE_COPY = 12, /* block-format outputs: payload placement */
+  MS_K_COUNT = 13
 } ms_kernel;
 
 typedef struct {

@@ -1,0 +1,230 @@
+// ms_consume.cu -- consuming kernels (no output column): the select / semi-join
+// mark step and its count scan, agg_sum, group_sum and the semi-join build side,
+// plus their launchers.
+#include "ms_launch.h"
+
+namespace ms {
+
+// Mark kernel of select / semi-join: every warp streams its own chunks (no block
+// barrier, no look-back) and writes per 512-row chunk a 512-bit match bitmap
+// (lane j's 16 rows -> halfword j) and the chunk's match count.
+
+
+__global__ void __launch_bounds__(kThreads, 2) k_mark(MarkArgs a) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto* sm = reinterpret_cast<StreamSmem<kMarkDepth>*>(smem_raw) + warp;
+  const ColView c = view_of(a.in);
+  const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
+  stream_chunks<kMarkDepth>(c, gw, W, sm, lane, a.ctl, [&](uint64_t g, const uint64_t* v, int valid) {
+    uint32_t m16 = 0;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      bool hit;
+      if (a.keybits) {
+        const uint64_t x = v[k];
+        hit = x < a.domain && ((__ldg(a.keybits + (x >> 5)) >> (x & 31)) & 1u);
+      } else {
+        hit = pred(a.cmp, v[k], a.c1, a.c2);
+      }
+      if (hit && 16 * lane + k < valid) m16 |= 1u << k;
+    }
+    a.bitmap[g * 32 + lane] = (uint16_t)m16;
+    const uint32_t cnt = __reduce_add_sync(kFull, (uint32_t)__popc(m16));
+    if (lane == 0) a.counts[g] = cnt;
+  });
+}
+
+// Exclusive scan of the per-chunk match counts (decoupled look-back over tiles of
+// 4096 chunks).  Writes coff (with coff[nchunks] = total), the first chunk of every
+// output block (bstart) and the total into ctl->op_n.
+
+__global__ void __launch_bounds__(kThreads) k_scan_counts(ScanArgs a) {
+  __shared__ uint64_t s_warp[kWarps];
+  __shared__ uint64_t s_excl;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t nch = (a.in->n + kBlock - 1) / kBlock;
+  constexpr int kPer = 16;
+  const uint64_t per_tile = (uint64_t)kThreads * kPer;
+  const uint64_t ntiles = (nch + per_tile - 1) / per_tile;
+  if (nch == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    a.coff[0] = 0;
+    a.ctl->op_n = 0;
+  }
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t g0 = tile * per_tile + (uint64_t)threadIdx.x * kPer;
+    uint32_t cnt[kPer];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+      cnt[k] = (g0 + k < nch) ? a.counts[g0 + k] : 0;
+      sum += cnt[k];
+    }
+    const uint32_t texcl = warp_excl_scan32(sum, lane);
+    if (lane == 31) s_warp[warp] = texcl + sum;
+    __syncthreads();
+    if (warp == 0) {
+      const uint64_t wt = lane < kWarps ? s_warp[lane] : 0;
+      const uint64_t wex = warp_excl_scan(wt, lane);
+      const uint64_t agg = warp_sum(wt);
+      const uint64_t ex = lookback(a.status, tile, agg, lane, a.ctl);
+      if (lane < kWarps) s_warp[lane] = wex;
+      if (lane == 0) s_excl = ex;
+    }
+    __syncthreads();
+    uint64_t o = s_excl + s_warp[warp] + texcl;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+      const uint64_t g = g0 + k;
+      if (g < nch) {
+        a.coff[g] = o;
+        if (cnt[k]) {
+          for (uint64_t h = (o + kBlock - 1) / kBlock; h <= (o + cnt[k] - 1) / kBlock; h++) a.bstart[h] = g;
+        }
+        o += cnt[k];
+        if (g == nch - 1) {
+          a.coff[nch] = o;
+          a.ctl->op_n = o;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+
+// ----------------------------------------------------------------- aggregates
+
+__global__ void __launch_bounds__(kThreads, 2) k_agg_sum(const DevMeta* in, uint64_t* result, DevCtl* ctl) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  __shared__ uint64_t s_part[kWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto* sm = reinterpret_cast<StreamSmem<kMarkDepth>*>(smem_raw) + warp;
+  const ColView c = view_of(in);
+  const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
+  uint64_t acc = 0;
+  stream_chunks<kMarkDepth>(c, gw, W, sm, lane, ctl, [&](uint64_t, const uint64_t* v, int valid) {
+#pragma unroll
+    for (int k = 0; k < 16; k++) acc += (16 * lane + k < valid) ? v[k] : 0;
+  });
+  acc = warp_sum(acc);
+  if (lane == 0) s_part[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t t = 0;
+    for (int w = 0; w < kWarps; w++) t += s_part[w];
+    if (t) atomicAdd(reinterpret_cast<unsigned long long*>(result), (unsigned long long)t);
+  }
+}
+
+
+__global__ void __launch_bounds__(32 * kPairWarps, 4) k_group_sum(const DevMeta* gid, const DevMeta* val, uint64_t G,
+                                                               uint64_t* sums, DevCtl* ctl) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto* rings = reinterpret_cast<StreamSmem<kPairDepth>*>(smem_raw);
+  unsigned long long* hist =
+      reinterpret_cast<unsigned long long*>(smem_raw + 2 * kPairWarps * sizeof(StreamSmem<kPairDepth>));
+  const bool local = G <= kSmemGroups;
+  if (local)
+    for (uint64_t k = threadIdx.x; k < G; k += blockDim.x) hist[k] = 0;
+  __syncthreads();
+  const ColView cg = view_of(gid), cv = view_of(val);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && cg.n != cv.n) set_error(ctl, MS_ERR_INVALID_ARG, cv.n);
+  const uint64_t n = min(cg.n, cv.n);
+  const uint64_t gw = (uint64_t)blockIdx.x * kPairWarps + warp, W = (uint64_t)gridDim.x * kPairWarps;
+  stream_pairs(cg, cv, n, gw, W, rings + 2 * warp, rings + 2 * warp + 1, lane, ctl,
+               [&](uint64_t, const uint64_t* g8, const uint64_t* v, int valid) {
+#pragma unroll
+                 for (int k = 0; k < 16; k++) {
+                   if (16 * lane + k < valid) {
+                     if (g8[k] < G) {
+                       if (local) atomicAdd(hist + g8[k], (unsigned long long)v[k]);
+                       else atomicAdd(reinterpret_cast<unsigned long long*>(sums) + g8[k], (unsigned long long)v[k]);
+                     } else {
+                       set_error(ctl, MS_ERR_OUT_OF_RANGE, g8[k]);
+                     }
+                   }
+                 }
+               });
+  if (!local) return;
+  __syncthreads();
+  for (uint64_t k = threadIdx.x; k < G; k += blockDim.x)
+    if (hist[k]) atomicAdd(reinterpret_cast<unsigned long long*>(sums) + k, hist[k]);
+}
+
+// Semi-join build side: set bit key for every key of the build column.
+__global__ void __launch_bounds__(kThreads, 2) k_build_keys(const DevMeta* keys, uint64_t domain, uint32_t* bits,
+                                                             DevCtl* ctl) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto* sm = reinterpret_cast<StreamSmem<kMarkDepth>*>(smem_raw) + warp;
+  const ColView c = view_of(keys);
+  const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
+  stream_chunks<kMarkDepth>(c, gw, W, sm, lane, ctl, [&](uint64_t, const uint64_t* v, int valid) {
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      if (16 * lane + k < valid) {
+        if (v[k] < domain) atomicOr(bits + (v[k] >> 5), 1u << (v[k] & 31));
+        else set_error(ctl, MS_ERR_OUT_OF_RANGE, v[k]);
+      }
+    }
+  });
+}
+
+
+constexpr size_t kStreamSmem = sizeof(StreamSmem<kMarkDepth>) * kWarps;
+
+ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max, cudaStream_t s) {
+  a.bitmap = w.bitmap;
+  a.counts = w.counts;
+  const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
+  {
+    const int grid = grid_for(c, k_mark, kStreamSmem, tiles);
+    ProfScope ps(c, MS_K_MARK, s);
+    k_mark<<<grid, kThreads, kStreamSmem, s>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
+  }
+  ScanArgs sa{};
+  sa.in = a.in;
+  sa.ctl = c->ctl;
+  sa.counts = w.counts;
+  sa.coff = w.coff;
+  sa.bstart = w.bstart;
+  sa.status = w.status;
+  const uint64_t stiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), (uint64_t)kThreads * 16);
+  const int grid = grid_for(c, k_scan_counts, 0, stiles);
+  ProfScope ps(c, MS_K_SCAN, s);
+  k_scan_counts<<<grid, kThreads, 0, s>>>(sa);
+  return cuda_status(cudaGetLastError());
+}
+
+ms_status launch_agg_sum(ms_ctx* c, const DevMeta* in, uint64_t* d_result, uint64_t n_max, cudaStream_t s) {
+  const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
+  const int grid = grid_for(c, k_agg_sum, kStreamSmem, tiles);
+  ProfScope ps(c, MS_K_AGG_SUM, s);
+  k_agg_sum<<<grid, kThreads, kStreamSmem, s>>>(in, d_result, c->ctl);
+  return cuda_status(cudaGetLastError());
+}
+
+ms_status launch_group_sum(ms_ctx* c, const DevMeta* gid, const DevMeta* val, uint64_t G, uint64_t* d_sums,
+                           uint64_t n_max, cudaStream_t s) {
+  const size_t smem = 2 * kPairWarps * sizeof(StreamSmem<kPairDepth>) +
+                      (G <= (uint64_t)kSmemGroups ? 8 * std::max<uint64_t>(G, 1) : 0);
+  const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kPairWarps);
+  const int grid = grid_for(c, k_group_sum, smem, tiles, 32 * kPairWarps);
+  ProfScope ps(c, MS_K_GROUP_SUM, s);
+  k_group_sum<<<grid, 32 * kPairWarps, smem, s>>>(gid, val, G, d_sums, c->ctl);
+  return cuda_status(cudaGetLastError());
+}
+
+ms_status launch_build_keys(ms_ctx* c, const DevMeta* keys, uint64_t domain, uint32_t* bits, uint64_t n_max,
+                            cudaStream_t s) {
+  const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
+  const int grid = grid_for(c, k_build_keys, kStreamSmem, tiles);
+  ProfScope ps(c, MS_K_BUILD_KEYS, s);
+  k_build_keys<<<grid, kThreads, kStreamSmem, s>>>(keys, domain, bits, c->ctl);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace ms

@@ -157,70 +157,97 @@ MS_DEV int swz(int o) { return o ^ ((o >> 4) & 15); }
 
 // ------------------------------------------------------- lane bit streams
 
-// Reads lane `lane`'s 16 values of width b from a block payload in shared memory
-// (stream halfword q of the lane at s[32*q + lane]).
-MS_DEV void read_lane_stream(const uint16_t* s, int lane, int b, uint64_t v[16]) {
-  if (b == 0) {
+// Width-specialised lane-stream codecs.  Lane `lane`'s stream at width B is B
+// halfwords (s[32*q + lane], q < B); its 16 values sit at stream bits [k*B, k*B+B).
+// The halfwords are gathered into 32-bit words once and every value is cut out
+// with compile-time shifts.
+template <int B>
+MS_DEV void unpack16(const uint16_t* s, int lane, uint64_t v[16]) {
+  if constexpr (B == 0) {
 #pragma unroll
     for (int k = 0; k < 16; k++) v[k] = 0;
-    return;
-  }
-  const uint64_t mask = lowmask(b);
-  uint64_t acc = 0;
-  int have = 0, q = 0;
+  } else {
+    constexpr int NW = (B + 1) / 2;  // 32-bit words of the lane stream
+    uint32_t w[NW + 1];
 #pragma unroll
-  for (int k = 0; k < 16; k++) {
-    while (have < b && have <= 48) {
-      acc |= (uint64_t)s[32 * q + lane] << have;
-      have += 16;
-      q++;
+    for (int i = 0; i < NW; i++) {
+      const uint32_t lo = s[32 * (2 * i) + lane];
+      const uint32_t hi = (2 * i + 1 < B) ? (uint32_t)s[32 * (2 * i + 1) + lane] : 0u;
+      w[i] = lo | (hi << 16);
     }
-    uint64_t x;
-    if (have >= b) {
-      x = acc & mask;
-      acc = (b == 64) ? 0 : (acc >> b);
-      have -= b;
-    } else {  // b > 48 and 48 < have < b: the value continues in the next halfword
-      uint64_t h = s[32 * q + lane];
-      q++;
-      x = (acc | (h << have)) & mask;
-      int used = b - have;
-      acc = h >> used;
-      have = 16 - used;
+    w[NW] = 0;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      constexpr uint64_t kMask = B >= 64 ? ~0ull : ((1ull << (B & 63)) - 1ull);
+      const int bit = k * B, wi = bit >> 5, sh = bit & 31;
+      if constexpr (B <= 32) {
+        uint32_t x = sh ? __funnelshift_r(w[wi], w[wi + 1], sh) : w[wi];
+        v[k] = (uint64_t)(B == 32 ? x : (x & (uint32_t)kMask));
+      } else {
+        const uint32_t x0 = sh ? __funnelshift_r(w[wi], w[wi + 1], sh) : w[wi];
+        const uint32_t x1 = sh ? __funnelshift_r(w[wi + 1], (wi + 2 <= NW) ? w[wi + 2] : 0u, sh) : w[wi + 1];
+        v[k] = (((uint64_t)x1 << 32) | x0) & kMask;
+      }
     }
-    v[k] = x;
+  }
+}
+
+template <int B>
+MS_DEV void pack16(uint16_t* s, int lane, const uint64_t r[16]) {
+  if constexpr (B > 0) {
+    constexpr int NW = (B + 1) / 2;
+    uint32_t w[NW + 1];
+#pragma unroll
+    for (int i = 0; i <= NW; i++) w[i] = 0;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const int bit = k * B, wi = bit >> 5, sh = bit & 31;
+      const uint64_t x = r[k];
+      w[wi] |= (uint32_t)(x << sh);
+      if (sh + B > 32) w[wi + 1] |= (uint32_t)(x >> (32 - sh));
+      if (sh + B > 64) w[wi + 2] |= (uint32_t)(x >> (64 - sh));
+    }
+#pragma unroll
+    for (int i = 0; i < NW; i++) {
+      s[32 * (2 * i) + lane] = (uint16_t)w[i];
+      if (2 * i + 1 < B) s[32 * (2 * i + 1) + lane] = (uint16_t)(w[i] >> 16);
+    }
+  }
+}
+
+#define MS_WIDTH_CASES(M)                                                                                       \
+  M(0) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16) M(17) M(18) M(19) \
+  M(20) M(21) M(22) M(23) M(24) M(25) M(26) M(27) M(28) M(29) M(30) M(31) M(32) M(33) M(34) M(35) M(36) M(37)  \
+  M(38) M(39) M(40) M(41) M(42) M(43) M(44) M(45) M(46) M(47) M(48) M(49) M(50) M(51) M(52) M(53) M(54) M(55)  \
+  M(56) M(57) M(58) M(59) M(60) M(61) M(62) M(63) M(64)
+
+// Reads lane `lane`'s 16 values of width b (0..64) from a block payload in shared
+// memory (stream halfword q of the lane at s[32*q + lane]).
+MS_DEV void read_lane_stream(const uint16_t* s, int lane, int b, uint64_t v[16]) {
+  switch (b) {
+#define MS_UNPACK_CASE(B) \
+  case B:                 \
+    unpack16<B>(s, lane, v); \
+    break;
+    MS_WIDTH_CASES(MS_UNPACK_CASE)
+#undef MS_UNPACK_CASE
+    default:
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] = 0;
   }
 }
 
 // Writes lane `lane`'s 16 residuals (each < 2^b) as its stream into shared memory.
 MS_DEV void write_lane_stream(uint16_t* s, int lane, int b, const uint64_t r[16]) {
-  if (b == 0) return;
-  uint64_t acc = 0;
-  int have = 0, q = 0;
-#pragma unroll
-  for (int k = 0; k < 16; k++) {
-    uint64_t x = r[k];
-    if (have + b <= 64) {
-      acc |= x << have;  // have <= 15 < 64
-      have += b;
-    } else {  // the value straddles the 64-bit accumulator: flush four halfwords
-      acc |= x << have;
-#pragma unroll
-      for (int t = 0; t < 4; t++) {
-        s[32 * q + lane] = (uint16_t)acc;
-        acc >>= 16;
-        q++;
-      }
-      int fit = 64 - have;
-      acc = x >> fit;
-      have = b - fit;
-    }
-    while (have >= 16) {
-      s[32 * q + lane] = (uint16_t)acc;
-      acc >>= 16;
-      have -= 16;
-      q++;
-    }
+  switch (b) {
+#define MS_PACK_CASE(B) \
+  case B:               \
+    pack16<B>(s, lane, r); \
+    break;
+    MS_WIDTH_CASES(MS_PACK_CASE)
+#undef MS_PACK_CASE
+    default:
+      break;
   }
 }
 
@@ -334,6 +361,179 @@ MS_DEV int decode_chunk(const ColView& c, uint64_t g, int lane, uint64_t v[16], 
   }
   return valid;
 }
+
+// ------------------------------------------------ asynchronous chunk streams
+
+MS_DEV void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+MS_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+MS_DEV void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Per-warp shared memory of one column stream: D payload slots of 4 KB (a 512-value
+// block at up to 64 bits) and 2D header slots.
+template <int D>
+struct StreamSmem {
+  uint16_t slot[D][2048];
+  uint64_t hdr[2 * D][2];
+};
+
+// A warp walks chunks first, first+stride, ... (count of them) of one column and
+// keeps kDepth chunk payloads in flight with cp.async.  Block headers travel one
+// level further ahead, so issuing a payload copy never waits on a header load.
+// Groups: the prologue fetches the first kDepth headers synchronously, then
+// commits P_j = {header j+D, payload j} for j < D-1, and iteration i commits
+// G_i = {header i+2D-1, payload i+D-1}.  After cp.async.wait_group(D-2) at the
+// top of iteration i, the payload of chunk i and every header up to chunk
+// i+D-1 have landed.
+template <int kDepth>
+struct ChunkStream {
+  ColView c;
+  uint64_t first, stride, count;
+  StreamSmem<kDepth>* sm;
+  int lane;
+
+  MS_DEV uint64_t chunk(uint64_t i) const { return first + i * stride; }
+
+  MS_DEV void issue_header(uint64_t i) {
+    if (i >= count || lane != 0 || !is_block_fmt(c.fmt)) return;
+    const uint64_t g = chunk(i);
+    if (g < c.nb) cp_async16(sm->hdr[i % (2 * kDepth)], c.p + 16 * g);
+  }
+
+  MS_DEV void issue_payload(uint64_t i) {
+    if (i >= count) return;
+    const uint64_t g = chunk(i);
+    const uint8_t* src = nullptr;
+    int units = 0;
+    bool swizzle = false;
+    if (c.fmt == MS_UNCOMPR) {
+      if ((g + 1) * kBlock <= c.n) {
+        src = c.p + 4096 * g;
+        units = 256;
+        swizzle = true;
+      }
+    } else if (c.fmt == MS_STATIC_BP) {
+      if (g < c.n / kBlock) {
+        src = c.p + 64ull * c.bw * g;
+        units = 4 * c.bw;
+      }
+    } else if (g < c.nb) {
+      const uint64_t w0 = sm->hdr[i % (2 * kDepth)][0];
+      const int b = (int)min((uint64_t)64, w0 & 255);
+      src = c.p + 16 * c.nb + 8 * (w0 >> 8);
+      units = 4 * b;
+    }
+    uint4* dst = reinterpret_cast<uint4*>(sm->slot[i % kDepth]);
+    for (int u = lane; u < units; u += 32) {
+      const int d = swizzle ? (((u >> 3) << 3) | ((u & 7) ^ ((u >> 3) & 7))) : u;
+      cp_async16(dst + d, reinterpret_cast<const uint4*>(src) + u);
+    }
+  }
+
+  MS_DEV void prologue() {
+    for (int i = 0; i < kDepth; i++) issue_header(i);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+  }
+  MS_DEV void prologue_step(int j) {  // j < kDepth-1, commit by the caller
+    issue_header(j + kDepth);
+    issue_payload(j);
+  }
+  MS_DEV void step(uint64_t i) {  // at iteration i, commit by the caller
+    issue_header(i + 2 * kDepth - 1);
+    issue_payload(i + kDepth - 1);
+  }
+
+  // Decodes chunk i (already landed) into lane registers; returns its valid count.
+  MS_DEV int decode(uint64_t i, uint64_t v[16], DevCtl* ctl) const {
+    const uint64_t g = chunk(i);
+    const uint64_t base = g * kBlock;
+    if (i >= count || base >= c.n) {
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] = 0;
+      return 0;
+    }
+    const int valid = (int)min((uint64_t)kBlock, c.n - base);
+    const uint16_t* slot = sm->slot[i % kDepth];
+    if (c.fmt == MS_UNCOMPR) {
+      if (valid == kBlock) {
+        const uint4* st = reinterpret_cast<const uint4*>(slot);
+#pragma unroll
+        for (int cc = 0; cc < 8; cc++) {
+          const uint4 q = st[lane * 8 + (cc ^ (lane & 7))];
+          v[2 * cc] = (uint64_t)q.x | ((uint64_t)q.y << 32);
+          v[2 * cc + 1] = (uint64_t)q.z | ((uint64_t)q.w << 32);
+        }
+      } else {
+        const uint64_t* src = reinterpret_cast<const uint64_t*>(c.p) + base;
+#pragma unroll
+        for (int k = 0; k < 16; k++) v[k] = (16 * lane + k < valid) ? ldg64(src + 16 * lane + k) : 0;
+      }
+      return valid;
+    }
+    if (c.fmt == MS_STATIC_BP) {
+      const int b = c.bw;
+      const uint64_t C = c.n / kBlock;
+      if (g < C) {
+        read_lane_stream(slot, lane, b, v);
+      } else {
+        const uint64_t* tail = reinterpret_cast<const uint64_t*>(c.p + 64ull * b * C);
+        const uint64_t mask = lowmask(b);
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          const int t = 16 * lane + k;
+          uint64_t x = 0;
+          if (t < valid) {
+            const uint64_t bit = (uint64_t)t * b;
+            const int s = (int)(bit & 63);
+            x = ldg64(tail + (bit >> 6)) >> s;
+            if (s + b > 64) x |= ldg64(tail + (bit >> 6) + 1) << (64 - s);
+            x &= mask;
+          }
+          v[k] = x;
+        }
+      }
+      return valid;
+    }
+    if (g < c.nb) {
+      const uint64_t w0 = sm->hdr[i % (2 * kDepth)][0], ref = sm->hdr[i % (2 * kDepth)][1];
+      int b = (int)(w0 & 255);
+      if (b > 64) {
+        if (lane == 0) set_error(ctl, MS_ERR_FORMAT, g);
+        b = 0;
+      }
+      read_lane_stream(slot, lane, b, v);
+      if (c.fmt == MS_FOR_BP) {
+#pragma unroll
+        for (int k = 0; k < 16; k++) v[k] += ref;
+      } else if (c.fmt == MS_DELTA_BP) {
+        uint64_t s = 0;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          s += v[k];
+          v[k] = s;
+        }
+        const uint64_t excl = warp_excl_scan(s, lane) + ref;
+#pragma unroll
+        for (int k = 0; k < 16; k++) v[k] += excl;
+      }
+    } else {
+      const uint64_t* rem = reinterpret_cast<const uint64_t*>(c.p + 16 * c.nb + 8 * c.pwords);
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        const int t = 16 * lane + k;
+        v[k] = t < valid ? ldg64(rem + t) : 0;
+      }
+    }
+    return valid;
+  }
+};
 
 // Random read of value i (< c.n) of a non-DELTA column (Sec. 4.2 random access).
 MS_DEV uint64_t read_at(const ColView& c, uint64_t i) {

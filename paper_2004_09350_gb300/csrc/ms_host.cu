@@ -400,8 +400,10 @@ ms_status ms_profile_collect(ms_ctx* c, ms_kernel_time* out, int max, int* n_out
 }
 
 const char* ms_kernel_name(int k) {
-  static const char* names[MS_K_COUNT] = {"mark", "emit", "compress", "decompress", "project",
-                                          "calc", "agg_sum", "group_sum", "build_keys", "validate"};
+  static const char* names[MS_K_COUNT] = {"mark",      "emit",       "compress", "decompress",
+                                          "project",   "calc",       "agg_sum",  "group_sum",
+                                          "build_keys", "validate",  "scan",     "place_scan",
+                                          "place_copy"};
   return (k >= 0 && k < MS_K_COUNT) ? names[k] : "?";
 }
 

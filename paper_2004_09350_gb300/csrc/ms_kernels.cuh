@@ -8,6 +8,8 @@
 // compressed bytes travel to and from device memory.  The payload offsets of
 // dynamically sized output blocks come from a decoupled look-back over tiles.
 #pragma once
+#include <type_traits>
+
 #include "ms_device.cuh"
 
 namespace ms {
@@ -26,10 +28,38 @@ MS_DEV bool pred(int cmp, uint64_t x, uint64_t c1, uint64_t c2) {
   }
 }
 
-// Mark kernel of select / semi-join.  Writes, per 512-row chunk of the input, a
-// 512-bit match bitmap (lane j's 16 rows -> halfword j), the exclusive output offset
-// of the chunk (coff, with coff[nchunks] = total), and for every output block h
-// the chunk holding output element 512h (bstart).  The total goes to ctl->op_n.
+// Walks the chunks first, first+stride, ... of one column with a per-warp
+// asynchronous stream and calls body(i, g, v, valid) for each decoded chunk.
+template <int D, class Body>
+MS_DEV void stream_chunks(const ColView& c, uint64_t first, uint64_t stride, StreamSmem<D>* sm, int lane,
+                          DevCtl* ctl, Body body) {
+  const uint64_t nch = (c.n + kBlock - 1) / kBlock;
+  const uint64_t count = first < nch ? (nch - first + stride - 1) / stride : 0;
+  ChunkStream<D> cs{c, first, stride, count, sm, lane};
+  if (count == 0) return;
+  cs.prologue();
+  for (int j = 0; j < D - 1; j++) {
+    cs.prologue_step(j);
+    cp_async_commit();
+  }
+  for (uint64_t i = 0; i < count; i++) {
+    cp_async_wait<D - 2>();
+    __syncwarp();
+    cs.step(i);
+    cp_async_commit();
+    uint64_t v[16];
+    const int valid = cs.decode(i, v, ctl);
+    body(cs.chunk(i), v, valid);
+    __syncwarp();
+  }
+  cp_async_wait<0>();
+}
+
+
+
+// ---------------------------------------------------- consumer kernel arguments
+
+// Select / semi-join mark kernel arguments (kernel in ms_consume.cu).
 struct MarkArgs {
   const DevMeta* in;
   DevCtl* ctl;
@@ -38,67 +68,62 @@ struct MarkArgs {
   const uint32_t* keybits;  // semi-join: membership bitmap over the key domain
   uint64_t domain;
   uint16_t* bitmap;
+  uint32_t* counts;
+};
+
+constexpr int kMarkDepth = 3;
+
+// Scan of per-chunk match counts (kernel in ms_consume.cu).
+struct ScanArgs {
+  const DevMeta* in;
+  DevCtl* ctl;
+  const uint32_t* counts;
   uint64_t* coff;
   uint64_t* bstart;
   uint64_t* status;
 };
 
-#ifndef MS_PRODUCE_ONLY  // translation units that only instantiate k_produce
-__global__ void __launch_bounds__(kThreads) k_mark(MarkArgs a) {
-  extern __shared__ __align__(16) uint8_t smem_raw[];
-  __shared__ uint64_t s_cnt[kWarps];
-  __shared__ uint64_t s_excl;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint16_t* stage = reinterpret_cast<uint16_t*>(smem_raw) + warp * 2048;
-  const ColView c = view_of(a.in);
-  const uint64_t nch = (c.n + kBlock - 1) / kBlock, ntiles = (nch + kWarps - 1) / kWarps;
-  if (c.n == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
-    a.coff[0] = 0;
-    a.ctl->op_n = 0;
+constexpr int kSmemGroups = 4096;
+constexpr int kPairDepth = 2;        // two columns per warp: shallower rings
+constexpr int kPairWarps = 4;        // 128-thread CTAs for the two-column consumers
+
+// Two-column consumer: gid and val chunks of the same index stream side by side.
+template <class Body>
+MS_DEV void stream_pairs(const ColView& c0, const ColView& c1, uint64_t n, uint64_t first, uint64_t stride,
+                         StreamSmem<kPairDepth>* s0, StreamSmem<kPairDepth>* s1, int lane, DevCtl* ctl, Body body) {
+  constexpr int D = kPairDepth;
+  const uint64_t nch = (n + kBlock - 1) / kBlock;
+  const uint64_t count = first < nch ? (nch - first + stride - 1) / stride : 0;
+  ChunkStream<D> a{c0, first, stride, count, s0, lane};
+  ChunkStream<D> b{c1, first, stride, count, s1, lane};
+  if (count == 0) return;
+  for (int i = 0; i < D; i++) {
+    a.issue_header(i);
+    b.issue_header(i);
   }
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const uint64_t g = tile * kWarps + warp;
-    uint64_t v[16];
-    const int valid = decode_chunk(c, g, lane, v, stage, a.ctl);
-    uint32_t m16 = 0;
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-      bool hit;
-      if (a.keybits) {
-        const uint64_t x = v[k];
-        hit = x < a.domain && ((__ldg(a.keybits + (x >> 5)) >> (x & 31)) & 1u);
-      } else {
-        hit = pred(a.cmp, v[k], a.c1, a.c2);
-      }
-      if (hit && 16 * lane + k < valid) m16 |= 1u << k;
-    }
-    if (g < nch) a.bitmap[g * 32 + lane] = (uint16_t)m16;
-    const uint64_t cnt = warp_sum(__popc(m16));
-    if (lane == 0) s_cnt[warp] = cnt;
-    __syncthreads();
-    if (warp == 0) {
-      const uint64_t agg = warp_sum(lane < kWarps ? s_cnt[lane] : 0);
-      const uint64_t ex = lookback(a.status, tile, agg, lane, a.ctl);
-      if (lane == 0) s_excl = ex;
-    }
-    __syncthreads();
-    if (g < nch && lane == 0) {
-      uint64_t o0 = s_excl;
-      for (int w = 0; w < warp; w++) o0 += s_cnt[w];
-      a.coff[g] = o0;
-      if (cnt) {
-        for (uint64_t h = (o0 + kBlock - 1) / kBlock; h <= (o0 + cnt - 1) / kBlock; h++) a.bstart[h] = g;
-      }
-      if (g == nch - 1) {
-        a.coff[nch] = o0 + cnt;
-        a.ctl->op_n = o0 + cnt;
-      }
-    }
-    __syncthreads();
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncwarp();
+  for (int j = 0; j < D - 1; j++) {
+    a.prologue_step(j);
+    b.prologue_step(j);
+    cp_async_commit();
   }
+  for (uint64_t i = 0; i < count; i++) {
+    cp_async_wait<D - 2>();
+    __syncwarp();
+    a.step(i);
+    b.step(i);
+    cp_async_commit();
+    uint64_t u[16], v[16];
+    const int va = a.decode(i, u, ctl);
+    const int vb = b.decode(i, v, ctl);
+    body(a.chunk(i), u, v, min(va, vb));
+    __syncwarp();
+  }
+  cp_async_wait<0>();
 }
 
-#endif  // MS_PRODUCE_ONLY
 
 // ------------------------------------------------------- produce (map) kernel
 
@@ -107,7 +132,7 @@ enum ProduceOp { OP_COMPRESS = 0, OP_DECOMPRESS = 1, OP_PROJECT = 2, OP_CALC = 3
 struct ProduceArgs {
   DevCtl* ctl;
   // inputs
-  const DevMeta* in0;      // compress: unused; decompress/calc a/project data
+  const DevMeta* in0;      // decompress / calc a / project data
   const DevMeta* in1;      // calc b (NULL: scalar) / project positions
   const uint64_t* raw_in;  // compress input
   uint64_t raw_n;          // compress input length
@@ -124,11 +149,42 @@ struct ProduceArgs {
   uint64_t raw_cap;
   int fmt, bw;
   uint64_t* status;
+  // staged block-format output (k_map): one 4 KB slot per output block and its
+  // {width, reference} pair; k_scan_widths and k_copy_blocks place them
+  uint8_t* stage;
+  uint64_t* stage_meta;
+};
+
+// Per-warp shared memory of each producing operator.  The slot of the main input
+// stream that a warp has just decoded doubles as its output stage.
+constexpr int kProdDepth = 3;   // single-input producers
+constexpr int kProdDepth2 = 2;  // two-input producers
+constexpr int kEmitSpan = 32;   // bitmap chunks an emit warp stages at once
+
+struct SmemSingle {
+  StreamSmem<kProdDepth> s0;
+};
+struct SmemPair {
+  StreamSmem<kProdDepth2> s0, s1;
+};
+struct SmemProject {
+  StreamSmem<kProdDepth2> s0, s1;
+  uint64_t aux[kBlock];
+};
+struct SmemEmit {
+  uint32_t bits[kEmitSpan * 16];
+  uint64_t coff[kEmitSpan + 2];
+  uint64_t aux[kBlock];
+  uint16_t out[2048];
 };
 
 template <int OP>
-struct SmemPlan {
-  static constexpr int kPerWarp = (OP == OP_PROJECT || OP == OP_EMIT) ? 12288 : 8192;
+struct ProducePlan {
+  using Smem = typename std::conditional<
+      OP == OP_CALC, SmemPair,
+      typename std::conditional<OP == OP_PROJECT, SmemProject,
+                                typename std::conditional<OP == OP_EMIT, SmemEmit, SmemSingle>::type>::type>::type;
+  static constexpr int kMinBlocks = (OP == OP_PROJECT || OP == OP_CALC) ? 1 : 2;
 };
 
 // Output length of the operator (device-side, may depend on previous kernels).
@@ -145,56 +201,81 @@ MS_DEV uint64_t arith(int op, uint64_t x, uint64_t y) {
   return op == MS_ADD ? x + y : op == MS_SUB ? x - y : x * y;
 }
 
-// Produces output chunk g into v; returns its valid count.
-template <int OP>
-MS_DEV int produce_chunk(const ProduceArgs& a, const ColView& c0, const ColView& c1, uint64_t n_out,
-                         uint64_t g, int lane, uint64_t v[16], uint16_t* in_stage, uint64_t* aux) {
-  if (g * kBlock >= n_out) {
-#pragma unroll
-    for (int k = 0; k < 16; k++) v[k] = 0;
-    return 0;
+// Runs a nested chunk stream over data blocks lo..lo+count-1 and calls
+// body(block, v) for each decoded block (all values valid for full blocks).
+template <int D, class Body>
+MS_DEV void stream_blocks(const ColView& c, uint64_t lo, uint64_t count, StreamSmem<D>* sm, int lane, DevCtl* ctl,
+                          Body body) {
+  ChunkStream<D> cs{c, lo, 1, count, sm, lane};
+  if (count == 0) return;
+  cs.prologue();
+  for (int j = 0; j < D - 1; j++) {
+    cs.prologue_step(j);
+    cp_async_commit();
   }
-  if (OP == OP_COMPRESS || OP == OP_DECOMPRESS) {
-    const int valid = decode_chunk(c0, g, lane, v, in_stage, a.ctl);
-    return (int)min((uint64_t)valid, n_out - g * kBlock);
+  for (uint64_t i = 0; i < count; i++) {
+    cp_async_wait<D - 2>();
+    __syncwarp();
+    cs.step(i);
+    cp_async_commit();
+    uint64_t t[16];
+    cs.decode(i, t, ctl);
+    body(cs.chunk(i), t);
+    __syncwarp();
   }
-  if (OP == OP_CALC) {
-    int valid = decode_chunk(c0, g, lane, v, in_stage, a.ctl);
-    if (a.in1) {
-      uint64_t w[16];
-      const int v2 = decode_chunk(c1, g, lane, w, in_stage, a.ctl);
-      valid = min(valid, v2);
+  cp_async_wait<0>();
+  __syncwarp();
+}
+
+// project core for one output chunk: positions p (lane-blocked), values into v.
+template <class Smem>
+MS_DEV void project_gather(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
+                           uint64_t v[16], Smem* sm) {
+  uint32_t pending = 0;
+  uint64_t lo = ~0ull, hi = 0;
+  bool sorted = true;
 #pragma unroll
-      for (int k = 0; k < 16; k++) v[k] = arith(a.arith, v[k], w[k]);
-    } else {
-#pragma unroll
-      for (int k = 0; k < 16; k++) v[k] = arith(a.arith, v[k], a.scalar);
-    }
-    return valid;
-  }
-  if (OP == OP_PROJECT) {
-    // c0 = data column, c1 = positions column
-    uint64_t p[16];
-    const int valid = decode_chunk(c1, g, lane, p, in_stage, a.ctl);
-    uint32_t pending = 0;
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-      v[k] = 0;
-      if (16 * lane + k < valid) {
-        if (p[k] < c0.n) {
-          pending |= 1u << k;
-        } else {
-          set_error(a.ctl, MS_ERR_OUT_OF_RANGE, p[k]);
-        }
+  for (int k = 0; k < 16; k++) {
+    v[k] = 0;
+    if (16 * lane + k < valid) {
+      if (p[k] < d.n) {
+        pending |= 1u << k;
+        lo = min(lo, p[k]);
+        hi = max(hi, p[k]);
+        if (k > 0 && p[k] < p[k - 1]) sorted = false;
+      } else {
+        set_error(a.ctl, MS_ERR_OUT_OF_RANGE, p[k]);
       }
     }
-    if (c0.fmt != MS_DELTA_BP) {
+  }
+  // sortedness across lanes: each lane's first value >= the previous lane's last
+  const uint64_t prev_last = __shfl_up_sync(kFull, (16 * lane + 15 < valid) ? p[15] : hi, 1);
+  if (lane > 0 && 16 * lane < valid && p[0] < prev_last) sorted = false;
+  const uint64_t blo = warp_min(lo == ~0ull ? ~0ull : lo / kBlock);
+  uint64_t bhi = hi / kBlock;
 #pragma unroll
-      for (int k = 0; k < 16; k++)
-        if (pending & (1u << k)) v[k] = read_at(c0, p[k]);
-      return valid;
+  for (int d2 = 16; d2; d2 >>= 1) bhi = max(bhi, __shfl_xor_sync(kFull, bhi, d2));
+  const bool all_sorted = __all_sync(kFull, sorted);
+  if (blo == ~0ull) return;  // no valid position
+  const uint64_t span = bhi - blo + 1;
+  if ((all_sorted && span <= 64) || d.fmt == MS_DELTA_BP) {
+    if (all_sorted && span <= 64) {
+      // dense: stream the spanned data blocks once and gather from shared memory
+      stream_blocks<kProdDepth2>(d, blo, span, &sm->s1, lane, a.ctl, [&](uint64_t B, const uint64_t* t) {
+#pragma unroll
+        for (int k = 0; k < 16; k++) sm->aux[swz(16 * lane + k)] = t[k];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          if ((pending & (1u << k)) && p[k] / kBlock == B) {
+            v[k] = sm->aux[swz((int)(p[k] % kBlock))];
+            pending &= ~(1u << k);
+          }
+        }
+      });
+      return;
     }
-    // DELTA data: decode each distinct block touched by the warp once (in order)
+    // DELTA data, unsorted or sparse positions: decode each distinct block once
     while (true) {
       uint64_t mb = ~0ull;
 #pragma unroll
@@ -202,62 +283,82 @@ MS_DEV int produce_chunk(const ProduceArgs& a, const ColView& c0, const ColView&
         if (pending & (1u << k)) mb = min(mb, p[k] / kBlock);
       const uint64_t B = warp_min(mb);
       if (B == ~0ull) break;
-      uint64_t t[16];
-      decode_chunk(c0, B, lane, t, in_stage, a.ctl);
+      stream_blocks<kProdDepth2>(d, B, 1, &sm->s1, lane, a.ctl, [&](uint64_t, const uint64_t* t) {
 #pragma unroll
-      for (int k = 0; k < 16; k++) aux[swz(16 * lane + k)] = t[k];
-      __syncwarp();
+        for (int k = 0; k < 16; k++) sm->aux[swz(16 * lane + k)] = t[k];
+        __syncwarp();
 #pragma unroll
-      for (int k = 0; k < 16; k++) {
-        if ((pending & (1u << k)) && p[k] / kBlock == B) {
-          v[k] = aux[swz((int)(p[k] % kBlock))];
-          pending &= ~(1u << k);
+        for (int k = 0; k < 16; k++) {
+          if ((pending & (1u << k)) && p[k] / kBlock == B) {
+            v[k] = sm->aux[swz((int)(p[k] % kBlock))];
+            pending &= ~(1u << k);
+          }
         }
-      }
-      __syncwarp();
+      });
     }
-    return valid;
+    return;
   }
-  // OP_EMIT: positions of output block g from the match bitmap
+  // sparse: random reads through the header directory
+#pragma unroll
+  for (int k = 0; k < 16; k++)
+    if (pending & (1u << k)) v[k] = read_at(d, p[k]);
+}
+
+// emit core: positions of output block g (lane-blocked) from the match bitmap.
+MS_DEV int emit_gather(const ProduceArgs& a, uint64_t n_out, uint64_t g, int lane, uint64_t v[16], SmemEmit* sm) {
   const uint64_t lo = g * kBlock;
   const int valid = (int)min((uint64_t)kBlock, n_out - lo);
   const uint64_t hi = lo + valid;
   // chunk range holding the block's outputs (clamped: scratch is never trusted blindly)
   const uint64_t cfirst = min(a.bstart[g], a.emit_nch - 1);
   const uint64_t clast = max(cfirst, min((hi < n_out) ? a.bstart[g + 1] : a.emit_nch - 1, a.emit_nch - 1));
-  if (clast - cfirst < 32) {
-    for (uint64_t ch = cfirst; ch <= clast; ch++) {
-      uint32_t hw = a.bitmap[ch * 32 + lane];
-      uint64_t o = a.coff[ch] + warp_excl_scan32(__popc(hw), lane);
-      while (hw) {
-        const int bb = __ffs(hw) - 1;
-        hw &= hw - 1;
-        if (o >= lo && o < hi) aux[swz((int)(o - lo))] = ch * kBlock + 16 * lane + bb;
-        o++;
-      }
-    }
-  } else {
-    for (uint64_t ch = cfirst + lane; ch <= clast; ch += 32) {
-      uint64_t o = a.coff[ch];
-      const uint64_t e = a.coff[ch + 1];
-      if (e <= o || e <= lo || o >= hi) continue;
-      const uint32_t* w32 = reinterpret_cast<const uint32_t*>(a.bitmap + ch * 32);
-      for (int w = 0; w < 16 && o < hi; w++) {
-        uint32_t bits = w32[w];
-        while (bits) {
-          const int bb = __ffs(bits) - 1;
-          bits &= bits - 1;
-          if (o >= lo && o < hi) aux[swz((int)(o - lo))] = ch * kBlock + 32 * w + bb;
+  // dense blocks (<= 64 chunks): a warp expands one chunk at a time; sparse: a lane per chunk
+  const bool dense = clast - cfirst < 64;
+  for (uint64_t c0 = cfirst; c0 <= clast; c0 += kEmitSpan) {
+    const int nc = (int)min((uint64_t)kEmitSpan, clast - c0 + 1);
+    // stage the bitmap words and offsets of up to kEmitSpan chunks at once
+    for (int u = lane; u < nc * 4; u += 32)
+      cp_async16(sm->bits + 4 * u, reinterpret_cast<const uint4*>(a.bitmap + c0 * 32) + u);
+    if (lane <= nc) sm->coff[lane] = a.coff[c0 + lane];
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+    if (dense) {  // each lane expands its 16 rows of the chunk
+      for (int ci = 0; ci < nc; ci++) {
+        uint32_t hw = (sm->bits[ci * 16 + (lane >> 1)] >> (16 * (lane & 1))) & 0xffffu;
+        uint64_t o = sm->coff[ci] + warp_excl_scan32(__popc(hw), lane);
+        const uint64_t ch = c0 + ci;
+        while (hw) {
+          const int bb = __ffs(hw) - 1;
+          hw &= hw - 1;
+          if (o >= lo && o < hi) sm->aux[swz((int)(o - lo))] = ch * kBlock + 16 * lane + bb;
           o++;
         }
       }
+    } else {
+      if (lane < nc) {
+        uint64_t o = sm->coff[lane];
+        const uint64_t e = sm->coff[lane + 1];
+        const uint64_t ch = c0 + lane;
+        if (e > o && e > lo && o < hi) {
+          for (int w = 0; w < 16 && o < hi; w++) {
+            uint32_t bits = sm->bits[lane * 16 + w];
+            while (bits) {
+              const int bb = __ffs(bits) - 1;
+              bits &= bits - 1;
+              if (o >= lo && o < hi) sm->aux[swz((int)(o - lo))] = ch * kBlock + 32 * w + bb;
+              o++;
+            }
+          }
+        }
+      }
     }
+    __syncwarp();
   }
-  __syncwarp();
 #pragma unroll
   for (int k = 0; k < 16; k++) {
     const int t = 16 * lane + k;
-    v[k] = t < valid ? aux[swz(t)] : 0;
+    v[k] = t < valid ? sm->aux[swz(t)] : 0;
   }
   __syncwarp();
   return valid;
@@ -290,15 +391,13 @@ MS_DEV int encode_block(int fmt, uint64_t v[16], int lane, uint64_t* ref_out) {
 }
 
 template <int OP>
-__global__ void __launch_bounds__(kThreads) k_produce(ProduceArgs a) {
+__global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_produce(ProduceArgs a) {
+  using Smem = typename ProducePlan<OP>::Smem;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ uint64_t s_words[kWarps];
   __shared__ uint64_t s_excl;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint8_t* ws = smem_raw + warp * SmemPlan<OP>::kPerWarp;
-  uint16_t* in_stage = reinterpret_cast<uint16_t*>(ws);
-  uint16_t* out_stage = reinterpret_cast<uint16_t*>(ws + 4096);
-  uint64_t* aux = reinterpret_cast<uint64_t*>(ws + 8192);
+  Smem* sm = reinterpret_cast<Smem*>(smem_raw) + warp;
 
   DevCtl* ctl = a.ctl;
   const bool raw = a.out_meta == nullptr;
@@ -320,12 +419,80 @@ __global__ void __launch_bounds__(kThreads) k_produce(ProduceArgs a) {
   const uint64_t nch = (n_out + kBlock - 1) / kBlock, ntiles = (nch + kWarps - 1) / kWarps;
   const uint64_t nb_out = blockfmt ? n_out / kBlock : 0;
   const uint64_t static_chunks = n_out / kBlock;
+  const uint64_t G = gridDim.x;
+  const uint64_t my_tiles = blockIdx.x < ntiles ? (ntiles - blockIdx.x + G - 1) / G : 0;
+  const uint64_t first = (uint64_t)blockIdx.x * kWarps + warp, stride = kWarps * G;
 
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  // input streams: chunk i of a warp is first + i*stride, for every tile of the CTA
+  constexpr int D = (OP == OP_CALC || OP == OP_PROJECT) ? kProdDepth2 : kProdDepth;
+  StreamSmem<D>* ring0 = nullptr;
+  StreamSmem<D>* ring1 = nullptr;
+  if constexpr (OP == OP_COMPRESS || OP == OP_DECOMPRESS) ring0 = &sm->s0;
+  if constexpr (OP == OP_CALC) {
+    ring0 = &sm->s0;
+    ring1 = &sm->s1;
+  }
+  if constexpr (OP == OP_PROJECT) ring0 = &sm->s0;
+  const ColView main_col = (OP == OP_PROJECT) ? c1 : c0;
+  ChunkStream<D> st0{main_col, first, stride, (OP == OP_EMIT) ? 0 : my_tiles, ring0, lane};
+  ChunkStream<D> st1{c1, first, stride, (OP == OP_CALC && a.in1) ? my_tiles : 0, ring1, lane};
+  if (OP != OP_EMIT && my_tiles) {
+    for (int i = 0; i < D; i++) {
+      st0.issue_header(i);
+      st1.issue_header(i);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+    for (int j = 0; j < D - 1; j++) {
+      st0.prologue_step(j);
+      st1.prologue_step(j);
+      cp_async_commit();
+    }
+  }
+
+  for (uint64_t i = 0; i < my_tiles; i++) {
+    const uint64_t tile = blockIdx.x + i * G;
     const uint64_t g = tile * kWarps + warp;
     uint64_t v[16];
-    const int valid = produce_chunk<OP>(a, c0, c1, n_out, g, lane, v, in_stage, aux);
-    // ---- encode into the warp's shared stage
+    int valid = 0;
+    uint16_t* out_stage;
+    if constexpr (OP == OP_EMIT) {
+      out_stage = sm->out;
+      if (g < nch) valid = emit_gather(a, n_out, g, lane, v, sm);
+      else {
+#pragma unroll
+        for (int k = 0; k < 16; k++) v[k] = 0;
+      }
+    } else {
+      cp_async_wait<D - 2>();
+      __syncwarp();
+      st0.step(i);
+      st1.step(i);
+      cp_async_commit();
+      out_stage = ring0->slot[i % D];
+      if constexpr (OP == OP_COMPRESS || OP == OP_DECOMPRESS) {
+        valid = st0.decode(i, v, ctl);
+        valid = (int)min((uint64_t)valid, g * kBlock < n_out ? n_out - g * kBlock : 0);
+      } else if constexpr (OP == OP_CALC) {
+        valid = st0.decode(i, v, ctl);
+        if (a.in1) {
+          uint64_t w[16];
+          valid = min(valid, st1.decode(i, w, ctl));
+#pragma unroll
+          for (int k = 0; k < 16; k++) v[k] = arith(a.arith, v[k], w[k]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; k++) v[k] = arith(a.arith, v[k], a.scalar);
+        }
+      } else {  // OP_PROJECT: c0 = data, st0 streams the positions (c1)
+        uint64_t p[16];
+        valid = st0.decode(i, p, ctl);
+        project_gather(a, c0, p, valid, lane, v, sm);
+      }
+      __syncwarp();
+    }
+    // ---- encode into the warp's output stage
     int b = 0;
     uint64_t ref = 0, words = 0;
     if (blockfmt) {
@@ -347,7 +514,7 @@ __global__ void __launch_bounds__(kThreads) k_produce(ProduceArgs a) {
         write_lane_stream(out_stage, lane, bw, v);
       } else {  // horizontal tail
         uint32_t* w32 = reinterpret_cast<uint32_t*>(out_stage);
-        for (int i = lane; i < 1024; i += 32) w32[i] = 0;
+        for (int t = lane; t < 1024; t += 32) w32[t] = 0;
         __syncwarp();
 #pragma unroll
         for (int k = 0; k < 16; k++) {
@@ -398,7 +565,7 @@ __global__ void __launch_bounds__(kThreads) k_produce(ProduceArgs a) {
             }
             uint4* dst = reinterpret_cast<uint4*>(base + pay);
             const uint4* src = reinterpret_cast<const uint4*>(out_stage);
-            for (int i = lane; i < 4 * b; i += 32) dst[i] = src[i];
+            for (int t = lane; t < 4 * b; t += 32) dst[t] = src[t];
           } else if (lane == 0) {
             set_error(ctl, MS_ERR_NOMEM, g);
           }
@@ -419,7 +586,7 @@ __global__ void __launch_bounds__(kThreads) k_produce(ProduceArgs a) {
           if (pay + 64ull * bw <= avail) {
             uint4* dst = reinterpret_cast<uint4*>(base + pay);
             const uint4* src = reinterpret_cast<const uint4*>(out_stage);
-            for (int i = lane; i < 4 * bw; i += 32) dst[i] = src[i];
+            for (int t = lane; t < 4 * bw; t += 32) dst[t] = src[t];
           } else if (lane == 0) {
             set_error(ctl, MS_ERR_NOMEM, g);
           }
@@ -429,7 +596,7 @@ __global__ void __launch_bounds__(kThreads) k_produce(ProduceArgs a) {
           if (pay + 8ull * nw <= avail) {
             uint64_t* dst = reinterpret_cast<uint64_t*>(base + pay);
             const uint64_t* src = reinterpret_cast<const uint64_t*>(out_stage);
-            for (int i = lane; i < nw; i += 32) dst[i] = src[i];
+            for (int t = lane; t < nw; t += 32) dst[t] = src[t];
           } else if (lane == 0) {
             set_error(ctl, MS_ERR_NOMEM, g);
           }
@@ -439,17 +606,17 @@ __global__ void __launch_bounds__(kThreads) k_produce(ProduceArgs a) {
         if (pay + 8ull * valid <= avail) {
           uint64_t* dst = reinterpret_cast<uint64_t*>(base + pay);
           if (valid == kBlock) {
-            uint4* st = reinterpret_cast<uint4*>(out_stage);
+            uint4* stg = reinterpret_cast<uint4*>(out_stage);
 #pragma unroll
             for (int cc = 0; cc < 8; cc++)
-              st[lane * 8 + (cc ^ (lane & 7))] =
+              stg[lane * 8 + (cc ^ (lane & 7))] =
                   make_uint4((uint32_t)v[2 * cc], (uint32_t)(v[2 * cc] >> 32), (uint32_t)v[2 * cc + 1],
                              (uint32_t)(v[2 * cc + 1] >> 32));
             __syncwarp();
 #pragma unroll
             for (int it = 0; it < 8; it++) {
               const int ci = lane + 32 * it, L = ci >> 3, cc = ci & 7;
-              reinterpret_cast<uint4*>(dst)[ci] = st[L * 8 + (cc ^ (L & 7))];
+              reinterpret_cast<uint4*>(dst)[ci] = stg[L * 8 + (cc ^ (L & 7))];
             }
           } else {
 #pragma unroll
@@ -464,6 +631,7 @@ __global__ void __launch_bounds__(kThreads) k_produce(ProduceArgs a) {
     __syncwarp();
     if (blockfmt) __syncthreads();
   }
+  cp_async_wait<0>();
 
   // ---- epilogue: the last CTA to finish describes the output column and moves
   // the arena's top past it.
@@ -504,93 +672,366 @@ __global__ void __launch_bounds__(kThreads) k_produce(ProduceArgs a) {
   }
 }
 
-#ifndef MS_PRODUCE_ONLY
-// ----------------------------------------------------------------- aggregates
-
-__global__ void __launch_bounds__(kThreads) k_agg_sum(const DevMeta* in, uint64_t* result, DevCtl* ctl) {
+// Warp-independent producing kernel.  Every warp streams its own chunks (chunk
+// gw, gw + W, ... for warp gw of W), runs the operator and encodes each output
+// block.  Uncompressed and static-BP outputs have fixed offsets and are stored in
+// place.  A block-format output block goes to its own 4 KB staging slot, and its
+// {width, reference} to stage_meta.  k_scan_widths and k_copy_blocks then compute
+// the payload offsets and move the compressed bytes into place.  No block
+// barrier and no look-back, so no warp waits for another.
+template <int OP>
+__global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(ProduceArgs a) {
+  using Smem = typename ProducePlan<OP>::Smem;
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  __shared__ uint64_t s_part[kWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint16_t* stage = reinterpret_cast<uint16_t*>(smem_raw) + warp * 2048;
-  const ColView c = view_of(in);
-  const uint64_t nch = (c.n + kBlock - 1) / kBlock, ntiles = (nch + kWarps - 1) / kWarps;
-  uint64_t acc = 0;
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  Smem* sm = reinterpret_cast<Smem*>(smem_raw) + warp;
+
+  DevCtl* ctl = a.ctl;
+  const bool raw = a.out_meta == nullptr;
+  const uint64_t top = raw ? 0 : *reinterpret_cast<volatile uint64_t*>(&ctl->top);
+  const uint64_t avail = raw ? 8 * a.raw_cap : ctl->cap - top;
+  uint8_t* base = raw ? reinterpret_cast<uint8_t*>(a.raw_out) : reinterpret_cast<uint8_t*>(ctl->arena + top);
+
+  ColView c0{}, c1{};
+  if (OP == OP_COMPRESS) c0 = view_raw(a.raw_in, a.raw_n);
+  if (OP == OP_DECOMPRESS || OP == OP_CALC || OP == OP_PROJECT) c0 = view_of(a.in0);
+  if ((OP == OP_CALC || OP == OP_PROJECT) && a.in1) c1 = view_of(a.in1);
+  const uint64_t n_out = produce_n<OP>(a);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (OP == OP_DECOMPRESS && a.in0->n > a.raw_cap) set_error(ctl, MS_ERR_INVALID_ARG, a.in0->n);
+    if (OP == OP_CALC && a.in1 && a.in0->n != a.in1->n) set_error(ctl, MS_ERR_INVALID_ARG, a.in1->n);
+  }
+  const int fmt = a.fmt, bw = a.bw;
+  const bool blockfmt = is_block_fmt(fmt);
+  const uint64_t nch = (n_out + kBlock - 1) / kBlock;
+  const uint64_t static_chunks = n_out / kBlock;
+  const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
+  const uint64_t count = gw < nch ? (nch - gw + W - 1) / W : 0;
+
+  constexpr int D = (OP == OP_CALC || OP == OP_PROJECT) ? kProdDepth2 : kProdDepth;
+  StreamSmem<D>* ring0 = nullptr;
+  StreamSmem<D>* ring1 = nullptr;
+  if constexpr (OP == OP_COMPRESS || OP == OP_DECOMPRESS || OP == OP_PROJECT) ring0 = &sm->s0;
+  if constexpr (OP == OP_CALC) {
+    ring0 = &sm->s0;
+    ring1 = &sm->s1;
+  }
+  const ColView main_col = (OP == OP_PROJECT) ? c1 : c0;
+  ChunkStream<D> st0{main_col, gw, W, (OP == OP_EMIT) ? 0 : count, ring0, lane};
+  ChunkStream<D> st1{c1, gw, W, (OP == OP_CALC && a.in1) ? count : 0, ring1, lane};
+  if (OP != OP_EMIT && count) {
+    for (int i = 0; i < D; i++) {
+      st0.issue_header(i);
+      st1.issue_header(i);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+    for (int j = 0; j < D - 1; j++) {
+      st0.prologue_step(j);
+      st1.prologue_step(j);
+      cp_async_commit();
+    }
+  }
+
+  for (uint64_t i = 0; i < count; i++) {
+    const uint64_t g = gw + i * W;
     uint64_t v[16];
-    const int valid = decode_chunk(c, tile * kWarps + warp, lane, v, stage, ctl);
+    int valid = 0;
+    uint16_t* out_stage;
+    if constexpr (OP == OP_EMIT) {
+      out_stage = sm->out;
+      valid = emit_gather(a, n_out, g, lane, v, sm);
+    } else {
+      cp_async_wait<D - 2>();
+      __syncwarp();
+      st0.step(i);
+      st1.step(i);
+      cp_async_commit();
+      out_stage = ring0->slot[i % D];
+      if constexpr (OP == OP_COMPRESS || OP == OP_DECOMPRESS) {
+        valid = st0.decode(i, v, ctl);
+        valid = (int)min((uint64_t)valid, n_out - g * kBlock);
+      } else if constexpr (OP == OP_CALC) {
+        valid = st0.decode(i, v, ctl);
+        if (a.in1) {
+          uint64_t w[16];
+          valid = min(valid, st1.decode(i, w, ctl));
 #pragma unroll
-    for (int k = 0; k < 16; k++) acc += (16 * lane + k < valid) ? v[k] : 0;
-  }
-  acc = warp_sum(acc);
-  if (lane == 0) s_part[warp] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint64_t t = 0;
-    for (int w = 0; w < kWarps; w++) t += s_part[w];
-    if (t) atomicAdd(reinterpret_cast<unsigned long long*>(result), (unsigned long long)t);
-  }
-}
-
-constexpr int kSmemGroups = 4096;
-
-__global__ void __launch_bounds__(kThreads) k_group_sum(const DevMeta* gid, const DevMeta* val, uint64_t G,
-                                                         uint64_t* sums, DevCtl* ctl) {
-  extern __shared__ __align__(16) uint8_t smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint16_t* stage = reinterpret_cast<uint16_t*>(smem_raw) + warp * 2048;
-  unsigned long long* hist = reinterpret_cast<unsigned long long*>(smem_raw + kWarps * 4096);
-  const bool local = G <= kSmemGroups;
-  if (local)
-    for (uint64_t k = threadIdx.x; k < G; k += blockDim.x) hist[k] = 0;
-  __syncthreads();
-  const ColView cg = view_of(gid), cv = view_of(val);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && cg.n != cv.n) set_error(ctl, MS_ERR_INVALID_ARG, cv.n);
-  const uint64_t n = min(cg.n, cv.n);
-  const uint64_t nch = (n + kBlock - 1) / kBlock, ntiles = (nch + kWarps - 1) / kWarps;
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const uint64_t g = tile * kWarps + warp;
-    uint64_t k8[16], v[16];
-    int valid = decode_chunk(cg, g, lane, k8, stage, ctl);
-    valid = min(valid, decode_chunk(cv, g, lane, v, stage, ctl));
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-      if (16 * lane + k < valid) {
-        if (k8[k] < G) {
-          if (local) atomicAdd(hist + k8[k], (unsigned long long)v[k]);
-          else atomicAdd(reinterpret_cast<unsigned long long*>(sums) + k8[k], (unsigned long long)v[k]);
+          for (int k = 0; k < 16; k++) v[k] = arith(a.arith, v[k], w[k]);
         } else {
-          set_error(ctl, MS_ERR_OUT_OF_RANGE, k8[k]);
+#pragma unroll
+          for (int k = 0; k < 16; k++) v[k] = arith(a.arith, v[k], a.scalar);
+        }
+      } else {  // OP_PROJECT: c0 = data, st0 streams the positions (c1)
+        uint64_t p[16];
+        valid = st0.decode(i, p, ctl);
+        project_gather(a, c0, p, valid, lane, v, sm);
+      }
+      __syncwarp();
+    }
+    if (blockfmt) {
+      uint4* slot = reinterpret_cast<uint4*>(a.stage + 4096 * g);
+      if (valid == kBlock) {
+        uint64_t ref;
+        const int b = encode_block(fmt, v, lane, &ref);
+        write_lane_stream(out_stage, lane, b, v);
+        __syncwarp();
+        const uint4* src = reinterpret_cast<const uint4*>(out_stage);
+        for (int t = lane; t < 4 * b; t += 32) slot[t] = src[t];
+        if (lane == 0) {
+          a.stage_meta[2 * g] = (uint64_t)b;
+          a.stage_meta[2 * g + 1] = ref;
+        }
+      } else if (valid > 0) {  // remainder: raw values, placed behind the payload later
+        uint64_t* dst = reinterpret_cast<uint64_t*>(slot);
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+          if (16 * lane + k < valid) dst[16 * lane + k] = v[k];
+      }
+    } else if (fmt == MS_STATIC_BP) {
+      uint64_t o = 0;
+#pragma unroll
+      for (int k = 0; k < 16; k++) o |= (16 * lane + k < valid) ? v[k] : 0;
+      o = warp_or(o);
+      if (bw64(o) > bw && lane == 0) set_error(ctl, MS_ERR_VALUE_TOO_WIDE, g);
+      const uint64_t mask = lowmask(bw);
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] &= mask;
+      if (g < static_chunks) {
+        write_lane_stream(out_stage, lane, bw, v);
+        __syncwarp();
+        const uint64_t pay = 64ull * bw * g;
+        if (pay + 64ull * bw <= avail) {
+          uint4* dst = reinterpret_cast<uint4*>(base + pay);
+          const uint4* src = reinterpret_cast<const uint4*>(out_stage);
+          for (int t = lane; t < 4 * bw; t += 32) dst[t] = src[t];
+        } else if (lane == 0) {
+          set_error(ctl, MS_ERR_NOMEM, g);
+        }
+      } else {  // horizontal tail
+        uint32_t* w32 = reinterpret_cast<uint32_t*>(out_stage);
+        for (int t = lane; t < 1024; t += 32) w32[t] = 0;
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          const int t = 16 * lane + k;
+          if (t < valid && v[k]) {
+            const uint64_t bit = (uint64_t)t * bw;
+            const int sh = (int)(bit & 31);
+            const uint64_t x = v[k];
+            int wi = (int)(bit >> 5);
+            atomicOr(w32 + wi, (uint32_t)(x << sh));
+            uint64_t rest = (sh == 0) ? (x >> 32) : (x >> (32 - sh));
+            int have = 32 - sh;
+            while (have < bw && rest) {
+              atomicOr(w32 + (++wi), (uint32_t)rest);
+              rest >>= 32;
+              have += 32;
+            }
+          }
+        }
+        __syncwarp();
+        const uint64_t pay = 64ull * bw * static_chunks;
+        const int nw = (int)(((uint64_t)valid * bw + 63) / 64);
+        if (pay + 8ull * nw <= avail) {
+          uint64_t* dst = reinterpret_cast<uint64_t*>(base + pay);
+          const uint64_t* src = reinterpret_cast<const uint64_t*>(out_stage);
+          for (int t = lane; t < nw; t += 32) dst[t] = src[t];
+        } else if (lane == 0) {
+          set_error(ctl, MS_ERR_NOMEM, g);
         }
       }
-    }
-  }
-  if (!local) return;
-  __syncthreads();
-  for (uint64_t k = threadIdx.x; k < G; k += blockDim.x)
-    if (hist[k]) atomicAdd(reinterpret_cast<unsigned long long*>(sums) + k, hist[k]);
-}
-
-// Semi-join build side: set bit key for every key of the build column.
-__global__ void __launch_bounds__(kThreads) k_build_keys(const DevMeta* keys, uint64_t domain, uint32_t* bits,
-                                                          DevCtl* ctl) {
-  extern __shared__ __align__(16) uint8_t smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint16_t* stage = reinterpret_cast<uint16_t*>(smem_raw) + warp * 2048;
-  const ColView c = view_of(keys);
-  const uint64_t nch = (c.n + kBlock - 1) / kBlock, ntiles = (nch + kWarps - 1) / kWarps;
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    uint64_t v[16];
-    const int valid = decode_chunk(c, tile * kWarps + warp, lane, v, stage, ctl);
+    } else if (valid > 0) {  // uncompressed output (arena column or caller buffer)
+      const uint64_t pay = 8ull * kBlock * g;
+      if (pay + 8ull * valid <= avail) {
+        uint64_t* dst = reinterpret_cast<uint64_t*>(base + pay);
+        if (valid == kBlock) {
+          uint4* stg = reinterpret_cast<uint4*>(out_stage);
 #pragma unroll
-    for (int k = 0; k < 16; k++) {
-      if (16 * lane + k < valid) {
-        if (v[k] < domain) atomicOr(bits + (v[k] >> 5), 1u << (v[k] & 31));
-        else set_error(ctl, MS_ERR_OUT_OF_RANGE, v[k]);
+          for (int cc = 0; cc < 8; cc++)
+            stg[lane * 8 + (cc ^ (lane & 7))] = make_uint4((uint32_t)v[2 * cc], (uint32_t)(v[2 * cc] >> 32),
+                                                          (uint32_t)v[2 * cc + 1], (uint32_t)(v[2 * cc + 1] >> 32));
+          __syncwarp();
+#pragma unroll
+          for (int it = 0; it < 8; it++) {
+            const int ci = lane + 32 * it, L = ci >> 3, cc = ci & 7;
+            reinterpret_cast<uint4*>(dst)[ci] = stg[L * 8 + (cc ^ (L & 7))];
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; k++)
+            if (16 * lane + k < valid) dst[16 * lane + k] = v[k];
+        }
+      } else if (lane == 0) {
+        set_error(ctl, MS_ERR_NOMEM, g);
       }
     }
+    __syncwarp();
+  }
+  cp_async_wait<0>();
+
+  // ---- epilogue: the last CTA to finish records the output length; fixed-offset
+  // formats are complete here, block formats are completed by k_copy_blocks.
+  if (raw) return;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&ctl->done, 1u);
+    if (prev == gridDim.x - 1) {
+      __threadfence();
+      DevMeta* m = a.out_meta;
+      m->n = n_out;
+      m->ptr = reinterpret_cast<uint64_t>(base);
+      m->fmt = (uint32_t)fmt;
+      m->bw = (uint32_t)(fmt == MS_STATIC_BP ? bw : 0);
+      m->nb = blockfmt ? n_out / kBlock : 0;
+      if (!blockfmt) {
+        const uint64_t size = fmt == MS_UNCOMPR ? 8 * n_out : 8 * ((n_out * (uint64_t)bw + 63) / 64);
+        m->size = size;
+        m->pwords = 0;
+        const uint64_t grow = (size + 255) / 256 * 256;
+        if (size > avail) {
+          set_error(ctl, MS_ERR_NOMEM, size);
+        } else {
+          ctl->top = top + grow;
+          if (top + grow > ctl->high) ctl->high = top + grow;
+        }
+      }
+      ctl->done = 0;
+      __threadfence();
+    }
   }
 }
 
-#endif  // MS_PRODUCE_ONLY
+// Placement of a staged block-format column, step 1: the exclusive scan of the
+// blocks' payload words (8 * width) over tiles of 4096 blocks with a decoupled
+// look-back.  It writes the final header entries {(offset << 8) | width, ref} at the
+// arena top and the total payload words into ctl->op_words.
+struct PlaceArgs {
+  DevCtl* ctl;
+  DevMeta* out_meta;
+  const uint8_t* stage;
+  const uint64_t* stage_meta;
+  uint64_t* offsets;  // per-block payload word offset
+  uint64_t* status;
+};
+
+template <int kUnused = 0>
+__global__ void __launch_bounds__(kThreads) k_scan_widths(PlaceArgs a) {
+  __shared__ uint64_t s_warp[kWarps];
+  __shared__ uint64_t s_excl;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  DevCtl* ctl = a.ctl;
+  const uint64_t nb = a.out_meta->n / kBlock;
+  const uint64_t top = *reinterpret_cast<volatile uint64_t*>(&ctl->top);
+  const uint64_t avail = ctl->cap - top;
+  uint64_t* hdr = reinterpret_cast<uint64_t*>(ctl->arena + top);
+  constexpr int kPer = 16;
+  const uint64_t per_tile = (uint64_t)kThreads * kPer;
+  const uint64_t ntiles = (nb + per_tile - 1) / per_tile;
+  if (nb == 0 && blockIdx.x == 0 && threadIdx.x == 0) ctl->op_words = 0;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t g0 = tile * per_tile + (uint64_t)threadIdx.x * kPer;
+    uint32_t wds[kPer];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+      const uint64_t b = (g0 + k < nb) ? min((uint64_t)64, a.stage_meta[2 * (g0 + k)]) : 0;
+      wds[k] = (uint32_t)(8 * b);
+      sum += wds[k];
+    }
+    const uint32_t texcl = warp_excl_scan32(sum, lane);
+    if (lane == 31) s_warp[warp] = texcl + sum;
+    __syncthreads();
+    if (warp == 0) {
+      const uint64_t wt = lane < kWarps ? s_warp[lane] : 0;
+      const uint64_t wex = warp_excl_scan(wt, lane);
+      const uint64_t agg = warp_sum(wt);
+      const uint64_t ex = lookback(a.status, tile, agg, lane, ctl);
+      if (lane < kWarps) s_warp[lane] = wex;
+      if (lane == 0) s_excl = ex;
+    }
+    __syncthreads();
+    uint64_t o = s_excl + s_warp[warp] + texcl;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+      const uint64_t g = g0 + k;
+      if (g < nb) {
+        a.offsets[g] = o;
+        if (16 * (g + 1) <= avail) {
+          hdr[2 * g] = (o << 8) | (wds[k] / 8);
+          hdr[2 * g + 1] = a.stage_meta[2 * g + 1];
+        } else {
+          set_error(ctl, MS_ERR_NOMEM, g);
+        }
+        o += wds[k];
+        if (g == nb - 1) ctl->op_words = o;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Placement, step 2: every warp copies staged block payloads to their final
+// offsets (and the last chunk's raw remainder behind the payload); the last CTA
+// completes the column record and moves the arena top past the column.
+template <int kUnused = 0>
+__global__ void __launch_bounds__(kThreads) k_copy_blocks(PlaceArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  DevCtl* ctl = a.ctl;
+  const uint64_t n = a.out_meta->n, nb = n / kBlock, r = n % kBlock;
+  const uint64_t top = *reinterpret_cast<volatile uint64_t*>(&ctl->top);
+  const uint64_t avail = ctl->cap - top;
+  uint8_t* base = reinterpret_cast<uint8_t*>(ctl->arena + top);
+  const uint64_t pwords = nb ? *reinterpret_cast<volatile uint64_t*>(&ctl->op_words) : 0;
+  const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
+  for (uint64_t g = gw; g < nb; g += W) {
+    const uint64_t off = a.offsets[g];
+    const int b = (int)min((uint64_t)64, a.stage_meta[2 * g]);
+    const uint64_t pay = 16 * nb + 8 * off;
+    if (pay + 64ull * b <= avail) {
+      const uint4* src = reinterpret_cast<const uint4*>(a.stage + 4096 * g);
+      uint4* dst = reinterpret_cast<uint4*>(base + pay);
+      for (int t = lane; t < 4 * b; t += 32) dst[t] = src[t];
+    } else if (lane == 0) {
+      set_error(ctl, MS_ERR_NOMEM, g);
+    }
+  }
+  if (r && gw == (nb % W)) {  // one warp places the remainder
+    const uint64_t rem = 16 * nb + 8 * pwords;
+    if (rem + 8 * r <= avail) {
+      const uint64_t* src = reinterpret_cast<const uint64_t*>(a.stage + 4096 * nb);
+      uint64_t* dst = reinterpret_cast<uint64_t*>(base + rem);
+      for (uint64_t t = lane; t < r; t += 32) dst[t] = src[t];
+    } else if (lane == 0) {
+      set_error(ctl, MS_ERR_NOMEM, nb);
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&ctl->done, 1u);
+    if (prev == gridDim.x - 1) {
+      __threadfence();
+      const uint64_t size = 16 * nb + 8 * pwords + 8 * r;
+      DevMeta* m = a.out_meta;
+      m->ptr = reinterpret_cast<uint64_t>(base);
+      m->size = size;
+      m->nb = nb;
+      m->pwords = pwords;
+      const uint64_t grow = (size + 255) / 256 * 256;
+      if (size > avail) {
+        set_error(ctl, MS_ERR_NOMEM, size);
+      } else {
+        ctl->top = top + grow;
+        if (top + grow > ctl->high) ctl->high = top + grow;
+      }
+      ctl->done = 0;
+      __threadfence();
+    }
+  }
+}
+
 
 }  // namespace ms

@@ -1,0 +1,11 @@
+// ms_map_project.cu -- k_map instantiation(s): OP_PROJECT (compiled on its own for build parallelism).
+#include "ms_launch.h"
+
+namespace ms {
+
+template <>
+ms_status launch_map<OP_PROJECT>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
+  return launch_map_impl<OP_PROJECT>(c, a, n_max, s);
+}
+
+}  // namespace ms

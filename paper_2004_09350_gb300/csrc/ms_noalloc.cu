@@ -18,7 +18,6 @@
 #include <algorithm>
 
 #include "ms_device.cuh"
-#define MS_PRODUCE_ONLY
 #include "ms_kernels.cuh"
 
 namespace ms {
@@ -111,7 +110,7 @@ extern "C" ms_status ms_compress_noalloc(const uint64_t* d_in, uint64_t n, int f
   a.fmt = fmt;
   a.bw = fmt == MS_STATIC_BP ? bw : 0;
   a.status = reinterpret_cast<uint64_t*>(scratch + kCtlBytes + kMetaBytes);
-  const size_t smem = (size_t)SmemPlan<OP_COMPRESS>::kPerWarp * kWarps;
+  const size_t smem = sizeof(typename ProducePlan<OP_COMPRESS>::Smem) * kWarps;
   if (cudaFuncSetAttribute(k_produce<OP_COMPRESS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return MS_ERR_CUDA;
