@@ -221,9 +221,47 @@ MS_DEV void pack16(uint16_t* s, int lane, const uint64_t r[16]) {
   M(38) M(39) M(40) M(41) M(42) M(43) M(44) M(45) M(46) M(47) M(48) M(49) M(50) M(51) M(52) M(53) M(54) M(55)  \
   M(56) M(57) M(58) M(59) M(60) M(61) M(62) M(63) M(64)
 
+// Compact lane-stream codec: one loop for every width (a running 64-bit window).
+// Slower per value than the width-specialised one but a fraction of its code;
+// translation units whose kernels juggle several streams can build with
+// MS_COMPACT_CODEC to keep their instruction footprint small.
+MS_DEV void read_lane_stream_compact(const uint16_t* s, int lane, int b, uint64_t v[16]) {
+  const uint64_t mask = lowmask(b);
+  uint64_t acc = 0;
+  int have = 0, q = 0;
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    uint64_t x = 0;
+    if (b) {
+      while (have < b && have <= 48) {
+        acc |= (uint64_t)s[32 * q + lane] << have;
+        have += 16;
+        q++;
+      }
+      if (have >= b) {
+        x = acc & mask;
+        acc = (b == 64) ? 0 : (acc >> b);
+        have -= b;
+      } else {  // b > 48: the value continues in the next halfword
+        const uint64_t h = s[32 * q + lane];
+        q++;
+        x = (acc | (h << have)) & mask;
+        const int used = b - have;
+        acc = h >> used;
+        have = 16 - used;
+      }
+    }
+    v[k] = x;
+  }
+}
+
 // Reads lane `lane`'s 16 values of width b (0..64) from a block payload in shared
 // memory (stream halfword q of the lane at s[32*q + lane]).
 MS_DEV void read_lane_stream(const uint16_t* s, int lane, int b, uint64_t v[16]) {
+#ifdef MS_COMPACT_CODEC
+  read_lane_stream_compact(s, lane, b, v);
+  return;
+#endif
   switch (b) {
 #define MS_UNPACK_CASE(B) \
   case B:                 \
@@ -397,7 +435,9 @@ struct ChunkStream {
   StreamSmem<kDepth>* sm;
   int lane;
 
-  MS_DEV uint64_t chunk(uint64_t i) const { return first + i * stride; }
+  const uint32_t* list = nullptr;  // when set: chunk i is first + list[i] (ascending)
+
+  MS_DEV uint64_t chunk(uint64_t i) const { return list ? first + list[i] : first + i * stride; }
 
   MS_DEV void issue_header(uint64_t i) {
     if (i >= count || lane != 0 || !is_block_fmt(c.fmt)) return;

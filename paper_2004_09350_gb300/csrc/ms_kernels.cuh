@@ -168,8 +168,11 @@ struct SmemPair {
   StreamSmem<kProdDepth2> s0, s1;
 };
 struct SmemProject {
-  StreamSmem<kProdDepth2> s0, s1;
-  uint64_t aux[kBlock];
+  StreamSmem<kProdDepth2> s0;  // positions
+  StreamSmem<kProdDepth> s1;   // data blocks gathered densely
+  uint64_t aux[kBlock];        // one decoded data block
+  uint32_t list[kBlock];       // data blocks to decode, relative to the first one
+  uint16_t runs[32];           // run-start mask per lane
 };
 struct SmemEmit {
   uint32_t bits[kEmitSpan * 16];
@@ -178,13 +181,17 @@ struct SmemEmit {
   uint16_t out[2048];
 };
 
+#ifndef MS_PROJECT_MIN_BLOCKS
+#define MS_PROJECT_MIN_BLOCKS 1  // resident CTAs per SM the project kernel is compiled for
+#endif
+
 template <int OP>
 struct ProducePlan {
   using Smem = typename std::conditional<
       OP == OP_CALC, SmemPair,
       typename std::conditional<OP == OP_PROJECT, SmemProject,
                                 typename std::conditional<OP == OP_EMIT, SmemEmit, SmemSingle>::type>::type>::type;
-  static constexpr int kMinBlocks = (OP == OP_PROJECT || OP == OP_CALC) ? 1 : 2;
+  static constexpr int kMinBlocks = OP == OP_PROJECT ? MS_PROJECT_MIN_BLOCKS : (OP == OP_CALC ? 1 : 2);
 };
 
 // Output length of the operator (device-side, may depend on previous kernels).
@@ -227,12 +234,58 @@ MS_DEV void stream_blocks(const ColView& c, uint64_t lo, uint64_t count, StreamS
   __syncwarp();
 }
 
-// project core for one output chunk: positions p (lane-blocked), values into v.
+// Decodes the data blocks lo + list[0..count) with a prefetching chunk stream and,
+// after each block, fills v[k] for the pending positions inside it (gathered from
+// the block decoded into sm->aux).  One decode site per kernel keeps the
+// width-specialised decoder's code footprint small.
+template <class Smem>
+MS_DEV void gather_listed(const ColView& d, uint64_t lo, uint64_t count, const uint64_t p[16], uint32_t& pending,
+                          uint64_t v[16], int lane, Smem* sm, DevCtl* ctl) {
+  constexpr int D = kProdDepth;
+  ChunkStream<D> cs{d, lo, 1, count, &sm->s1, lane};
+  cs.list = sm->list;
+  if (count == 0) return;
+  cs.prologue();
+  for (int j = 0; j < D - 1; j++) {
+    cs.prologue_step(j);
+    cp_async_commit();
+  }
+  for (uint64_t i = 0; i < count; i++) {
+    cp_async_wait<D - 2>();
+    __syncwarp();
+    cs.step(i);
+    cp_async_commit();
+    {
+      uint64_t t[16];
+      cs.decode(i, t, ctl);
+#pragma unroll
+      for (int k = 0; k < 16; k++) sm->aux[swz(16 * lane + k)] = t[k];
+    }
+    __syncwarp();
+    const uint64_t B = cs.chunk(i);
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      if ((pending & (1u << k)) && p[k] / kBlock == B) {
+        v[k] = sm->aux[swz((int)(p[k] % kBlock))];
+        pending &= ~(1u << k);
+      }
+    }
+    __syncwarp();
+  }
+  cp_async_wait<0>();
+  __syncwarp();
+}
+
+// project core for one output chunk: positions p (lane-blocked) -> values v.
+// Sorted positions fall into runs, one per touched data block.  Blocks with a long
+// run (every run for DELTA data, whose values need the block's prefix sum) are
+// decoded once with a prefetching stream and gathered from shared memory.  The
+// remaining positions are random reads through the header directory (Sec. 4.2
+// random access, extended to the dynamic formats).
 template <class Smem>
 MS_DEV void project_gather(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
                            uint64_t v[16], Smem* sm) {
   uint32_t pending = 0;
-  uint64_t lo = ~0ull, hi = 0;
   bool sorted = true;
 #pragma unroll
   for (int k = 0; k < 16; k++) {
@@ -240,65 +293,75 @@ MS_DEV void project_gather(const ProduceArgs& a, const ColView& d, const uint64_
     if (16 * lane + k < valid) {
       if (p[k] < d.n) {
         pending |= 1u << k;
-        lo = min(lo, p[k]);
-        hi = max(hi, p[k]);
-        if (k > 0 && p[k] < p[k - 1]) sorted = false;
       } else {
         set_error(a.ctl, MS_ERR_OUT_OF_RANGE, p[k]);
       }
+      if (k > 0 && p[k] < p[k - 1]) sorted = false;
     }
   }
-  // sortedness across lanes: each lane's first value >= the previous lane's last
-  const uint64_t prev_last = __shfl_up_sync(kFull, (16 * lane + 15 < valid) ? p[15] : hi, 1);
+  const uint64_t prev_last = __shfl_up_sync(kFull, p[15], 1);
   if (lane > 0 && 16 * lane < valid && p[0] < prev_last) sorted = false;
-  const uint64_t blo = warp_min(lo == ~0ull ? ~0ull : lo / kBlock);
-  uint64_t bhi = hi / kBlock;
+  bool runs_pass = __all_sync(kFull, sorted);
+  const bool delta = d.fmt == MS_DELTA_BP;
+  // Each pass lists data blocks to decode: the sorted case lists every block with a
+  // long run in one pass; unsorted positions into DELTA data list one distinct
+  // block per pass (ascending).
+  while (__ballot_sync(kFull, pending) != 0) {
+    uint64_t lo;
+    uint32_t total;
+    if (runs_pass) {
+      runs_pass = false;
+      // pending slots are a prefix of each lane's slots (sorted; out-of-range ones come last)
+      lo = warp_min((pending & 1u) ? p[0] / kBlock : ~0ull);
+      uint32_t starts = 0;
+      const uint64_t prevb = __shfl_up_sync(kFull, p[15] / kBlock, 1);
 #pragma unroll
-  for (int d2 = 16; d2; d2 >>= 1) bhi = max(bhi, __shfl_xor_sync(kFull, bhi, d2));
-  const bool all_sorted = __all_sync(kFull, sorted);
-  if (blo == ~0ull) return;  // no valid position
-  const uint64_t span = bhi - blo + 1;
-  if ((all_sorted && span <= 64) || d.fmt == MS_DELTA_BP) {
-    if (all_sorted && span <= 64) {
-      // dense: stream the spanned data blocks once and gather from shared memory
-      stream_blocks<kProdDepth2>(d, blo, span, &sm->s1, lane, a.ctl, [&](uint64_t B, const uint64_t* t) {
+      for (int k = 0; k < 16; k++) {
+        const uint64_t bk = p[k] / kBlock;
+        if ((pending & (1u << k)) && (k == 0 ? (lane == 0 || bk != prevb) : bk != p[k - 1] / kBlock))
+          starts |= 1u << k;
+      }
+      sm->runs[lane] = (uint16_t)starts;
+      const uint32_t lanes_with = __ballot_sync(kFull, starts != 0);
+      __syncwarp();
+      const uint32_t min_run = delta ? 1u : (d.fmt == MS_UNCOMPR ? 128u : 8u);
+      uint32_t dense_here = 0;
 #pragma unroll
-        for (int k = 0; k < 16; k++) sm->aux[swz(16 * lane + k)] = t[k];
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < 16; k++) {
-          if ((pending & (1u << k)) && p[k] / kBlock == B) {
-            v[k] = sm->aux[swz((int)(p[k] % kBlock))];
-            pending &= ~(1u << k);
+      for (int k = 0; k < 16; k++) {
+        if (starts & (1u << k)) {
+          const uint32_t later = starts & ~((2u << k) - 1u);
+          int next;
+          if (later) {
+            next = 16 * lane + __ffs(later) - 1;
+          } else {
+            const uint32_t nl = lanes_with & ~((2u << lane) - 1u);
+            next = nl ? 16 * (__ffs(nl) - 1) + __ffs(sm->runs[__ffs(nl) - 1]) - 1 : valid;
           }
+          if ((uint32_t)(next - (16 * lane + k)) >= min_run) dense_here |= 1u << k;
         }
-      });
-      return;
-    }
-    // DELTA data, unsorted or sparse positions: decode each distinct block once
-    while (true) {
+      }
+      const uint32_t nd = __popc(dense_here);
+      const uint32_t at = warp_excl_scan32(nd, lane);
+      total = __shfl_sync(kFull, at + nd, 31);
+      uint32_t o = at;
+#pragma unroll
+      for (int k = 0; k < 16; k++)
+        if (dense_here & (1u << k)) sm->list[o++] = (uint32_t)(p[k] / kBlock - lo);
+    } else if (delta) {
       uint64_t mb = ~0ull;
 #pragma unroll
       for (int k = 0; k < 16; k++)
         if (pending & (1u << k)) mb = min(mb, p[k] / kBlock);
-      const uint64_t B = warp_min(mb);
-      if (B == ~0ull) break;
-      stream_blocks<kProdDepth2>(d, B, 1, &sm->s1, lane, a.ctl, [&](uint64_t, const uint64_t* t) {
-#pragma unroll
-        for (int k = 0; k < 16; k++) sm->aux[swz(16 * lane + k)] = t[k];
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < 16; k++) {
-          if ((pending & (1u << k)) && p[k] / kBlock == B) {
-            v[k] = sm->aux[swz((int)(p[k] % kBlock))];
-            pending &= ~(1u << k);
-          }
-        }
-      });
+      lo = warp_min(mb);
+      total = 1;
+      if (lane == 0) sm->list[0] = 0;
+    } else {
+      break;
     }
-    return;
+    __syncwarp();
+    gather_listed(d, lo, total, p, pending, v, lane, sm, a.ctl);
   }
-  // sparse: random reads through the header directory
+  // short runs or unsorted positions: random reads (never DELTA: its runs are all listed)
 #pragma unroll
   for (int k = 0; k < 16; k++)
     if (pending & (1u << k)) v[k] = read_at(d, p[k]);
