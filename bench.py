@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=2020)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["sweep-plan", "star"], default="sweep-plan",
+                    help="sweep-plan: the 2^28-row select/project/calc/sum plan (default); "
+                         "star: the star-schema plan on a 6e8-row fact table")
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
     return a
@@ -472,8 +475,105 @@ def bench_reference(args):
             "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------- star plan
+
+def oracle_star_plan(fact, dims):
+    import oracle
+    from paper_2004_09350_gb300 import plans, synth
+    t0 = time.perf_counter()
+    s1 = oracle.select(dims["d1_c5"], oracle.EQ, 0)
+    s2 = oracle.select(dims["d2_c25"], oracle.LT, 15)
+    p1 = oracle.semijoin(fact["fk1"], s1, synth.DIM_SIZES[0])
+    q2 = oracle.semijoin(oracle.project(fact["fk2"], p1), s2, synth.DIM_SIZES[1])
+    p2 = oracle.project(p1, q2)
+    p3 = oracle.project(p2, oracle.select(oracle.project(fact["discount"], p2), oracle.BETWEEN, 1, 3))
+    p4 = oracle.project(p3, oracle.select(oracle.project(fact["quantity"], p3), oracle.LT, 25))
+    year = oracle.project(dims["date_year"], oracle.project(fact["fk_date"], p4))
+    c25 = oracle.project(dims["d2_c25"], oracle.project(fact["fk2"], p4))
+    gid = oracle.calc(oracle.ADD, oracle.calc(oracle.MUL, year, c=15), c25)
+    sums = oracle.group_sum(gid, oracle.project(fact["revenue"], p4), plans.STAR_GROUPS)
+    return time.perf_counter() - t0, sums
+
+
+def bench_star(args):
+    import torch
+    from paper_2004_09350_gb300 import morphstore as ms
+    from paper_2004_09350_gb300 import plans, synth
+
+    n = args.rows if args.rows != (1 << 28) else 600_000_000
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    fact = synth.star_fact_torch(args.seed, n, dev)
+    dims = {k: ms.as_device_u64(v, dev) for k, v in synth.star_dims(args.seed + 1).items()}
+    raw = {**fact, **dims}
+    # arena: uncompressed base columns (7 fact columns) plus every intermediate
+    ctx = ms.Ctx(0, arena_bytes=8 * 8 * n + (4 << 30), max_rows=n)
+    out = {}
+    for label, base_fm, fm in (("compressed", plans.STAR_BASE_COMPRESSED, plans.STAR_COMPRESSED),
+                               ("uncompressed", plans.STAR_BASE_UNCOMPRESSED, plans.STAR_UNCOMPRESSED)):
+        base = {k: ctx.compress(v, base_fm[k]) for k, v in raw.items()}
+        ctx.check(what="star base")
+        base_bytes = sum(ctx.info(c)["size_bytes"] for c in base.values())
+        res = torch.zeros(plans.STAR_GROUPS, dtype=torch.int64, device=dev)
+        for _ in range(args.warmup):
+            _, cols = plans.star_plan(ctx, base, fm, out=res)
+            plans.free_lifo(ctx, cols)
+        use0, _ = ctx.arena_usage()
+        ctx.reset_high_water()
+        _, cols = plans.star_plan(ctx, base, fm, out=res)
+        inter_bytes = plans.footprint(ctx, cols)
+        _, high = ctx.arena_usage()
+        plans.free_lifo(ctx, cols)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(args.steps):
+            _, cols = plans.star_plan(ctx, base, fm, out=res)
+            plans.free_lifo(ctx, cols)
+        t1.record()
+        torch.cuda.synchronize()
+        prof = ctx.profile_collect()
+        ctx.profile(False)
+        ctx.check(what="star plan")
+        ms_step = t0.elapsed_time(t1) / args.steps
+        out[label] = {"ms_per_step": round(ms_step, 3), "rows_per_s": n / (ms_step * 1e-3),
+                      "base_bytes": base_bytes, "intermediate_bytes": inter_bytes,
+                      "arena_peak_intermediates": int(high - use0),
+                      "footprint_bytes": base_bytes + inter_bytes,
+                      "sums": ms.to_numpy_u64(res).tolist(),
+                      "per_kernel_ms": {k: round(v[1] / args.steps, 3) for k, v in prof.items()}}
+        for c in reversed(list(base.values())):
+            ctx.free(c)
+    assert out["compressed"]["sums"] == out["uncompressed"]["sums"], "star pipelines disagree"
+    cpu = None
+    if not args.no_cpu_baseline:
+        rows = min(n, 1 << 23)
+        f = {k: v[:rows].cpu().numpy().view(np.uint64) for k, v in fact.items()}
+        d = {k: v.cpu().numpy().view(np.uint64) for k, v in dims.items()}
+        t, _ = oracle_star_plan(f, d)
+        cpu = {"value": rows / t, "unit": "rows/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {rows} fact rows, same plan on uncompressed arrays ({t:.1f} s)"}
+    ctx.close()
+    comp, unc = out["compressed"], out["uncompressed"]
+    for v in (comp, unc):
+        v.pop("sums")
+    return {"metric": METRIC, "workload": "star", "value": comp["rows_per_s"], "unit": "rows/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": comp["ms_per_step"],
+            "higher_is_better": True, "dtype": "u64", "data": "synthetic (seeded SplitMix64, generated on the GPU)",
+            "config": {"workload": "star-schema plan: 2 dimension selects, 2 semi-joins, 2 range selects, "
+                                   "projects, calc, 105-group sum", "fact_rows": n},
+            "compressed": comp, "uncompressed": unc,
+            "speedup_vs_uncompressed": round(unc["ms_per_step"] / comp["ms_per_step"], 3),
+            "footprint_ratio": round(comp["footprint_bytes"] / unc["footprint_bytes"], 4),
+            "cpu_baseline": cpu}
+
+
 def main():
     args = parse()
+    if args.workload == "star" and args.impl == "ours":
+        print(json.dumps(bench_star(args)))
+        return
     line = bench_reference(args) if args.impl == "reference" else bench_ours(args)
     if line is not None:
         print(json.dumps(line))

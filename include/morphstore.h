@@ -138,6 +138,11 @@ ms_status ms_get_error(ms_ctx *ctx, void *stream);
    valid after ms_get_error returned an error. */
 uint64_t ms_last_error_info(ms_ctx *ctx);
 
+/* The cudaError_t of the last CUDA call that made an entry point return
+   MS_ERR_CUDA (0 if none), and its description. */
+int ms_last_cuda_error(void);
+const char *ms_cuda_error_string(int code);
+
 /* Arena bytes in use (current) and the high-water mark since the last reset;
    both synchronise `stream`.  The high-water mark is the peak footprint of the
    operator outputs. */

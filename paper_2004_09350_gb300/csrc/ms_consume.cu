@@ -47,9 +47,12 @@ __global__ void __launch_bounds__(kThreads) k_scan_counts(ScanArgs a) {
   constexpr int kPer = 16;
   const uint64_t per_tile = (uint64_t)kThreads * kPer;
   const uint64_t ntiles = (nch + per_tile - 1) / per_tile;
-  if (nch == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
-    a.coff[0] = 0;
-    a.ctl->op_n = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ctl->op_nch = nch;
+    if (nch == 0) {
+      a.coff[0] = 0;
+      a.ctl->op_n = 0;
+    }
   }
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const uint64_t g0 = tile * per_tile + (uint64_t)threadIdx.x * kPer;
@@ -183,7 +186,7 @@ ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max
     const int grid = grid_for(c, k_mark, kStreamSmem, tiles);
     ProfScope ps(c, MS_K_MARK, s);
     k_mark<<<grid, kThreads, kStreamSmem, s>>>(a);
-    if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
+    if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
   }
   ScanArgs sa{};
   sa.in = a.in;

@@ -46,7 +46,8 @@ struct DevCtl {
   uint64_t err_info;  // detail of the first device error
   uint64_t op_n;      // element count produced by the last mark kernel
   uint64_t op_words;  // payload words published by an op's final tile
-  uint64_t rsv[8];
+  uint64_t op_nch;    // input chunks of the last mark step (its real length, not a bound)
+  uint64_t rsv[7];
 };
 
 // Read-only view of a column inside a kernel.
@@ -442,7 +443,7 @@ struct ChunkStream {
   MS_DEV void issue_header(uint64_t i) {
     if (i >= count || lane != 0 || !is_block_fmt(c.fmt)) return;
     const uint64_t g = chunk(i);
-    if (g < c.nb) cp_async16(sm->hdr[i % (2 * kDepth)], c.p + 16 * g);
+    if (g < c.nb && 16 * (g + 1) <= c.size) cp_async16(sm->hdr[i % (2 * kDepth)], c.p + 16 * g);
   }
 
   MS_DEV void issue_payload(uint64_t i) {
@@ -465,8 +466,11 @@ struct ChunkStream {
     } else if (g < c.nb) {
       const uint64_t w0 = sm->hdr[i % (2 * kDepth)][0];
       const int b = (int)min((uint64_t)64, w0 & 255);
-      src = c.p + 16 * c.nb + 8 * (w0 >> 8);
-      units = 4 * b;
+      // a payload outside the column (corrupt metadata) is never read
+      if (16 * c.nb + 8 * ((w0 >> 8) + 8ull * b) <= c.size) {
+        src = c.p + 16 * c.nb + 8 * (w0 >> 8);
+        units = 4 * b;
+      }
     }
     uint4* dst = reinterpret_cast<uint4*>(sm->slot[i % kDepth]);
     for (int u = lane; u < units; u += 32) {
@@ -544,7 +548,7 @@ struct ChunkStream {
     if (g < c.nb) {
       const uint64_t w0 = sm->hdr[i % (2 * kDepth)][0], ref = sm->hdr[i % (2 * kDepth)][1];
       int b = (int)(w0 & 255);
-      if (b > 64) {
+      if (b > 64 || 16 * (g + 1) > c.size || 16 * c.nb + 8 * ((w0 >> 8) + 8ull * b) > c.size) {
         if (lane == 0) set_error(ctl, MS_ERR_FORMAT, g);
         b = 0;
       }
@@ -565,10 +569,12 @@ struct ChunkStream {
       }
     } else {
       const uint64_t* rem = reinterpret_cast<const uint64_t*>(c.p + 16 * c.nb + 8 * c.pwords);
+      const bool inside = 16 * c.nb + 8 * (c.pwords + (uint64_t)valid) <= c.size;
+      if (!inside && lane == 0) set_error(ctl, MS_ERR_FORMAT, g);
 #pragma unroll
       for (int k = 0; k < 16; k++) {
         const int t = 16 * lane + k;
-        v[k] = t < valid ? ldg64(rem + t) : 0;
+        v[k] = (t < valid && inside) ? ldg64(rem + t) : 0;
       }
     }
     return valid;
@@ -596,11 +602,15 @@ MS_DEV uint64_t read_at(const ColView& c, uint64_t i) {
     }
     payload = c.p + 64ull * b * g;
   } else {
-    if (g >= c.nb) return ldg64(c.p + 16 * c.nb + 8 * c.pwords + 8 * (uint64_t)r);
+    if (g >= c.nb) {
+      const uint64_t at = 16 * c.nb + 8 * c.pwords + 8 * (uint64_t)r;
+      return at + 8 <= c.size ? ldg64(c.p + at) : 0;
+    }
     const uint64_t* hdr = reinterpret_cast<const uint64_t*>(c.p) + 2 * g;
     const uint64_t w0 = ldg64(hdr);
     b = (int)min((uint64_t)64, w0 & 255);
     ref = ldg64(hdr + 1);
+    if (16 * c.nb + 8 * ((w0 >> 8) + 8ull * b) > c.size) return 0;  // corrupt metadata: never read outside
     payload = c.p + 16 * c.nb + 8 * (w0 >> 8);
   }
   if (b == 0) return ref;

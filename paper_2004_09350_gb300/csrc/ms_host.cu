@@ -9,7 +9,13 @@
 
 namespace ms {
 
-ms_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MS_OK : MS_ERR_CUDA; }
+static int g_last_cuda_error = 0;  // last failing cudaError_t seen by the library
+
+ms_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return MS_OK;
+  g_last_cuda_error = (int)e;
+  return MS_ERR_CUDA;
+}
 
 void* dev_alloc(ms_ctx* c, size_t bytes) {
   if (bytes == 0) bytes = 256;
@@ -72,7 +78,7 @@ void drop_new_column(ms_ctx* c, ms_column* col) {
 
 ms_status ensure_work(ms_ctx* c, uint64_t bytes) {
   if (bytes <= c->work_cap) return MS_OK;
-  if (cudaDeviceSynchronize() != cudaSuccess) return MS_ERR_CUDA;
+  if (cuda_status(cudaDeviceSynchronize()) != MS_OK) return MS_ERR_CUDA;
   dev_free(c, c->work);
   uint64_t cap = std::max(bytes, c->work_cap * 2);
   c->work = static_cast<uint8_t*>(dev_alloc(c, cap));
@@ -146,7 +152,7 @@ ms_status ms_ctx_create(ms_ctx** out, int device, uint64_t arena_bytes, uint64_t
   if (!out) return MS_ERR_INVALID_ARG;
   *out = nullptr;
   if ((alloc == nullptr) != (free_fn == nullptr)) return MS_ERR_INVALID_ARG;
-  if (cudaSetDevice(device) != cudaSuccess) return MS_ERR_CUDA;
+  if (cuda_status(cudaSetDevice(device)) != MS_OK) return MS_ERR_CUDA;
   ms_ctx* c = new (std::nothrow) ms_ctx;
   if (!c) return MS_ERR_NOMEM;
   c->device = device;
@@ -218,7 +224,7 @@ ms_status ms_get_error(ms_ctx* c, void* stream) {
   c->last_err_info = c->pin[1];
   if (err != 0) {
     uint32_t zero = 0;
-    if (cudaMemcpy(&c->ctl->err, &zero, 4, cudaMemcpyHostToDevice) != cudaSuccess) return MS_ERR_CUDA;
+    if (cuda_status(cudaMemcpy(&c->ctl->err, &zero, 4, cudaMemcpyHostToDevice)) != MS_OK) return MS_ERR_CUDA;
   }
   return static_cast<ms_status>(err);
 }
@@ -345,7 +351,7 @@ ms_status ms_column_free(ms_ctx* c, ms_column* col, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!col->arena) {
     // the buffer may still be read by enqueued work: drain the stream first
-    if (cudaStreamSynchronize(s) != cudaSuccess) return MS_ERR_CUDA;
+    if (cuda_status(cudaStreamSynchronize(s)) != MS_OK) return MS_ERR_CUDA;
     dev_free(c, col->ext);
     c->free_slots.push_back(col->slot);
     c->live.erase(std::remove(c->live.begin(), c->live.end(), col), c->live.end());
@@ -366,7 +372,7 @@ ms_status ms_column_free(ms_ctx* c, ms_column* col, void* stream) {
     // the arena top returns to the start of the lowest popped column; the slot's
     // metadata is read by the kernel before any later kernel can reuse the slot
     k_set_top<<<1, 1, 0, s>>>(c->ctl, c->metas + lowest);
-    if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
+    if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
   }
   return MS_OK;
 }
@@ -379,7 +385,7 @@ ms_status ms_profile_enable(ms_ctx* c, int on) {
 
 ms_status ms_profile_collect(ms_ctx* c, ms_kernel_time* out, int max, int* n_out) {
   if (!c || (!out && max > 0)) return MS_ERR_INVALID_ARG;
-  if (cudaDeviceSynchronize() != cudaSuccess) return MS_ERR_CUDA;
+  if (cuda_status(cudaDeviceSynchronize()) != MS_OK) return MS_ERR_CUDA;
   ms_kernel_time acc[MS_K_COUNT];
   for (int k = 0; k < MS_K_COUNT; k++) acc[k] = ms_kernel_time{k, 0, 0.0};
   for (auto& r : c->prof) {
@@ -406,5 +412,9 @@ const char* ms_kernel_name(int k) {
                                           "place_copy"};
   return (k >= 0 && k < MS_K_COUNT) ? names[k] : "?";
 }
+
+int ms_last_cuda_error(void) { return g_last_cuda_error; }
+
+const char* ms_cuda_error_string(int code) { return cudaGetErrorString((cudaError_t)code); }
 
 }  // extern "C"

@@ -372,9 +372,12 @@ MS_DEV int emit_gather(const ProduceArgs& a, uint64_t n_out, uint64_t g, int lan
   const uint64_t lo = g * kBlock;
   const int valid = (int)min((uint64_t)kBlock, n_out - lo);
   const uint64_t hi = lo + valid;
-  // chunk range holding the block's outputs (clamped: scratch is never trusted blindly)
-  const uint64_t cfirst = min(a.bstart[g], a.emit_nch - 1);
-  const uint64_t clast = max(cfirst, min((hi < n_out) ? a.bstart[g + 1] : a.emit_nch - 1, a.emit_nch - 1));
+  // chunk range holding the block's outputs, within the input's real chunk count
+  // (clamped: scratch is never trusted blindly)
+  const uint64_t nch_in =
+      max((uint64_t)1, min(a.emit_nch, *reinterpret_cast<volatile const uint64_t*>(&a.ctl->op_nch)));
+  const uint64_t cfirst = min(a.bstart[g], nch_in - 1);
+  const uint64_t clast = max(cfirst, min((hi < n_out) ? a.bstart[g + 1] : nch_in - 1, nch_in - 1));
   // dense blocks (<= 64 chunks): a warp expands one chunk at a time; sparse: a lane per chunk
   const bool dense = clast - cfirst < 64;
   for (uint64_t c0 = cfirst; c0 <= clast; c0 += kEmitSpan) {
@@ -724,7 +727,12 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_produ
       m->bw = (uint32_t)(fmt == MS_STATIC_BP ? bw : 0);
       const uint64_t grow = (size + 255) / 256 * 256;
       if (size > avail) {
+        // the column did not fit: publish it empty so no reader leaves the buffer
         set_error(ctl, MS_ERR_NOMEM, size);
+        m->n = 0;
+        m->size = 0;
+        m->nb = 0;
+        m->pwords = 0;
       } else {
         ctl->top = top + grow;
         if (top + grow > ctl->high) ctl->high = top + grow;
@@ -955,7 +963,11 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
         m->pwords = 0;
         const uint64_t grow = (size + 255) / 256 * 256;
         if (size > avail) {
+          // the column did not fit: publish it empty so no reader leaves the arena
           set_error(ctl, MS_ERR_NOMEM, size);
+          m->n = 0;
+          m->size = 0;
+          m->nb = 0;
         } else {
           ctl->top = top + grow;
           if (top + grow > ctl->high) ctl->high = top + grow;
@@ -1085,7 +1097,12 @@ __global__ void __launch_bounds__(kThreads) k_copy_blocks(PlaceArgs a) {
       m->pwords = pwords;
       const uint64_t grow = (size + 255) / 256 * 256;
       if (size > avail) {
+        // the column did not fit: publish it empty so no reader leaves the arena
         set_error(ctl, MS_ERR_NOMEM, size);
+        m->n = 0;
+        m->size = 0;
+        m->nb = 0;
+        m->pwords = 0;
       } else {
         ctl->top = top + grow;
         if (top + grow > ctl->high) ctl->high = top + grow;

@@ -69,7 +69,7 @@ ms_status launch_map_impl(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_
   const int grid = grid_for(c, k_map<OP>, smem, tiles);
   ProfScope ps(c, kMapKernel[OP], s);
   k_map<OP><<<grid, kThreads, smem, s>>>(a);
-  return cuda_status(cudaGetLastError());
+  return cuda_status(cudaGetLastError());  // records the failing code
 }
 
 }  // namespace ms

@@ -172,7 +172,7 @@ ms_status ms_calc(ms_ctx* c, int op, const ms_column* x, const ms_column* y, uin
 ms_status ms_agg_sum(ms_ctx* c, const ms_column* in, uint64_t* d_result, void* stream) {
   if (!c || !owned(c, in) || !d_result) return MS_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(d_result, 0, 8, s) != cudaSuccess) return MS_ERR_CUDA;
+  if (cuda_status(cudaMemsetAsync(d_result, 0, 8, s)) != MS_OK) return MS_ERR_CUDA;
   return launch_agg_sum(c, c->metas + in->slot, d_result, in->n_max, s);
 }
 
@@ -180,7 +180,7 @@ ms_status ms_group_sum(ms_ctx* c, const ms_column* gid, const ms_column* val, ui
                        void* stream) {
   if (!c || !owned(c, gid) || !owned(c, val) || (!d_sums && G)) return MS_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (G && cudaMemsetAsync(d_sums, 0, 8 * G, s) != cudaSuccess) return MS_ERR_CUDA;
+  if (G && cuda_status(cudaMemsetAsync(d_sums, 0, 8 * G, s)) != MS_OK) return MS_ERR_CUDA;
   return launch_group_sum(c, c->metas + gid->slot, c->metas + val->slot, G, d_sums,
                           std::min(gid->n_max, val->n_max), s);
 }
@@ -194,7 +194,7 @@ ms_status ms_semijoin(ms_ctx* c, const ms_column* probe, const ms_column* keys, 
   Work w;
   ms_status st = carve(c, std::max(probe->n_max, keys->n_max), domain, &w, s);
   if (st != MS_OK) return st;
-  if (cudaMemsetAsync(w.keybits, 0, 4 * cdiv(domain, 32), s) != cudaSuccess) return MS_ERR_CUDA;
+  if (cuda_status(cudaMemsetAsync(w.keybits, 0, 4 * cdiv(domain, 32), s)) != MS_OK) return MS_ERR_CUDA;
   st = launch_build_keys(c, c->metas + keys->slot, domain, w.keybits, keys->n_max, s);
   if (st != MS_OK) return st;
   MarkArgs m{};

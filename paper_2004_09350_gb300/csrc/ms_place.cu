@@ -17,7 +17,7 @@ ms_status launch_place(ms_ctx* c, const Work& w, DevMeta* out, uint64_t n_max, c
     const int grid = grid_for(c, k_scan_widths<>, 0, cdiv(nb_max, (uint64_t)kThreads * 16));
     ProfScope ps(c, MS_K_PLACE_SCAN, s);
     k_scan_widths<><<<grid, kThreads, 0, s>>>(a);
-    if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
+    if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
   }
   const int grid = grid_for(c, k_copy_blocks<>, 0, cdiv(nb_max + 1, kWarps));
   ProfScope ps(c, MS_K_PLACE_COPY, s);

@@ -97,6 +97,10 @@ def load() -> ctypes.CDLL:
     lib.ms_profile_collect.restype = ctypes.c_int
     lib.ms_kernel_name.argtypes = [i32]
     lib.ms_kernel_name.restype = ctypes.c_char_p
+    lib.ms_last_cuda_error.argtypes = []
+    lib.ms_last_cuda_error.restype = ctypes.c_int
+    lib.ms_cuda_error_string.argtypes = [ctypes.c_int]
+    lib.ms_cuda_error_string.restype = ctypes.c_char_p
     lib.ms_last_error_info.argtypes = [p]
     lib.ms_last_error_info.restype = u64
     lib.ms_column_max_rows.argtypes = [p]
@@ -109,7 +113,7 @@ def header_symbols() -> list[str]:
     """Names of the functions include/morphstore.h declares."""
     with open(_HEADER) as f:
         text = f.read()
-    return sorted(set(re.findall(r"^\s*(?:ms_status|uint64_t|const char \*)\s*(ms_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:ms_status|uint64_t|int|const char \*)\s*(ms_\w+)\s*\(", text, re.M)))
 
 
 def _stream_handle(stream) -> ctypes.c_void_p:
@@ -123,6 +127,9 @@ def _check(code: int, what: str, ctx=None):
         info = 0
         if ctx is not None:
             info = load().ms_last_error_info(ctx)
+        if code == MS_ERR_CUDA:
+            e = load().ms_last_cuda_error()
+            what = f"{what} [cuda error {e}: {load().ms_cuda_error_string(e).decode()}]"
         raise MSError(code, what, info)
 
 

@@ -35,7 +35,8 @@ def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
 
 
 def uniform(seed: int, n: int, lo: int, hi: int) -> np.ndarray:
-    """Integers in [lo, hi) (hi - lo >= 1).  Power-of-two spans take the top bits."""
+    """Integers in [lo, hi) (hi - lo >= 1).  Power-of-two spans take the top bits;
+    other spans (< 2^32) scale the top 32 bits: ((z >> 32) * span) >> 32."""
     span = hi - lo
     if span <= 0:
         raise ValueError("empty range")
@@ -44,9 +45,48 @@ def uniform(seed: int, n: int, lo: int, hi: int) -> np.ndarray:
         k = span.bit_length() - 1
         r = (z >> np.uint64(64 - k)) if k > 0 else np.zeros(n, dtype=np.uint64)
     else:
-        r = z % np.uint64(span)
+        if span >= 1 << 32:
+            raise ValueError("non-power-of-two spans must be < 2^32")
+        r = ((z >> np.uint64(32)) * np.uint64(span)) >> np.uint64(32)
     with np.errstate(over="ignore"):
         return r + np.uint64(lo)
+
+
+# ------------------------------------------------ the same streams on the GPU
+
+def _torch_mix(z):
+    import torch
+    m30 = (1 << 34) - 1
+    m27 = (1 << 37) - 1
+    m31 = (1 << 33) - 1
+    z = z ^ ((z >> 30) & m30)
+    z = z * torch.tensor(int(np.int64(np.uint64(0xBF58476D1CE4E5B9).view(np.int64))), dtype=torch.int64,
+                         device=z.device)
+    z = z ^ ((z >> 27) & m27)
+    z = z * torch.tensor(int(np.int64(np.uint64(0x94D049BB133111EB).view(np.int64))), dtype=torch.int64,
+                         device=z.device)
+    return z ^ ((z >> 31) & m31)
+
+
+def splitmix64_torch(seed: int, n: int, device, offset: int = 0):
+    """splitmix64() computed with int64 tensor arithmetic on `device` (same bits)."""
+    import torch
+    gamma = int(np.uint64(GAMMA).view(np.int64))
+    s = int(np.uint64(seed & 0xFFFFFFFFFFFFFFFF).view(np.int64))
+    i = torch.arange(offset + 1, offset + n + 1, dtype=torch.int64, device=device)
+    return _torch_mix(i * gamma + s)
+
+
+def uniform_torch(seed: int, n: int, lo: int, hi: int, device):
+    """uniform() on `device`, as an int64 tensor holding the same uint64 bits."""
+    span = hi - lo
+    z = splitmix64_torch(seed, n, device)
+    if span & (span - 1) == 0:
+        k = span.bit_length() - 1
+        r = ((z >> (64 - k)) & ((1 << k) - 1)) if k > 0 else z * 0
+    else:
+        r = (((z >> 32) & 0xFFFFFFFF) * span) >> 32
+    return r + lo
 
 
 def geometric_gaps(seed: int, n: int) -> np.ndarray:
@@ -141,9 +181,28 @@ def value_at_rank(x: np.ndarray, s: float) -> int:
 DIM_SIZES = (2_500_000, 200_000, 30_000, 2556)
 
 
-def star_dims(seed: int = 7):
-    """Dimension attributes: D1.c5 ~ U[0,5) over 2.5e6 keys, D2.c25 ~ U[0,25) over 2e5 keys."""
-    return uniform(seed, DIM_SIZES[0], 0, 5), uniform(seed + 1, DIM_SIZES[1], 0, 25)
+def star_dims(seed: int = 7) -> dict:
+    """Dimension attributes: D1.c5 ~ U[0,5) over 2.5e6 keys, D2.c25 ~ U[0,25) over
+    2e5 keys, and the date dimension's year = (7 * key) // 2556 over 2556 keys
+    (seven equal years)."""
+    return {"d1_c5": uniform(seed, DIM_SIZES[0], 0, 5),
+            "d2_c25": uniform(seed + 1, DIM_SIZES[1], 0, 25),
+            "date_year": (np.arange(DIM_SIZES[3], dtype=np.uint64) * np.uint64(7)) // np.uint64(DIM_SIZES[3])}
+
+
+def star_fact_torch(seed: int, n: int, device) -> dict:
+    """star_fact() generated on `device` (int64 tensors with the same bits)."""
+    import torch
+    day = (torch.arange(n, dtype=torch.int64, device=device) * DIM_SIZES[3]) // max(n, 1)
+    return {
+        "fk1": uniform_torch(seed + 10, n, 0, DIM_SIZES[0], device),
+        "fk2": uniform_torch(seed + 11, n, 0, DIM_SIZES[1], device),
+        "fk3": uniform_torch(seed + 12, n, 0, DIM_SIZES[2], device),
+        "fk_date": day,
+        "quantity": uniform_torch(seed + 13, n, 1, 51, device),
+        "discount": uniform_torch(seed + 14, n, 0, 11, device),
+        "revenue": uniform_torch(seed + 15, n, 0, 1 << 23, device),
+    }
 
 
 def star_fact(seed: int, n: int) -> dict:

@@ -315,3 +315,42 @@ def test_arena_is_lifo_and_tracks_high_water(ctx):
     ctx.free(b)  # pops both
     assert ctx.arena_usage()[0] == base
     assert ctx.arena_usage()[1] == high
+
+
+@pytest.mark.parametrize("fmt", [ms.UNCOMPR, ms.DELTA_BP, ms.DYN_BP])
+def test_select_and_semijoin_on_short_intermediates(ctx, fmt):
+    """Operators on intermediates whose real length is far below the host-side
+    bound must not read scratch past the real input (stale data from a larger
+    earlier operator sits there)."""
+    n = 40 * 4096 + 123
+    x = synth.uniform(61, n, 0, 1000)
+    cx, _ = gpu_col(ctx, x, ms.DYN_BP)
+    big = ctx.select(cx, ms.LT, 900, fmt=fmt)  # leaves a large bitmap in scratch
+    ctx.free(big)
+    pos = ctx.select(cx, ms.LT, 37, fmt=fmt)  # ~3.7% of n, bound n
+    want_pos = oracle.select(x, oracle.LT, 37)
+    vals = ctx.project(cx, pos, fmt=fmt)
+    want_vals = oracle.project(x, want_pos)
+    q = ctx.select(vals, ms.GE, 20, fmt=fmt)
+    assert_column(ctx, q, oracle.select(want_vals, oracle.GE, 20), fmt)
+    keys_np = np.arange(0, 1000, 7, dtype=np.uint64)
+    keys, _ = gpu_col(ctx, keys_np, ms.DELTA_BP)
+    sj = ctx.semijoin(vals, keys, 1000, fmt=fmt)
+    assert_column(ctx, sj, oracle.semijoin(want_vals, keys_np, 1000), fmt)
+    for col in (sj, keys, q, vals, pos, cx):
+        ctx.free(col)
+
+
+@pytest.mark.parametrize("fmt", [ms.UNCOMPR, ms.DYN_BP, ms.STATIC_BP])
+def test_arena_exhaustion_reports_nomem_and_leaves_an_empty_column(fmt):
+    """A column that does not fit the arena is reported (MS_ERR_NOMEM) and
+    published empty, so operators downstream never read outside the arena."""
+    with ms.Ctx(0, arena_bytes=1 << 20, max_rows=1 << 20) as small:
+        x = synth.skewed_widths(71, 600_000)  # > 1 MB in every format
+        col = small.compress(ms.as_device_u64(x, small.device), fmt, 40 if fmt == ms.STATIC_BP else 0)
+        assert small.get_error() == ms.MS_ERR_NOMEM
+        assert small.info(col)["n"] == 0 and small.info(col)["size_bytes"] == 0
+        s = small.agg_sum(col)
+        pos = small.select(col, ms.LT, 5, fmt=fmt, bw=20 if fmt == ms.STATIC_BP else 0)
+        assert int(ms.to_numpy_u64(s)[0]) == 0 and small.info(pos)["n"] == 0
+        assert small.get_error() == ms.MS_OK
