@@ -16,19 +16,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_mark(MarkArgs a) {
   auto* sm = reinterpret_cast<StreamSmem<kMarkDepth>*>(smem_raw) + warp;
   const ColView c = view_of(a.in);
   const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
+  const uint64_t lo = a.lo, span = a.span;
+  const uint32_t negate = a.negate ? 0xffffu : 0u, live = a.empty ? 0u : 0xffffu;
   stream_chunks<kMarkDepth>(c, gw, W, sm, lane, a.ctl, [&](uint64_t g, const uint64_t* v, int valid) {
     uint32_t m16 = 0;
+    if (a.keybits) {
 #pragma unroll
-    for (int k = 0; k < 16; k++) {
-      bool hit;
-      if (a.keybits) {
+      for (int k = 0; k < 16; k++) {
         const uint64_t x = v[k];
-        hit = x < a.domain && ((__ldg(a.keybits + (x >> 5)) >> (x & 31)) & 1u);
-      } else {
-        hit = pred(a.cmp, v[k], a.c1, a.c2);
+        const bool hit = x < a.domain && ((__ldg(a.keybits + (x >> 5)) >> (x & 31)) & 1u);
+        m16 |= (uint32_t)hit << k;
       }
-      if (hit && 16 * lane + k < valid) m16 |= 1u << k;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; k++) m16 |= (uint32_t)(v[k] - lo <= span) << k;
+      m16 = (m16 ^ negate) & live;
     }
+    // rows past the column's end never match
+    const int first = 16 * lane;
+    m16 &= valid >= first + 16 ? 0xffffu : (valid > first ? (1u << (valid - first)) - 1u : 0u);
     a.bitmap[g * 32 + lane] = (uint16_t)m16;
     const uint32_t cnt = __reduce_add_sync(kFull, (uint32_t)__popc(m16));
     if (lane == 0) a.counts[g] = cnt;

@@ -14,20 +14,6 @@
 
 namespace ms {
 
-// ------------------------------------------------------------------ select core
-
-MS_DEV bool pred(int cmp, uint64_t x, uint64_t c1, uint64_t c2) {
-  switch (cmp) {
-    case MS_EQ: return x == c1;
-    case MS_NE: return x != c1;
-    case MS_LT: return x < c1;
-    case MS_LE: return x <= c1;
-    case MS_GT: return x > c1;
-    case MS_GE: return x >= c1;
-    default: return x >= c1 && x <= c2;
-  }
-}
-
 // Walks the chunks first, first+stride, ... of one column with a per-warp
 // asynchronous stream and calls body(i, g, v, valid) for each decoded chunk.
 template <int D, class Body>
@@ -63,8 +49,9 @@ MS_DEV void stream_chunks(const ColView& c, uint64_t first, uint64_t stride, Str
 struct MarkArgs {
   const DevMeta* in;
   DevCtl* ctl;
-  int cmp;
-  uint64_t c1, c2;
+  // the predicate as one range test: hit = ((x - lo) <= span) != negate, never if empty
+  uint64_t lo, span;
+  uint32_t negate, empty;
   const uint32_t* keybits;  // semi-join: membership bitmap over the key domain
   uint64_t domain;
   uint16_t* bitmap;
@@ -127,7 +114,7 @@ MS_DEV void stream_pairs(const ColView& c0, const ColView& c1, uint64_t n, uint6
 
 // ------------------------------------------------------- produce (map) kernel
 
-enum ProduceOp { OP_COMPRESS = 0, OP_DECOMPRESS = 1, OP_PROJECT = 2, OP_CALC = 3, OP_EMIT = 4 };
+enum ProduceOp { OP_COMPRESS = 0, OP_DECOMPRESS = 1, OP_PROJECT = 2, OP_CALC = 3, OP_EMIT = 4, OP_PROJECT_DELTA = 5 };
 
 struct ProduceArgs {
   DevCtl* ctl;
@@ -174,6 +161,14 @@ struct SmemProject {
   uint32_t list[kBlock];       // data blocks to decode, relative to the first one
   uint16_t runs[32];           // run-start mask per lane
 };
+struct SmemProjectRandom {
+  StreamSmem<kProdDepth> s0;  // positions
+};
+struct SmemProjectDelta {
+  StreamSmem<kProdDepth2> s0;  // positions
+  StreamSmem<kProdDepth> s1;   // the data blocks, one continuous (seekable) stream
+  uint64_t aux[kBlock];        // the data block decoded last
+};
 struct SmemEmit {
   uint32_t bits[kEmitSpan * 16];
   uint64_t coff[kEmitSpan + 2];
@@ -189,9 +184,20 @@ template <int OP>
 struct ProducePlan {
   using Smem = typename std::conditional<
       OP == OP_CALC, SmemPair,
-      typename std::conditional<OP == OP_PROJECT, SmemProject,
-                                typename std::conditional<OP == OP_EMIT, SmemEmit, SmemSingle>::type>::type>::type;
-  static constexpr int kMinBlocks = OP == OP_PROJECT ? MS_PROJECT_MIN_BLOCKS : (OP == OP_CALC ? 1 : 2);
+      typename std::conditional<
+          OP == OP_PROJECT, SmemProjectRandom,
+          typename std::conditional<
+              OP == OP_PROJECT_DELTA, SmemProjectDelta,
+              typename std::conditional<OP == OP_EMIT, SmemEmit, SmemSingle>::type>::type>::type>::type;
+  static constexpr int kMinBlocks =
+      (OP == OP_PROJECT_DELTA || OP == OP_PROJECT) ? MS_PROJECT_MIN_BLOCKS : (OP == OP_CALC ? 1 : 2);
+};
+
+// Direct-offset kernel (k_produce, the no-allocation path) keeps the list-based
+// project layout.
+template <int OP>
+struct DirectPlan {
+  using Smem = typename std::conditional<OP == OP_PROJECT, SmemProject, typename ProducePlan<OP>::Smem>::type;
 };
 
 // Output length of the operator (device-side, may depend on previous kernels).
@@ -199,7 +205,7 @@ template <int OP>
 MS_DEV uint64_t produce_n(const ProduceArgs& a) {
   if (OP == OP_COMPRESS) return a.raw_n;
   if (OP == OP_DECOMPRESS) return min(a.in0->n, a.raw_cap);
-  if (OP == OP_PROJECT) return a.in1->n;
+  if (OP == OP_PROJECT || OP == OP_PROJECT_DELTA) return a.in1->n;
   if (OP == OP_CALC) return a.in1 ? min(a.in0->n, a.in1->n) : a.in0->n;
   return *reinterpret_cast<volatile uint64_t*>(&a.ctl->op_n);  // OP_EMIT
 }
@@ -367,6 +373,169 @@ MS_DEV void project_gather(const ProduceArgs& a, const ColView& d, const uint64_
     if (pending & (1u << k)) v[k] = read_at(d, p[k]);
 }
 
+// project core for DELTA data (a value needs its block's prefix sum, so blocks are
+// decoded whole).  The warp keeps one data stream across its output chunks.
+// While positions advance through nearby blocks, the stream flows; a gap of more
+// than kSeekGap blocks, or a step backwards (unsorted positions), restarts it at
+// the needed block.  Blocks the stream passes over are fetched but not decoded.
+constexpr uint64_t kSeekGap = 4;
+
+template <class Smem, class DS>
+MS_DEV void merge_gather(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
+                         uint64_t v[16], Smem* sm, DS& ds, uint64_t& ds_next, uint64_t& cur_blk) {
+  constexpr int D = kProdDepth;
+  uint32_t pending = 0;
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    v[k] = 0;
+    if (16 * lane + k < valid) {
+      if (p[k] < d.n) pending |= 1u << k;
+      else set_error(a.ctl, MS_ERR_OUT_OF_RANGE, p[k]);
+    }
+  }
+  const uint64_t d_nch = (d.n + kBlock - 1) / kBlock;
+  while (__ballot_sync(kFull, pending) != 0) {
+    uint64_t mb = ~0ull;
+#pragma unroll
+    for (int k = 0; k < 16; k++)
+      if (pending & (1u << k)) mb = min(mb, p[k] / kBlock);
+    const uint64_t B = warp_min(mb);
+    if (B != cur_blk) {
+      const bool live = ds.count > 0 && ds_next < ds.count;
+      const uint64_t nxt = live ? ds.first + ds_next : ~0ull;
+      if (!live || B < nxt || B > nxt + kSeekGap) {  // (re)start the stream at block B
+        cp_async_wait<0>();
+        __syncwarp();
+        ds.first = B;
+        ds.count = d_nch - B;
+        ds_next = 0;
+        ds.prologue();
+        for (int j = 0; j < D - 1; j++) {
+          ds.prologue_step(j);
+          cp_async_commit();
+        }
+      }
+      while (ds.first + ds_next <= B) {
+        cp_async_wait<D - 2>();
+        __syncwarp();
+        ds.step(ds_next);
+        cp_async_commit();
+        if (ds.first + ds_next == B) {
+          uint64_t t[16];
+          ds.decode(ds_next, t, a.ctl);
+#pragma unroll
+          for (int k = 0; k < 16; k++) sm->aux[swz(16 * lane + k)] = t[k];
+        }
+        __syncwarp();
+        ds_next++;
+      }
+      cur_blk = B;
+    }
+    if (mb == B) {  // only lanes with positions in block B gather
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        if ((pending & (1u << k)) && p[k] / kBlock == B) {
+          v[k] = sm->aux[swz((int)(p[k] % kBlock))];
+          pending &= ~(1u << k);
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// project core for non-DELTA data: every position is a random read through the
+// header directory (Sec. 4.2 random access, extended to the dynamic formats).
+// Written without data-dependent branches so that a lane's 16 header loads, and
+// then its payload halfword loads, are all in flight together.
+MS_DEV void gather_random(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
+                          uint64_t v[16]) {
+  uint64_t q[16];
+  uint32_t pending = 0;
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    const bool in = 16 * lane + k < valid;
+    if (in && p[k] >= d.n) set_error(a.ctl, MS_ERR_OUT_OF_RANGE, p[k]);
+    const bool ok = in && p[k] < d.n;
+    pending |= (uint32_t)ok << k;
+    q[k] = ok ? p[k] : 0;
+  }
+  if (d.n == 0) {
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = 0;
+    return;
+  }
+  if (d.fmt == MS_UNCOMPR) {
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = ldg64(d.p + 8 * q[k]);
+  } else {
+    const uint64_t nb = d.fmt == MS_STATIC_BP ? d.n / kBlock : d.nb;
+    const uint64_t rem_base = d.fmt == MS_STATIC_BP ? 64ull * d.bw * nb : 16 * nb + 8 * d.pwords;
+    uint64_t w0[16], ref[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) {  // phase 1: the block headers (or the fixed static width)
+      const uint64_t g = q[k] / kBlock;
+      if (d.fmt == MS_STATIC_BP) {
+        w0[k] = ((64ull * d.bw * g / 8) << 8) | (uint64_t)d.bw;  // payload word offset of chunk g
+        ref[k] = 0;
+      } else {
+        const uint64_t gg = min(g, nb ? nb - 1 : 0);
+        w0[k] = nb ? ldg64(d.p + 16 * gg) : 0;
+        ref[k] = nb ? ldg64(d.p + 16 * gg + 8) : 0;
+      }
+    }
+    const uint64_t pay_base = d.fmt == MS_STATIC_BP ? 0 : 16 * nb;
+#pragma unroll
+    for (int half = 0; half < 2; half++) {  // phase 2: payload halfwords, 8 values at a time
+      uint32_t h[8][5];
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const int k = 8 * half + u;
+        const uint64_t g = q[k] / kBlock;
+        const int r = (int)(q[k] % kBlock);
+        const int b = (int)min((uint64_t)64, w0[k] & 255);
+        const int bit0 = (r & 15) * b, j = r >> 4;
+        const uint64_t pay = pay_base + 8 * (w0[k] >> 8);
+        const bool ok = g < nb && b > 0 && pay + 64ull * b <= d.size;
+        const uint16_t* hw = reinterpret_cast<const uint16_t*>(d.p + (ok ? pay : 0));
+        const int q0 = bit0 >> 4;
+        const int nq = ok ? (((bit0 & 15) + b + 15) >> 4) : 0;
+#pragma unroll
+        for (int t = 0; t < 5; t++) h[u][t] = t < nq ? (uint32_t)__ldg(hw + 32 * (q0 + t) + j) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const int k = 8 * half + u;
+        const uint64_t g = q[k] / kBlock;
+        const int r = (int)(q[k] % kBlock);
+        const int b = (int)min((uint64_t)64, w0[k] & 255);
+        const int sh = ((r & 15) * b) & 15;
+        uint64_t lo = (uint64_t)h[u][0] | ((uint64_t)h[u][1] << 16) | ((uint64_t)h[u][2] << 32) |
+                      ((uint64_t)h[u][3] << 48);
+        uint64_t x = (lo >> sh) | (sh ? ((uint64_t)h[u][4] << (64 - sh)) : 0);
+        x = (x & lowmask(b)) + ref[k];
+        if (g >= nb) {  // remainder (or the horizontal static-BP tail)
+          if (d.fmt == MS_STATIC_BP) {
+            const uint64_t bit = (uint64_t)r * d.bw;
+            const int s2 = (int)(bit & 63);
+            const uint64_t at = rem_base + 8 * (bit >> 6);
+            uint64_t y = at + 8 <= d.size ? ldg64(d.p + at) >> s2 : 0;
+            if (s2 + d.bw > 64 && at + 16 <= d.size) y |= ldg64(d.p + at + 8) << (64 - s2);
+            x = y & lowmask(d.bw);
+          } else {
+            const uint64_t at = rem_base + 8 * (uint64_t)r;
+            x = at + 8 <= d.size ? ldg64(d.p + at) : 0;
+          }
+        }
+        v[k] = (pending >> k) & 1u ? x : 0;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 16; k++)
+    if (!((pending >> k) & 1u)) v[k] = 0;
+}
+
 // emit core: positions of output block g (lane-blocked) from the match bitmap.
 MS_DEV int emit_gather(const ProduceArgs& a, uint64_t n_out, uint64_t g, int lane, uint64_t v[16], SmemEmit* sm) {
   const uint64_t lo = g * kBlock;
@@ -458,7 +627,7 @@ MS_DEV int encode_block(int fmt, uint64_t v[16], int lane, uint64_t* ref_out) {
 
 template <int OP>
 __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_produce(ProduceArgs a) {
-  using Smem = typename ProducePlan<OP>::Smem;
+  using Smem = typename DirectPlan<OP>::Smem;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ uint64_t s_words[kWarps];
   __shared__ uint64_t s_excl;
@@ -765,8 +934,9 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
 
   ColView c0{}, c1{};
   if (OP == OP_COMPRESS) c0 = view_raw(a.raw_in, a.raw_n);
-  if (OP == OP_DECOMPRESS || OP == OP_CALC || OP == OP_PROJECT) c0 = view_of(a.in0);
-  if ((OP == OP_CALC || OP == OP_PROJECT) && a.in1) c1 = view_of(a.in1);
+  constexpr bool kProject = OP == OP_PROJECT || OP == OP_PROJECT_DELTA;
+  if (OP == OP_DECOMPRESS || OP == OP_CALC || kProject) c0 = view_of(a.in0);
+  if ((OP == OP_CALC || kProject) && a.in1) c1 = view_of(a.in1);
   const uint64_t n_out = produce_n<OP>(a);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (OP == OP_DECOMPRESS && a.in0->n > a.raw_cap) set_error(ctl, MS_ERR_INVALID_ARG, a.in0->n);
@@ -777,19 +947,28 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
   const uint64_t nch = (n_out + kBlock - 1) / kBlock;
   const uint64_t static_chunks = n_out / kBlock;
   const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
-  const uint64_t count = gw < nch ? (nch - gw + W - 1) / W : 0;
+  // chunk i of a warp: gw + i*W (interleaved), or, for project, a contiguous segment
+  // so that a warp's data accesses move forward through the data column
+  const uint64_t seg = (nch + W - 1) / W;
+  const uint64_t first = kProject ? gw * seg : gw;
+  const uint64_t stride = kProject ? 1 : W;
+  const uint64_t count = kProject ? (first < nch ? min(seg, nch - first) : 0) : (gw < nch ? (nch - gw + W - 1) / W : 0);
 
-  constexpr int D = (OP == OP_CALC || OP == OP_PROJECT) ? kProdDepth2 : kProdDepth;
+  constexpr int D = (OP == OP_CALC || OP == OP_PROJECT_DELTA) ? kProdDepth2 : kProdDepth;
   StreamSmem<D>* ring0 = nullptr;
   StreamSmem<D>* ring1 = nullptr;
-  if constexpr (OP == OP_COMPRESS || OP == OP_DECOMPRESS || OP == OP_PROJECT) ring0 = &sm->s0;
+  if constexpr (OP == OP_COMPRESS || OP == OP_DECOMPRESS || kProject) ring0 = &sm->s0;
   if constexpr (OP == OP_CALC) {
     ring0 = &sm->s0;
     ring1 = &sm->s1;
   }
-  const ColView main_col = (OP == OP_PROJECT) ? c1 : c0;
-  ChunkStream<D> st0{main_col, gw, W, (OP == OP_EMIT) ? 0 : count, ring0, lane};
-  ChunkStream<D> st1{c1, gw, W, (OP == OP_CALC && a.in1) ? count : 0, ring1, lane};
+  const ColView main_col = kProject ? c1 : c0;
+  ChunkStream<D> st0{main_col, first, stride, (OP == OP_EMIT) ? 0 : count, ring0, lane};
+  ChunkStream<D> st1{c1, first, stride, (OP == OP_CALC && a.in1) ? count : 0, ring1, lane};
+  // DELTA project: one data stream per warp that survives across output chunks
+  ChunkStream<kProdDepth> ds{c0, 0, 1, 0, nullptr, lane};
+  uint64_t ds_next = 0, cur_blk = ~0ull;
+  if constexpr (OP == OP_PROJECT_DELTA) ds.sm = &sm->s1;
   if (OP != OP_EMIT && count) {
     for (int i = 0; i < D; i++) {
       st0.issue_header(i);
@@ -806,7 +985,7 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
   }
 
   for (uint64_t i = 0; i < count; i++) {
-    const uint64_t g = gw + i * W;
+    const uint64_t g = first + i * stride;
     uint64_t v[16];
     int valid = 0;
     uint16_t* out_stage;
@@ -834,10 +1013,14 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
 #pragma unroll
           for (int k = 0; k < 16; k++) v[k] = arith(a.arith, v[k], a.scalar);
         }
-      } else {  // OP_PROJECT: c0 = data, st0 streams the positions (c1)
+      } else if constexpr (OP == OP_PROJECT) {  // c0 = data, st0 streams the positions (c1)
         uint64_t p[16];
         valid = st0.decode(i, p, ctl);
-        project_gather(a, c0, p, valid, lane, v, sm);
+        gather_random(a, c0, p, valid, lane, v);
+      } else {  // OP_PROJECT_DELTA
+        uint64_t p[16];
+        valid = st0.decode(i, p, ctl);
+        merge_gather(a, c0, p, valid, lane, v, sm, ds, ds_next, cur_blk);
       }
       __syncwarp();
     }

@@ -1,4 +1,4 @@
-// ms_map_project.cu -- k_map instantiation(s): OP_PROJECT (compiled on its own for build parallelism).
+// ms_map_project.cu -- k_map instantiation(s): OP_PROJECT (random access) and OP_PROJECT_DELTA (compiled on its own for build parallelism).
 #include "ms_launch.h"
 
 namespace ms {
@@ -6,6 +6,11 @@ namespace ms {
 template <>
 ms_status launch_map<OP_PROJECT>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
   return launch_map_impl<OP_PROJECT>(c, a, n_max, s);
+}
+
+template <>
+ms_status launch_map<OP_PROJECT_DELTA>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
+  return launch_map_impl<OP_PROJECT_DELTA>(c, a, n_max, s);
 }
 
 }  // namespace ms

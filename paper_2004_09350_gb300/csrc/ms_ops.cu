@@ -47,6 +47,23 @@ namespace {
 
 bool owned(ms_ctx* c, const ms_column* col) { return col && col->ctx == c && !col->freed; }
 
+// Every select predicate as one range test over uint64 (Sec. 5.1 point and range
+// predicates): x matches iff ((x - lo) <= span) != negate, and never if empty.
+void predicate_as_range(int cmp, uint64_t c1, uint64_t c2, MarkArgs* m) {
+  const uint64_t kMax = ~0ull;
+  m->negate = 0;
+  m->empty = 0;
+  switch (cmp) {
+    case MS_EQ: m->lo = c1; m->span = 0; break;
+    case MS_NE: m->lo = c1; m->span = 0; m->negate = 1; break;
+    case MS_LT: m->lo = 0; m->span = c1 - 1; m->empty = c1 == 0; break;
+    case MS_LE: m->lo = 0; m->span = c1; break;
+    case MS_GT: m->lo = c1 + 1; m->span = kMax - c1 - 1; m->empty = c1 == kMax; break;
+    case MS_GE: m->lo = c1; m->span = kMax - c1; break;
+    default: m->lo = c1; m->span = c2 - c1; m->empty = c2 < c1; break;  // MS_BETWEEN
+  }
+}
+
 // Launches k_map<OP> into a new arena column and, for block formats, places the
 // staged blocks.
 template <int OP>
@@ -128,9 +145,7 @@ ms_status ms_select(ms_ctx* c, const ms_column* in, int cmp, uint64_t c1, uint64
   MarkArgs m{};
   m.in = c->metas + in->slot;
   m.ctl = c->ctl;
-  m.cmp = cmp;
-  m.c1 = c1;
-  m.c2 = c2;
+  predicate_as_range(cmp, c1, c2, &m);
   st = launch_mark_scan(c, m, w, in->n_max, s);
   if (st != MS_OK) return st;
   return emit_positions(c, w, in->n_max, fmt, bw, out, s);
@@ -147,6 +162,9 @@ ms_status ms_project(ms_ctx* c, const ms_column* data, const ms_column* pos, int
   ProduceArgs a{};
   a.in0 = c->metas + data->slot;
   a.in1 = c->metas + pos->slot;
+  // DELTA data needs whole-block decoding (prefix sums); every other format is read
+  // at random through its header directory
+  if (data->fmt == MS_DELTA_BP) return produce_column<OP_PROJECT_DELTA>(c, a, w, pos->n_max, fmt, bw, out, s);
   return produce_column<OP_PROJECT>(c, a, w, pos->n_max, fmt, bw, out, s);
 }
 
