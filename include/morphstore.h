@@ -254,6 +254,47 @@ ms_status ms_compress_noalloc(const uint64_t *d_in, uint64_t n, int fmt, int sta
                               void *d_out, uint64_t out_cap, uint64_t *d_result,
                               void *stream);
 
+/* ------------------------------------------------------ format selector */
+
+/* The paper chooses formats with a gray-box cost model (Sec. 5.2, "Determining a
+   good format combination") that it does not print.  This library learns one
+   instead.  A small MLP maps 16 statistics of an intermediate to the predicted
+   log2 bytes per value and log2 nanoseconds per value of each of the five formats
+   (outputs 0..4: size, 5..9: time, in ms_fmt order).  Labels come from the engine
+   itself, by compressing every intermediate into every format (the exhaustive
+   try-all choice, which also judges the selector's regret).
+
+   Network: 16 -> 64 -> 64 -> 10, ReLU between layers, fp32.  Parameters are
+   one packed array: W1[16][64], b1[64], W2[64][64], b2[64], W3[64][10], b3[10],
+   row-major with the input index first (MS_MLP_PARAMS floats). */
+#define MS_MLP_PARAMS 5898
+
+/* y[n][10] = MLP(x[n][16]) (all device memory). */
+ms_status ms_mlp_forward(const float *d_params, const float *d_x, uint64_t n, float *d_y,
+                         void *stream);
+/* Loss L = inv_count * sum over samples r and outputs o of mask[r][o] *
+   (y_hat[r][o] - y[r][o])^2, and its gradient dL/dparams into d_grad
+   (MS_MLP_PARAMS floats) and L into *d_loss.  d_partials is caller scratch of
+   partials_floats floats (at least MS_MLP_PARAMS + 1).  More scratch lets more
+   CTAs share the samples.  The result is deterministic: partial gradients are
+   summed in a fixed order. */
+ms_status ms_mlp_loss_grad(const float *d_params, const float *d_x, const float *d_y,
+                           const float *d_mask, uint64_t n, float inv_count, float *d_grad,
+                           float *d_loss, float *d_partials, uint64_t partials_floats,
+                           void *stream);
+/* One Adam step (Kingma & Ba 2015) on d_params with moments d_m, d_v; step >= 1. */
+ms_status ms_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, uint64_t step,
+                      float lr, float beta1, float beta2, float eps, void *stream);
+
+/* Statistics of a column, one decoding pass, into d_stats (MS_STATS_WORDS device
+   words, overwritten).  For 512-value chunks (the last may be partial):
+   [0] n, [1] maximum value, [2] chunks, [3] sum of bw(max - min) per chunk,
+   [4] sum of bw(largest difference to the predecessor) per chunk,
+   [5] pairs with x_i >= x_{i-1} inside chunks, [6] pairs with x_i != x_{i-1}
+   inside chunks, [8 + b] chunks whose maximum has bit width b (b = 0..64). */
+#define MS_STATS_WORDS 80
+ms_status ms_column_stats(ms_ctx *ctx, const ms_column *col, uint64_t *d_stats, void *stream);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Kernels of the library, as reported by ms_profile_collect. */
@@ -271,7 +312,8 @@ typedef enum {
   MS_K_SCAN = 10,      /* select / semi-join: exclusive scan of per-chunk match counts */
   MS_K_PLACE_SCAN = 11, /* block-format outputs: payload offsets and headers */
   MS_K_PLACE_COPY = 12, /* block-format outputs: payload placement */
-  MS_K_COUNT = 13
+  MS_K_STATS = 13,      /* column statistics for the format selector */
+  MS_K_COUNT = 14
 } ms_kernel;
 
 typedef struct {

@@ -182,7 +182,71 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_keys(const DevMeta* keys,
 }
 
 
+// Column statistics for the format selector (see ms_column_stats): one decoding
+// pass, per chunk reductions, block-level accumulation in shared memory, one
+// global atomic per statistic per CTA.
+__global__ void __launch_bounds__(kThreads, 2) k_stats(const DevMeta* in, uint64_t* stats, DevCtl* ctl) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  __shared__ unsigned long long s_acc[MS_STATS_WORDS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < MS_STATS_WORDS; i += blockDim.x) s_acc[i] = 0;
+  __syncthreads();
+  auto* sm = reinterpret_cast<StreamSmem<kMarkDepth>*>(smem_raw) + warp;
+  const ColView c = view_of(in);
+  const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
+  stream_chunks<kMarkDepth>(c, gw, W, sm, lane, ctl, [&](uint64_t, const uint64_t* v, int valid) {
+    uint64_t mx = 0, mn = ~0ull, dmax = 0;
+    uint32_t sorted = 0, runs = 0;
+    const uint64_t prev_last = __shfl_up_sync(kFull, v[15], 1);
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const int i = 16 * lane + k;
+      if (i < valid) {
+        mx = max(mx, v[k]);
+        mn = min(mn, v[k]);
+        if (i > 0) {
+          const uint64_t prev = k ? v[k - 1] : prev_last;
+          dmax = max(dmax, v[k] - prev);
+          sorted += v[k] >= prev;
+          runs += v[k] != prev;
+        }
+      }
+    }
+    uint64_t cmx = mx;
+#pragma unroll
+    for (int d = 16; d; d >>= 1) cmx = max(cmx, __shfl_xor_sync(kFull, cmx, d));
+    const uint64_t cmn = warp_min(mn);
+    uint64_t cdm = dmax;
+#pragma unroll
+    for (int d = 16; d; d >>= 1) cdm = max(cdm, __shfl_xor_sync(kFull, cdm, d));
+    const uint32_t s_sorted = __reduce_add_sync(kFull, sorted), s_runs = __reduce_add_sync(kFull, runs);
+    if (lane == 0 && valid > 0) {
+      atomicMax(&s_acc[1], (unsigned long long)cmx);
+      atomicAdd(&s_acc[2], 1ull);
+      atomicAdd(&s_acc[3], (unsigned long long)bw64(cmx - cmn));
+      atomicAdd(&s_acc[4], (unsigned long long)bw64(cdm));
+      atomicAdd(&s_acc[5], (unsigned long long)s_sorted);
+      atomicAdd(&s_acc[6], (unsigned long long)s_runs);
+      atomicAdd(&s_acc[8 + bw64(cmx)], 1ull);
+    }
+  });
+  __syncthreads();
+  for (int i = threadIdx.x; i < MS_STATS_WORDS; i += blockDim.x) {
+    if (i == 1) atomicMax(reinterpret_cast<unsigned long long*>(stats) + 1, s_acc[1]);
+    else if (i != 0 && s_acc[i]) atomicAdd(reinterpret_cast<unsigned long long*>(stats) + i, s_acc[i]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) stats[0] = c.n;
+}
+
 constexpr size_t kStreamSmem = sizeof(StreamSmem<kMarkDepth>) * kWarps;
+
+ms_status launch_stats(ms_ctx* c, const DevMeta* in, uint64_t* d_stats, uint64_t n_max, cudaStream_t s) {
+  const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
+  const int grid = grid_for(c, k_stats, kStreamSmem, tiles);
+  ProfScope ps(c, MS_K_STATS, s);
+  k_stats<<<grid, kThreads, kStreamSmem, s>>>(in, d_stats, c->ctl);
+  return cuda_status(cudaGetLastError());
+}
 
 ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max, cudaStream_t s) {
   a.bitmap = w.bitmap;

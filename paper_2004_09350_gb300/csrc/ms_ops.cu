@@ -225,4 +225,11 @@ ms_status ms_semijoin(ms_ctx* c, const ms_column* probe, const ms_column* keys, 
   return emit_positions(c, w, probe->n_max, fmt, bw, out, s);
 }
 
+ms_status ms_column_stats(ms_ctx* c, const ms_column* col, uint64_t* d_stats, void* stream) {
+  if (!c || !owned(c, col) || !d_stats) return MS_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cuda_status(cudaMemsetAsync(d_stats, 0, 8 * MS_STATS_WORDS, s)) != MS_OK) return MS_ERR_CUDA;
+  return launch_stats(c, c->metas + col->slot, d_stats, col->n_max, s);
+}
+
 }  // extern "C"

@@ -86,6 +86,10 @@ def load() -> ctypes.CDLL:
         "ms_group_sum": [p, p, p, u64, p, p],
         "ms_semijoin": [p, p, p, u64, i32, i32, pp, p],
         "ms_compress_noalloc": [p, u64, i32, i32, p, u64, p, p],
+        "ms_column_stats": [p, p, p, p],
+        "ms_mlp_forward": [p, p, u64, p, p],
+        "ms_mlp_loss_grad": [p, p, p, p, u64, ctypes.c_float, p, p, p, u64, p],
+        "ms_mlp_adam": [p, p, p, p, u64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, p],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -230,6 +234,15 @@ class Ctx:
     def reset_high_water(self, stream=None):
         _check(load().ms_arena_reset_high_water(self.h, _stream_handle(stream)), "reset_high_water")
 
+    # ---------------------------------------------------------- statistics
+    def column_stats(self, col: Column, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """ms_column_stats into an int64 device tensor of STATS_WORDS words."""
+        if out is None:
+            out = torch.empty(STATS_WORDS, dtype=torch.int64, device=self.device)
+        _check(load().ms_column_stats(self.h, col.ptr, ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+               "ms_column_stats")
+        return out
+
     # ------------------------------------------------------------- profiling
     def profile(self, on: bool = True):
         _check(load().ms_profile_enable(self.h, 1 if on else 0), "ms_profile_enable")
@@ -340,6 +353,33 @@ class Ctx:
 
 
 NOALLOC_MAX_ROWS = 1 << 24
+MLP_PARAMS = 5898
+STATS_WORDS = 80
+
+
+def _dp(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mlp_forward(params: torch.Tensor, x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """ms_mlp_forward: y[n][10] = MLP(x[n][16]) on the device (fp32)."""
+    n = x.shape[0]
+    if out is None:
+        out = torch.empty((n, 10), dtype=torch.float32, device=x.device)
+    _check(load().ms_mlp_forward(_dp(params), _dp(x), n, _dp(out), _stream_handle(stream)), "ms_mlp_forward")
+    return out
+
+
+def mlp_loss_grad(params, x, y, mask, inv_count: float, grad, loss, partials, stream=None):
+    """ms_mlp_loss_grad into the caller's grad (5898 floats), loss (1 float) and scratch."""
+    _check(load().ms_mlp_loss_grad(_dp(params), _dp(x), _dp(y), _dp(mask), x.shape[0], float(inv_count),
+                                   _dp(grad), _dp(loss), _dp(partials), partials.numel(), _stream_handle(stream)),
+           "ms_mlp_loss_grad")
+
+
+def mlp_adam(params, grad, m, v, step: int, lr=3e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().ms_mlp_adam(_dp(params), _dp(grad), _dp(m), _dp(v), step, lr, beta1, beta2, eps,
+                              _stream_handle(stream)), "ms_mlp_adam")
 
 
 def compress_noalloc(d_in: torch.Tensor, fmt: int, d_out: torch.Tensor, d_result: torch.Tensor,

@@ -1,0 +1,109 @@
+"""Learned format selector: the library's MLP kernels against the fp64 reference,
+the GPU column statistics against their plain definition, and the trained
+selector's regret against the exhaustive try-all-formats choice."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp
+from paper_2004_09350_gb300 import morphstore as ms
+from paper_2004_09350_gb300 import selector, synth
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.random((n, 16)).astype(np.float32)
+    y = rng.normal(size=(n, 10)).astype(np.float32)
+    m = (rng.random((n, 10)) < 0.9).astype(np.float32)
+    return x, y, m
+
+
+def test_mlp_forward_matches_reference():
+    theta = mlp.init(1).astype(np.float32)
+    x, _, _ = _data(1000, 2)
+    got = ms.mlp_forward(torch.from_numpy(theta).to(DEV), torch.from_numpy(x).to(DEV)).cpu().numpy()
+    want, _ = mlp.forward(theta.astype(np.float64), x.astype(np.float64))
+    np.testing.assert_allclose(got, want, rtol=1e-4, atol=1e-4)
+
+
+@pytest.mark.parametrize("n", [1, 37, 3000])
+def test_mlp_gradient_matches_reference(n):
+    theta = mlp.init(3).astype(np.float32)
+    x, y, m = _data(n, 4)
+    inv = 1.0 / max(m.sum(), 1.0)
+    grad = torch.zeros(ms.MLP_PARAMS, device=DEV)
+    loss = torch.zeros(1, device=DEV)
+    parts = torch.zeros(700 * (ms.MLP_PARAMS + 1), device=DEV)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    ms.mlp_loss_grad(t(theta), t(x), t(y), t(m), inv, grad, loss, parts)
+    L, g = mlp.loss_grad(theta.astype(np.float64), x, y, m, inv)
+    assert abs(float(loss.item()) - L) <= 1e-4 * abs(L) + 1e-7
+    got = grad.cpu().numpy()
+    scale = np.abs(g).max()
+    np.testing.assert_allclose(got, g, rtol=1e-3, atol=1e-4 * scale)
+    # deterministic: the same call gives the same bits
+    grad2 = torch.zeros_like(grad)
+    ms.mlp_loss_grad(t(theta), t(x), t(y), t(m), inv, grad2, loss, parts)
+    assert torch.equal(grad, grad2)
+
+
+def test_mlp_training_reduces_loss():
+    x, _, _ = _data(2000, 5)
+    # a learnable target: fixed random linear map of the features
+    w = np.random.default_rng(6).normal(size=(16, 10))
+    y = (x @ w).astype(np.float32)
+    sel = selector.Selector(DEV, seed=7)
+    hist = sel.train(x, y, epochs=300, lr=3e-3)
+    assert hist[-1][1] < 0.1 * hist[0][1]
+
+
+def _plain_stats(x):
+    n = x.size
+    st = np.zeros(80, dtype=np.uint64)
+    st[0] = n
+    if n == 0:
+        return st
+    st[1] = x.max()
+    for c in range(0, n, 512):
+        blk = x[c:c + 512].astype(object)
+        st[2] += 1
+        st[3] += (max(blk) - min(blk)).bit_length()
+        d = [(blk[i] - blk[i - 1]) % 2**64 for i in range(1, len(blk))]
+        st[4] += (max(d) if d else 0).bit_length()
+        st[5] += sum(1 for i in range(1, len(blk)) if blk[i] >= blk[i - 1])
+        st[6] += sum(1 for i in range(1, len(blk)) if blk[i] != blk[i - 1])
+        st[8 + max(blk).bit_length()] += 1
+    return st
+
+
+@pytest.mark.parametrize("fmt", [ms.UNCOMPR, ms.DYN_BP, ms.DELTA_BP])
+@pytest.mark.parametrize("kind", ["skewed", "sorted", "C2"])
+def test_column_stats_match_plain_definition(fmt, kind):
+    n = 6 * 512 + 77
+    x = {"skewed": synth.skewed_widths(1, n), "sorted": synth.sorted_gaps(2, n),
+         "C2": synth.table1_column("C2", n)}[kind]
+    with ms.Ctx(0, arena_bytes=64 << 20, max_rows=n) as ctx:
+        col = ctx.compress(ms.as_device_u64(x, DEV), fmt)
+        got = ctx.column_stats(col).cpu().numpy().view(np.uint64)
+        ctx.check()
+    np.testing.assert_array_equal(got, _plain_stats(x))
+
+
+def test_selector_regret_against_exhaustive_choice():
+    with ms.Ctx(0, arena_bytes=1 << 30, max_rows=1 << 20) as ctx:
+        items = list(selector.synthetic_intermediates(11, 330, lo_log2=14, hi_log2=18))
+        X, Y, S, T, names = selector.harvest(ctx, items, reps=1)
+    rng = np.random.default_rng(0)
+    idx = rng.permutation(len(X))
+    tr, te = idx[:264], idx[264:]
+    sel = selector.Selector(DEV, seed=1)
+    sel.train(X[tr], Y[tr], epochs=600, lr=3e-3)
+    chosen = sel.choose(X[te], "size")
+    r = selector.regret(chosen, S[te])
+    static_all = selector.regret(np.full(len(te), ms.STATIC_BP), S[te])
+    best_fixed = min(selector.regret(np.full(len(te), f), S[te]) for f in range(5))
+    assert r <= 0.05, r
+    assert r < static_all and r < best_fixed, (r, static_all, best_fixed)
