@@ -51,9 +51,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=2020)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["sweep-plan", "star"], default="sweep-plan",
+    ap.add_argument("--workload", choices=["sweep-plan", "star", "selector"], default="sweep-plan",
                     help="sweep-plan: the 2^28-row select/project/calc/sum plan (default); "
-                         "star: the star-schema plan on a 6e8-row fact table")
+                         "star: the star-schema plan on a 6e8-row fact table; "
+                         "selector: train the learned format selector on engine traces and judge it")
+    ap.add_argument("--selector-items", type=int, default=3000)
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
     return a
@@ -569,8 +571,109 @@ def bench_star(args):
             "cpu_baseline": cpu}
 
 
+# ------------------------------------------------------- learned selector
+
+PLAN_INTERMEDIATES = ("P", "X'", "K'", "Y")
+
+
+def plan_time(ctx, cx, ck, c, fm, res, reps=3):
+    import torch
+    for _ in range(2):
+        free_all(ctx, run_plan(ctx, cx, ck, c, fm, res))
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(reps):
+        free_all(ctx, run_plan(ctx, cx, ck, c, fm, res))
+    t1.record()
+    t1.synchronize()
+    return t0.elapsed_time(t1) / reps
+
+
+def bench_selector(args):
+    import torch
+    from paper_2004_09350_gb300 import morphstore as ms
+    from paper_2004_09350_gb300 import selector, synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = ms.Ctx(0, arena_bytes=3 << 30, max_rows=1 << 22)
+    # ---- 1. traces: every intermediate compressed into every format
+    t_h = time.perf_counter()
+    items = list(selector.synthetic_intermediates(args.seed, args.selector_items, lo_log2=14, hi_log2=22))
+    X, Y, S, T, names = selector.harvest(ctx, items, reps=2)
+    harvest_s = time.perf_counter() - t_h
+    ctx.close()
+    idx = np.random.default_rng(args.seed).permutation(len(X))
+    cut = int(0.8 * len(X))
+    tr, te = idx[:cut], idx[cut:]
+    # ---- 2. training with the library's kernels
+    sel = selector.Selector(dev, seed=args.seed)
+    t_t = time.perf_counter()
+    hist = sel.train(X[tr], Y[tr], epochs=800, lr=3e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t_t
+    held = {}
+    for obj, costs in (("size", S[te]), ("time", T[te])):
+        chosen = sel.choose(X[te], obj)
+        held[obj] = {"regret": round(selector.regret(chosen, costs), 4),
+                     "static_bp_for_all_regret": round(selector.regret(np.full(len(te), 1), costs), 4),
+                     "best_fixed_format_regret": round(min(selector.regret(np.full(len(te), f), costs)
+                                                           for f in range(5)), 4)}
+    # ---- 3. the 2^28-row plan with formats picked from a prefix sample
+    n = args.rows
+    x, k, c = make_inputs(n, args.seed, args.selectivity)
+    ctx = ms.Ctx(0, arena_bytes=int(2.5 * 8 * n) + (1 << 30), max_rows=n)
+    res = torch.zeros(1, dtype=torch.int64, device=dev)
+    cx = ctx.compress(ms.as_device_u64(x, dev), ms.DYN_BP)
+    ck = ctx.compress(ms.as_device_u64(k, dev), ms.DELTA_BP)
+    sample = 1 << 16
+    sx = ctx.compress(ms.as_device_u64(x[:sample], dev), ms.UNCOMPR)
+    sk = ctx.compress(ms.as_device_u64(k[:sample], dev), ms.UNCOMPR)
+    cols = run_plan(ctx, sx, sk, c, UNCOMPRESSED, res)  # [Y, K', X', P]
+    ops = {"P": ("select", False), "X'": ("project", False), "K'": ("project", False), "Y": ("calc", False)}
+    feats = {name: selector.column_features(ctx, col, *ops[name], n_scale=n / sample)
+             for name, col in zip(("Y", "K'", "X'", "P"), cols)}
+    free_all(ctx, cols)
+    for col in (sk, sx):
+        ctx.free(col)
+    plan_formats = (ms.UNCOMPR, ms.DYN_BP, ms.DELTA_BP, ms.FOR_BP)
+    picks = {name: int(sel.choose(feats[name], "time", allowed=plan_formats)[0]) for name in PLAN_INTERMEDIATES}
+    fm_sel = {name: ms.FORMAT_NAMES[picks[name]] for name in PLAN_INTERMEDIATES}
+    # greedy per-intermediate runtime search (Sec. 5.2): one intermediate at a time,
+    # try every format, keep the fastest, move on
+    fm_g = dict(COMPRESSED)
+    for name in PLAN_INTERMEDIATES:
+        best = None
+        for f in ms.FORMAT_NAMES:
+            if f == "static_bp":
+                continue  # static BP needs a width known only after the intermediate exists
+            trial = dict(fm_g, **{name: f})
+            t = plan_time(ctx, cx, ck, c, trial, res)
+            if best is None or t < best[0]:
+                best = (t, f)
+        fm_g[name] = best[1]
+    t_sel = plan_time(ctx, cx, ck, c, dict(COMPRESSED, **fm_sel), res, reps=10)
+    t_greedy = plan_time(ctx, cx, ck, c, fm_g, res, reps=10)
+    t_fixed = plan_time(ctx, cx, ck, c, COMPRESSED, res, reps=10)
+    ctx.check(what="selector plans")
+    ctx.close()
+    return {"workload": "selector", "metric": "learned format selector: regret vs exhaustive choice",
+            "items": len(X), "train_items": len(tr), "heldout_items": len(te),
+            "harvest_s": round(harvest_s, 1), "train_s": round(train_s, 2),
+            "loss_first_last": [hist[0][1], hist[-1][1]], "heldout": held,
+            "plan_2e28": {"rows": n, "selector_formats": fm_sel, "greedy_formats": {k2: fm_g[k2] for k2 in PLAN_INTERMEDIATES},
+                          "ms_selector": round(t_sel, 4), "ms_greedy_search": round(t_greedy, 4),
+                          "ms_fixed_formats": round(t_fixed, 4),
+                          "regret_vs_greedy": round(t_sel / t_greedy - 1.0, 4)},
+            "note": "time labels: write + one read of the intermediate; static BP excluded from the plan search "
+                    "because its width must be known before the intermediate exists"}
+
+
 def main():
     args = parse()
+    if args.workload == "selector" and args.impl == "ours":
+        print(json.dumps(bench_selector(args)))
+        return
     if args.workload == "star" and args.impl == "ours":
         print(json.dumps(bench_star(args)))
         return

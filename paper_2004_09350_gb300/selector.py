@@ -148,9 +148,16 @@ class Selector:
         y = ms.mlp_forward(self.params, x).cpu().numpy()
         return y * self.sd + self.mu
 
-    def choose(self, X: np.ndarray, objective: str = "size") -> np.ndarray:
+    def choose(self, X: np.ndarray, objective: str = "size", allowed=None) -> np.ndarray:
+        """Format with the smallest predicted cost; `allowed` restricts the candidates
+        (a plan cannot pick static BP before the intermediate's width is known)."""
         y = self.predict(np.atleast_2d(X))
-        return np.argmin(y[:, :5] if objective == "size" else y[:, 5:], axis=1)
+        cost = (y[:, :5] if objective == "size" else y[:, 5:]).copy()
+        if allowed is not None:
+            mask = np.ones(5, dtype=bool)
+            mask[list(allowed)] = False
+            cost[:, mask] = np.inf
+        return np.argmin(cost, axis=1)
 
 
 def regret(chosen: np.ndarray, costs: np.ndarray) -> float:
