@@ -51,11 +51,15 @@ def parse():
     ap.add_argument("--seed", type=int, default=2020)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["sweep-plan", "star", "selector"], default="sweep-plan",
+    ap.add_argument("--workload", choices=["sweep-plan", "star", "selector", "batch"], default="sweep-plan",
                     help="sweep-plan: the 2^28-row select/project/calc/sum plan (default); "
                          "star: the star-schema plan on a 6e8-row fact table; "
-                         "selector: train the learned format selector on engine traces and judge it")
+                         "selector: train the learned format selector on engine traces and judge it; "
+                         "batch: 4096 select->project->agg_sum fragments in one persistent launch")
     ap.add_argument("--selector-items", type=int, default=3000)
+    ap.add_argument("--fragments", type=int, default=4096)
+    ap.add_argument("--batch-max-log2", type=float, default=24.0)
+    ap.add_argument("--batch-train-items", type=int, default=400)
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
     return a
@@ -669,8 +673,187 @@ def bench_selector(args):
                     "because its width must be known before the intermediate exists"}
 
 
+# ------------------------------------------------------- batched fragments
+
+def _events_ms(fn, steps, stream):
+    """Per-step device milliseconds of fn() (CUDA events on `stream`)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+
+def oracle_fragment(sp):
+    import oracle
+    from paper_2004_09350_gb300 import synth
+    x, y = synth.batch_x(sp), synth.batch_y(sp)
+    t = time.perf_counter()
+    pos = oracle.select(x, sp["cmp"], sp["c1"], sp["c2"])
+    s = oracle.agg_sum(oracle.project(y, pos))
+    return s, time.perf_counter() - t
+
+
+def column_bound(n, fmt, bits):
+    """Upper bound of a column's bytes in `fmt` for values of at most `bits` bits."""
+    nb = n // BLOCK
+    if fmt == 0:
+        return 8 * n
+    if fmt == 1:
+        return (n * bits + 63) // 64 * 8
+    w = 64 if fmt == 3 else bits
+    return 16 * nb + nb * 64 * w + 8 * (n % BLOCK) + 256
+
+
+def bench_batch(args):
+    import torch
+    from paper_2004_09350_gb300 import autotune, selector, synth
+    from paper_2004_09350_gb300 import morphstore as ms
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    F = args.fragments
+    specs = synth.batch_fragments(args.seed, F, lo_log2=10, hi_log2=args.batch_max_log2)
+    rows = sum(sp["n"] for sp in specs)
+    max_n = max(sp["n"] for sp in specs)
+    # ---- 1. the format selector, trained on engine traces with the library's kernels
+    t_s = time.perf_counter()
+    hctx = ms.Ctx(0, arena_bytes=1 << 30, max_rows=1 << 18)
+    items = list(selector.synthetic_intermediates(args.seed + 1, args.batch_train_items, lo_log2=12, hi_log2=18))
+    X, Y, _, _, _ = selector.harvest(hctx, items, reps=1)
+    hctx.close()
+    sel = selector.Selector(dev, seed=args.seed)
+    sel.train(X, Y, epochs=800, lr=3e-3)
+    # ---- 2. statistics of every base column, then one batched prediction
+    gens = (synth.batch_x_torch, synth.batch_y_torch)
+    sctx = ms.Ctx(0, arena_bytes=8 * max_n + (64 << 20), max_rows=max_n)
+    stats = torch.zeros((2 * F, ms.STATS_WORDS), dtype=torch.int64, device=dev)
+    for f, sp in enumerate(specs):
+        for j in range(2):
+            col = sctx.compress(gens[j](sp, dev), ms.UNCOMPR)
+            sctx.column_stats(col, out=stats[2 * f + j])
+            sctx.free(col)
+    sctx.check(what="batch statistics")
+    sctx.close()
+    st = stats.cpu().numpy().view(np.uint64)
+    feats = np.stack([selector.features_from_stats(st[i], "base") for i in range(2 * F)])
+    fmts = sel.choose(feats, "size", allowed=(ms.STATIC_BP, ms.DYN_BP, ms.DELTA_BP, ms.FOR_BP))
+    bits = [max(1, int(st[i][1]).bit_length()) for i in range(2 * F)]
+    setup_sel_s = time.perf_counter() - t_s
+    # ---- 3. the base columns in the chosen formats
+    arena = sum(column_bound(specs[i // 2]["n"], int(fmts[i]), bits[i]) for i in range(2 * F)) + (1 << 30)
+    ctx = ms.Ctx(0, arena_bytes=arena, max_rows=max_n)
+    cols = []
+    for f, sp in enumerate(specs):
+        for j in range(2):
+            i = 2 * f + j
+            cols.append(ctx.compress(gens[j](sp, dev), int(fmts[i]), bits[i] if fmts[i] == ms.STATIC_BP else 0))
+    ctx.check(what="batch base columns")
+    batch = ms.Batch(ctx, cols[0::2], cols[1::2], [sp["cmp"] for sp in specs], [sp["c1"] for sp in specs],
+                     [sp["c2"] for sp in specs])
+    info = batch.info()
+    sums = torch.zeros(F, dtype=torch.int64, device=dev)
+    # ---- 4. autotuning (every candidate gives the same bits)
+    best, table = autotune.tune(batch, sums, reps=3, use_cache=False)
+    default_ms = table.get(ms.DEFAULT_BATCH_CONFIG) or autotune.time_config(batch, sums, ms.DEFAULT_BATCH_CONFIG)
+    # ---- 5. timing: one persistent launch (graph) vs one launch per fragment
+    g_one = batch.graph(sums, cfg=best)
+    for _ in range(args.warmup):
+        g_one.launch(stream)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    t_wall = time.perf_counter()
+    one = _events_ms(lambda: g_one.launch(stream), args.steps, stream)
+    while time.perf_counter() - t_wall < 1.0:  # let the clock sampler see the load
+        one += _events_ms(lambda: g_one.launch(stream), args.steps, stream)
+    clk = clocks.stop()
+    got = ms.to_numpy_u64(sums).copy()
+    ctx.profile(True)
+    for _ in range(args.steps):
+        batch.run(sums, cfg=best, stream=stream)
+    prof = ctx.profile_collect()
+    ctx.profile(False)
+    k_ms = prof["batch"][1] / prof["batch"][0]
+    each = _events_ms(lambda: batch.run(sums, cfg=best, per_fragment=True, stream=stream), args.warmup, stream)
+    each = _events_ms(lambda: batch.run(sums, cfg=best, per_fragment=True, stream=stream), args.steps, stream)
+    got_each = ms.to_numpy_u64(sums).copy()
+    g_each = batch.graph(sums, cfg=best, per_fragment=True)
+    _events_ms(lambda: g_each.launch(stream), args.warmup, stream)
+    each_g = _events_ms(lambda: g_each.launch(stream), args.steps, stream)
+    g_each.close()
+    ctx.check(what="batch runs")
+    # operator-at-a-time per fragment: ms_select -> ms_project -> ms_agg_sum
+    res = torch.zeros(F, dtype=torch.int64, device=dev)
+
+    def op_at_a_time():
+        for f in range(F):
+            pos = ctx.select(cols[2 * f], specs[f]["cmp"], specs[f]["c1"], specs[f]["c2"], fmt=ms.DELTA_BP)
+            yv = ctx.project(cols[2 * f + 1], pos, fmt=ms.DYN_BP)
+            ctx.agg_sum(yv, out=res[f:f + 1])
+            ctx.free(yv)
+            ctx.free(pos)
+    op_at_a_time()
+    ops_ms = _events_ms(op_at_a_time, 1, stream)[0]
+    ctx.check(what="operator-at-a-time fragments")
+    got_ops = ms.to_numpy_u64(res).copy()
+    assert (got == got_each).all() and (got == got_ops).all(), "batched runs disagree"
+    # ---- 6. parity against the oracle on sampled fragments, and the CPU baseline
+    order = np.argsort([sp["n"] for sp in specs])
+    rng = np.random.default_rng(args.seed)
+    sample = sorted(set(order[-4:].tolist()) | set(order[:4].tolist()) | set(rng.choice(F, 4, replace=False).tolist()))
+    mism, cpu_rows, cpu_t = 0, 0, 0.0
+    for f in sample:
+        want, t = oracle_fragment(specs[f])
+        mism += int(want != int(got[f]))
+        cpu_rows += specs[f]["n"]
+        cpu_t += t
+    med = statistics.median(one)
+    peak, peak_kind = peaks()
+    achieved = info["bytes"] / (k_ms * 1e-3) / 1e9
+    batch.close()
+    g_one.close()
+    counts = {ms.FORMAT_NAMES[k]: int((fmts == k).sum()) for k in range(5)}
+    ctx.close()
+    return {
+        "metric": "aggregate rows/s of batched select->project->agg_sum fragments", "workload": "batch",
+        "value": rows / (med * 1e-3), "unit": "rows/s", "n_gpus": 1, "steps": len(one), "warmup": args.warmup,
+        "ms_per_step": round(med, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic (seeded SplitMix64, generated on the GPU)",
+        "config": {"workload": f"{F} fragments sum(y[i] for x[i] <cmp> c), lengths log-uniform in "
+                               f"[2^10, 2^{args.batch_max_log2:g}], x ~ U[0,2^bx), y uniform/offset/sorted/skewed "
+                               f"at width by, bx, by ~ U[1,40]; base formats chosen by the learned selector",
+                   "fragments": F, "rows": info["rows"], "chunks": info["chunks"], "bytes": info["bytes"],
+                   "l2": "inputs larger than L2 (no flush)", "launch": "one persistent launch in a CUDA graph"},
+        "gb_per_s": info["bytes"] / (med * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "k_batch", "kernel_ms": round(k_ms, 4)},
+        "per_fragment_launches": {"ms_per_step": round(statistics.median(each), 3),
+                                  "rows_per_s": rows / (statistics.median(each) * 1e-3),
+                                  "speedup_of_one_launch": round(statistics.median(each) / med, 2)},
+        "per_fragment_graph": {"ms_per_step": round(statistics.median(each_g), 3),
+                               "speedup_of_one_launch": round(statistics.median(each_g) / med, 2)},
+        "operator_at_a_time": {"ms_per_step": round(ops_ms, 2), "speedup_of_one_launch": round(ops_ms / med, 1)},
+        "autotune": {"best": list(best), "best_ms": round(table[best], 4), "default_ms": round(default_ms, 4),
+                     "worst_ms": round(max(table.values()), 4), "candidates": len(table)},
+        "selector": {"train_items": len(X), "setup_s": round(setup_sel_s, 1), "base_formats": counts},
+        "parity": {"sampled_fragments": len(sample), "mismatches": mism, "all_launch_modes_agree": True},
+        "cpu_baseline": {"value": cpu_rows / cpu_t, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(sample)} fragments ({cpu_rows} rows) through the oracle's "
+                                   f"select, project and agg_sum ({cpu_t:.1f} s)"},
+        "clocks": clk, "gpu_launches": len(one),
+    }
+
+
 def main():
     args = parse()
+    if args.workload == "batch" and args.impl == "ours":
+        print(json.dumps(bench_batch(args)))
+        return
     if args.workload == "selector" and args.impl == "ours":
         print(json.dumps(bench_selector(args)))
         return

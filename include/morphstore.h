@@ -295,6 +295,75 @@ ms_status ms_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d
 #define MS_STATS_WORDS 80
 ms_status ms_column_stats(ms_ctx *ctx, const ms_column *col, uint64_t *d_stats, void *stream);
 
+/* ----------------------------------------------------- batched fragments */
+
+/* Many small queries in one launch.  The paper runs one query at a time.  Serving
+   thousands of short query fragments over columns of uneven length one launch
+   each leaves the GPU idle between launches, so a batch runs them all in one
+   persistent kernel.
+
+   Fragment f is the Sec. 5.1 "Simple Query" shape select -> project -> agg_sum
+   over two columns x_f and y_f of equal length:
+       sum_f = sum of y_f[i] over the rows i with x_f[i] <cmp_f> c1_f (c2_f),
+   modulo 2^64.  This is the value of ms_select(x_f) -> ms_project(y_f, positions)
+   -> ms_agg_sum.  The select's positions inside one 512-row chunk of x index the
+   same chunk of y.  So the three operators fuse per chunk: decode the chunk of x,
+   test the predicate, decode the chunk of y, and add the matching values.  Sums
+   modulo 2^64 do not depend on the order of the additions, so every
+   configuration gives the same bits.
+
+   The batch numbers the chunks of all fragments consecutively (fragment f owns
+   chunks cs[f] .. cs[f+1]-1).  Each warp takes tiles of `tile_chunks` chunks
+   from a device work counter and keeps `depth` chunks of both columns in flight
+   with asynchronous copies.  The last CTA resets the counter, so a run needs no
+   set-up launch. */
+typedef struct ms_batch ms_batch;
+typedef struct ms_graph ms_graph;
+
+typedef struct {
+  uint32_t warps;       /* warps per CTA: 4 or 8 */
+  uint32_t depth;       /* chunks in flight per warp: 2, 3 or 4 */
+  uint32_t tile_chunks; /* chunks per work-counter grab: a power of two in 8..1024 */
+  uint32_t ctas_per_sm; /* CTAs per SM, 0 = as many as fit */
+  uint32_t compact;     /* 1: one decoding loop for every width (small code);
+                           0: width-specialised decoders */
+} ms_batch_config;
+
+/* ms_batch_run flags */
+#define MS_BATCH_ZERO 1u         /* zero d_sums[f0..f1) first (one memset) */
+#define MS_BATCH_PER_FRAGMENT 2u /* one launch per fragment instead of one in all */
+
+/* Binds n_frags fragments: x[f], y[f] (columns of ctx, equal lengths), cmp[f]
+   (ms_cmp) and c1[f], c2[f] (c2 is used by MS_BETWEEN only; c2 may be NULL).
+   Host arrays.  Reads the columns' device metadata and synchronises `stream`.
+   The columns must outlive the batch and must not be freed before it.
+   Errors: MS_ERR_INVALID_ARG (NULL pointers, n_frags == 0, a foreign or freed
+   column, an unknown cmp, x and y of unequal length, more than 2^32 chunks),
+   MS_ERR_NOMEM, MS_ERR_CUDA. */
+ms_status ms_batch_create(ms_ctx *ctx, uint32_t n_frags, ms_column *const *x,
+                          ms_column *const *y, const int32_t *cmp, const uint64_t *c1,
+                          const uint64_t *c2, ms_batch **out, void *stream);
+/* Totals over the fragments: rows (of x), 512-row chunks, and compressed bytes of
+   the x and y columns (the bytes a run reads).  Any pointer may be NULL. */
+ms_status ms_batch_info(const ms_batch *b, uint64_t *rows, uint64_t *chunks,
+                        uint64_t *bytes);
+/* Computes fragments f0 .. f1-1 (f0 <= f1 <= n_frags) into d_sums[f] (device
+   memory with n_frags words, indexed by fragment; other entries untouched).
+   Without MS_BATCH_ZERO the sums are added to d_sums.  cfg NULL means the
+   default configuration {8, 3, 32, 0, 0}; MS_ERR_INVALID_ARG for a value
+   outside the ranges above.  Asynchronous on `stream`; runs of one batch share
+   its work counter and must be ordered on one stream.  Allocates nothing and does
+   not synchronise, so it can be captured in a CUDA graph. */
+ms_status ms_batch_run(ms_batch *b, uint32_t f0, uint32_t f1, const ms_batch_config *cfg,
+                       uint32_t flags, uint64_t *d_sums, void *stream);
+/* Captures ms_batch_run(b, f0, f1, cfg, flags, d_sums) into an instantiated CUDA
+   graph (on a private stream).  The graph replays it with ms_graph_launch. */
+ms_status ms_batch_graph(ms_batch *b, uint32_t f0, uint32_t f1, const ms_batch_config *cfg,
+                         uint32_t flags, uint64_t *d_sums, ms_graph **out);
+ms_status ms_graph_launch(ms_graph *g, void *stream);
+ms_status ms_graph_destroy(ms_graph *g);
+ms_status ms_batch_destroy(ms_batch *b);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Kernels of the library, as reported by ms_profile_collect. */
@@ -313,7 +382,8 @@ typedef enum {
   MS_K_PLACE_SCAN = 11, /* block-format outputs: payload offsets and headers */
   MS_K_PLACE_COPY = 12, /* block-format outputs: payload placement */
   MS_K_STATS = 13,      /* column statistics for the format selector */
-  MS_K_COUNT = 14
+  MS_K_BATCH = 14,      /* batched select -> project -> agg_sum fragments */
+  MS_K_COUNT = 15
 } ms_kernel;
 
 typedef struct {

@@ -1,0 +1,95 @@
+"""Autotuner of the batched fragment kernel (ms_batch_run).
+
+The knobs are the kernel's launch shape and pipeline: warps per CTA (block size),
+chunks in flight per warp (the software-pipeline unroll), chunks per work grab
+(the unit a warp packs into one scheduling step), CTAs per SM, and the decoder
+variant (width-specialised code, or one compact loop whose smaller instruction
+footprint can win when warps on one SM decode many different widths).
+
+``tune`` times every candidate on the caller's batch with CUDA events and
+returns the fastest.  Results are cached per device and batch signature in a
+JSON file (``MS_AUTOTUNE_CACHE``, default ``~/.cache/morphstore_gb300/autotune.json``).
+All candidates give the same bits: the choice changes time only.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+
+import torch
+
+from . import morphstore as ms
+
+WARPS = (4, 8)
+DEPTHS = (2, 3, 4)
+TILES = (16, 64, 256)
+CTAS_PER_SM = (0,)
+COMPACT = (0, 1)
+
+
+def candidates(warps=WARPS, depths=DEPTHS, tiles=TILES, ctas=CTAS_PER_SM, compact=COMPACT):
+    return [c for c in itertools.product(warps, depths, tiles, ctas, compact) if c[2] >= 2 * c[1]]
+
+
+def cache_path() -> str:
+    return os.environ.get("MS_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "morphstore_gb300", "autotune.json"))
+
+
+def signature(batch: "ms.Batch", device) -> str:
+    """Device name and SM count, fragment count, and the batch's size on a log2 grid."""
+    p = torch.cuda.get_device_properties(device)
+    info = batch.info()
+    rows = max(info["rows"], 1)
+    return "%s/%dsm/f%d/r2^%d/b%.1f" % (p.name, p.multi_processor_count, batch.n, round(math.log2(rows)),
+                                          8.0 * info["bytes"] / rows)
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def time_config(batch, sums, cfg, reps=3, stream=None) -> float:
+    """Median milliseconds of one run of `cfg` (after one untimed run)."""
+    stream = stream or torch.cuda.current_stream()
+    batch.run(sums, cfg=cfg, stream=stream)
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.run(sums, cfg=cfg, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return sorted(times)[len(times) // 2]
+
+
+def tune(batch, sums, cands=None, reps=3, use_cache=True, stream=None):
+    """Fastest configuration for `batch`: (config tuple, {config: ms}).  A cached
+    entry for the same signature is returned without timing when use_cache."""
+    path = cache_path()
+    key = signature(batch, sums.device)
+    if use_cache:
+        hit = _load(path).get(key)
+        if hit:
+            return tuple(hit["cfg"]), {tuple(hit["cfg"]): hit["ms"]}
+    table = {}
+    for cfg in cands or candidates():
+        table[tuple(cfg)] = time_config(batch, sums, cfg, reps=reps, stream=stream)
+    best = min(table, key=table.get)
+    if use_cache:
+        data = _load(path)
+        data[key] = {"cfg": list(best), "ms": table[best]}
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            with open(path, "w") as f:
+                json.dump(data, f, indent=1, sort_keys=True)
+        except OSError:
+            pass
+    return best, table

@@ -256,13 +256,14 @@ MS_DEV void read_lane_stream_compact(const uint16_t* s, int lane, int b, uint64_
   }
 }
 
-// Reads lane `lane`'s 16 values of width b (0..64) from a block payload in shared
-// memory (stream halfword q of the lane at s[32*q + lane]).
-MS_DEV void read_lane_stream(const uint16_t* s, int lane, int b, uint64_t v[16]) {
-#ifdef MS_COMPACT_CODEC
-  read_lane_stream_compact(s, lane, b, v);
-  return;
-#endif
+// Reads lane `lane`'s 16 values of width b (0..64) from a block payload (stream
+// halfword q of the lane at s[32*q + lane]; shared or global memory).
+template <bool kCompact>
+MS_DEV void read_lane_stream_as(const uint16_t* s, int lane, int b, uint64_t v[16]) {
+  if constexpr (kCompact) {
+    read_lane_stream_compact(s, lane, b, v);
+    return;
+  }
   switch (b) {
 #define MS_UNPACK_CASE(B) \
   case B:                 \
@@ -274,6 +275,16 @@ MS_DEV void read_lane_stream(const uint16_t* s, int lane, int b, uint64_t v[16])
 #pragma unroll
       for (int k = 0; k < 16; k++) v[k] = 0;
   }
+}
+
+#ifdef MS_COMPACT_CODEC
+constexpr bool kCompactCodec = true;
+#else
+constexpr bool kCompactCodec = false;
+#endif
+
+MS_DEV void read_lane_stream(const uint16_t* s, int lane, int b, uint64_t v[16]) {
+  read_lane_stream_as<kCompactCodec>(s, lane, b, v);
 }
 
 // Writes lane `lane`'s 16 residuals (each < 2^b) as its stream into shared memory.
@@ -429,54 +440,163 @@ struct StreamSmem {
 // G_i = {header i+2D-1, payload i+D-1}.  After cp.async.wait_group(D-2) at the
 // top of iteration i, the payload of chunk i and every header up to chunk
 // i+D-1 have landed.
+// Staging of one chunk g of column c (used by the streams below): the block header
+// (16 bytes, one lane) and the chunk's packed payload (16-byte cp.async units,
+// swizzled for uncompressed chunks so that blocked reads are conflict-free).
+MS_DEV void stage_header(const ColView& c, uint64_t g, uint64_t* hdr, int lane) {
+  if (lane != 0 || !is_block_fmt(c.fmt)) return;
+  if (g < c.nb && 16 * (g + 1) <= c.size) cp_async16(hdr, c.p + 16 * g);
+}
+
+// A payload of more than max_units 16-byte units is not staged; decode_staged with
+// the same max_units then reads it in place from global memory.
+MS_DEV void stage_payload(const ColView& c, uint64_t g, const uint64_t* hdr, uint16_t* slot, int lane,
+                          int max_units = 256) {
+  const uint8_t* src = nullptr;
+  int units = 0;
+  bool swizzle = false;
+  if (c.fmt == MS_UNCOMPR) {
+    if ((g + 1) * kBlock <= c.n) {
+      src = c.p + 4096 * g;
+      units = 256;
+      swizzle = true;
+    }
+  } else if (c.fmt == MS_STATIC_BP) {
+    if (g < c.n / kBlock) {
+      src = c.p + 64ull * c.bw * g;
+      units = 4 * c.bw;
+    }
+  } else if (g < c.nb) {
+    const uint64_t w0 = hdr[0];
+    const int b = (int)min((uint64_t)64, w0 & 255);
+    // a payload outside the column (corrupt metadata) is never read
+    if (16 * c.nb + 8 * ((w0 >> 8) + 8ull * b) <= c.size) {
+      src = c.p + 16 * c.nb + 8 * (w0 >> 8);
+      units = 4 * b;
+    }
+  }
+  if (units > max_units) return;
+  uint4* dst = reinterpret_cast<uint4*>(slot);
+  for (int u = lane; u < units; u += 32) {
+    const int d = swizzle ? (((u >> 3) << 3) | ((u & 7) ^ ((u >> 3) & 7))) : u;
+    cp_async16(dst + d, reinterpret_cast<const uint4*>(src) + u);
+  }
+}
+
+// Decodes staged chunk g of column c into lane registers; returns its valid count.
+// Payloads above max_units 16-byte units (not staged) are read from global memory.
+template <bool kCompact = kCompactCodec>
+MS_DEV int decode_staged(const ColView& c, uint64_t g, const uint64_t* hdr, const uint16_t* slot, int lane,
+                         uint64_t v[16], DevCtl* ctl, int max_units = 256) {
+  const uint64_t base = g * kBlock;
+  if (base >= c.n) {
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = 0;
+    return 0;
+  }
+  const int valid = (int)min((uint64_t)kBlock, c.n - base);
+  if (c.fmt == MS_UNCOMPR) {
+    if (valid == kBlock && max_units >= 256) {
+      const uint4* st = reinterpret_cast<const uint4*>(slot);
+#pragma unroll
+      for (int cc = 0; cc < 8; cc++) {
+        const uint4 q = st[lane * 8 + (cc ^ (lane & 7))];
+        v[2 * cc] = (uint64_t)q.x | ((uint64_t)q.y << 32);
+        v[2 * cc + 1] = (uint64_t)q.z | ((uint64_t)q.w << 32);
+      }
+    } else if (valid == kBlock) {
+      const uint4* src = reinterpret_cast<const uint4*>(c.p + 4096 * g) + 8 * lane;
+#pragma unroll
+      for (int cc = 0; cc < 8; cc++) {
+        const uint4 q = __ldg(src + cc);
+        v[2 * cc] = (uint64_t)q.x | ((uint64_t)q.y << 32);
+        v[2 * cc + 1] = (uint64_t)q.z | ((uint64_t)q.w << 32);
+      }
+    } else {
+      const uint64_t* src = reinterpret_cast<const uint64_t*>(c.p) + base;
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] = (16 * lane + k < valid) ? ldg64(src + 16 * lane + k) : 0;
+    }
+    return valid;
+  }
+  if (c.fmt == MS_STATIC_BP) {
+    const int b = c.bw;
+    const uint64_t C = c.n / kBlock;
+    if (g < C) {
+      const bool staged = 4 * b <= max_units;
+      read_lane_stream_as<kCompact>(staged ? slot : reinterpret_cast<const uint16_t*>(c.p + 64ull * b * g), lane, b,
+                                    v);
+    } else {
+      const uint64_t* tail = reinterpret_cast<const uint64_t*>(c.p + 64ull * b * C);
+      const uint64_t mask = lowmask(b);
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        const int t = 16 * lane + k;
+        uint64_t x = 0;
+        if (t < valid) {
+          const uint64_t bit = (uint64_t)t * b;
+          const int s = (int)(bit & 63);
+          x = ldg64(tail + (bit >> 6)) >> s;
+          if (s + b > 64) x |= ldg64(tail + (bit >> 6) + 1) << (64 - s);
+          x &= mask;
+        }
+        v[k] = x;
+      }
+    }
+    return valid;
+  }
+  if (g < c.nb) {
+    const uint64_t w0 = hdr[0], ref = hdr[1];
+    int b = (int)(w0 & 255);
+    if (b > 64 || 16 * (g + 1) > c.size || 16 * c.nb + 8 * ((w0 >> 8) + 8ull * b) > c.size) {
+      if (lane == 0) set_error(ctl, MS_ERR_FORMAT, g);
+      b = 0;
+    }
+    const bool staged = 4 * b <= max_units;
+    read_lane_stream_as<kCompact>(
+        staged ? slot : reinterpret_cast<const uint16_t*>(c.p + 16 * c.nb + 8 * (w0 >> 8)), lane, b, v);
+    if (c.fmt == MS_FOR_BP) {
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] += ref;
+    } else if (c.fmt == MS_DELTA_BP) {
+      uint64_t s = 0;
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        s += v[k];
+        v[k] = s;
+      }
+      const uint64_t excl = warp_excl_scan(s, lane) + ref;
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] += excl;
+    }
+  } else {
+    const uint64_t* rem = reinterpret_cast<const uint64_t*>(c.p + 16 * c.nb + 8 * c.pwords);
+    const bool inside = 16 * c.nb + 8 * (c.pwords + (uint64_t)valid) <= c.size;
+    if (!inside && lane == 0) set_error(ctl, MS_ERR_FORMAT, g);
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const int t = 16 * lane + k;
+      v[k] = (t < valid && inside) ? ldg64(rem + t) : 0;
+    }
+  }
+  return valid;
+}
+
 template <int kDepth>
 struct ChunkStream {
   ColView c;
   uint64_t first, stride, count;
   StreamSmem<kDepth>* sm;
   int lane;
-
   const uint32_t* list = nullptr;  // when set: chunk i is first + list[i] (ascending)
 
   MS_DEV uint64_t chunk(uint64_t i) const { return list ? first + list[i] : first + i * stride; }
 
   MS_DEV void issue_header(uint64_t i) {
-    if (i >= count || lane != 0 || !is_block_fmt(c.fmt)) return;
-    const uint64_t g = chunk(i);
-    if (g < c.nb && 16 * (g + 1) <= c.size) cp_async16(sm->hdr[i % (2 * kDepth)], c.p + 16 * g);
+    if (i < count) stage_header(c, chunk(i), sm->hdr[i % (2 * kDepth)], lane);
   }
-
   MS_DEV void issue_payload(uint64_t i) {
-    if (i >= count) return;
-    const uint64_t g = chunk(i);
-    const uint8_t* src = nullptr;
-    int units = 0;
-    bool swizzle = false;
-    if (c.fmt == MS_UNCOMPR) {
-      if ((g + 1) * kBlock <= c.n) {
-        src = c.p + 4096 * g;
-        units = 256;
-        swizzle = true;
-      }
-    } else if (c.fmt == MS_STATIC_BP) {
-      if (g < c.n / kBlock) {
-        src = c.p + 64ull * c.bw * g;
-        units = 4 * c.bw;
-      }
-    } else if (g < c.nb) {
-      const uint64_t w0 = sm->hdr[i % (2 * kDepth)][0];
-      const int b = (int)min((uint64_t)64, w0 & 255);
-      // a payload outside the column (corrupt metadata) is never read
-      if (16 * c.nb + 8 * ((w0 >> 8) + 8ull * b) <= c.size) {
-        src = c.p + 16 * c.nb + 8 * (w0 >> 8);
-        units = 4 * b;
-      }
-    }
-    uint4* dst = reinterpret_cast<uint4*>(sm->slot[i % kDepth]);
-    for (int u = lane; u < units; u += 32) {
-      const int d = swizzle ? (((u >> 3) << 3) | ((u & 7) ^ ((u >> 3) & 7))) : u;
-      cp_async16(dst + d, reinterpret_cast<const uint4*>(src) + u);
-    }
+    if (i < count) stage_payload(c, chunk(i), sm->hdr[i % (2 * kDepth)], sm->slot[i % kDepth], lane);
   }
 
   MS_DEV void prologue() {
@@ -496,88 +616,12 @@ struct ChunkStream {
 
   // Decodes chunk i (already landed) into lane registers; returns its valid count.
   MS_DEV int decode(uint64_t i, uint64_t v[16], DevCtl* ctl) const {
-    const uint64_t g = chunk(i);
-    const uint64_t base = g * kBlock;
-    if (i >= count || base >= c.n) {
+    if (i >= count) {
 #pragma unroll
       for (int k = 0; k < 16; k++) v[k] = 0;
       return 0;
     }
-    const int valid = (int)min((uint64_t)kBlock, c.n - base);
-    const uint16_t* slot = sm->slot[i % kDepth];
-    if (c.fmt == MS_UNCOMPR) {
-      if (valid == kBlock) {
-        const uint4* st = reinterpret_cast<const uint4*>(slot);
-#pragma unroll
-        for (int cc = 0; cc < 8; cc++) {
-          const uint4 q = st[lane * 8 + (cc ^ (lane & 7))];
-          v[2 * cc] = (uint64_t)q.x | ((uint64_t)q.y << 32);
-          v[2 * cc + 1] = (uint64_t)q.z | ((uint64_t)q.w << 32);
-        }
-      } else {
-        const uint64_t* src = reinterpret_cast<const uint64_t*>(c.p) + base;
-#pragma unroll
-        for (int k = 0; k < 16; k++) v[k] = (16 * lane + k < valid) ? ldg64(src + 16 * lane + k) : 0;
-      }
-      return valid;
-    }
-    if (c.fmt == MS_STATIC_BP) {
-      const int b = c.bw;
-      const uint64_t C = c.n / kBlock;
-      if (g < C) {
-        read_lane_stream(slot, lane, b, v);
-      } else {
-        const uint64_t* tail = reinterpret_cast<const uint64_t*>(c.p + 64ull * b * C);
-        const uint64_t mask = lowmask(b);
-#pragma unroll
-        for (int k = 0; k < 16; k++) {
-          const int t = 16 * lane + k;
-          uint64_t x = 0;
-          if (t < valid) {
-            const uint64_t bit = (uint64_t)t * b;
-            const int s = (int)(bit & 63);
-            x = ldg64(tail + (bit >> 6)) >> s;
-            if (s + b > 64) x |= ldg64(tail + (bit >> 6) + 1) << (64 - s);
-            x &= mask;
-          }
-          v[k] = x;
-        }
-      }
-      return valid;
-    }
-    if (g < c.nb) {
-      const uint64_t w0 = sm->hdr[i % (2 * kDepth)][0], ref = sm->hdr[i % (2 * kDepth)][1];
-      int b = (int)(w0 & 255);
-      if (b > 64 || 16 * (g + 1) > c.size || 16 * c.nb + 8 * ((w0 >> 8) + 8ull * b) > c.size) {
-        if (lane == 0) set_error(ctl, MS_ERR_FORMAT, g);
-        b = 0;
-      }
-      read_lane_stream(slot, lane, b, v);
-      if (c.fmt == MS_FOR_BP) {
-#pragma unroll
-        for (int k = 0; k < 16; k++) v[k] += ref;
-      } else if (c.fmt == MS_DELTA_BP) {
-        uint64_t s = 0;
-#pragma unroll
-        for (int k = 0; k < 16; k++) {
-          s += v[k];
-          v[k] = s;
-        }
-        const uint64_t excl = warp_excl_scan(s, lane) + ref;
-#pragma unroll
-        for (int k = 0; k < 16; k++) v[k] += excl;
-      }
-    } else {
-      const uint64_t* rem = reinterpret_cast<const uint64_t*>(c.p + 16 * c.nb + 8 * c.pwords);
-      const bool inside = 16 * c.nb + 8 * (c.pwords + (uint64_t)valid) <= c.size;
-      if (!inside && lane == 0) set_error(ctl, MS_ERR_FORMAT, g);
-#pragma unroll
-      for (int k = 0; k < 16; k++) {
-        const int t = 16 * lane + k;
-        v[k] = (t < valid && inside) ? ldg64(rem + t) : 0;
-      }
-    }
-    return valid;
+    return decode_staged(c, chunk(i), sm->hdr[i % (2 * kDepth)], sm->slot[i % kDepth], lane, v, ctl);
   }
 };
 

@@ -409,7 +409,7 @@ const char* ms_kernel_name(int k) {
   static const char* names[MS_K_COUNT] = {"mark",      "emit",       "compress", "decompress",
                                           "project",   "calc",       "agg_sum",  "group_sum",
                                           "build_keys", "validate",  "scan",     "place_scan",
-                                          "place_copy", "stats"};
+                                          "place_copy", "stats",      "batch"};
   return (k >= 0 && k < MS_K_COUNT) ? names[k] : "?";
 }
 

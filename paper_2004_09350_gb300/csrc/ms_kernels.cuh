@@ -554,7 +554,8 @@ MS_DEV int emit_gather(const ProduceArgs& a, uint64_t n_out, uint64_t g, int lan
     // stage the bitmap words and offsets of up to kEmitSpan chunks at once
     for (int u = lane; u < nc * 4; u += 32)
       cp_async16(sm->bits + 4 * u, reinterpret_cast<const uint4*>(a.bitmap + c0 * 32) + u);
-    if (lane <= nc) sm->coff[lane] = a.coff[c0 + lane];
+    // nc + 1 offsets: the sparse path reads the end offset of the span's last chunk
+    for (int u = lane; u <= nc; u += 32) sm->coff[u] = a.coff[c0 + u];
     cp_async_commit();
     cp_async_wait<0>();
     __syncwarp();

@@ -24,6 +24,9 @@ struct Work {
 
 ms_status carve(ms_ctx* c, uint64_t n_max, uint64_t key_domain, Work* w, cudaStream_t s);
 
+// Every select predicate as one range test (ms_ops.cu).
+void predicate_as_range(int cmp, uint64_t c1, uint64_t c2, MarkArgs* m);
+
 template <class K>
 int grid_for(ms_ctx* c, K kernel, size_t smem, uint64_t tiles, int threads = kThreads) {
   if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -43,10 +43,6 @@ ms_status carve(ms_ctx* c, uint64_t n_max, uint64_t key_domain, Work* w, cudaStr
   return cuda_status(cudaMemsetAsync(c->work, 0, 2 * st_b, s));
 }
 
-namespace {
-
-bool owned(ms_ctx* c, const ms_column* col) { return col && col->ctx == c && !col->freed; }
-
 // Every select predicate as one range test over uint64 (Sec. 5.1 point and range
 // predicates): x matches iff ((x - lo) <= span) != negate, and never if empty.
 void predicate_as_range(int cmp, uint64_t c1, uint64_t c2, MarkArgs* m) {
@@ -63,6 +59,11 @@ void predicate_as_range(int cmp, uint64_t c1, uint64_t c2, MarkArgs* m) {
     default: m->lo = c1; m->span = c2 - c1; m->empty = c2 < c1; break;  // MS_BETWEEN
   }
 }
+
+namespace {
+
+bool owned(ms_ctx* c, const ms_column* col) { return col && col->ctx == c && !col->freed; }
+
 
 // Launches k_map<OP> into a new arena column and, for block formats, places the
 // staged blocks.

@@ -11,6 +11,7 @@ from __future__ import annotations
 import ctypes
 import os
 import re
+import weakref
 
 import numpy as np
 import torch
@@ -39,6 +40,23 @@ class MSError(RuntimeError):
 
 class KernelTime(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("launches", ctypes.c_uint32), ("total_ms", ctypes.c_double)]
+
+
+class BatchConfig(ctypes.Structure):
+    """ms_batch_config: warps per CTA, chunks in flight per warp, chunks per work
+    grab (power of two), CTAs per SM (0 = as many as fit), compact codec flag."""
+    _fields_ = [("warps", ctypes.c_uint32), ("depth", ctypes.c_uint32), ("tile_chunks", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("compact", ctypes.c_uint32)]
+
+    def as_tuple(self):
+        return (self.warps, self.depth, self.tile_chunks, self.ctas_per_sm, self.compact)
+
+    def __repr__(self):
+        return "BatchConfig(warps=%d, depth=%d, tile_chunks=%d, ctas_per_sm=%d, compact=%d)" % self.as_tuple()
+
+
+DEFAULT_BATCH_CONFIG = (8, 3, 32, 0, 0)
+BATCH_ZERO, BATCH_PER_FRAGMENT = 1, 2
 
 
 class ColumnMeta(ctypes.Structure):
@@ -91,6 +109,15 @@ def load() -> ctypes.CDLL:
         "ms_mlp_loss_grad": [p, p, p, p, u64, ctypes.c_float, p, p, p, u64, p],
         "ms_mlp_adam": [p, p, p, p, u64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, p],
     }
+    sigs.update({
+        "ms_batch_create": [p, ctypes.c_uint32, p, p, p, p, p, pp, p],
+        "ms_batch_info": [p, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)],
+        "ms_batch_run": [p, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(BatchConfig), ctypes.c_uint32, p, p],
+        "ms_batch_graph": [p, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(BatchConfig), ctypes.c_uint32, p, pp],
+        "ms_graph_launch": [p, p],
+        "ms_graph_destroy": [p],
+        "ms_batch_destroy": [p],
+    })
     for name, args in sigs.items():
         fn = getattr(lib, name)
         fn.argtypes = args
@@ -197,6 +224,10 @@ class Ctx:
     # -------------------------------------------------------------- lifecycle
     def close(self):
         if getattr(self, "h", None):
+            for ref in getattr(self, "_batches", ()):
+                b = ref()
+                if b is not None:
+                    b.close()
             load().ms_ctx_destroy(self.h)
             self.h = None
             self._blocks.clear()
@@ -399,3 +430,98 @@ def compress_noalloc(d_in: torch.Tensor, fmt: int, d_out: torch.Tensor, d_result
 def to_numpy_u64(t: torch.Tensor) -> np.ndarray:
     """int64 tensor holding uint64 bits -> numpy uint64."""
     return t.detach().cpu().numpy().view(np.uint64)
+
+
+def batch_config(cfg=None) -> BatchConfig:
+    """BatchConfig from a tuple/dict/BatchConfig (None = the library default)."""
+    if cfg is None:
+        cfg = DEFAULT_BATCH_CONFIG
+    if isinstance(cfg, BatchConfig):
+        return cfg
+    if isinstance(cfg, dict):
+        return BatchConfig(**cfg)
+    return BatchConfig(*cfg)
+
+
+class Graph:
+    """An instantiated CUDA graph of a batch run (opaque ms_graph*)."""
+
+    def __init__(self, ptr: int):
+        self.ptr = ptr
+
+    def launch(self, stream=None):
+        _check(load().ms_graph_launch(self.ptr, _stream_handle(stream)), "ms_graph_launch")
+
+    def close(self):
+        if self.ptr:
+            load().ms_graph_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Fragments sum(y_f[i] for x_f[i] <cmp_f> c1_f (c2_f)) bound to a context's
+    columns (ms_batch_*).  Results go to a caller-owned int64 tensor indexed by
+    fragment."""
+
+    def __init__(self, ctx: "Ctx", xs, ys, cmps, c1s, c2s=None, stream=None):
+        n = len(xs)
+        if not (len(ys) == len(cmps) == len(c1s) == n) or (c2s is not None and len(c2s) != n):
+            raise ValueError("fragment arrays differ in length")
+        self.ctx = ctx
+        self.n = n
+        self.columns = list(xs) + list(ys)  # keep the handles alive with the batch
+        px = (ctypes.c_void_p * n)(*[c.ptr for c in xs])
+        py = (ctypes.c_void_p * n)(*[c.ptr for c in ys])
+        cmp = np.ascontiguousarray(cmps, dtype=np.int32)
+        c1 = np.ascontiguousarray(np.asarray(c1s, dtype=np.uint64))
+        c2 = np.ascontiguousarray(np.asarray(c2s if c2s is not None else np.zeros(n), dtype=np.uint64))
+        out = ctypes.c_void_p()
+        _check(load().ms_batch_create(ctx.h, n, px, py, cmp.ctypes.data_as(ctypes.c_void_p),
+                                      c1.ctypes.data_as(ctypes.c_void_p), c2.ctypes.data_as(ctypes.c_void_p),
+                                      ctypes.byref(out), _stream_handle(stream)), "ms_batch_create", ctx.h)
+        self.ptr = out.value
+        if not hasattr(ctx, "_batches"):
+            ctx._batches = []
+        ctx._batches.append(weakref.ref(self))
+
+    def info(self) -> dict:
+        r, c, b = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().ms_batch_info(self.ptr, ctypes.byref(r), ctypes.byref(c), ctypes.byref(b)), "ms_batch_info")
+        return {"rows": r.value, "chunks": c.value, "bytes": b.value}
+
+    def run(self, sums: torch.Tensor, cfg=None, f0: int = 0, f1: int | None = None, zero: bool = True,
+            per_fragment: bool = False, stream=None) -> torch.Tensor:
+        f1 = self.n if f1 is None else f1
+        assert sums.is_cuda and sums.dtype == torch.int64 and sums.numel() >= self.n
+        flags = (BATCH_ZERO if zero else 0) | (BATCH_PER_FRAGMENT if per_fragment else 0)
+        c = batch_config(cfg)
+        _check(load().ms_batch_run(self.ptr, f0, f1, ctypes.byref(c), flags, _dp(sums), _stream_handle(stream)),
+               "ms_batch_run", self.ctx.h)
+        return sums
+
+    def graph(self, sums: torch.Tensor, cfg=None, f0: int = 0, f1: int | None = None, zero: bool = True,
+              per_fragment: bool = False) -> Graph:
+        f1 = self.n if f1 is None else f1
+        flags = (BATCH_ZERO if zero else 0) | (BATCH_PER_FRAGMENT if per_fragment else 0)
+        c = batch_config(cfg)
+        out = ctypes.c_void_p()
+        _check(load().ms_batch_graph(self.ptr, f0, f1, ctypes.byref(c), flags, _dp(sums), ctypes.byref(out)),
+               "ms_batch_graph", self.ctx.h)
+        return Graph(out.value)
+
+    def close(self):
+        if self.ptr:
+            load().ms_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

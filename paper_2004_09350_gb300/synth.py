@@ -12,7 +12,9 @@ and the workloads this project measures:
   * ``tiny_fragment``   -- two 2^20-row columns: A ~ U[0,2^12), B ~ U[0,2^20),
   * ``skewed_widths``   -- per-512-block bit width drawn from {3,8,16,27,40},
   * ``sorted_gaps``     -- sorted keys with geometric gaps of mean 4,
-  * ``star_fact`` / ``star_dims`` -- a star-schema-shaped fact table and dimensions.
+  * ``star_fact`` / ``star_dims`` -- a star-schema-shaped fact table and dimensions,
+  * ``batch_fragments`` -- thousands of select -> project -> agg_sum fragments with
+    log-uniform lengths and per-fragment widths and shapes.
 """
 from __future__ import annotations
 
@@ -219,3 +221,101 @@ def star_fact(seed: int, n: int) -> dict:
         "discount": uniform(seed + 14, n, 0, 11),
         "revenue": uniform(seed + 15, n, 0, 1 << 23),
     }
+
+
+# ----------------------------------------------------------- batched fragments
+
+# ms_cmp ids: LT three times as often as the others
+BATCH_CMPS = (2, 2, 2, 6, 5, 0, 1, 3, 4)
+BATCH_Y_SHAPES = ("uniform", "offset", "sorted", "skewed")
+
+
+def _unit(z) -> float:
+    return float(int(z) >> 11) / float(1 << 53)
+
+
+def batch_fragments(seed: int, count: int, lo_log2: float = 10, hi_log2: float = 24, max_bits: int = 40) -> list:
+    """Parameters of `count` fragments sum(y[i] for x[i] <cmp> c1 (c2)):
+    n = floor(2^(lo + u (hi - lo))) (log-uniform), x ~ U[0, 2^bx), y of one of
+    BATCH_Y_SHAPES at width by, with bx, by uniform in [1, max_bits], and a
+    predicate whose constant sits at a uniformly drawn quantile of x's range."""
+    z = splitmix64(seed, 8 * count).reshape(count, 8)
+    out = []
+    for f in range(count):
+        n = int(2.0 ** (lo_log2 + _unit(z[f, 0]) * (hi_log2 - lo_log2)))
+        bx = 1 + int(z[f, 1] % np.uint64(max_bits))
+        by = 1 + int(z[f, 2] % np.uint64(max_bits))
+        shape = BATCH_Y_SHAPES[int(z[f, 3] % np.uint64(len(BATCH_Y_SHAPES)))]
+        cmp = BATCH_CMPS[int(z[f, 4] % np.uint64(len(BATCH_CMPS)))]
+        c1 = int(_unit(z[f, 5]) * (1 << bx))
+        c2 = c1 + int(_unit(z[f, 6]) * (1 << bx) / 2)
+        sx = int(z[f, 7] & np.uint64(0xFFFFFFFF))
+        out.append({"n": n, "bx": bx, "by": by, "shape": shape, "cmp": cmp, "c1": c1, "c2": c2,
+                    "seed_x": sx, "seed_y": sx + 0x1000})
+    return out
+
+
+def _skew_widths(by: int):
+    return (max(1, by // 4), max(1, by // 2), by)
+
+
+def _sorted_gap_bits(by: int) -> int:
+    return 1 + (by - 1) % 8
+
+
+def batch_x(spec: dict) -> np.ndarray:
+    return uniform(spec["seed_x"], spec["n"], 0, 1 << spec["bx"])
+
+
+def batch_y(spec: dict) -> np.ndarray:
+    """y of the fragment's shape: uniform U[0, 2^by); offset 2^(by-1) + U[0, 2^max(by-8,0))
+    (narrow range, FOR-friendly); sorted prefix sums of U[0, 2^g) gaps, g = 1 + (by-1) % 8
+    (DELTA-friendly); skewed per-block widths from {by/4, by/2, by} (dynamic-BP-friendly)."""
+    n, by, sy, shape = spec["n"], spec["by"], spec["seed_y"], spec["shape"]
+    if shape == "uniform":
+        return uniform(sy, n, 0, 1 << by)
+    if shape == "offset":
+        with np.errstate(over="ignore"):
+            return uniform(sy, n, 0, 1 << max(by - 8, 0)) + np.uint64(1 << (by - 1))
+    if shape == "sorted":
+        return np.cumsum(uniform(sy, n, 0, 1 << _sorted_gap_bits(by)), dtype=np.uint64)
+    return skewed_widths(sy, n, _skew_widths(by))
+
+
+def _umod_torch(z, m: int):
+    """(z as uint64) mod m for an int64 tensor z and 0 < m < 2^31."""
+    hi = (z >> 32) & 0xFFFFFFFF
+    lo = z & 0xFFFFFFFF
+    return ((hi % m) * ((1 << 32) % m) + lo % m) % m
+
+
+def skewed_widths_torch(seed: int, n: int, widths, device):
+    """skewed_widths() on `device` (int64 tensor, same bits)."""
+    import torch
+    nblk = (n + BLOCK - 1) // BLOCK
+    w = torch.tensor(list(widths), dtype=torch.int64, device=device)
+    choice = w[_umod_torch(splitmix64_torch(seed, nblk, device), len(widths))]
+    b = choice.repeat_interleave(BLOCK)[:n]
+    z = splitmix64_torch(seed + 1, n, device)
+    x = (z >> (64 - b)) & ((torch.ones_like(b) << b) - 1)
+    first = torch.arange(0, n, BLOCK, dtype=torch.int64, device=device)
+    forced_at = torch.clamp(first + _umod_torch(splitmix64_torch(seed + 2, nblk, device), BLOCK), max=n - 1)
+    x[forced_at] |= torch.ones_like(forced_at) << (b[forced_at] - 1)
+    return x
+
+
+def batch_x_torch(spec: dict, device):
+    return uniform_torch(spec["seed_x"], spec["n"], 0, 1 << spec["bx"], device)
+
+
+def batch_y_torch(spec: dict, device):
+    """batch_y() on `device` (int64 tensor, same bits)."""
+    import torch
+    n, by, sy, shape = spec["n"], spec["by"], spec["seed_y"], spec["shape"]
+    if shape == "uniform":
+        return uniform_torch(sy, n, 0, 1 << by, device)
+    if shape == "offset":
+        return uniform_torch(sy, n, 0, 1 << max(by - 8, 0), device) + (1 << (by - 1))
+    if shape == "sorted":
+        return torch.cumsum(uniform_torch(sy, n, 0, 1 << _sorted_gap_bits(by), device), 0)
+    return skewed_widths_torch(sy, n, _skew_widths(by), device)

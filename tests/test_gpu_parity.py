@@ -126,6 +126,23 @@ def test_select_predicates(ctx, cmp):
     ctx.free(col)
 
 
+@pytest.mark.parametrize("out_fmt", FMTS)
+def test_select_sparse_output_blocks(ctx, out_fmt):
+    """Selectivities below 1/64: an output block of 512 positions gathers from more
+    than 64 input chunks (several 32-chunk spans per block, the last span full)."""
+    n = 400 * 512 + 77
+    x = synth.uniform(13, n, 0, 1 << 30)
+    col, _ = gpu_col(ctx, x, ms.DYN_BP)
+    for sel in (0.0005, 0.002, 0.01, 0.015, 0.03):
+        c = synth.value_at_rank(x, sel)
+        want = oracle.select(x, oracle.LT, c)
+        bw = static_bw(np.array([n], dtype=np.uint64)) if out_fmt == ms.STATIC_BP else 0
+        pos = ctx.select(col, ms.LT, c, fmt=out_fmt, bw=bw)
+        assert_column(ctx, pos, want, out_fmt, bw)
+        ctx.free(pos)
+    ctx.free(col)
+
+
 def test_select_none_and_all(ctx):
     x = synth.uniform(5, 4096 * 4 + 17, 10, 20)
     col, _ = gpu_col(ctx, x, ms.FOR_BP)
