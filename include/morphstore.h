@@ -313,21 +313,28 @@ ms_status ms_column_stats(ms_ctx *ctx, const ms_column *col, uint64_t *d_stats, 
    configuration gives the same bits.
 
    The batch numbers the chunks of all fragments consecutively (fragment f owns
-   chunks cs[f] .. cs[f+1]-1).  Each warp takes tiles of `tile_chunks` chunks
-   from a device work counter and keeps `depth` chunks of both columns in flight
-   with asynchronous copies.  The last CTA resets the counter, so a run needs no
-   set-up launch. */
+   chunks cs[f] .. cs[f+1]-1) and cuts them into tiles of `tile_chunks` chunks.
+   Tiles go to warps from a device work counter (the last CTA resets it, so a
+   run needs no set-up launch) or round-robin to CTAs.  Each warp keeps `depth`
+   chunks of both columns in flight with asynchronous copies. */
 typedef struct ms_batch ms_batch;
 typedef struct ms_graph ms_graph;
 
 typedef struct {
-  uint32_t warps;       /* warps per CTA: 4 or 8 */
-  uint32_t depth;       /* chunks in flight per warp: 2, 3 or 4 */
-  uint32_t tile_chunks; /* chunks per work-counter grab: a power of two in 8..1024 */
+  uint32_t warps;       /* warps per CTA */
+  uint32_t depth;       /* chunks in flight per warp */
+  uint32_t tile_chunks; /* chunks per tile: a power of two in 8..1024, at least
+                           2*depth (schedule 0) or warps (schedule 1) */
   uint32_t ctas_per_sm; /* CTAs per SM, 0 = as many as fit */
   uint32_t compact;     /* 1: one decoding loop for every width (small code);
                            0: width-specialised decoders */
+  uint32_t schedule;    /* 0: each warp takes whole tiles from the work counter;
+                           1: CTA b takes tiles b, b + grid, ... and its warps
+                           share each tile (one fragment per CTA at a time) */
 } ms_batch_config;
+/* Supported (warps, depth, compact, schedule): schedule 0 with warps 4 or 8,
+   depth 2..4, either decoder; schedule 1 with warps 4, 8 (depth 2 or 3) or 16
+   (depth 2) and the width-specialised decoders. */
 
 /* ms_batch_run flags */
 #define MS_BATCH_ZERO 1u         /* zero d_sums[f0..f1) first (one memset) */
@@ -338,7 +345,7 @@ typedef struct {
    Host arrays.  Reads the columns' device metadata and synchronises `stream`.
    The columns must outlive the batch and must not be freed before it.
    Errors: MS_ERR_INVALID_ARG (NULL pointers, n_frags == 0, a foreign or freed
-   column, an unknown cmp, x and y of unequal length, more than 2^32 chunks),
+   column, an unknown cmp, x and y of unequal length, 2^31 chunks or more),
    MS_ERR_NOMEM, MS_ERR_CUDA. */
 ms_status ms_batch_create(ms_ctx *ctx, uint32_t n_frags, ms_column *const *x,
                           ms_column *const *y, const int32_t *cmp, const uint64_t *c1,
@@ -350,8 +357,8 @@ ms_status ms_batch_info(const ms_batch *b, uint64_t *rows, uint64_t *chunks,
 /* Computes fragments f0 .. f1-1 (f0 <= f1 <= n_frags) into d_sums[f] (device
    memory with n_frags words, indexed by fragment; other entries untouched).
    Without MS_BATCH_ZERO the sums are added to d_sums.  cfg NULL means the
-   default configuration {8, 3, 32, 0, 0}; MS_ERR_INVALID_ARG for a value
-   outside the ranges above.  Asynchronous on `stream`; runs of one batch share
+   default configuration {8, 2, 32, 0, 0, 1}; MS_ERR_INVALID_ARG for an
+   unsupported configuration (including one whose shared memory does not fit).  Asynchronous on `stream`; runs of one batch share
    its work counter and must be ordered on one stream.  Allocates nothing and does
    not synchronise, so it can be captured in a CUDA graph. */
 ms_status ms_batch_run(ms_batch *b, uint32_t f0, uint32_t f1, const ms_batch_config *cfg,

@@ -1,10 +1,11 @@
 """Autotuner of the batched fragment kernel (ms_batch_run).
 
 The knobs are the kernel's launch shape and pipeline: warps per CTA (block size),
-chunks in flight per warp (the software-pipeline unroll), chunks per work grab
-(the unit a warp packs into one scheduling step), CTAs per SM, and the decoder
-variant (width-specialised code, or one compact loop whose smaller instruction
-footprint can win when warps on one SM decode many different widths).
+chunks in flight per warp (the software-pipeline unroll), chunks per tile (the
+unit of work a warp or CTA packs into one scheduling step), CTAs per SM, the
+decoder variant (width-specialised code, or one compact loop with a smaller
+instruction footprint) and the schedule (tiles to warps from a work counter, or
+round-robin to CTAs so that the warps of one SM decode few distinct widths).
 
 ``tune`` times every candidate on the caller's batch with CUDA events and
 returns the fastest.  Results are cached per device and batch signature in a
@@ -22,15 +23,18 @@ import torch
 
 from . import morphstore as ms
 
-WARPS = (4, 8)
-DEPTHS = (2, 3, 4)
 TILES = (16, 64, 256)
 CTAS_PER_SM = (0,)
-COMPACT = (0, 1)
 
 
-def candidates(warps=WARPS, depths=DEPTHS, tiles=TILES, ctas=CTAS_PER_SM, compact=COMPACT):
-    return [c for c in itertools.product(warps, depths, tiles, ctas, compact) if c[2] >= 2 * c[1]]
+def candidates(variants=None, tiles=TILES, ctas=CTAS_PER_SM):
+    """Every built (warps, depth, compact, schedule) variant with every tile size and
+    CTA cap that the variant accepts, as ms_batch_config tuples."""
+    out = []
+    for (w, d, c, s), t, k in itertools.product(variants or ms.BATCH_VARIANTS, tiles, ctas):
+        if (s == 0 and t >= 2 * d) or (s == 1 and t >= w):
+            out.append((w, d, t, k, c, s))
+    return out
 
 
 def cache_path() -> str:
@@ -81,7 +85,11 @@ def tune(batch, sums, cands=None, reps=3, use_cache=True, stream=None):
             return tuple(hit["cfg"]), {tuple(hit["cfg"]): hit["ms"]}
     table = {}
     for cfg in cands or candidates():
-        table[tuple(cfg)] = time_config(batch, sums, cfg, reps=reps, stream=stream)
+        try:
+            table[tuple(cfg)] = time_config(batch, sums, cfg, reps=reps, stream=stream)
+        except ms.MSError as e:
+            if e.code != ms.MS_ERR_INVALID_ARG:  # a variant whose shared memory does not fit is skipped
+                raise
     best = min(table, key=table.get)
     if use_cache:
         data = _load(path)

@@ -11,6 +11,7 @@ struct ms_batch {
   uint32_t n;
   ms::BatchFrag* d_frags;
   uint64_t* d_cs;
+  ms::ChunkRec* d_dir;            // one record per chunk
   unsigned long long* d_counter;  // [0] work counter, [1] finished CTAs
   std::vector<uint64_t> cs;       // host copy of the chunk prefix
   uint64_t rows, bytes;
@@ -22,9 +23,12 @@ struct ms_graph {
 
 namespace ms {
 
-MS_BATCH_DECLARE(2)
-MS_BATCH_DECLARE(3)
-MS_BATCH_DECLARE(4)
+#define MS_EXTERN extern
+MS_BATCH_DYNAMIC(MS_EXTERN, 2)
+MS_BATCH_DYNAMIC(MS_EXTERN, 3)
+MS_BATCH_DYNAMIC(MS_EXTERN, 4)
+MS_BATCH_STATIC(MS_EXTERN)
+#undef MS_EXTERN
 
 // Host-built part of a fragment: the column slots and the predicate.
 struct BatchInit {
@@ -54,12 +58,44 @@ __global__ void k_batch_bind(const BatchInit* init, uint32_t n, const DevMeta* m
   }
 }
 
-BatchLauncher batch_launcher(uint32_t warps, uint32_t depth, bool compact) {
-#define MS_PICK(W, D)                                                               \
-  if (warps == W && depth == D)                                                     \
-    return compact ? &launch_batch_kernel<W, D, true> : &launch_batch_kernel<W, D, false>;
-  MS_PICK(4, 2) MS_PICK(8, 2) MS_PICK(4, 3) MS_PICK(8, 3) MS_PICK(4, 4) MS_PICK(8, 4)
+// Builds the chunk directory: one thread per chunk, its fragment by binary search.
+__global__ void k_batch_dir(const BatchFrag* frags, const uint64_t* cs, uint32_t n_frags, ChunkRec* dir,
+                            DevCtl* ctl) {
+  const uint64_t total = cs[n_frags];
+  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total;
+       g += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = n_frags;  // cs[lo] <= g < cs[hi]
+    while (hi - lo > 1) {
+      const uint32_t mid = lo + ((hi - lo) >> 1);
+      if (cs[mid] <= g) lo = mid;
+      else hi = mid;
+    }
+    const BatchFrag fr = frags[lo];
+    const uint64_t lg = g - cs[lo];
+    ChunkRec r;
+    resolve_chunk(fr.x, lg, &r.addr[0], &r.ref[0], &r.code[0], ctl);
+    resolve_chunk(fr.y, lg, &r.addr[1], &r.ref[1], &r.code[1], ctl);
+    r.lo = fr.lo;
+    r.span = fr.span;
+    r.frag = lo;
+    r.meta = (uint32_t)min((uint64_t)kBlock, fr.x.n - lg * kBlock) | fr.negate << 16 | fr.empty << 17;
+    dir[g] = r;
+  }
+}
+
+BatchLauncher batch_launcher(uint32_t warps, uint32_t depth, bool compact, uint32_t schedule) {
+  if (schedule == 0) {
+#define MS_PICK(W, D)                                                                                   \
+  if (warps == W && depth == D)                                                                         \
+    return compact ? &launch_batch_kernel<W, D, true, false> : &launch_batch_kernel<W, D, false, false>;
+    MS_PICK(4, 2) MS_PICK(8, 2) MS_PICK(4, 3) MS_PICK(8, 3) MS_PICK(4, 4) MS_PICK(8, 4)
 #undef MS_PICK
+  } else if (schedule == 1 && !compact) {
+#define MS_PICK(W, D) \
+  if (warps == W && depth == D) return &launch_batch_kernel<W, D, false, true>;
+    MS_PICK(4, 2) MS_PICK(8, 2) MS_PICK(16, 2) MS_PICK(4, 3) MS_PICK(8, 3)
+#undef MS_PICK
+  }
   return nullptr;
 }
 
@@ -80,10 +116,7 @@ ms_status run_range(ms_batch* b, uint32_t f0, uint32_t f1, BatchLauncher launch,
   const uint64_t c0 = b->cs[f0], c1 = b->cs[f1];
   if (c1 == c0) return MS_OK;
   BatchArgs a{};
-  a.frags = b->d_frags;
-  a.cs = b->d_cs;
-  a.f0 = f0;
-  a.f1 = f1;
+  a.dir = b->d_dir;
   a.c0 = c0;
   a.c1 = c1;
   a.log2_tile = (uint32_t)lt;
@@ -149,10 +182,19 @@ ms_status ms_batch_create(ms_ctx* c, uint32_t n, ms_column* const* x, ms_column*
       b->rows += sizes[f].nx;
       b->bytes += sizes[f].sx + sizes[f].sy;
     }
-    if (st == MS_OK && b->cs[n] >= (1ull << 32)) st = MS_ERR_INVALID_ARG;
+    if (st == MS_OK && b->cs[n] >= (1ull << 31)) st = MS_ERR_INVALID_ARG;
   }
   if (st == MS_OK)
     st = cuda_status(cudaMemcpyAsync(b->d_cs, b->cs.data(), sizeof(uint64_t) * (n + 1), cudaMemcpyHostToDevice, s));
+  if (st == MS_OK) {
+    b->d_dir = static_cast<ChunkRec*>(dev_alloc(c, sizeof(ChunkRec) * std::max<uint64_t>(b->cs[n], 1)));
+    if (!b->d_dir) st = MS_ERR_NOMEM;
+  }
+  if (st == MS_OK && b->cs[n]) {
+    const int grid = (int)std::min<uint64_t>(cdiv(b->cs[n], 256), 65536);
+    k_batch_dir<<<grid, 256, 0, s>>>(b->d_frags, b->d_cs, n, b->d_dir, c->ctl);
+    st = cuda_status(cudaGetLastError());
+  }
   if (st == MS_OK) st = cuda_status(cudaStreamSynchronize(s));
   else cudaStreamSynchronize(s);
   dev_free(c, d_init);
@@ -177,10 +219,12 @@ ms_status ms_batch_run(ms_batch* b, uint32_t f0, uint32_t f1, const ms_batch_con
                        uint64_t* d_sums, void* stream) {
   if (!b || !d_sums || f0 > f1 || f1 > b->n || (flags & ~(MS_BATCH_ZERO | MS_BATCH_PER_FRAGMENT)))
     return MS_ERR_INVALID_ARG;
-  const ms_batch_config cfg = cfg_in ? *cfg_in : ms_batch_config{8, 3, 32, 0, 0};
-  const BatchLauncher launch = batch_launcher(cfg.warps, cfg.depth, cfg.compact != 0);
+  const ms_batch_config cfg = cfg_in ? *cfg_in : ms_batch_config{8, 2, 32, 0, 0, 1};
+  const BatchLauncher launch = batch_launcher(cfg.warps, cfg.depth, cfg.compact != 0, cfg.schedule);
   const int lt = log2_exact(cfg.tile_chunks);
-  if (!launch || lt < 3 || lt > 10 || cfg.tile_chunks < 2 * cfg.depth || cfg.compact > 1) return MS_ERR_INVALID_ARG;
+  if (!launch || lt < 3 || lt > 10 || cfg.compact > 1) return MS_ERR_INVALID_ARG;
+  if (cfg.schedule == 0 && cfg.tile_chunks < 2 * cfg.depth) return MS_ERR_INVALID_ARG;
+  if (cfg.schedule == 1 && cfg.tile_chunks < cfg.warps) return MS_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (f0 == f1) return MS_OK;
   if ((flags & MS_BATCH_ZERO) &&
@@ -198,8 +242,8 @@ ms_status ms_batch_graph(ms_batch* b, uint32_t f0, uint32_t f1, const ms_batch_c
                          uint64_t* d_sums, ms_graph** out) {
   if (!b || !out) return MS_ERR_INVALID_ARG;
   *out = nullptr;
-  const ms_batch_config conf = cfg ? *cfg : ms_batch_config{8, 3, 32, 0, 0};
-  const BatchLauncher launch = batch_launcher(conf.warps, conf.depth, conf.compact != 0);
+  const ms_batch_config conf = cfg ? *cfg : ms_batch_config{8, 2, 32, 0, 0, 1};
+  const BatchLauncher launch = batch_launcher(conf.warps, conf.depth, conf.compact != 0, conf.schedule);
   if (!launch) return MS_ERR_INVALID_ARG;
   // kernel attributes are set outside the capture
   BatchArgs none{};
@@ -243,6 +287,7 @@ ms_status ms_batch_destroy(ms_batch* b) {
   cudaDeviceSynchronize();
   dev_free(b->ctx, b->d_frags);
   dev_free(b->ctx, b->d_cs);
+  dev_free(b->ctx, b->d_dir);
   dev_free(b->ctx, b->d_counter);
   delete b;
   return MS_OK;

@@ -23,11 +23,30 @@ struct BatchFrag {
 };
 static_assert(sizeof(BatchFrag) == 128, "fragment descriptor size");
 
+// One 512-row chunk of a fragment, resolved once when the batch is bound (64 bytes).
+// The hot loop reads this record instead of the columns' metadata and block
+// headers: where each column's chunk lives, how it is coded, and the fragment's
+// predicate.
+//   code[c] = b | kind << 8 | fmt << 12 for column c (0 = x, 1 = y):
+//     kind 0: a packed block of width b at addr (64*b bytes; FOR/DELTA use ref),
+//     kind 1: raw uint64 values at addr (uncompressed chunk or block-format remainder),
+//     kind 2: the horizontally packed tail of a static-BP column at width b.
+//   meta = valid rows (1..512) | negate << 16 | empty << 17.
+struct ChunkRec {
+  uint64_t addr[2];
+  uint64_t ref[2];
+  uint64_t lo, span;  // predicate: ((x - lo) <= span) != negate, never if empty
+  uint32_t code[2];
+  uint32_t frag;
+  uint32_t meta;
+};
+static_assert(sizeof(ChunkRec) == 64, "chunk record size");
+
+constexpr int kKindPacked = 0, kKindRaw = 1, kKindTail = 2;
+
 struct BatchArgs {
-  const BatchFrag* frags;
-  const uint64_t* cs;  // cs[f] = first chunk of fragment f; cs[n_frags] = all chunks
-  uint32_t f0, f1;     // fragments of this run
-  uint64_t c0, c1;     // their chunks: [cs[f0], cs[f1])
+  const ChunkRec* dir;
+  uint64_t c0, c1;     // chunks of this run: [c0, c1)
   uint64_t ntiles;     // ceil((c1 - c0) / tile_chunks)
   uint32_t log2_tile;  // tile_chunks = 1 << log2_tile
   unsigned long long* counter;  // work counter (0 between runs)
@@ -38,93 +57,164 @@ struct BatchArgs {
 
 template <int D>
 struct BatchSmem {
-  uint16_t xs[D][32 * kBatchSlotW];
-  uint16_t ys[D][32 * kBatchSlotW];
-  uint64_t xh[2 * D][2];
-  uint64_t yh[2 * D][2];
+  uint16_t slot[D][2][32 * kBatchSlotW];
+  ChunkRec rec[2 * D];
 };
 
-// The fragment that owns chunk g, found from the cursor's last fragment forward.
-struct FragCursor {
-  uint32_t f;
-  uint64_t beg, end;  // chunk range of fragment f
+constexpr uint32_t kNoChunk = ~0u;
 
-  MS_DEV void seek(uint64_t g, const uint64_t* cs, uint32_t f_hi) {
-    if (g < end) return;
-    // cs[lo] <= g < cs[hi]: the owner is the last fragment starting at or before g
-    // (empty fragments start where their successor does).
-    uint32_t lo = f + 1, hi = f_hi;
-    while (hi - lo > 1) {
-      const uint32_t mid = lo + ((hi - lo) >> 1);
-      if (__ldg(reinterpret_cast<const unsigned long long*>(cs) + mid) <= g) lo = mid;
-      else hi = mid;
+// Record of chunk g of column c (the directory builder's per-column part).
+MS_DEV void resolve_chunk(const ColView& c, uint64_t g, uint64_t* addr, uint64_t* ref, uint32_t* code,
+                          DevCtl* ctl) {
+  const uint64_t base = (uint64_t)c.p;
+  *ref = 0;
+  if (c.fmt == MS_UNCOMPR) {
+    *addr = base + 4096 * g;
+    *code = (uint32_t)kKindRaw << 8 | (uint32_t)MS_UNCOMPR << 12 | 64;
+  } else if (c.fmt == MS_STATIC_BP) {
+    const uint64_t full = c.n / kBlock;
+    *addr = base + 64ull * c.bw * min(g, full);
+    *code = (uint32_t)(g < full ? kKindPacked : kKindTail) << 8 | (uint32_t)MS_STATIC_BP << 12 | (uint32_t)c.bw;
+  } else if (g < c.nb) {
+    uint64_t w0 = 0, r = 0;
+    if (16 * (g + 1) <= c.size) {
+      w0 = ldg64(c.p + 16 * g);
+      r = ldg64(c.p + 16 * g + 8);
     }
-    f = lo;
-    beg = __ldg(reinterpret_cast<const unsigned long long*>(cs) + lo);
-    end = __ldg(reinterpret_cast<const unsigned long long*>(cs) + lo + 1);
+    uint32_t b = (uint32_t)(w0 & 255);
+    if (16 * (g + 1) > c.size || b > 64 || 16 * c.nb + 8 * ((w0 >> 8) + 8ull * b) > c.size) {
+      set_error(ctl, MS_ERR_FORMAT, g);
+      b = 0;
+      w0 = 0;
+    }
+    *addr = base + 16 * c.nb + 8 * (w0 >> 8);
+    *ref = r;
+    *code = (uint32_t)kKindPacked << 8 | (uint32_t)c.fmt << 12 | b;
+  } else {
+    *addr = base + 16 * c.nb + 8 * c.pwords;
+    const uint64_t valid = min((uint64_t)kBlock, c.n - g * kBlock);
+    if (16 * c.nb + 8 * (c.pwords + valid) > c.size) set_error(ctl, MS_ERR_FORMAT, g);
+    *code = (uint32_t)kKindRaw << 8 | (uint32_t)c.fmt << 12 | 64;
   }
-};
-
-MS_DEV ColView load_view(const ColView* p) {
-  ColView c;
-  c.p = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&p->p)));
-  c.n = __ldg(reinterpret_cast<const unsigned long long*>(&p->n));
-  c.nb = __ldg(reinterpret_cast<const unsigned long long*>(&p->nb));
-  c.pwords = __ldg(reinterpret_cast<const unsigned long long*>(&p->pwords));
-  c.size = __ldg(reinterpret_cast<const unsigned long long*>(&p->size));
-  c.fmt = __ldg(&p->fmt);
-  c.bw = __ldg(&p->bw);
-  return c;
 }
 
-constexpr uint64_t kNoChunk = ~0ull;
+// Decodes one column's chunk from its record into lane registers.
+template <bool kCompact>
+MS_DEV void decode_rec(uint64_t addr, uint64_t ref, uint32_t code, int valid, const uint16_t* slot, int lane,
+                       uint64_t v[16]) {
+  const int b = (int)(code & 255), kind = (int)((code >> 8) & 15), fmt = (int)(code >> 12);
+  if (kind == kKindPacked) {
+    const uint16_t* src = b <= kBatchSlotW ? slot : reinterpret_cast<const uint16_t*>(addr);
+    read_lane_stream_as<kCompact>(src, lane, b, v);
+    if (fmt == MS_FOR_BP) {
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] += ref;
+    } else if (fmt == MS_DELTA_BP) {
+      uint64_t s = 0;
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        s += v[k];
+        v[k] = s;
+      }
+      const uint64_t excl = warp_excl_scan(s, lane) + ref;
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] += excl;
+    }
+  } else if (kind == kKindRaw) {
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(addr) + 16 * lane;
+    if (valid == kBlock) {
+#pragma unroll
+      for (int cc = 0; cc < 8; cc++) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(src) + cc);
+        v[2 * cc] = (uint64_t)q.x | ((uint64_t)q.y << 32);
+        v[2 * cc + 1] = (uint64_t)q.z | ((uint64_t)q.w << 32);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] = (16 * lane + k < valid) ? ldg64(src + k) : 0;
+    }
+  } else {  // static-BP tail: values one after the other at width b
+    const uint64_t* tail = reinterpret_cast<const uint64_t*>(addr);
+    const uint64_t mask = lowmask(b);
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const int t = 16 * lane + k;
+      uint64_t x = 0;
+      if (t < valid && b) {
+        const uint64_t bit = (uint64_t)t * b;
+        const int sh = (int)(bit & 63);
+        x = ldg64(tail + (bit >> 6)) >> sh;
+        if (sh + b > 64) x |= ldg64(tail + (bit >> 6) + 1) << (64 - sh);
+        x &= mask;
+      }
+      v[k] = x;
+    }
+  }
+}
 
-// Persistent kernel: every warp grabs tiles of 2^log2_tile consecutive chunks of
-// the batch's chunk space and streams both columns of each chunk with `D` chunks
-// in flight.  Positions s = 0, 1, ... of a warp's stream map to tile ring[(s >>
+// Persistent kernel over the batch's chunk space, tiles of 2^log2_tile chunks,
+// both columns of each chunk streamed with `D` chunks in flight per warp: chunk
+// records travel 2D-1 positions ahead of use, payloads D-1 positions ahead.
+//
+// Dynamic schedule (kStatic false): every warp grabs whole tiles from the work
+// counter.  Positions s = 0, 1, ... of a warp's stream map to tile ring[(s >>
 // log2_tile) & 1]; the issue stages run at most 2D-1 positions ahead, so two
 // tiles (the current and the next) cover them when the tile holds >= 2D chunks.
-template <int WARPS, int D, bool kCompact>
+//
+// Static schedule (kStatic true): CTA b owns tiles b, b + gridDim.x, ... and its
+// warps share each tile (warp w takes chunks w, w + WARPS, ...).  All warps of a
+// CTA then decode the same fragment, so the few width-specialised decoders it
+// needs stay in the instruction cache.
+template <int WARPS, int D, bool kCompact, bool kStatic>
 __global__ void __launch_bounds__(32 * WARPS) k_batch(BatchArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   BatchSmem<D>* sm = reinterpret_cast<BatchSmem<D>*>(smem_raw) + warp;
   const uint32_t lt = a.log2_tile;
-  const uint64_t kmask = (1ull << lt) - 1;
+  const uint32_t kmask = (1u << lt) - 1;
+  // static schedule: 2^lp positions of a warp per tile
+  constexpr int kLogW = WARPS == 16 ? 4 : (WARPS == 8 ? 3 : 2);
+  const uint32_t lp = lt - kLogW;
+  const uint32_t pmask = (1u << lp) - 1;
+  const uint32_t span = (uint32_t)(a.c1 - a.c0);  // chunks of this run (< 2^32)
 
-  auto grab = [&]() -> uint64_t {
+  auto grab = [&]() -> uint32_t {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(a.counter, 1ull);
-    return __shfl_sync(kFull, (uint64_t)t, 0);
+    return (uint32_t)min((unsigned long long)__shfl_sync(kFull, t, 0), (unsigned long long)a.ntiles);
   };
-  uint64_t ring0 = grab(), ring1 = a.ntiles;
-  auto chunk_at = [&](uint64_t s) -> uint64_t {
-    const uint64_t t = ((s >> lt) & 1) ? ring1 : ring0;
-    if (t >= a.ntiles) return kNoChunk;
-    const uint64_t g = a.c0 + (t << lt) + (s & kmask);
-    return g < a.c1 ? g : kNoChunk;
+  const uint32_t ntiles = (uint32_t)a.ntiles;
+  uint32_t ring0 = kStatic ? blockIdx.x : grab(), ring1 = ntiles;
+  auto tile_of = [&](uint32_t s) -> uint32_t {
+    if constexpr (kStatic) return blockIdx.x + (s >> lp) * gridDim.x;
+    return ((s >> lt) & 1) ? ring1 : ring0;
   };
-  const uint64_t cs0 = __ldg(reinterpret_cast<const unsigned long long*>(a.cs) + a.f0);
-  const uint64_t cs1 = __ldg(reinterpret_cast<const unsigned long long*>(a.cs) + a.f0 + 1);
-  FragCursor hc{a.f0, cs0, cs1}, pc = hc, dc = hc;
+  // run-relative chunk at stream position s, or kNoChunk
+  auto chunk_at = [&](uint32_t s) -> uint32_t {
+    const uint32_t t = tile_of(s);
+    if (t >= ntiles) return kNoChunk;
+    const uint32_t g = kStatic ? (t << lt) + warp + ((s & pmask) << kLogW) : (t << lt) + (s & kmask);
+    return g < span ? g : kNoChunk;
+  };
+  const ChunkRec* dir = a.dir + a.c0;
 
-  auto issue_header = [&](uint64_t s) {
-    const uint64_t g = chunk_at(s);
-    if (g == kNoChunk) return;
-    hc.seek(g, a.cs, a.f1);
-    const BatchFrag* fr = a.frags + hc.f;
-    const int h = (int)(s % (2 * D));
-    stage_header(load_view(&fr->x), g - hc.beg, sm->xh[h], lane);
-    stage_header(load_view(&fr->y), g - hc.beg, sm->yh[h], lane);
+  auto issue_rec = [&](uint32_t s) {
+    const uint32_t g = chunk_at(s);
+    if (g != kNoChunk && lane < 4)
+      cp_async16(reinterpret_cast<uint4*>(&sm->rec[s % (2 * D)]) + lane, reinterpret_cast<const uint4*>(dir + g) + lane);
   };
-  auto issue_payload = [&](uint64_t s) {
-    const uint64_t g = chunk_at(s);
-    if (g == kNoChunk) return;
-    pc.seek(g, a.cs, a.f1);
-    const BatchFrag* fr = a.frags + pc.f;
-    const int h = (int)(s % (2 * D)), p = (int)(s % D);
-    stage_payload(load_view(&fr->x), g - pc.beg, sm->xh[h], sm->xs[p], lane, kBatchUnits);
-    stage_payload(load_view(&fr->y), g - pc.beg, sm->yh[h], sm->ys[p], lane, kBatchUnits);
+  auto issue_payload = [&](uint32_t s) {
+    if (chunk_at(s) == kNoChunk) return;
+    const ChunkRec& r = sm->rec[s % (2 * D)];
+#pragma unroll
+    for (int col = 0; col < 2; col++) {
+      const uint32_t code = r.code[col];
+      const int b = (int)(code & 255);
+      if (((code >> 8) & 15) != kKindPacked || b > kBatchSlotW) continue;
+      const uint4* src = reinterpret_cast<const uint4*>(r.addr[col]);
+      uint4* dst = reinterpret_cast<uint4*>(sm->slot[s % D][col]);
+      for (int u = lane; u < 4 * b; u += 32) cp_async16(dst + u, src + u);
+    }
   };
 
   uint64_t acc = 0;          // this lane's part of fragment acc_f's sum
@@ -135,59 +225,57 @@ __global__ void __launch_bounds__(32 * WARPS) k_batch(BatchArgs a) {
     acc = 0;
   };
 
-  if (ring0 < a.ntiles) {
-    for (int i = 0; i < D; i++) issue_header(i);
+  if (ring0 < ntiles) {
+    for (int i = 0; i < D; i++) issue_rec(i);
     cp_async_commit();
     cp_async_wait<0>();
     __syncwarp();
     for (int j = 0; j < D - 1; j++) {
-      issue_header(j + D);
+      issue_rec(j + D);
       issue_payload(j);
       cp_async_commit();
     }
-    for (uint64_t s = 0;; s++) {
-      if ((s & kmask) == 0) {
+    for (uint32_t s = 0;; s++) {
+      if constexpr (kStatic) {
+        if ((s & pmask) == 0 && tile_of(s) >= ntiles) break;
+      } else if ((s & kmask) == 0) {
         // entering tile s >> lt: stop at a dead tile, else fetch the one after it
-        if ((((s >> lt) & 1) ? ring1 : ring0) >= a.ntiles) break;
-        const uint64_t nxt = grab();
+        if ((((s >> lt) & 1) ? ring1 : ring0) >= ntiles) break;
+        const uint32_t nxt = grab();
         if ((s >> lt) & 1) ring0 = nxt;
         else ring1 = nxt;
       }
       cp_async_wait<D - 2>();
       __syncwarp();
-      issue_header(s + 2 * D - 1);
+      issue_rec(s + 2 * D - 1);
       issue_payload(s + D - 1);
       cp_async_commit();
-      const uint64_t g = chunk_at(s);
-      if (g != kNoChunk) {
-        dc.seek(g, a.cs, a.f1);
-        if (dc.f != acc_f) {
+      if (chunk_at(s) != kNoChunk) {
+        const ChunkRec& r = sm->rec[s % (2 * D)];
+        const uint32_t f = r.frag;
+        if (f != acc_f) {
           flush();
-          acc_f = dc.f;
+          acc_f = f;
         }
-        const BatchFrag* fr = a.frags + dc.f;
-        const uint64_t lg = g - dc.beg;
-        const int h = (int)(s % (2 * D)), p = (int)(s % D);
-        const uint64_t lo = __ldg(reinterpret_cast<const unsigned long long*>(&fr->lo));
-        const uint64_t span = __ldg(reinterpret_cast<const unsigned long long*>(&fr->span));
-        const uint32_t negate = __ldg(&fr->negate) ? 0xffffu : 0u;
-        const uint32_t live = __ldg(&fr->empty) ? 0u : 0xffffu;
+        const uint32_t meta = r.meta;
+        const int valid = (int)(meta & 1023);
+        const uint64_t lo = r.lo, pspan = r.span;
         uint32_t m16 = 0;
         // one decoder instance for both columns keeps the instruction footprint small
 #pragma unroll 1
         for (int col = 0; col < 2; col++) {
           uint64_t v[16];
-          const int valid = decode_staged<kCompact>(load_view(col ? &fr->y : &fr->x), lg, col ? sm->yh[h] : sm->xh[h],
-                                                    col ? sm->ys[p] : sm->xs[p], lane, v, a.ctl, kBatchUnits);
+          decode_rec<kCompact>(r.addr[col], r.ref[col], r.code[col], valid, sm->slot[s % D][col], lane, v);
           if (col == 0) {
 #pragma unroll
-            for (int k = 0; k < 16; k++) m16 |= (uint32_t)(v[k] - lo <= span) << k;
+            for (int k = 0; k < 16; k++) m16 |= (uint32_t)(v[k] - lo <= pspan) << k;
             const int first = 16 * lane;
-            m16 = (m16 ^ negate) & live &
+            m16 = (m16 ^ ((meta >> 16) & 1 ? 0xffffu : 0u)) & ((meta >> 17) & 1 ? 0u : 0xffffu) &
                   (valid >= first + 16 ? 0xffffu : (valid > first ? (1u << (valid - first)) - 1u : 0u));
           } else {
 #pragma unroll
-            for (int k = 0; k < 16; k++) acc += ((m16 >> k) & 1u) ? v[k] : 0ull;
+            for (int k = 0; k < 16; k++)
+              if ((m16 >> k) & 1u) acc += v[k];
           }
         }
       }
@@ -196,6 +284,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_batch(BatchArgs a) {
     cp_async_wait<0>();
     flush();
   }
+  if constexpr (kStatic) return;
   // the last CTA to finish resets the work counter for the next run
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -212,45 +301,55 @@ __global__ void __launch_bounds__(32 * WARPS) k_batch(BatchArgs a) {
 // resident CTAs (ctas_per_sm per SM when nonzero).  With a.ntiles == 0 it only sets
 // the kernel's shared-memory attribute and caches its occupancy (done before a
 // stream capture).
-template <int WARPS, int D, bool kCompact>
+template <int WARPS, int D, bool kCompact, bool kStatic>
 ms_status launch_batch_kernel(ms_ctx* c, const BatchArgs& a, uint32_t ctas_per_sm, cudaStream_t s) {
-  static int occ_cache[16];  // per device; 0 = not yet known
+  static int occ_cache[16];  // per device; 0 = not yet known, -1 = does not fit
   const size_t smem = sizeof(BatchSmem<D>) * WARPS;
   const int dev = c->device;
   int occ = (dev >= 0 && dev < 16) ? occ_cache[dev] : 0;
   if (occ == 0) {
-    if (smem > 48 * 1024 &&
-        cuda_status(cudaFuncSetAttribute(k_batch<WARPS, D, kCompact>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem)) != MS_OK)
-      return MS_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<WARPS, D, kCompact>, 32 * WARPS, smem) !=
-            cudaSuccess ||
-        occ < 1)
-      occ = 1;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem > (size_t)optin) {
+      occ = -1;
+    } else {
+      if (smem > 48 * 1024 &&
+          cuda_status(cudaFuncSetAttribute(k_batch<WARPS, D, kCompact, kStatic>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != MS_OK)
+        return MS_ERR_CUDA;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<WARPS, D, kCompact, kStatic>, 32 * WARPS,
+                                                        smem) != cudaSuccess ||
+          occ < 1)
+        occ = 1;
+    }
     if (dev >= 0 && dev < 16) occ_cache[dev] = occ;
   }
+  if (occ < 0) return MS_ERR_INVALID_ARG;  // the configuration's shared memory does not fit
   if (a.ntiles == 0) return MS_OK;
   if (ctas_per_sm) occ = std::min<int>(occ, (int)ctas_per_sm);
   const uint64_t full = (uint64_t)occ * (uint64_t)c->sms;
-  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(full, cdiv(a.ntiles, WARPS)));
-  k_batch<WARPS, D, kCompact><<<grid, 32 * WARPS, smem, s>>>(a);
+  const uint64_t want = kStatic ? a.ntiles : cdiv(a.ntiles, WARPS);
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(full, want));
+  k_batch<WARPS, D, kCompact, kStatic><<<grid, 32 * WARPS, smem, s>>>(a);
   return cuda_status(cudaGetLastError());
 }
 
 using BatchLauncher = ms_status (*)(ms_ctx*, const BatchArgs&, uint32_t, cudaStream_t);
 
-// Launcher of (warps, depth, compact), or nullptr for an unsupported combination.
-BatchLauncher batch_launcher(uint32_t warps, uint32_t depth, bool compact);
+// Launcher of (warps, depth, compact, schedule), or nullptr for an unsupported
+// combination.
+BatchLauncher batch_launcher(uint32_t warps, uint32_t depth, bool compact, uint32_t schedule);
 
-#define MS_BATCH_DECLARE(D)                                                                                  \
-  extern template ms_status launch_batch_kernel<4, D, false>(ms_ctx*, const BatchArgs&, uint32_t, cudaStream_t); \
-  extern template ms_status launch_batch_kernel<8, D, false>(ms_ctx*, const BatchArgs&, uint32_t, cudaStream_t); \
-  extern template ms_status launch_batch_kernel<4, D, true>(ms_ctx*, const BatchArgs&, uint32_t, cudaStream_t);  \
-  extern template ms_status launch_batch_kernel<8, D, true>(ms_ctx*, const BatchArgs&, uint32_t, cudaStream_t);
-#define MS_BATCH_INSTANTIATE(D)                                                                       \
-  template ms_status launch_batch_kernel<4, D, false>(ms_ctx*, const BatchArgs&, uint32_t, cudaStream_t); \
-  template ms_status launch_batch_kernel<8, D, false>(ms_ctx*, const BatchArgs&, uint32_t, cudaStream_t); \
-  template ms_status launch_batch_kernel<4, D, true>(ms_ctx*, const BatchArgs&, uint32_t, cudaStream_t);  \
-  template ms_status launch_batch_kernel<8, D, true>(ms_ctx*, const BatchArgs&, uint32_t, cudaStream_t);
+#define MS_BATCH_LAUNCHER(W, D, C, S) \
+  launch_batch_kernel<W, D, C, S>(ms_ctx*, const BatchArgs&, uint32_t, cudaStream_t);
+// dynamic schedule: warps {4, 8} x depth D x both decoders
+#define MS_BATCH_DYNAMIC(X, D) \
+  X template ms_status MS_BATCH_LAUNCHER(4, D, false, false) X template ms_status MS_BATCH_LAUNCHER(8, D, false, false) \
+  X template ms_status MS_BATCH_LAUNCHER(4, D, true, false) X template ms_status MS_BATCH_LAUNCHER(8, D, true, false)
+// static schedule: width-specialised decoders, warps {4, 8, 16} x depth {2, 3}
+#define MS_BATCH_STATIC(X)                                                                                        \
+  X template ms_status MS_BATCH_LAUNCHER(4, 2, false, true) X template ms_status MS_BATCH_LAUNCHER(8, 2, false, true) \
+  X template ms_status MS_BATCH_LAUNCHER(16, 2, false, true) X template ms_status MS_BATCH_LAUNCHER(4, 3, false, true) \
+  X template ms_status MS_BATCH_LAUNCHER(8, 3, false, true)
 
 }  // namespace ms

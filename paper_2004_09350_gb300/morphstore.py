@@ -43,19 +43,24 @@ class KernelTime(ctypes.Structure):
 
 
 class BatchConfig(ctypes.Structure):
-    """ms_batch_config: warps per CTA, chunks in flight per warp, chunks per work
-    grab (power of two), CTAs per SM (0 = as many as fit), compact codec flag."""
+    """ms_batch_config: warps per CTA, chunks in flight per warp, chunks per tile
+    (power of two), CTAs per SM (0 = as many as fit), compact decoder flag,
+    schedule (0 = tiles to warps from a work counter, 1 = tiles round-robin to CTAs)."""
     _fields_ = [("warps", ctypes.c_uint32), ("depth", ctypes.c_uint32), ("tile_chunks", ctypes.c_uint32),
-                ("ctas_per_sm", ctypes.c_uint32), ("compact", ctypes.c_uint32)]
+                ("ctas_per_sm", ctypes.c_uint32), ("compact", ctypes.c_uint32), ("schedule", ctypes.c_uint32)]
 
     def as_tuple(self):
-        return (self.warps, self.depth, self.tile_chunks, self.ctas_per_sm, self.compact)
+        return (self.warps, self.depth, self.tile_chunks, self.ctas_per_sm, self.compact, self.schedule)
 
     def __repr__(self):
-        return "BatchConfig(warps=%d, depth=%d, tile_chunks=%d, ctas_per_sm=%d, compact=%d)" % self.as_tuple()
+        return ("BatchConfig(warps=%d, depth=%d, tile_chunks=%d, ctas_per_sm=%d, compact=%d, schedule=%d)"
+                % self.as_tuple())
 
 
-DEFAULT_BATCH_CONFIG = (8, 3, 32, 0, 0)
+DEFAULT_BATCH_CONFIG = (8, 2, 32, 0, 0, 1)
+# (warps, depth, compact, schedule) combinations the library is built with
+BATCH_VARIANTS = tuple([(w, d, c, 0) for w in (4, 8) for d in (2, 3, 4) for c in (0, 1)] +
+                       [(4, 2, 0, 1), (8, 2, 0, 1), (16, 2, 0, 1), (4, 3, 0, 1), (8, 3, 0, 1)])
 BATCH_ZERO, BATCH_PER_FRAGMENT = 1, 2
 
 

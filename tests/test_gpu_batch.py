@@ -86,11 +86,11 @@ def test_batch_matches_oracle(ctx, batch):
     np.testing.assert_array_equal(run(ctx, b), want)
 
 
-CONFIGS = [(w, d, t, k, c) for w in (4, 8) for d in (2, 3, 4) for c in (0, 1)
-           for t, k in ((8, 0), (64, 1), (1024, 0))]
+CONFIGS = [(w, d, t, k, c, s) for (w, d, c, s) in ms.BATCH_VARIANTS
+           for t, k in ((max(8, w), 0), (64, 1), (1024, 0))]
 
 
-@pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: "w%d-d%d-t%d-k%d-c%d" % c)
+@pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: "w%d-d%d-t%d-k%d-c%d-s%d" % c)
 def test_every_configuration_gives_the_same_bits(ctx, batch, cfg):
     b, want, _ = batch
     np.testing.assert_array_equal(run(ctx, b, cfg=cfg), want)
@@ -106,7 +106,7 @@ def test_sub_range_accumulates_and_leaves_the_rest(ctx, batch):
     sums = torch.full((b.n,), 7, dtype=torch.int64, device=ctx.device)
     f0, f1 = 5, 31
     b.run(sums, f0=f0, f1=f1)
-    b.run(sums, f0=f0, f1=f1, zero=False, cfg=(4, 2, 16, 1, 1))
+    b.run(sums, f0=f0, f1=f1, zero=False, cfg=(4, 2, 16, 1, 1, 0))
     ctx.check(what="batch")
     got = ms.to_numpy_u64(sums)
     with np.errstate(over="ignore"):
@@ -118,7 +118,8 @@ def test_graph_replay_is_identical(ctx, batch):
     b, want, _ = batch
     sums = torch.zeros(b.n, dtype=torch.int64, device=ctx.device)
     for per_fragment in (False, True):
-        g = b.graph(sums, cfg=(8, 4, 32, 0, 0), per_fragment=per_fragment)
+        g = b.graph(sums, cfg=(8, 4, 32, 0, 0, 0) if per_fragment else (16, 2, 64, 0, 0, 1),
+                    per_fragment=per_fragment)
         for _ in range(3):
             sums.fill_(-1)
             g.launch()
@@ -165,8 +166,9 @@ def test_errors_are_reported(ctx, batch):
     with pytest.raises(ms.MSError):
         ms.Batch(ctx, [a], [a], [9], [3])
     sums = torch.zeros(b.n, dtype=torch.int64, device=ctx.device)
-    for cfg in ((6, 3, 32, 0, 0), (8, 5, 32, 0, 0), (8, 4, 4, 0, 0), (8, 3, 24, 0, 0), (8, 3, 2048, 0, 0),
-                (8, 3, 32, 0, 2)):
+    for cfg in ((6, 3, 32, 0, 0, 0), (8, 5, 32, 0, 0, 0), (8, 4, 4, 0, 0, 0), (8, 3, 24, 0, 0, 0),
+                (8, 3, 2048, 0, 0, 0), (8, 3, 32, 0, 2, 0), (16, 2, 8, 0, 0, 1), (16, 3, 64, 0, 0, 1),
+                (8, 2, 64, 0, 1, 1), (8, 2, 64, 0, 0, 2)):
         with pytest.raises(ms.MSError) as e:
             b.run(sums, cfg=cfg)
         assert e.value.code == ms.MS_ERR_INVALID_ARG
@@ -188,7 +190,9 @@ def test_batch_at_scale_sampled_against_oracle(ctx):
         ys.append(col_t(c, synth.batch_y_torch(sp, c.device), FMTS[(3 * i) % 5], None))
     bt = ms.Batch(c, xs, ys, [s["cmp"] for s in specs], [s["c1"] for s in specs], [s["c2"] for s in specs])
     got = run(c, bt)
-    each = run(c, bt, per_fragment=True, cfg=(4, 2, 8, 0, 1))
+    each = run(c, bt, per_fragment=True, cfg=(4, 2, 8, 0, 1, 0))
+    stat = run(c, bt, cfg=(16, 2, 16, 0, 0, 1))
+    np.testing.assert_array_equal(got, stat)
     np.testing.assert_array_equal(got, each)
     rng = np.random.default_rng(0)
     order = np.argsort([s["n"] for s in specs])
