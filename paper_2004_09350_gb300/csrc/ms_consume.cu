@@ -10,15 +10,14 @@ namespace ms {
 // (lane j's 16 rows -> halfword j) and the chunk's match count.
 
 
-__global__ void __launch_bounds__(kThreads, 2) k_mark(MarkArgs a) {
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark(MarkArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  auto* sm = reinterpret_cast<StreamSmem<kMarkDepth>*>(smem_raw) + warp;
+  const int lane = threadIdx.x & 31;
+  auto* sm = reinterpret_cast<TileSmem<kTileBuf>*>(smem_raw);
   const ColView c = view_of(a.in);
-  const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
   const uint64_t lo = a.lo, span = a.span;
   const uint32_t negate = a.negate ? 0xffffu : 0u, live = a.empty ? 0u : 0xffffu;
-  stream_chunks<kMarkDepth>(c, gw, W, sm, lane, a.ctl, [&](uint64_t g, const uint64_t* v, int valid) {
+  cta_stream<kTileBuf>(c, sm, a.ctl, [&](uint64_t g, const uint64_t* v, int valid) {
     uint32_t m16 = 0;
     if (a.keybits) {
 #pragma unroll
@@ -104,26 +103,19 @@ __global__ void __launch_bounds__(kThreads) k_scan_counts(ScanArgs a) {
 
 // ----------------------------------------------------------------- aggregates
 
-__global__ void __launch_bounds__(kThreads, 2) k_agg_sum(const DevMeta* in, uint64_t* result, DevCtl* ctl) {
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_agg_sum(const DevMeta* in, uint64_t* result,
+                                                                          DevCtl* ctl) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  __shared__ uint64_t s_part[kWarps];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  auto* sm = reinterpret_cast<StreamSmem<kMarkDepth>*>(smem_raw) + warp;
+  const int lane = threadIdx.x & 31;
+  auto* sm = reinterpret_cast<TileSmem<kTileBuf>*>(smem_raw);
   const ColView c = view_of(in);
-  const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
   uint64_t acc = 0;
-  stream_chunks<kMarkDepth>(c, gw, W, sm, lane, ctl, [&](uint64_t, const uint64_t* v, int valid) {
+  cta_stream<kTileBuf>(c, sm, ctl, [&](uint64_t, const uint64_t* v, int) {
 #pragma unroll
-    for (int k = 0; k < 16; k++) acc += (16 * lane + k < valid) ? v[k] : 0;
+    for (int k = 0; k < 16; k++) acc += v[k];  // zero past the column's end
   });
   acc = warp_sum(acc);
-  if (lane == 0) s_part[warp] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint64_t t = 0;
-    for (int w = 0; w < kWarps; w++) t += s_part[w];
-    if (t) atomicAdd(reinterpret_cast<unsigned long long*>(result), (unsigned long long)t);
-  }
+  if (lane == 0 && acc) atomicAdd(reinterpret_cast<unsigned long long*>(result), (unsigned long long)acc);
 }
 
 
@@ -167,10 +159,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_keys(const DevMeta* keys,
                                                              DevCtl* ctl) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  auto* sm = reinterpret_cast<StreamSmem<kMarkDepth>*>(smem_raw) + warp;
+  auto* sm = reinterpret_cast<MarkSmem<kMarkDepth>*>(smem_raw) + warp;
   const ColView c = view_of(keys);
   const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
-  stream_chunks<kMarkDepth>(c, gw, W, sm, lane, ctl, [&](uint64_t, const uint64_t* v, int valid) {
+  stream_chunks<kMarkDepth, kMarkSlotW>(c, gw, W, sm, lane, ctl, [&](uint64_t, const uint64_t* v, int valid) {
 #pragma unroll
     for (int k = 0; k < 16; k++) {
       if (16 * lane + k < valid) {
@@ -191,10 +183,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_stats(const DevMeta* in, uint64
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < MS_STATS_WORDS; i += blockDim.x) s_acc[i] = 0;
   __syncthreads();
-  auto* sm = reinterpret_cast<StreamSmem<kMarkDepth>*>(smem_raw) + warp;
+  auto* sm = reinterpret_cast<MarkSmem<kMarkDepth>*>(smem_raw) + warp;
   const ColView c = view_of(in);
   const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
-  stream_chunks<kMarkDepth>(c, gw, W, sm, lane, ctl, [&](uint64_t, const uint64_t* v, int valid) {
+  stream_chunks<kMarkDepth, kMarkSlotW>(c, gw, W, sm, lane, ctl, [&](uint64_t, const uint64_t* v, int valid) {
     uint64_t mx = 0, mn = ~0ull, dmax = 0;
     uint32_t sorted = 0, runs = 0;
     const uint64_t prev_last = __shfl_up_sync(kFull, v[15], 1);
@@ -238,7 +230,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_stats(const DevMeta* in, uint64
   if (blockIdx.x == 0 && threadIdx.x == 0) stats[0] = c.n;
 }
 
-constexpr size_t kStreamSmem = sizeof(StreamSmem<kMarkDepth>) * kWarps;
+constexpr size_t kStreamSmem = sizeof(MarkSmem<kMarkDepth>) * kWarps;
+constexpr size_t kTileSmemBytes = sizeof(TileSmem<kTileBuf>);
 
 ms_status launch_stats(ms_ctx* c, const DevMeta* in, uint64_t* d_stats, uint64_t n_max, cudaStream_t s) {
   const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
@@ -253,9 +246,10 @@ ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max
   a.counts = w.counts;
   const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
   {
-    const int grid = grid_for(c, k_mark, kStreamSmem, tiles);
+    const int grid = grid_for(c, k_mark, kTileSmemBytes, cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kClaim),
+                              kTileThreads);
     ProfScope ps(c, MS_K_MARK, s);
-    k_mark<<<grid, kThreads, kStreamSmem, s>>>(a);
+    k_mark<<<grid, kTileThreads, kTileSmemBytes, s>>>(a);
     if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
   }
   ScanArgs sa{};
@@ -274,9 +268,9 @@ ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max
 
 ms_status launch_agg_sum(ms_ctx* c, const DevMeta* in, uint64_t* d_result, uint64_t n_max, cudaStream_t s) {
   const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
-  const int grid = grid_for(c, k_agg_sum, kStreamSmem, tiles);
+  const int grid = grid_for(c, k_agg_sum, kTileSmemBytes, cdiv(tiles * kWarps, kClaim), kTileThreads);
   ProfScope ps(c, MS_K_AGG_SUM, s);
-  k_agg_sum<<<grid, kThreads, kStreamSmem, s>>>(in, d_result, c->ctl);
+  k_agg_sum<<<grid, kTileThreads, kTileSmemBytes, s>>>(in, d_result, c->ctl);
   return cuda_status(cudaGetLastError());
 }
 

@@ -47,7 +47,9 @@ struct DevCtl {
   uint64_t op_n;      // element count produced by the last mark kernel
   uint64_t op_words;  // payload words published by an op's final tile
   uint64_t op_nch;    // input chunks of the last mark step (its real length, not a bound)
-  uint64_t rsv[7];
+  unsigned long long work;       // tile counter of the streaming consumers (0 between launches)
+  unsigned long long work_done;  // their finished CTAs (0 between launches)
+  uint64_t rsv[5];
 };
 
 // Read-only view of a column inside a kernel.
@@ -423,12 +425,27 @@ template <int N>
 MS_DEV void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
+// cp.async.wait_group with a run-time count (0 .. 15; larger counts wait for all).
+MS_DEV void cp_async_wait_dyn(int n) {
+  switch (n) {
+#define MS_WAIT_CASE(N) \
+  case N:               \
+    cp_async_wait<N>(); \
+    break;
+    MS_WAIT_CASE(1) MS_WAIT_CASE(2) MS_WAIT_CASE(3) MS_WAIT_CASE(4) MS_WAIT_CASE(5) MS_WAIT_CASE(6)
+    MS_WAIT_CASE(7) MS_WAIT_CASE(8) MS_WAIT_CASE(9) MS_WAIT_CASE(10) MS_WAIT_CASE(11) MS_WAIT_CASE(12)
+    MS_WAIT_CASE(13) MS_WAIT_CASE(14) MS_WAIT_CASE(15)
+#undef MS_WAIT_CASE
+    default:
+      cp_async_wait<0>();
+  }
+}
 
 // Per-warp shared memory of one column stream: D payload slots of 4 KB (a 512-value
 // block at up to 64 bits) and 2D header slots.
-template <int D>
+template <int D, int SW = 64>
 struct StreamSmem {
-  uint16_t slot[D][2048];
+  uint16_t slot[D][32 * SW];
   uint64_t hdr[2 * D][2];
 };
 
@@ -582,11 +599,11 @@ MS_DEV int decode_staged(const ColView& c, uint64_t g, const uint64_t* hdr, cons
   return valid;
 }
 
-template <int kDepth>
+template <int kDepth, int SW = 64>
 struct ChunkStream {
   ColView c;
   uint64_t first, stride, count;
-  StreamSmem<kDepth>* sm;
+  StreamSmem<kDepth, SW>* sm;
   int lane;
   const uint32_t* list = nullptr;  // when set: chunk i is first + list[i] (ascending)
 
@@ -596,7 +613,7 @@ struct ChunkStream {
     if (i < count) stage_header(c, chunk(i), sm->hdr[i % (2 * kDepth)], lane);
   }
   MS_DEV void issue_payload(uint64_t i) {
-    if (i < count) stage_payload(c, chunk(i), sm->hdr[i % (2 * kDepth)], sm->slot[i % kDepth], lane);
+    if (i < count) stage_payload(c, chunk(i), sm->hdr[i % (2 * kDepth)], sm->slot[i % kDepth], lane, 4 * SW);
   }
 
   MS_DEV void prologue() {
@@ -621,7 +638,7 @@ struct ChunkStream {
       for (int k = 0; k < 16; k++) v[k] = 0;
       return 0;
     }
-    return decode_staged(c, chunk(i), sm->hdr[i % (2 * kDepth)], sm->slot[i % kDepth], lane, v, ctl);
+    return decode_staged(c, chunk(i), sm->hdr[i % (2 * kDepth)], sm->slot[i % kDepth], lane, v, ctl, 4 * SW);
   }
 };
 

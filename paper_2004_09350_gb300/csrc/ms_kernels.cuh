@@ -16,12 +16,12 @@ namespace ms {
 
 // Walks the chunks first, first+stride, ... of one column with a per-warp
 // asynchronous stream and calls body(i, g, v, valid) for each decoded chunk.
-template <int D, class Body>
-MS_DEV void stream_chunks(const ColView& c, uint64_t first, uint64_t stride, StreamSmem<D>* sm, int lane,
+template <int D, int SW, class Body>
+MS_DEV void stream_chunks(const ColView& c, uint64_t first, uint64_t stride, StreamSmem<D, SW>* sm, int lane,
                           DevCtl* ctl, Body body) {
   const uint64_t nch = (c.n + kBlock - 1) / kBlock;
   const uint64_t count = first < nch ? (nch - first + stride - 1) / stride : 0;
-  ChunkStream<D> cs{c, first, stride, count, sm, lane};
+  ChunkStream<D, SW> cs{c, first, stride, count, sm, lane};
   if (count == 0) return;
   cs.prologue();
   for (int j = 0; j < D - 1; j++) {
@@ -43,6 +43,449 @@ MS_DEV void stream_chunks(const ColView& c, uint64_t first, uint64_t stride, Str
 
 
 
+// ------------------------------------------------------ byte-ring streams
+
+// A warp's stream of one column through a byte ring in shared memory.  Chunks are
+// copied at their packed size (64*b bytes; 4 KB for an uncompressed chunk), so
+// narrow blocks keep many chunks in flight: the depth adapts to the data, up to
+// kRingMaxFlight chunks.  Work comes in tiles of kRingTile consecutive chunks from
+// the context's tile counter; the first kRingTile lanes load a tile's block
+// headers with one coalesced load each (lane k: chunk k), one tile ahead of use.
+constexpr int kRingTile = 16;
+constexpr int kRingMaxFlight = 12;
+#ifndef MS_RING_BYTES
+#define MS_RING_BYTES 8192
+#endif
+#ifndef MS_RING_MINB
+#define MS_RING_MINB 3
+#endif
+constexpr int kRingBytes = MS_RING_BYTES;       // per warp
+constexpr int kRingMinBlocks = MS_RING_MINB;    // resident CTAs per SM the kernels are compiled for
+
+struct RingEntry {
+  uint64_t ref;
+  uint32_t g;     // chunk
+  uint32_t code;  // b | kind << 8 (kind 0: packed in the ring, 1: uncompressed in the ring, 2: read in place)
+  uint32_t roff;  // ring offset of the payload
+  uint32_t rend;  // ring allocation end (monotone byte count)
+};
+
+template <int R>
+struct RingSmem {
+  uint8_t ring[R];
+  RingEntry fifo[kRingMaxFlight];
+};
+
+// The last CTA of a launch resets the tile counter for the next one.
+MS_DEV void ring_work_done(DevCtl* ctl) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl->work_done, 1ull) == gridDim.x - 1) {
+      ctl->work = 0;
+      ctl->work_done = 0;
+      __threadfence();
+    }
+  }
+}
+
+// Calls body(g, v, valid) for every chunk g of c (each exactly once across the
+// grid, in no particular order); v is zero past `valid`.  Every CTA must call
+// ring_work_done afterwards.
+template <int R, class Body>
+MS_DEV void ring_stream(const ColView& c, RingSmem<R>* sm, int lane, DevCtl* ctl, Body body) {
+  static_assert(R >= 4096 && (R & (R - 1)) == 0, "ring size");
+  const uint64_t nch = (c.n + kBlock - 1) / kBlock;
+  const uint64_t ntiles = (nch + kRingTile - 1) / kRingTile;
+  const bool blockfmt = is_block_fmt(c.fmt);
+  const uint64_t full = c.fmt == MS_STATIC_BP ? c.n / kBlock : (c.fmt == MS_UNCOMPR ? c.n / kBlock : c.nb);
+  auto grab = [&]() -> uint64_t {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(&ctl->work, 1ull);
+    return __shfl_sync(kFull, (uint64_t)t, 0);
+  };
+  auto load_hdr = [&](uint64_t t) -> uint4 {
+    const uint64_t g = t * kRingTile + lane;
+    uint4 h = make_uint4(0, 0, 0, 0);
+    if (blockfmt && lane < kRingTile && t < ntiles && g < c.nb && 16 * (g + 1) <= c.size)
+      h = __ldg(reinterpret_cast<const uint4*>(c.p) + g);
+    return h;
+  };
+  uint64_t ti = grab(), tn = ti < ntiles ? grab() : ntiles;
+  uint4 hi = load_hdr(ti), hn = load_hdr(tn);
+  uint32_t ki = 0;
+  // the next chunk to issue, resolved once: chunk, kind, width, source, units, ref
+  bool have = false;
+  uint64_t ng = 0, nsrc = 0, nref = 0;
+  uint32_t nkind = 2, nb = 0, nunits = 0;
+  auto next = [&]() {
+    have = false;
+    while (ti < ntiles) {
+      const uint64_t g = ti * kRingTile + ki;
+      if (ki == kRingTile || g >= nch) {  // next tile
+        ti = tn;
+        hi = hn;
+        ki = 0;
+        if (ti < ntiles) {
+          tn = grab();
+          hn = load_hdr(tn);
+        }
+        continue;
+      }
+      ng = g;
+      nkind = 2;
+      nb = 0;
+      nunits = 0;
+      nsrc = 0;
+      nref = 0;
+      if (c.fmt == MS_UNCOMPR) {
+        if (g < full) {
+          nkind = 1;
+          nunits = 256;
+          nsrc = (uint64_t)c.p + 4096 * g;
+        }
+      } else if (c.fmt == MS_STATIC_BP) {
+        nb = (uint32_t)c.bw;
+        if (g < full) {
+          nkind = 0;
+          nunits = 4 * nb;
+          nsrc = (uint64_t)c.p + 64ull * nb * g;
+        }
+      } else if (g < c.nb) {
+        const uint64_t w0 = (uint64_t)__shfl_sync(kFull, hi.x, ki) | (uint64_t)__shfl_sync(kFull, hi.y, ki) << 32;
+        nref = (uint64_t)__shfl_sync(kFull, hi.z, ki) | (uint64_t)__shfl_sync(kFull, hi.w, ki) << 32;
+        nb = (uint32_t)(w0 & 255);
+        if (nb > 64 || 16 * (g + 1) > c.size || 16 * c.nb + 8 * ((w0 >> 8) + 8ull * nb) > c.size) {
+          if (lane == 0) set_error(ctl, MS_ERR_FORMAT, g);
+          nb = 0;
+        }
+        nkind = 0;
+        nunits = 4 * nb;
+        nsrc = (uint64_t)c.p + 16 * c.nb + 8 * (w0 >> 8);
+      }
+      ki++;
+      have = true;
+      return;
+    }
+  };
+  next();
+  uint32_t head = 0, tail = 0, wr = 0, rd = 0;
+  int nfl = 0;
+  for (;;) {
+    // issue chunks while the ring and the entry queue have room
+    while (have && nfl < kRingMaxFlight) {
+      const uint32_t need = 16 * nunits;
+      uint32_t roff = 0;
+      if (need) {
+        const uint32_t pos = head & (R - 1);
+        const uint32_t skip = pos + need > R ? R - pos : 0;
+        if (head + skip + need - tail > R) break;  // full: decode first
+        head += skip;
+        roff = head & (R - 1);
+        head += need;
+        uint4* dst = reinterpret_cast<uint4*>(sm->ring + roff);
+        const uint4* s4 = reinterpret_cast<const uint4*>(nsrc);
+        if (nkind == 1) {
+          for (uint32_t u = lane; u < nunits; u += 32)
+            cp_async16(dst + (((u >> 3) << 3) | ((u & 7) ^ ((u >> 3) & 7))), s4 + u);
+        } else {
+          for (uint32_t u = lane; u < nunits; u += 32) cp_async16(dst + u, s4 + u);
+        }
+      }
+      if (lane == 0) sm->fifo[wr % kRingMaxFlight] = RingEntry{nref, (uint32_t)ng, nb | nkind << 8, roff, head};
+      cp_async_commit();
+      wr++;
+      nfl++;
+      next();
+    }
+    if (nfl == 0) break;
+    cp_async_wait_dyn(nfl - 1);
+    __syncwarp();
+    const RingEntry e = sm->fifo[rd % kRingMaxFlight];
+    const uint64_t g = e.g;
+    const int b = (int)(e.code & 255), kind = (int)(e.code >> 8);
+    const int valid = (int)min((uint64_t)kBlock, c.n - g * kBlock);
+    uint64_t v[16];
+    if (kind == 0) {
+      read_lane_stream(reinterpret_cast<const uint16_t*>(sm->ring + e.roff), lane, b, v);
+      if (c.fmt == MS_FOR_BP) {
+#pragma unroll
+        for (int k = 0; k < 16; k++) v[k] += e.ref;
+      } else if (c.fmt == MS_DELTA_BP) {
+        uint64_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          sum += v[k];
+          v[k] = sum;
+        }
+        const uint64_t excl = warp_excl_scan(sum, lane) + e.ref;
+#pragma unroll
+        for (int k = 0; k < 16; k++) v[k] += excl;
+      }
+    } else if (kind == 1) {
+      const uint4* st = reinterpret_cast<const uint4*>(sm->ring + e.roff);
+#pragma unroll
+      for (int cc = 0; cc < 8; cc++) {
+        const uint4 q = st[lane * 8 + (cc ^ (lane & 7))];
+        v[2 * cc] = (uint64_t)q.x | ((uint64_t)q.y << 32);
+        v[2 * cc + 1] = (uint64_t)q.z | ((uint64_t)q.w << 32);
+      }
+    } else if (c.fmt == MS_STATIC_BP) {  // horizontal tail
+      const uint64_t* tailp = reinterpret_cast<const uint64_t*>(c.p + 64ull * c.bw * full);
+      const int bw = c.bw;
+      const uint64_t mask = lowmask(bw);
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        const int t = 16 * lane + k;
+        uint64_t x = 0;
+        if (t < valid) {
+          const uint64_t bit = (uint64_t)t * bw;
+          const int sh = (int)(bit & 63);
+          x = ldg64(tailp + (bit >> 6)) >> sh;
+          if (sh + bw > 64) x |= ldg64(tailp + (bit >> 6) + 1) << (64 - sh);
+          x &= mask;
+        }
+        v[k] = x;
+      }
+    } else {  // raw values: a partial uncompressed chunk or the block formats' remainder
+      const uint64_t* rawp = reinterpret_cast<const uint64_t*>(
+          c.fmt == MS_UNCOMPR ? c.p + 4096 * g : c.p + 16 * c.nb + 8 * c.pwords);
+      const bool inside = c.fmt == MS_UNCOMPR || 16 * c.nb + 8 * (c.pwords + (uint64_t)valid) <= c.size;
+      if (!inside && lane == 0) set_error(ctl, MS_ERR_FORMAT, g);
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] = (16 * lane + k < valid && inside) ? ldg64(rawp + 16 * lane + k) : 0;
+    }
+    body(g, v, valid);
+    __syncwarp();
+    tail = e.rend;
+    rd++;
+    nfl--;
+  }
+  cp_async_wait<0>();
+}
+
+// --------------------------------------------------- CTA tile streams
+
+// A CTA's stream of one column through two large shared-memory buffers.  Block
+// payloads of consecutive chunks are contiguous in every format, so the CTA
+// copies a whole run of chunks (a sub-tile, as many as fit in one buffer) with
+// all its threads at once, and its warps then decode the run's chunks from
+// shared memory while the next run loads into the other buffer.  Per chunk this
+// leaves a header read from shared memory: no per-chunk copy bookkeeping.
+// Chunks come in claims of kClaim consecutive chunks, CTA b taking claims b,
+// b + gridDim.x, ...; a claim's block headers are loaded one claim ahead into a
+// ring of three header buffers.
+constexpr int kClaim = 128;
+#ifndef MS_TILE_BUF
+#define MS_TILE_BUF 32768
+#endif
+#ifndef MS_TILE_THREADS
+#define MS_TILE_THREADS 256
+#endif
+#ifndef MS_TILE_MINB
+#define MS_TILE_MINB 3
+#endif
+constexpr int kTileBuf = MS_TILE_BUF;          // bytes per buffer (two per CTA)
+constexpr int kTileThreads = MS_TILE_THREADS;  // threads per CTA of the tile-stream kernels
+constexpr int kTileMinBlocks = MS_TILE_MINB;
+
+template <int BUF>
+struct TileSmem {
+  uint8_t buf[2][BUF];
+  uint4 hdr[3][kClaim];  // the decoded claim, the scheduled claim, the next claim
+};
+
+// Calls body(g, v, valid) for every chunk g of c; v is zero past `valid`.  Every
+// thread of the CTA must call it (it synchronises the CTA).
+template <int BUF, class Body>
+MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body body) {
+  static_assert(BUF >= 4096 && BUF % 4096 == 0, "buffer size");
+  const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+  const uint64_t nch = (c.n + kBlock - 1) / kBlock;
+  const uint64_t nclaims = (nch + kClaim - 1) / kClaim;
+  const bool blockfmt = is_block_fmt(c.fmt);
+  const uint64_t full = blockfmt ? c.nb : c.n / kBlock;  // chunks held in the buffers
+  // fixed bytes per chunk (static / uncompressed); 0 for block formats
+  const uint32_t fixed = c.fmt == MS_UNCOMPR ? 4096u : (c.fmt == MS_STATIC_BP ? 64u * (uint32_t)c.bw : 0u);
+  const uint64_t pay0 = 16 * c.nb;  // byte offset of the block payloads (block formats)
+
+  auto load_hdr = [&](uint64_t claim, int hb) {
+    if (!blockfmt || claim >= nclaims) return;
+    for (int k = tid; k < kClaim; k += nthr) {
+      const uint64_t g = claim * kClaim + k;
+      if (g < c.nb && 16 * (g + 1) <= c.size) cp_async16(&sm->hdr[hb][k], reinterpret_cast<const uint4*>(c.p) + g);
+    }
+  };
+  // payload word offset and width of chunk g of the claim in header buffer hb
+  auto hdr_of = [&](uint64_t g, uint64_t cb, int hb, uint64_t* off, uint32_t* b, uint64_t* ref) {
+    const uint4 h = sm->hdr[hb][g - cb];
+    const uint64_t w0 = (uint64_t)h.x | (uint64_t)h.y << 32;
+    *ref = (uint64_t)h.z | (uint64_t)h.w << 32;
+    *off = w0 >> 8;
+    *b = (uint32_t)(w0 & 255);
+  };
+  // end (exclusive) of chunk g's payload, in bytes from the payload start
+  auto end_bytes = [&](uint64_t g, uint64_t cb, int hb) -> uint64_t {
+    if (!blockfmt) return (uint64_t)fixed * (g + 1);
+    if (g >= c.nb) return 8 * c.pwords;
+    uint64_t off, ref;
+    uint32_t b;
+    hdr_of(g, cb, hb, &off, &b, &ref);
+    return 8 * (off + 8ull * min(b, 64u));
+  };
+  auto start_bytes = [&](uint64_t g, uint64_t cb, int hb) -> uint64_t {
+    if (!blockfmt) return (uint64_t)fixed * g;
+    if (g >= c.nb) return 8 * c.pwords;
+    uint64_t off, ref;
+    uint32_t b;
+    hdr_of(g, cb, hb, &off, &b, &ref);
+    return 8 * off;
+  };
+
+  uint64_t claim = blockIdx.x;
+  if (claim >= nclaims) return;
+  int hb = 0;
+  uint64_t cb = claim * kClaim, ce = min(nch, cb + kClaim), g = cb;
+  load_hdr(claim, 0);
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  load_hdr(claim + gridDim.x, 1);  // one claim ahead (header buffers rotate 0, 1, 2)
+  // the sub-tile in flight / being decoded: chunks [ga, gb) of claim (hb_s, cb_s) in buffer bi
+  uint64_t ga = 0, gb = 0, base = 0, cb_s = cb;
+  int hb_s = 0, bi = 0;
+  bool live = false;
+  // schedules the next sub-tile from the current claim into buffer nbi and issues its copy
+  auto schedule = [&](int nbi) -> bool {
+    if (g >= ce) {  // next claim (its headers landed with an earlier group)
+      claim += gridDim.x;
+      if (claim >= nclaims) return false;
+      hb = hb == 2 ? 0 : hb + 1;
+      cb = claim * kClaim;
+      ce = min(nch, cb + kClaim);
+      g = cb;
+      load_hdr(claim + gridDim.x, hb == 2 ? 0 : hb + 1);
+    }
+    const uint64_t s0 = start_bytes(g, cb, hb);
+    // chunks of the claim whose payload ends within one buffer from s0 (ends are monotone)
+    uint64_t cnt;
+    if (blockfmt) {
+      const uint64_t k = g + tid;
+      const bool fits = k < ce && end_bytes(k, cb, hb) - s0 <= (uint64_t)BUF;
+      cnt = (uint64_t)__syncthreads_count(fits);
+      cnt = max(cnt, (uint64_t)1);  // a corrupt header never stalls the stream
+    } else {
+      cnt = min(ce - g, (uint64_t)(BUF / max(fixed, 1u)));
+    }
+    const uint64_t e = g + cnt;
+    uint64_t bytes = min(end_bytes(e - 1, cb, hb), blockfmt ? (uint64_t)(c.size - pay0) : (uint64_t)c.size) - s0;
+    bytes = min(bytes, (uint64_t)BUF) & ~15ull;
+    const uint8_t* src = c.p + (blockfmt ? pay0 : 0) + s0;
+    uint4* dst = reinterpret_cast<uint4*>(sm->buf[nbi]);
+    const uint32_t units = (uint32_t)(bytes >> 4);
+    if (c.fmt == MS_UNCOMPR) {
+      for (uint32_t u = tid; u < units; u += nthr)
+        cp_async16(dst + (((u >> 3) << 3) | ((u & 7) ^ ((u >> 3) & 7))), reinterpret_cast<const uint4*>(src) + u);
+    } else {
+      for (uint32_t u = tid; u < units; u += nthr) cp_async16(dst + u, reinterpret_cast<const uint4*>(src) + u);
+    }
+    ga = g;
+    gb = e;
+    base = s0;
+    cb_s = cb;
+    hb_s = hb;
+    g = e;
+    return true;
+  };
+  live = schedule(0);
+  cp_async_commit();
+  while (live) {
+    cp_async_wait<0>();
+    __syncthreads();
+    // this sub-tile (decoded below) and the next one (loading meanwhile)
+    const uint64_t da = ga, db = gb, dbase = base, dcb = cb_s;
+    const int dhb = hb_s, dbi = bi;
+    bi ^= 1;
+    live = schedule(bi);
+    cp_async_commit();
+    for (uint64_t k = da + warp; k < db; k += nwarps) {
+      const int valid = (int)min((uint64_t)kBlock, c.n - k * kBlock);
+      uint64_t v[16];
+      if (k < full) {
+        uint32_t b;
+        uint64_t off, ref = 0;
+        const uint8_t* at;
+        if (blockfmt) {
+          hdr_of(k, dcb, dhb, &off, &b, &ref);
+          // a corrupt header can point outside the column or the staged run
+          if (b > 64 || 8 * (off + 8ull * b) + pay0 > c.size || 8 * off < dbase ||
+              8 * (off + 8ull * b) - dbase > (uint64_t)BUF) {
+            if (lane == 0) set_error(ctl, MS_ERR_FORMAT, k);
+            b = 0;
+            off = dbase / 8;
+          }
+          at = sm->buf[dbi] + (8 * off - dbase);
+        } else {
+          b = (uint32_t)c.bw;
+          at = sm->buf[dbi] + (uint64_t)fixed * k - dbase;
+        }
+        if (c.fmt == MS_UNCOMPR) {
+          const uint4* st = reinterpret_cast<const uint4*>(at);
+#pragma unroll
+          for (int cc = 0; cc < 8; cc++) {
+            const uint4 q = st[lane * 8 + (cc ^ (lane & 7))];
+            v[2 * cc] = (uint64_t)q.x | ((uint64_t)q.y << 32);
+            v[2 * cc + 1] = (uint64_t)q.z | ((uint64_t)q.w << 32);
+          }
+        } else {
+          read_lane_stream(reinterpret_cast<const uint16_t*>(at), lane, (int)b, v);
+          if (c.fmt == MS_FOR_BP) {
+#pragma unroll
+            for (int q = 0; q < 16; q++) v[q] += ref;
+          } else if (c.fmt == MS_DELTA_BP) {
+            uint64_t sum = 0;
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+              sum += v[q];
+              v[q] = sum;
+            }
+            const uint64_t excl = warp_excl_scan(sum, lane) + ref;
+#pragma unroll
+            for (int q = 0; q < 16; q++) v[q] += excl;
+          }
+        }
+      } else if (c.fmt == MS_STATIC_BP) {  // horizontal tail
+        const uint64_t* tailp = reinterpret_cast<const uint64_t*>(c.p + 64ull * c.bw * full);
+        const int bw = c.bw;
+        const uint64_t mask = lowmask(bw);
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+          const int t = 16 * lane + q;
+          uint64_t x = 0;
+          if (t < valid) {
+            const uint64_t bit = (uint64_t)t * bw;
+            const int sh = (int)(bit & 63);
+            x = ldg64(tailp + (bit >> 6)) >> sh;
+            if (sh + bw > 64) x |= ldg64(tailp + (bit >> 6) + 1) << (64 - sh);
+            x &= mask;
+          }
+          v[q] = x;
+        }
+      } else {  // raw values: a partial uncompressed chunk or the block formats' remainder
+        const uint64_t* rawp = reinterpret_cast<const uint64_t*>(
+            c.fmt == MS_UNCOMPR ? c.p + 4096 * k : c.p + pay0 + 8 * c.pwords);
+        const bool inside = c.fmt == MS_UNCOMPR || pay0 + 8 * (c.pwords + (uint64_t)valid) <= c.size;
+        if (!inside && lane == 0) set_error(ctl, MS_ERR_FORMAT, k);
+#pragma unroll
+        for (int q = 0; q < 16; q++) v[q] = (16 * lane + q < valid && inside) ? ldg64(rawp + 16 * lane + q) : 0;
+      }
+      body(k, v, valid);
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
 // ---------------------------------------------------- consumer kernel arguments
 
 // Select / semi-join mark kernel arguments (kernel in ms_consume.cu).
@@ -58,7 +501,23 @@ struct MarkArgs {
   uint32_t* counts;
 };
 
-constexpr int kMarkDepth = 3;
+// Single-column streams (mark, agg_sum, semi-join build, statistics): chunks in
+// flight per warp, staging slot width in bits (wider blocks and uncompressed
+// chunks are decoded in place from global memory) and resident CTAs per SM.
+#ifndef MS_MARK_DEPTH
+#define MS_MARK_DEPTH 3
+#endif
+#ifndef MS_MARK_SLOTW
+#define MS_MARK_SLOTW 64
+#endif
+#ifndef MS_MARK_MINB
+#define MS_MARK_MINB 2
+#endif
+constexpr int kMarkDepth = MS_MARK_DEPTH;
+constexpr int kMarkSlotW = MS_MARK_SLOTW;
+constexpr int kMarkMinBlocks = MS_MARK_MINB;
+template <int D>
+using MarkSmem = StreamSmem<D, kMarkSlotW>;
 
 // Scan of per-chunk match counts (kernel in ms_consume.cu).
 struct ScanArgs {
