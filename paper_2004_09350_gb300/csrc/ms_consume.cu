@@ -155,14 +155,13 @@ __global__ void __launch_bounds__(32 * kPairWarps, 4) k_group_sum(const DevMeta*
 }
 
 // Semi-join build side: set bit key for every key of the build column.
-__global__ void __launch_bounds__(kThreads, 2) k_build_keys(const DevMeta* keys, uint64_t domain, uint32_t* bits,
-                                                             DevCtl* ctl) {
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_build_keys(const DevMeta* keys, uint64_t domain,
+                                                                             uint32_t* bits, DevCtl* ctl) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  auto* sm = reinterpret_cast<MarkSmem<kMarkDepth>*>(smem_raw) + warp;
+  const int lane = threadIdx.x & 31;
+  auto* sm = reinterpret_cast<TileSmem<kTileBuf>*>(smem_raw);
   const ColView c = view_of(keys);
-  const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
-  stream_chunks<kMarkDepth, kMarkSlotW>(c, gw, W, sm, lane, ctl, [&](uint64_t, const uint64_t* v, int valid) {
+  cta_stream<kTileBuf>(c, sm, ctl, [&](uint64_t, const uint64_t* v, int valid) {
 #pragma unroll
     for (int k = 0; k < 16; k++) {
       if (16 * lane + k < valid) {
@@ -177,16 +176,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_build_keys(const DevMeta* keys,
 // Column statistics for the format selector (see ms_column_stats): one decoding
 // pass, per chunk reductions, block-level accumulation in shared memory, one
 // global atomic per statistic per CTA.
-__global__ void __launch_bounds__(kThreads, 2) k_stats(const DevMeta* in, uint64_t* stats, DevCtl* ctl) {
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_stats(const DevMeta* in, uint64_t* stats,
+                                                                        DevCtl* ctl) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ unsigned long long s_acc[MS_STATS_WORDS];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < MS_STATS_WORDS; i += blockDim.x) s_acc[i] = 0;
   __syncthreads();
-  auto* sm = reinterpret_cast<MarkSmem<kMarkDepth>*>(smem_raw) + warp;
+  auto* sm = reinterpret_cast<TileSmem<kTileBuf>*>(smem_raw);
   const ColView c = view_of(in);
-  const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
-  stream_chunks<kMarkDepth, kMarkSlotW>(c, gw, W, sm, lane, ctl, [&](uint64_t, const uint64_t* v, int valid) {
+  cta_stream<kTileBuf>(c, sm, ctl, [&](uint64_t, const uint64_t* v, int valid) {
     uint64_t mx = 0, mn = ~0ull, dmax = 0;
     uint32_t sorted = 0, runs = 0;
     const uint64_t prev_last = __shfl_up_sync(kFull, v[15], 1);
@@ -230,14 +229,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_stats(const DevMeta* in, uint64
   if (blockIdx.x == 0 && threadIdx.x == 0) stats[0] = c.n;
 }
 
-constexpr size_t kStreamSmem = sizeof(MarkSmem<kMarkDepth>) * kWarps;
 constexpr size_t kTileSmemBytes = sizeof(TileSmem<kTileBuf>);
 
+// grid of a tile-stream kernel over a column of at most n_max rows: one CTA per
+// claim, at most the resident CTAs
+template <class K>
+int tile_grid(ms_ctx* c, K kernel, uint64_t n_max) {
+  return grid_for(c, kernel, kTileSmemBytes, cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kClaim), kTileThreads);
+}
+
 ms_status launch_stats(ms_ctx* c, const DevMeta* in, uint64_t* d_stats, uint64_t n_max, cudaStream_t s) {
-  const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
-  const int grid = grid_for(c, k_stats, kStreamSmem, tiles);
+  const int grid = tile_grid(c, k_stats, n_max);
   ProfScope ps(c, MS_K_STATS, s);
-  k_stats<<<grid, kThreads, kStreamSmem, s>>>(in, d_stats, c->ctl);
+  k_stats<<<grid, kTileThreads, kTileSmemBytes, s>>>(in, d_stats, c->ctl);
   return cuda_status(cudaGetLastError());
 }
 
@@ -246,8 +250,7 @@ ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max
   a.counts = w.counts;
   const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
   {
-    const int grid = grid_for(c, k_mark, kTileSmemBytes, cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kClaim),
-                              kTileThreads);
+    const int grid = tile_grid(c, k_mark, n_max);
     ProfScope ps(c, MS_K_MARK, s);
     k_mark<<<grid, kTileThreads, kTileSmemBytes, s>>>(a);
     if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
@@ -267,8 +270,7 @@ ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max
 }
 
 ms_status launch_agg_sum(ms_ctx* c, const DevMeta* in, uint64_t* d_result, uint64_t n_max, cudaStream_t s) {
-  const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
-  const int grid = grid_for(c, k_agg_sum, kTileSmemBytes, cdiv(tiles * kWarps, kClaim), kTileThreads);
+  const int grid = tile_grid(c, k_agg_sum, n_max);
   ProfScope ps(c, MS_K_AGG_SUM, s);
   k_agg_sum<<<grid, kTileThreads, kTileSmemBytes, s>>>(in, d_result, c->ctl);
   return cuda_status(cudaGetLastError());
@@ -287,10 +289,9 @@ ms_status launch_group_sum(ms_ctx* c, const DevMeta* gid, const DevMeta* val, ui
 
 ms_status launch_build_keys(ms_ctx* c, const DevMeta* keys, uint64_t domain, uint32_t* bits, uint64_t n_max,
                             cudaStream_t s) {
-  const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
-  const int grid = grid_for(c, k_build_keys, kStreamSmem, tiles);
+  const int grid = tile_grid(c, k_build_keys, n_max);
   ProfScope ps(c, MS_K_BUILD_KEYS, s);
-  k_build_keys<<<grid, kThreads, kStreamSmem, s>>>(keys, domain, bits, c->ctl);
+  k_build_keys<<<grid, kTileThreads, kTileSmemBytes, s>>>(keys, domain, bits, c->ctl);
   return cuda_status(cudaGetLastError());
 }
 

@@ -47,9 +47,7 @@ struct DevCtl {
   uint64_t op_n;      // element count produced by the last mark kernel
   uint64_t op_words;  // payload words published by an op's final tile
   uint64_t op_nch;    // input chunks of the last mark step (its real length, not a bound)
-  unsigned long long work;       // tile counter of the streaming consumers (0 between launches)
-  unsigned long long work_done;  // their finished CTAs (0 between launches)
-  uint64_t rsv[5];
+  uint64_t rsv[7];
 };
 
 // Read-only view of a column inside a kernel.
@@ -425,22 +423,6 @@ template <int N>
 MS_DEV void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
-// cp.async.wait_group with a run-time count (0 .. 15; larger counts wait for all).
-MS_DEV void cp_async_wait_dyn(int n) {
-  switch (n) {
-#define MS_WAIT_CASE(N) \
-  case N:               \
-    cp_async_wait<N>(); \
-    break;
-    MS_WAIT_CASE(1) MS_WAIT_CASE(2) MS_WAIT_CASE(3) MS_WAIT_CASE(4) MS_WAIT_CASE(5) MS_WAIT_CASE(6)
-    MS_WAIT_CASE(7) MS_WAIT_CASE(8) MS_WAIT_CASE(9) MS_WAIT_CASE(10) MS_WAIT_CASE(11) MS_WAIT_CASE(12)
-    MS_WAIT_CASE(13) MS_WAIT_CASE(14) MS_WAIT_CASE(15)
-#undef MS_WAIT_CASE
-    default:
-      cp_async_wait<0>();
-  }
-}
-
 // Per-warp shared memory of one column stream: D payload slots of 4 KB (a 512-value
 // block at up to 64 bits) and 2D header slots.
 template <int D, int SW = 64>

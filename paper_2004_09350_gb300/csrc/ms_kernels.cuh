@@ -14,256 +14,6 @@
 
 namespace ms {
 
-// Walks the chunks first, first+stride, ... of one column with a per-warp
-// asynchronous stream and calls body(i, g, v, valid) for each decoded chunk.
-template <int D, int SW, class Body>
-MS_DEV void stream_chunks(const ColView& c, uint64_t first, uint64_t stride, StreamSmem<D, SW>* sm, int lane,
-                          DevCtl* ctl, Body body) {
-  const uint64_t nch = (c.n + kBlock - 1) / kBlock;
-  const uint64_t count = first < nch ? (nch - first + stride - 1) / stride : 0;
-  ChunkStream<D, SW> cs{c, first, stride, count, sm, lane};
-  if (count == 0) return;
-  cs.prologue();
-  for (int j = 0; j < D - 1; j++) {
-    cs.prologue_step(j);
-    cp_async_commit();
-  }
-  for (uint64_t i = 0; i < count; i++) {
-    cp_async_wait<D - 2>();
-    __syncwarp();
-    cs.step(i);
-    cp_async_commit();
-    uint64_t v[16];
-    const int valid = cs.decode(i, v, ctl);
-    body(cs.chunk(i), v, valid);
-    __syncwarp();
-  }
-  cp_async_wait<0>();
-}
-
-
-
-// ------------------------------------------------------ byte-ring streams
-
-// A warp's stream of one column through a byte ring in shared memory.  Chunks are
-// copied at their packed size (64*b bytes; 4 KB for an uncompressed chunk), so
-// narrow blocks keep many chunks in flight: the depth adapts to the data, up to
-// kRingMaxFlight chunks.  Work comes in tiles of kRingTile consecutive chunks from
-// the context's tile counter; the first kRingTile lanes load a tile's block
-// headers with one coalesced load each (lane k: chunk k), one tile ahead of use.
-constexpr int kRingTile = 16;
-constexpr int kRingMaxFlight = 12;
-#ifndef MS_RING_BYTES
-#define MS_RING_BYTES 8192
-#endif
-#ifndef MS_RING_MINB
-#define MS_RING_MINB 3
-#endif
-constexpr int kRingBytes = MS_RING_BYTES;       // per warp
-constexpr int kRingMinBlocks = MS_RING_MINB;    // resident CTAs per SM the kernels are compiled for
-
-struct RingEntry {
-  uint64_t ref;
-  uint32_t g;     // chunk
-  uint32_t code;  // b | kind << 8 (kind 0: packed in the ring, 1: uncompressed in the ring, 2: read in place)
-  uint32_t roff;  // ring offset of the payload
-  uint32_t rend;  // ring allocation end (monotone byte count)
-};
-
-template <int R>
-struct RingSmem {
-  uint8_t ring[R];
-  RingEntry fifo[kRingMaxFlight];
-};
-
-// The last CTA of a launch resets the tile counter for the next one.
-MS_DEV void ring_work_done(DevCtl* ctl) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&ctl->work_done, 1ull) == gridDim.x - 1) {
-      ctl->work = 0;
-      ctl->work_done = 0;
-      __threadfence();
-    }
-  }
-}
-
-// Calls body(g, v, valid) for every chunk g of c (each exactly once across the
-// grid, in no particular order); v is zero past `valid`.  Every CTA must call
-// ring_work_done afterwards.
-template <int R, class Body>
-MS_DEV void ring_stream(const ColView& c, RingSmem<R>* sm, int lane, DevCtl* ctl, Body body) {
-  static_assert(R >= 4096 && (R & (R - 1)) == 0, "ring size");
-  const uint64_t nch = (c.n + kBlock - 1) / kBlock;
-  const uint64_t ntiles = (nch + kRingTile - 1) / kRingTile;
-  const bool blockfmt = is_block_fmt(c.fmt);
-  const uint64_t full = c.fmt == MS_STATIC_BP ? c.n / kBlock : (c.fmt == MS_UNCOMPR ? c.n / kBlock : c.nb);
-  auto grab = [&]() -> uint64_t {
-    unsigned long long t = 0;
-    if (lane == 0) t = atomicAdd(&ctl->work, 1ull);
-    return __shfl_sync(kFull, (uint64_t)t, 0);
-  };
-  auto load_hdr = [&](uint64_t t) -> uint4 {
-    const uint64_t g = t * kRingTile + lane;
-    uint4 h = make_uint4(0, 0, 0, 0);
-    if (blockfmt && lane < kRingTile && t < ntiles && g < c.nb && 16 * (g + 1) <= c.size)
-      h = __ldg(reinterpret_cast<const uint4*>(c.p) + g);
-    return h;
-  };
-  uint64_t ti = grab(), tn = ti < ntiles ? grab() : ntiles;
-  uint4 hi = load_hdr(ti), hn = load_hdr(tn);
-  uint32_t ki = 0;
-  // the next chunk to issue, resolved once: chunk, kind, width, source, units, ref
-  bool have = false;
-  uint64_t ng = 0, nsrc = 0, nref = 0;
-  uint32_t nkind = 2, nb = 0, nunits = 0;
-  auto next = [&]() {
-    have = false;
-    while (ti < ntiles) {
-      const uint64_t g = ti * kRingTile + ki;
-      if (ki == kRingTile || g >= nch) {  // next tile
-        ti = tn;
-        hi = hn;
-        ki = 0;
-        if (ti < ntiles) {
-          tn = grab();
-          hn = load_hdr(tn);
-        }
-        continue;
-      }
-      ng = g;
-      nkind = 2;
-      nb = 0;
-      nunits = 0;
-      nsrc = 0;
-      nref = 0;
-      if (c.fmt == MS_UNCOMPR) {
-        if (g < full) {
-          nkind = 1;
-          nunits = 256;
-          nsrc = (uint64_t)c.p + 4096 * g;
-        }
-      } else if (c.fmt == MS_STATIC_BP) {
-        nb = (uint32_t)c.bw;
-        if (g < full) {
-          nkind = 0;
-          nunits = 4 * nb;
-          nsrc = (uint64_t)c.p + 64ull * nb * g;
-        }
-      } else if (g < c.nb) {
-        const uint64_t w0 = (uint64_t)__shfl_sync(kFull, hi.x, ki) | (uint64_t)__shfl_sync(kFull, hi.y, ki) << 32;
-        nref = (uint64_t)__shfl_sync(kFull, hi.z, ki) | (uint64_t)__shfl_sync(kFull, hi.w, ki) << 32;
-        nb = (uint32_t)(w0 & 255);
-        if (nb > 64 || 16 * (g + 1) > c.size || 16 * c.nb + 8 * ((w0 >> 8) + 8ull * nb) > c.size) {
-          if (lane == 0) set_error(ctl, MS_ERR_FORMAT, g);
-          nb = 0;
-        }
-        nkind = 0;
-        nunits = 4 * nb;
-        nsrc = (uint64_t)c.p + 16 * c.nb + 8 * (w0 >> 8);
-      }
-      ki++;
-      have = true;
-      return;
-    }
-  };
-  next();
-  uint32_t head = 0, tail = 0, wr = 0, rd = 0;
-  int nfl = 0;
-  for (;;) {
-    // issue chunks while the ring and the entry queue have room
-    while (have && nfl < kRingMaxFlight) {
-      const uint32_t need = 16 * nunits;
-      uint32_t roff = 0;
-      if (need) {
-        const uint32_t pos = head & (R - 1);
-        const uint32_t skip = pos + need > R ? R - pos : 0;
-        if (head + skip + need - tail > R) break;  // full: decode first
-        head += skip;
-        roff = head & (R - 1);
-        head += need;
-        uint4* dst = reinterpret_cast<uint4*>(sm->ring + roff);
-        const uint4* s4 = reinterpret_cast<const uint4*>(nsrc);
-        if (nkind == 1) {
-          for (uint32_t u = lane; u < nunits; u += 32)
-            cp_async16(dst + (((u >> 3) << 3) | ((u & 7) ^ ((u >> 3) & 7))), s4 + u);
-        } else {
-          for (uint32_t u = lane; u < nunits; u += 32) cp_async16(dst + u, s4 + u);
-        }
-      }
-      if (lane == 0) sm->fifo[wr % kRingMaxFlight] = RingEntry{nref, (uint32_t)ng, nb | nkind << 8, roff, head};
-      cp_async_commit();
-      wr++;
-      nfl++;
-      next();
-    }
-    if (nfl == 0) break;
-    cp_async_wait_dyn(nfl - 1);
-    __syncwarp();
-    const RingEntry e = sm->fifo[rd % kRingMaxFlight];
-    const uint64_t g = e.g;
-    const int b = (int)(e.code & 255), kind = (int)(e.code >> 8);
-    const int valid = (int)min((uint64_t)kBlock, c.n - g * kBlock);
-    uint64_t v[16];
-    if (kind == 0) {
-      read_lane_stream(reinterpret_cast<const uint16_t*>(sm->ring + e.roff), lane, b, v);
-      if (c.fmt == MS_FOR_BP) {
-#pragma unroll
-        for (int k = 0; k < 16; k++) v[k] += e.ref;
-      } else if (c.fmt == MS_DELTA_BP) {
-        uint64_t sum = 0;
-#pragma unroll
-        for (int k = 0; k < 16; k++) {
-          sum += v[k];
-          v[k] = sum;
-        }
-        const uint64_t excl = warp_excl_scan(sum, lane) + e.ref;
-#pragma unroll
-        for (int k = 0; k < 16; k++) v[k] += excl;
-      }
-    } else if (kind == 1) {
-      const uint4* st = reinterpret_cast<const uint4*>(sm->ring + e.roff);
-#pragma unroll
-      for (int cc = 0; cc < 8; cc++) {
-        const uint4 q = st[lane * 8 + (cc ^ (lane & 7))];
-        v[2 * cc] = (uint64_t)q.x | ((uint64_t)q.y << 32);
-        v[2 * cc + 1] = (uint64_t)q.z | ((uint64_t)q.w << 32);
-      }
-    } else if (c.fmt == MS_STATIC_BP) {  // horizontal tail
-      const uint64_t* tailp = reinterpret_cast<const uint64_t*>(c.p + 64ull * c.bw * full);
-      const int bw = c.bw;
-      const uint64_t mask = lowmask(bw);
-#pragma unroll
-      for (int k = 0; k < 16; k++) {
-        const int t = 16 * lane + k;
-        uint64_t x = 0;
-        if (t < valid) {
-          const uint64_t bit = (uint64_t)t * bw;
-          const int sh = (int)(bit & 63);
-          x = ldg64(tailp + (bit >> 6)) >> sh;
-          if (sh + bw > 64) x |= ldg64(tailp + (bit >> 6) + 1) << (64 - sh);
-          x &= mask;
-        }
-        v[k] = x;
-      }
-    } else {  // raw values: a partial uncompressed chunk or the block formats' remainder
-      const uint64_t* rawp = reinterpret_cast<const uint64_t*>(
-          c.fmt == MS_UNCOMPR ? c.p + 4096 * g : c.p + 16 * c.nb + 8 * c.pwords);
-      const bool inside = c.fmt == MS_UNCOMPR || 16 * c.nb + 8 * (c.pwords + (uint64_t)valid) <= c.size;
-      if (!inside && lane == 0) set_error(ctl, MS_ERR_FORMAT, g);
-#pragma unroll
-      for (int k = 0; k < 16; k++) v[k] = (16 * lane + k < valid && inside) ? ldg64(rawp + 16 * lane + k) : 0;
-    }
-    body(g, v, valid);
-    __syncwarp();
-    tail = e.rend;
-    rd++;
-    nfl--;
-  }
-  cp_async_wait<0>();
-}
-
 // --------------------------------------------------- CTA tile streams
 
 // A CTA's stream of one column through two large shared-memory buffers.  Block
@@ -501,23 +251,7 @@ struct MarkArgs {
   uint32_t* counts;
 };
 
-// Single-column streams (mark, agg_sum, semi-join build, statistics): chunks in
-// flight per warp, staging slot width in bits (wider blocks and uncompressed
-// chunks are decoded in place from global memory) and resident CTAs per SM.
-#ifndef MS_MARK_DEPTH
-#define MS_MARK_DEPTH 3
-#endif
-#ifndef MS_MARK_SLOTW
-#define MS_MARK_SLOTW 64
-#endif
-#ifndef MS_MARK_MINB
-#define MS_MARK_MINB 2
-#endif
-constexpr int kMarkDepth = MS_MARK_DEPTH;
-constexpr int kMarkSlotW = MS_MARK_SLOTW;
-constexpr int kMarkMinBlocks = MS_MARK_MINB;
-template <int D>
-using MarkSmem = StreamSmem<D, kMarkSlotW>;
+
 
 // Scan of per-chunk match counts (kernel in ms_consume.cu).
 struct ScanArgs {

@@ -228,6 +228,7 @@ def star_fact(seed: int, n: int) -> dict:
 # ms_cmp ids: LT three times as often as the others
 BATCH_CMPS = (2, 2, 2, 6, 5, 0, 1, 3, 4)
 BATCH_Y_SHAPES = ("uniform", "offset", "sorted", "skewed")
+BATCH_SELECTIVITIES = (0.001, 0.1, 0.9)
 
 
 def _unit(z) -> float:
@@ -238,7 +239,8 @@ def batch_fragments(seed: int, count: int, lo_log2: float = 10, hi_log2: float =
     """Parameters of `count` fragments sum(y[i] for x[i] <cmp> c1 (c2)):
     n = floor(2^(lo + u (hi - lo))) (log-uniform), x ~ U[0, 2^bx), y of one of
     BATCH_Y_SHAPES at width by, with bx, by uniform in [1, max_bits], and a
-    predicate whose constant sits at a uniformly drawn quantile of x's range."""
+    predicate whose constant sits at the quantile s of x's range, s drawn from
+    BATCH_SELECTIVITIES (BETWEEN spans s/2 of the range above it)."""
     z = splitmix64(seed, 8 * count).reshape(count, 8)
     out = []
     for f in range(count):
@@ -247,8 +249,9 @@ def batch_fragments(seed: int, count: int, lo_log2: float = 10, hi_log2: float =
         by = 1 + int(z[f, 2] % np.uint64(max_bits))
         shape = BATCH_Y_SHAPES[int(z[f, 3] % np.uint64(len(BATCH_Y_SHAPES)))]
         cmp = BATCH_CMPS[int(z[f, 4] % np.uint64(len(BATCH_CMPS)))]
-        c1 = int(_unit(z[f, 5]) * (1 << bx))
-        c2 = c1 + int(_unit(z[f, 6]) * (1 << bx) / 2)
+        sel = BATCH_SELECTIVITIES[int(z[f, 5] % np.uint64(len(BATCH_SELECTIVITIES)))]
+        c1 = int(sel * (1 << bx))
+        c2 = c1 + int(sel * (1 << bx) / 2)
         sx = int(z[f, 7] & np.uint64(0xFFFFFFFF))
         out.append({"n": n, "bx": bx, "by": by, "shape": shape, "cmp": cmp, "c1": c1, "c2": c2,
                     "seed_x": sx, "seed_y": sx + 0x1000})
