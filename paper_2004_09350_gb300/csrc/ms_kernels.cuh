@@ -354,13 +354,16 @@ struct SmemProject {
   uint32_t list[kBlock];       // data blocks to decode, relative to the first one
   uint16_t runs[32];           // run-start mask per lane
 };
+constexpr int kSpanBytes = 16384;      // data blocks a project warp stages at once
+constexpr uint64_t kSpanMaxBlocks = 128;  // longest block span of one output chunk staged
 struct SmemProjectRandom {
   StreamSmem<kProdDepth> s0;  // positions
+  uint8_t span[kSpanBytes];   // consecutive data blocks touched by the output chunk
 };
 struct SmemProjectDelta {
   StreamSmem<kProdDepth2> s0;  // positions
-  StreamSmem<kProdDepth> s1;   // the data blocks, one continuous (seekable) stream
   uint64_t aux[kBlock];        // the data block decoded last
+  uint8_t span[kSpanBytes];    // consecutive data blocks touched by the output chunk
 };
 struct SmemEmit {
   uint32_t bits[kEmitSpan * 16];
@@ -566,17 +569,168 @@ MS_DEV void project_gather(const ProduceArgs& a, const ColView& d, const uint64_
     if (pending & (1u << k)) v[k] = read_at(d, p[k]);
 }
 
-// project core for DELTA data (a value needs its block's prefix sum, so blocks are
-// decoded whole).  The warp keeps one data stream across its output chunks.
-// While positions advance through nearby blocks, the stream flows; a gap of more
-// than kSeekGap blocks, or a step backwards (unsorted positions), restarts it at
-// the needed block.  Blocks the stream passes over are fetched but not decoded.
-constexpr uint64_t kSeekGap = 4;
+// project core for sorted positions into DYN / FOR / DELTA / static-BP data: the
+// data blocks the warp's positions span are copied into shared memory in pieces
+// of consecutive blocks (their payloads are contiguous), 16-byte coalesced
+// copies.  DYN / FOR / static values are cut out of their blocks there; DELTA
+// blocks are decoded whole (prefix sums) into `aux` and the positions read from
+// it.  A random read per position would touch up to 32 scattered sectors per
+// warp load and a DELTA block fetch per touched block; this copies each touched
+// block once, in full.  Returns false (nothing done) for unsorted or
+// out-of-range positions, other formats, or spans longer than kSpanMaxBlocks.
+MS_DEV bool gather_staged(const ColView& d, const uint64_t p[16], int valid, int lane, uint64_t v[16],
+                          uint8_t* span, uint64_t* aux, DevCtl* ctl) {
+  if (d.fmt == MS_UNCOMPR || (d.fmt == MS_DELTA_BP && !aux) || valid <= 0) return false;
+  const int nv = max(0, min(16, valid - 16 * lane));
+  bool ok = true;
+  uint64_t mn = ~0ull, mx = 0;
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    if (k < nv) {
+      ok &= p[k] < d.n;
+      if (k) ok &= p[k - 1] <= p[k];
+      mn = min(mn, p[k]);
+      mx = max(mx, p[k]);
+    }
+  }
+  const uint64_t prev_mx = __shfl_up_sync(kFull, mx, 1);
+  if (lane > 0 && nv > 0 && prev_mx > mn) ok = false;
+  if (!__all_sync(kFull, ok)) return false;
+  const uint64_t p_lo = __shfl_sync(kFull, mn, 0);
+  uint64_t p_hi = mx;
+#pragma unroll
+  for (int dd = 16; dd; dd >>= 1) p_hi = max(p_hi, __shfl_xor_sync(kFull, p_hi, dd));
+  const uint64_t B_lo = p_lo >> 9, B_hi = p_hi >> 9;
+  if (B_hi - B_lo >= kSpanMaxBlocks) return false;
+  const bool blockfmt = d.fmt != MS_STATIC_BP;
+  const uint64_t nfull = blockfmt ? d.nb : d.n / kBlock;  // blocks with a packed payload
+  const uint64_t pay0 = blockfmt ? 16 * d.nb : 0;
+  const uint16_t* s16 = reinterpret_cast<const uint16_t*>(span);
+#pragma unroll
+  for (int k = 0; k < 16; k++) v[k] = 0;
+  for (uint64_t lo_blk = B_lo; lo_blk <= B_hi && lo_blk < nfull;) {
+    // lane k: block lo_blk + k: payload word offset, width, reference
+    const uint64_t hb = lo_blk + lane;
+    const bool here = hb <= B_hi && hb < nfull;
+    uint64_t off = 0, ref = 0;
+    uint32_t b = 0;
+    if (here) {
+      if (blockfmt) {
+        const uint64_t w0 = 16 * (hb + 1) <= d.size ? ldg64(d.p + 16 * hb) : 0;
+        ref = 16 * (hb + 1) <= d.size ? ldg64(d.p + 16 * hb + 8) : 0;
+        off = w0 >> 8;
+        b = (uint32_t)(w0 & 255);
+        if (b > 64 || 16 * (hb + 1) > d.size || pay0 + 8 * (off + 8ull * b) > d.size) {
+          set_error(ctl, MS_ERR_FORMAT, hb);
+          b = 0;
+          off = 0;
+        }
+      } else {
+        b = (uint32_t)d.bw;
+        off = 8ull * b * hb;
+      }
+    }
+    const uint64_t off_lo = __shfl_sync(kFull, off, 0);
+    const uint64_t end = off + 8ull * b;
+    // blocks whose payload ends within one span buffer (ends are monotone); a
+    // corrupt header yields an empty block and never stalls the loop
+    const bool fits = here && off >= off_lo && 8 * (end - off_lo) <= (uint64_t)kSpanBytes;
+    const int cnt = max(1, __popc(__ballot_sync(kFull, fits)));
+    const uint64_t bytes = min(8 * (__shfl_sync(kFull, end, cnt - 1) - off_lo), (uint64_t)kSpanBytes);
+    const uint4* src = reinterpret_cast<const uint4*>(d.p + pay0 + 8 * off_lo);
+    for (uint32_t u = lane; u < (uint32_t)(bytes >> 4); u += 32) cp_async16(reinterpret_cast<uint4*>(span) + u, src + u);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+    const uint64_t hi_blk = lo_blk + cnt;  // exclusive
+    if (d.fmt == MS_DELTA_BP) {
+      for (int q = 0; q < cnt; q++) {
+        const uint64_t B = lo_blk + q;
+        const uint64_t boff = __shfl_sync(kFull, off, q) - off_lo;
+        const uint32_t bb = __shfl_sync(kFull, b, q);
+        const uint64_t rr = __shfl_sync(kFull, ref, q);
+        bool need = false;
+#pragma unroll
+        for (int k = 0; k < 16; k++) need |= k < nv && (p[k] >> 9) == B;
+        if (!__any_sync(kFull, need)) continue;
+        if (8 * boff + 64ull * bb > bytes) {  // a corrupt header chain: never read past the copy
+          if (lane == 0) set_error(ctl, MS_ERR_FORMAT, B);
+          continue;
+        }
+        uint64_t t[16];
+        read_lane_stream(reinterpret_cast<const uint16_t*>(span + 8 * boff), lane, (int)bb, t);
+        uint64_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          sum += t[k];
+          t[k] = sum;
+        }
+        const uint64_t excl = warp_excl_scan(sum, lane) + rr;
+#pragma unroll
+        for (int k = 0; k < 16; k++) aux[swz(16 * lane + k)] = t[k] + excl;
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+          if (k < nv && (p[k] >> 9) == B) v[k] = aux[swz((int)(p[k] & 511))];
+        __syncwarp();
+      }
+      __syncwarp();
+      lo_blk = hi_blk;
+      continue;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const uint64_t B = p[k] >> 9;
+      const bool mine = k < nv && B >= lo_blk && B < hi_blk;
+      const int sl = mine ? (int)(B - lo_blk) : 0;
+      const uint64_t boff = __shfl_sync(kFull, off, sl) - off_lo;
+      const uint32_t bb = __shfl_sync(kFull, b, sl);
+      const uint64_t rr = __shfl_sync(kFull, ref, sl);
+      if (mine && bb && 8 * boff + 64ull * bb > bytes) {  // a corrupt header chain: never read past the copy
+        set_error(ctl, MS_ERR_FORMAT, B);
+      } else if (mine && bb) {
+        const uint32_t r = (uint32_t)(p[k] & 511), j = r >> 4, kk = r & 15;
+        const uint32_t bit = kk * bb, q0 = bit >> 4, sh = bit & 15, nq = (sh + bb + 15) >> 4;
+        const uint32_t h0 = (uint32_t)(4 * boff) + 32 * q0 + j;  // halfword index in the span
+        uint64_t w = 0, h4 = 0;
+#pragma unroll
+        for (uint32_t t = 0; t < 4; t++)
+          if (t < nq) w |= (uint64_t)s16[h0 + 32 * t] << (16 * t);
+        if (nq > 4) h4 = s16[h0 + 128];
+        uint64_t x = (w >> sh) | (sh ? h4 << (64 - sh) : 0);
+        v[k] = (x & lowmask((int)bb)) + (d.fmt == MS_FOR_BP ? rr : 0);
+      } else if (mine) {
+        v[k] = d.fmt == MS_FOR_BP ? rr : 0;
+      }
+    }
+    __syncwarp();
+    lo_blk = hi_blk;
+  }
+  // positions in the uncompressed remainder (block formats) or the horizontal tail (static BP)
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    if (k < nv && (p[k] >> 9) >= nfull) {
+      if (blockfmt) {
+        const uint64_t at = pay0 + 8 * d.pwords + 8 * (p[k] - kBlock * d.nb);
+        v[k] = at + 8 <= d.size ? ldg64(d.p + at) : 0;
+      } else {
+        const uint64_t* tail = reinterpret_cast<const uint64_t*>(d.p + 64ull * d.bw * nfull);
+        const uint64_t bit = (p[k] - kBlock * nfull) * (uint64_t)d.bw;
+        const int sh = (int)(bit & 63);
+        uint64_t x = ldg64(tail + (bit >> 6)) >> sh;
+        if (sh + d.bw > 64) x |= ldg64(tail + (bit >> 6) + 1) << (64 - sh);
+        v[k] = x & lowmask(d.bw);
+      }
+    }
+  }
+  return true;
+}
 
-template <class Smem, class DS>
-MS_DEV void merge_gather(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
-                         uint64_t v[16], Smem* sm, DS& ds, uint64_t& ds_next, uint64_t& cur_blk) {
-  constexpr int D = kProdDepth;
+// project core for DELTA data when the positions are unsorted or spread over
+// more than kSpanMaxBlocks blocks: every distinct touched block is decoded once
+// (prefix sums) into `aux` and the positions in it read from there.
+MS_DEV void gather_delta_blocks(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
+                                uint64_t v[16], uint8_t* span, uint64_t* aux) {
   uint32_t pending = 0;
 #pragma unroll
   for (int k = 0; k < 16; k++) {
@@ -586,51 +740,22 @@ MS_DEV void merge_gather(const ProduceArgs& a, const ColView& d, const uint64_t 
       else set_error(a.ctl, MS_ERR_OUT_OF_RANGE, p[k]);
     }
   }
-  const uint64_t d_nch = (d.n + kBlock - 1) / kBlock;
   while (__ballot_sync(kFull, pending) != 0) {
     uint64_t mb = ~0ull;
 #pragma unroll
     for (int k = 0; k < 16; k++)
       if (pending & (1u << k)) mb = min(mb, p[k] / kBlock);
     const uint64_t B = warp_min(mb);
-    if (B != cur_blk) {
-      const bool live = ds.count > 0 && ds_next < ds.count;
-      const uint64_t nxt = live ? ds.first + ds_next : ~0ull;
-      if (!live || B < nxt || B > nxt + kSeekGap) {  // (re)start the stream at block B
-        cp_async_wait<0>();
-        __syncwarp();
-        ds.first = B;
-        ds.count = d_nch - B;
-        ds_next = 0;
-        ds.prologue();
-        for (int j = 0; j < D - 1; j++) {
-          ds.prologue_step(j);
-          cp_async_commit();
-        }
-      }
-      while (ds.first + ds_next <= B) {
-        cp_async_wait<D - 2>();
-        __syncwarp();
-        ds.step(ds_next);
-        cp_async_commit();
-        if (ds.first + ds_next == B) {
-          uint64_t t[16];
-          ds.decode(ds_next, t, a.ctl);
+    uint64_t t[16];
+    decode_chunk(d, B, lane, t, reinterpret_cast<uint16_t*>(span), a.ctl);
 #pragma unroll
-          for (int k = 0; k < 16; k++) sm->aux[swz(16 * lane + k)] = t[k];
-        }
-        __syncwarp();
-        ds_next++;
-      }
-      cur_blk = B;
-    }
-    if (mb == B) {  // only lanes with positions in block B gather
+    for (int k = 0; k < 16; k++) aux[swz(16 * lane + k)] = t[k];
+    __syncwarp();
 #pragma unroll
-      for (int k = 0; k < 16; k++) {
-        if ((pending & (1u << k)) && p[k] / kBlock == B) {
-          v[k] = sm->aux[swz((int)(p[k] % kBlock))];
-          pending &= ~(1u << k);
-        }
+    for (int k = 0; k < 16; k++) {
+      if ((pending & (1u << k)) && p[k] / kBlock == B) {
+        v[k] = aux[swz((int)(p[k] % kBlock))];
+        pending &= ~(1u << k);
       }
     }
     __syncwarp();
@@ -1159,10 +1284,6 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
   const ColView main_col = kProject ? c1 : c0;
   ChunkStream<D> st0{main_col, first, stride, (OP == OP_EMIT) ? 0 : count, ring0, lane};
   ChunkStream<D> st1{c1, first, stride, (OP == OP_CALC && a.in1) ? count : 0, ring1, lane};
-  // DELTA project: one data stream per warp that survives across output chunks
-  ChunkStream<kProdDepth> ds{c0, 0, 1, 0, nullptr, lane};
-  uint64_t ds_next = 0, cur_blk = ~0ull;
-  if constexpr (OP == OP_PROJECT_DELTA) ds.sm = &sm->s1;
   if (OP != OP_EMIT && count) {
     for (int i = 0; i < D; i++) {
       st0.issue_header(i);
@@ -1210,11 +1331,12 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
       } else if constexpr (OP == OP_PROJECT) {  // c0 = data, st0 streams the positions (c1)
         uint64_t p[16];
         valid = st0.decode(i, p, ctl);
-        gather_random(a, c0, p, valid, lane, v);
+        if (!gather_staged(c0, p, valid, lane, v, sm->span, nullptr, ctl)) gather_random(a, c0, p, valid, lane, v);
       } else {  // OP_PROJECT_DELTA
         uint64_t p[16];
         valid = st0.decode(i, p, ctl);
-        merge_gather(a, c0, p, valid, lane, v, sm, ds, ds_next, cur_blk);
+        if (!gather_staged(c0, p, valid, lane, v, sm->span, sm->aux, ctl))
+          gather_delta_blocks(a, c0, p, valid, lane, v, sm->span, sm->aux);
       }
       __syncwarp();
     }

@@ -173,6 +173,30 @@ def test_project_every_format_pair(ctx, data_fmt, out_fmt):
     ctx.free(dcol)
 
 
+@pytest.mark.parametrize("data_fmt", [ms.STATIC_BP, ms.DYN_BP, ms.FOR_BP])
+@pytest.mark.parametrize("step", [1, 3, 20, 70, 200, 2000])
+def test_project_sorted_spans(ctx, data_fmt, step):
+    """Sorted positions every `step` rows (plus a jitter): an output chunk spans from
+    one data block to hundreds of them, so its blocks are staged in one piece, in
+    several pieces of wide (40-bit) blocks, or read at random past the span limit;
+    positions also reach the uncompressed remainder / static tail."""
+    n = 300 * 512 + 301
+    d = synth.skewed_widths(41, n, widths=(1, 17, 40, 64)) if data_fmt != ms.STATIC_BP else synth.uniform(41, n, 0, 1 << 40)
+    dcol, bw = gpu_col(ctx, d, data_fmt)
+    base = np.arange(0, n, step, dtype=np.uint64)
+    jit = synth.uniform(42, base.size, 0, max(step // 2, 1))
+    pos = np.minimum(base + jit, np.uint64(n - 1))
+    pos = np.concatenate([pos, np.arange(n - 40, n, dtype=np.uint64)])
+    pos.sort()
+    pcol, _ = gpu_col(ctx, pos, ms.DELTA_BP)
+    want = oracle.project(d, pos)
+    out = ctx.project(dcol, pcol, fmt=ms.DYN_BP)
+    assert_column(ctx, out, want, ms.DYN_BP)
+    ctx.free(out)
+    ctx.free(pcol)
+    ctx.free(dcol)
+
+
 @pytest.mark.parametrize("data_fmt", FMTS)
 @pytest.mark.parametrize("pos_fmt", FMTS)
 def test_project_position_formats_and_unsorted(ctx, data_fmt, pos_fmt):
