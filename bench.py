@@ -129,31 +129,15 @@ def block_widths(x, delta=False):
 
 
 def touched_bytes_dyn(x_widths, n, pos):
-    """32-byte sectors of a dynamic-BP column that random reads at `pos` touch
-    (block header + the halfwords of each value's lane stream)."""
+    """Bytes of the 512-value blocks of a dynamic-BP column that positions `pos`
+    touch (header + payload of each touched block; the remainder's touched
+    32-byte sectors): the unit of data movement of a block-format gather."""
     nb = x_widths.size
-    pay_off = 16 * nb + 8 * np.concatenate([[0], np.cumsum(8 * x_widths)])[:-1]
-    total_bytes = 16 * nb + 64 * int(x_widths.sum()) + 8 * (n % BLOCK)
-    touched = np.zeros(total_bytes // 32 + 2, dtype=bool)
     p = pos.astype(np.int64)
-    inblk = p < nb * BLOCK
-    pm, pr = p[inblk], p[~inblk]
-    g = pm >> 9
-    r = pm & 511
-    j, kk = r >> 4, r & 15
-    b = x_widths[g]
-    touched[(16 * g) >> 5] = True
-    q0 = (kk * b) >> 4
-    q1 = np.where(b > 0, (kk * b + b - 1) >> 4, q0 - 1)
-    for t in range(6):
-        q = q0 + t
-        ok = q <= q1
-        addr = pay_off[g[ok]] + 2 * (32 * q[ok] + j[ok])
-        touched[addr >> 5] = True
-    if pr.size:
-        rem_off = 16 * nb + 64 * int(x_widths.sum())
-        touched[(rem_off + 8 * (pr - nb * BLOCK)) >> 5] = True
-    return int(touched.sum()) * 32
+    g = np.unique(p[p < nb * BLOCK] >> 9)
+    rem = p[p >= nb * BLOCK]
+    sectors = np.unique((8 * (rem - nb * BLOCK)) >> 5).size if rem.size else 0
+    return int(16 * g.size + 64 * int(x_widths[g].sum()) + 32 * sectors)
 
 
 def touched_bytes_delta(k_widths, pos):
@@ -174,7 +158,7 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -205,7 +189,7 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "period_ms": 50}
 
 
 # ------------------------------------------------------------- CPU oracle
@@ -317,17 +301,31 @@ def bench_ours(args):
         ctx.check(what=f"{label} warm-up")
         want = None
         barrier()
-        ctx.profile(True)
+        # the clock sampler (50 ms period) also runs over untimed steps just before and
+        # after the timed ones, so that a short timed region still gets samples
+        w0 = time.perf_counter()
+        free_all(ctx, run_plan(ctx, cx, ck, c, fm, res))
+        torch.cuda.synchronize()
+        pad = max(1, int(0.4 / max(time.perf_counter() - w0, 1e-4)))
         clocks = Clocks(local) if label == "compressed" else None
+        if clocks:
+            for _ in range(pad):
+                free_all(ctx, run_plan(ctx, cx, ck, c, fm, res))
+        barrier()
+        ctx.profile(True)
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record()
         for _ in range(args.steps):
             free_all(ctx, run_plan(ctx, cx, ck, c, fm, res))
         t1.record()
         barrier()
-        ck_info = clocks.stop() if clocks else None
         prof = ctx.profile_collect()
         ctx.profile(False)
+        if clocks:
+            for _ in range(pad):
+                free_all(ctx, run_plan(ctx, cx, ck, c, fm, res))
+            torch.cuda.synchronize()
+        ck_info = clocks.stop() if clocks else None
         ctx.check(what=f"{label} timed steps")
         ms_step = t0.elapsed_time(t1) / args.steps
         if world > 1:
