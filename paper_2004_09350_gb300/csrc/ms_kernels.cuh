@@ -354,16 +354,26 @@ struct SmemProject {
   uint32_t list[kBlock];       // data blocks to decode, relative to the first one
   uint16_t runs[32];           // run-start mask per lane
 };
-constexpr int kSpanBytes = 16384;      // data blocks a project warp stages at once
-constexpr uint64_t kSpanMaxBlocks = 128;  // longest block span of one output chunk staged
 struct SmemProjectRandom {
-  StreamSmem<kProdDepth> s0;  // positions
-  uint8_t span[kSpanBytes];   // consecutive data blocks touched by the output chunk
+  StreamSmem<kProdDepth2> s0;  // positions
 };
 struct SmemProjectDelta {
   StreamSmem<kProdDepth2> s0;  // positions
   uint64_t aux[kBlock];        // the data block decoded last
-  uint8_t span[kSpanBytes];    // consecutive data blocks touched by the output chunk
+};
+// Shared by the CTA of a project kernel: a piece of consecutive data blocks (their
+// payloads are contiguous) and the pieces' block headers.
+// (152 KB beside DYN/FOR/static data so that a typical tile's span is one piece;
+// 96 KB beside DELTA data, whose warps also keep a decoded block each)
+constexpr int kCtaHdr = 256;
+template <int kCtaBuf>
+struct ProjectCta {
+  static constexpr int kBuf = kCtaBuf;
+  uint8_t buf[kCtaBuf];
+  uint4 hdr[kCtaHdr];  // {(payload word offset << 8) | b, reference} of the piece's blocks
+  uint64_t lo[kWarps], hi[kWarps];
+  uint32_t ok[kWarps], nv[kWarps];
+  uint64_t off_lo;
 };
 struct SmemEmit {
   uint32_t bits[kEmitSpan * 16];
@@ -374,6 +384,12 @@ struct SmemEmit {
 
 #ifndef MS_PROJECT_MIN_BLOCKS
 #define MS_PROJECT_MIN_BLOCKS 1  // resident CTAs per SM the project kernel is compiled for
+#endif
+#ifndef MS_PROJECT_CTA_BUF
+#define MS_PROJECT_CTA_BUF (152 * 1024)  // staged data blocks per CTA (DYN / FOR / static data)
+#endif
+#ifndef MS_PROJECT_DELTA_CTA_BUF
+#define MS_PROJECT_DELTA_CTA_BUF (96 * 1024)  // staged data blocks per CTA (DELTA data)
 #endif
 
 template <int OP>
@@ -387,6 +403,9 @@ struct ProducePlan {
               typename std::conditional<OP == OP_EMIT, SmemEmit, SmemSingle>::type>::type>::type>::type;
   static constexpr int kMinBlocks =
       (OP == OP_PROJECT_DELTA || OP == OP_PROJECT) ? MS_PROJECT_MIN_BLOCKS : (OP == OP_CALC ? 1 : 2);
+  // CTA-shared shared memory behind the per-warp plans
+  using Cta = ProjectCta<OP == OP_PROJECT_DELTA ? MS_PROJECT_DELTA_CTA_BUF : MS_PROJECT_CTA_BUF>;
+  static constexpr size_t kCtaBytes = (OP == OP_PROJECT_DELTA || OP == OP_PROJECT) ? sizeof(Cta) : 0;
 };
 
 // Direct-offset kernel (k_produce, the no-allocation path) keeps the list-based
@@ -567,163 +586,6 @@ MS_DEV void project_gather(const ProduceArgs& a, const ColView& d, const uint64_
 #pragma unroll
   for (int k = 0; k < 16; k++)
     if (pending & (1u << k)) v[k] = read_at(d, p[k]);
-}
-
-// project core for sorted positions into DYN / FOR / DELTA / static-BP data: the
-// data blocks the warp's positions span are copied into shared memory in pieces
-// of consecutive blocks (their payloads are contiguous), 16-byte coalesced
-// copies.  DYN / FOR / static values are cut out of their blocks there; DELTA
-// blocks are decoded whole (prefix sums) into `aux` and the positions read from
-// it.  A random read per position would touch up to 32 scattered sectors per
-// warp load and a DELTA block fetch per touched block; this copies each touched
-// block once, in full.  Returns false (nothing done) for unsorted or
-// out-of-range positions, other formats, or spans longer than kSpanMaxBlocks.
-MS_DEV bool gather_staged(const ColView& d, const uint64_t p[16], int valid, int lane, uint64_t v[16],
-                          uint8_t* span, uint64_t* aux, DevCtl* ctl) {
-  if (d.fmt == MS_UNCOMPR || (d.fmt == MS_DELTA_BP && !aux) || valid <= 0) return false;
-  const int nv = max(0, min(16, valid - 16 * lane));
-  bool ok = true;
-  uint64_t mn = ~0ull, mx = 0;
-#pragma unroll
-  for (int k = 0; k < 16; k++) {
-    if (k < nv) {
-      ok &= p[k] < d.n;
-      if (k) ok &= p[k - 1] <= p[k];
-      mn = min(mn, p[k]);
-      mx = max(mx, p[k]);
-    }
-  }
-  const uint64_t prev_mx = __shfl_up_sync(kFull, mx, 1);
-  if (lane > 0 && nv > 0 && prev_mx > mn) ok = false;
-  if (!__all_sync(kFull, ok)) return false;
-  const uint64_t p_lo = __shfl_sync(kFull, mn, 0);
-  uint64_t p_hi = mx;
-#pragma unroll
-  for (int dd = 16; dd; dd >>= 1) p_hi = max(p_hi, __shfl_xor_sync(kFull, p_hi, dd));
-  const uint64_t B_lo = p_lo >> 9, B_hi = p_hi >> 9;
-  if (B_hi - B_lo >= kSpanMaxBlocks) return false;
-  const bool blockfmt = d.fmt != MS_STATIC_BP;
-  const uint64_t nfull = blockfmt ? d.nb : d.n / kBlock;  // blocks with a packed payload
-  const uint64_t pay0 = blockfmt ? 16 * d.nb : 0;
-  const uint16_t* s16 = reinterpret_cast<const uint16_t*>(span);
-#pragma unroll
-  for (int k = 0; k < 16; k++) v[k] = 0;
-  for (uint64_t lo_blk = B_lo; lo_blk <= B_hi && lo_blk < nfull;) {
-    // lane k: block lo_blk + k: payload word offset, width, reference
-    const uint64_t hb = lo_blk + lane;
-    const bool here = hb <= B_hi && hb < nfull;
-    uint64_t off = 0, ref = 0;
-    uint32_t b = 0;
-    if (here) {
-      if (blockfmt) {
-        const uint64_t w0 = 16 * (hb + 1) <= d.size ? ldg64(d.p + 16 * hb) : 0;
-        ref = 16 * (hb + 1) <= d.size ? ldg64(d.p + 16 * hb + 8) : 0;
-        off = w0 >> 8;
-        b = (uint32_t)(w0 & 255);
-        if (b > 64 || 16 * (hb + 1) > d.size || pay0 + 8 * (off + 8ull * b) > d.size) {
-          set_error(ctl, MS_ERR_FORMAT, hb);
-          b = 0;
-          off = 0;
-        }
-      } else {
-        b = (uint32_t)d.bw;
-        off = 8ull * b * hb;
-      }
-    }
-    const uint64_t off_lo = __shfl_sync(kFull, off, 0);
-    const uint64_t end = off + 8ull * b;
-    // blocks whose payload ends within one span buffer (ends are monotone); a
-    // corrupt header yields an empty block and never stalls the loop
-    const bool fits = here && off >= off_lo && 8 * (end - off_lo) <= (uint64_t)kSpanBytes;
-    const int cnt = max(1, __popc(__ballot_sync(kFull, fits)));
-    const uint64_t bytes = min(8 * (__shfl_sync(kFull, end, cnt - 1) - off_lo), (uint64_t)kSpanBytes);
-    const uint4* src = reinterpret_cast<const uint4*>(d.p + pay0 + 8 * off_lo);
-    for (uint32_t u = lane; u < (uint32_t)(bytes >> 4); u += 32) cp_async16(reinterpret_cast<uint4*>(span) + u, src + u);
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncwarp();
-    const uint64_t hi_blk = lo_blk + cnt;  // exclusive
-    if (d.fmt == MS_DELTA_BP) {
-      for (int q = 0; q < cnt; q++) {
-        const uint64_t B = lo_blk + q;
-        const uint64_t boff = __shfl_sync(kFull, off, q) - off_lo;
-        const uint32_t bb = __shfl_sync(kFull, b, q);
-        const uint64_t rr = __shfl_sync(kFull, ref, q);
-        bool need = false;
-#pragma unroll
-        for (int k = 0; k < 16; k++) need |= k < nv && (p[k] >> 9) == B;
-        if (!__any_sync(kFull, need)) continue;
-        if (8 * boff + 64ull * bb > bytes) {  // a corrupt header chain: never read past the copy
-          if (lane == 0) set_error(ctl, MS_ERR_FORMAT, B);
-          continue;
-        }
-        uint64_t t[16];
-        read_lane_stream(reinterpret_cast<const uint16_t*>(span + 8 * boff), lane, (int)bb, t);
-        uint64_t sum = 0;
-#pragma unroll
-        for (int k = 0; k < 16; k++) {
-          sum += t[k];
-          t[k] = sum;
-        }
-        const uint64_t excl = warp_excl_scan(sum, lane) + rr;
-#pragma unroll
-        for (int k = 0; k < 16; k++) aux[swz(16 * lane + k)] = t[k] + excl;
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < 16; k++)
-          if (k < nv && (p[k] >> 9) == B) v[k] = aux[swz((int)(p[k] & 511))];
-        __syncwarp();
-      }
-      __syncwarp();
-      lo_blk = hi_blk;
-      continue;
-    }
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-      const uint64_t B = p[k] >> 9;
-      const bool mine = k < nv && B >= lo_blk && B < hi_blk;
-      const int sl = mine ? (int)(B - lo_blk) : 0;
-      const uint64_t boff = __shfl_sync(kFull, off, sl) - off_lo;
-      const uint32_t bb = __shfl_sync(kFull, b, sl);
-      const uint64_t rr = __shfl_sync(kFull, ref, sl);
-      if (mine && bb && 8 * boff + 64ull * bb > bytes) {  // a corrupt header chain: never read past the copy
-        set_error(ctl, MS_ERR_FORMAT, B);
-      } else if (mine && bb) {
-        const uint32_t r = (uint32_t)(p[k] & 511), j = r >> 4, kk = r & 15;
-        const uint32_t bit = kk * bb, q0 = bit >> 4, sh = bit & 15, nq = (sh + bb + 15) >> 4;
-        const uint32_t h0 = (uint32_t)(4 * boff) + 32 * q0 + j;  // halfword index in the span
-        uint64_t w = 0, h4 = 0;
-#pragma unroll
-        for (uint32_t t = 0; t < 4; t++)
-          if (t < nq) w |= (uint64_t)s16[h0 + 32 * t] << (16 * t);
-        if (nq > 4) h4 = s16[h0 + 128];
-        uint64_t x = (w >> sh) | (sh ? h4 << (64 - sh) : 0);
-        v[k] = (x & lowmask((int)bb)) + (d.fmt == MS_FOR_BP ? rr : 0);
-      } else if (mine) {
-        v[k] = d.fmt == MS_FOR_BP ? rr : 0;
-      }
-    }
-    __syncwarp();
-    lo_blk = hi_blk;
-  }
-  // positions in the uncompressed remainder (block formats) or the horizontal tail (static BP)
-#pragma unroll
-  for (int k = 0; k < 16; k++) {
-    if (k < nv && (p[k] >> 9) >= nfull) {
-      if (blockfmt) {
-        const uint64_t at = pay0 + 8 * d.pwords + 8 * (p[k] - kBlock * d.nb);
-        v[k] = at + 8 <= d.size ? ldg64(d.p + at) : 0;
-      } else {
-        const uint64_t* tail = reinterpret_cast<const uint64_t*>(d.p + 64ull * d.bw * nfull);
-        const uint64_t bit = (p[k] - kBlock * nfull) * (uint64_t)d.bw;
-        const int sh = (int)(bit & 63);
-        uint64_t x = ldg64(tail + (bit >> 6)) >> sh;
-        if (sh + d.bw > 64) x |= ldg64(tail + (bit >> 6) + 1) << (64 - sh);
-        v[k] = x & lowmask(d.bw);
-      }
-    }
-  }
-  return true;
 }
 
 // project core for DELTA data when the positions are unsorted or spread over
@@ -916,6 +778,217 @@ MS_DEV int emit_gather(const ProduceArgs& a, uint64_t n_out, uint64_t g, int lan
   }
   __syncwarp();
   return valid;
+}
+
+// Sorted positions of a whole CTA tile (8 consecutive output chunks) into DYN /
+// FOR / DELTA / static-BP data.  The data blocks the tile's positions span have
+// contiguous payloads, so the CTA copies them into shared memory in pieces of up
+// to kCtaBuf bytes with all its threads (coalesced 16-byte copies), and each warp
+// then takes its values from there: DYN / FOR / static values are cut out of their
+// blocks, DELTA blocks are decoded whole (prefix sums) into the warp's `aux`.  A
+// random read per position would instead touch up to 32 scattered sectors per warp
+// load.  Unsorted, out-of-range or sparse positions (fewer positions than blocks
+// spanned) and uncompressed data go through the per-warp random path.  Every
+// thread of the CTA calls this once per tile (it synchronises the CTA).
+template <bool kDelta, class Cta>
+MS_DEV void gather_cta(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int warp, int lane,
+                       uint64_t v[16], Cta* cs, uint64_t* aux) {
+  constexpr int kCtaBuf = Cta::kBuf;
+  const int tid = threadIdx.x;
+  const int nv = max(0, min(16, valid - 16 * lane));
+  bool ok = d.fmt != MS_UNCOMPR;
+  uint64_t mn = ~0ull, mx = 0;
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    if (k < nv) {
+      ok &= p[k] < d.n;
+      if (k) ok &= p[k - 1] <= p[k];
+      mn = min(mn, p[k]);
+      mx = max(mx, p[k]);
+    }
+  }
+  const uint64_t prev_mx = __shfl_up_sync(kFull, mx, 1);
+  if (lane > 0 && nv > 0 && prev_mx > mn) ok = false;
+  const bool wok = __all_sync(kFull, ok);
+  uint64_t wmx = mx;
+#pragma unroll
+  for (int dd = 16; dd; dd >>= 1) wmx = max(wmx, __shfl_xor_sync(kFull, wmx, dd));
+  if (lane == 0) {
+    cs->lo[warp] = valid > 0 ? mn : ~0ull;
+    cs->hi[warp] = wmx;
+    cs->ok[warp] = wok;
+    cs->nv[warp] = (uint32_t)max(valid, 0);
+  }
+  __syncthreads();
+  bool tile_ok = true, any = false;
+  uint64_t lo = ~0ull, hi = 0, prev_hi = 0, npos = 0;
+  for (int w = 0; w < kWarps; w++) {
+    tile_ok &= cs->ok[w] != 0;
+    if (cs->nv[w]) {
+      if (any) tile_ok &= prev_hi <= cs->lo[w];
+      lo = min(lo, cs->lo[w]);
+      hi = max(hi, cs->hi[w]);
+      prev_hi = cs->hi[w];
+      npos += cs->nv[w];
+      any = true;
+    }
+  }
+  const uint64_t B_lo = lo >> 9, B_hi = hi >> 9;
+  tile_ok &= any && B_hi - B_lo + 1 <= npos;
+  __syncthreads();  // every thread has read the summaries
+  if (!tile_ok) {
+    if constexpr (kDelta) {
+      gather_delta_blocks(a, d, p, valid, lane, v, cs->buf + 4096 * warp, aux);
+    } else {
+      gather_random(a, d, p, valid, lane, v);
+    }
+    __syncthreads();
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < 16; k++) v[k] = 0;
+  const bool blockfmt = d.fmt != MS_STATIC_BP;
+  const uint64_t nfull = blockfmt ? d.nb : d.n / kBlock;  // blocks with a packed payload
+  const uint64_t pay0 = blockfmt ? 16 * d.nb : 0;
+  const uint64_t last = min(B_hi, nfull - 1);
+  for (uint64_t lo_blk = B_lo; nfull > 0 && lo_blk <= last;) {
+    // thread t: block lo_blk + t
+    const uint64_t hb = lo_blk + tid;
+    const bool here = tid < kCtaHdr && hb <= last;
+    uint64_t off = 0, ref = 0;
+    uint32_t b = 0;
+    if (here) {
+      if (blockfmt) {
+        const bool inh = 16 * (hb + 1) <= d.size;
+        const uint64_t w0 = inh ? ldg64(d.p + 16 * hb) : 0;
+        ref = inh ? ldg64(d.p + 16 * hb + 8) : 0;
+        off = w0 >> 8;
+        b = (uint32_t)(w0 & 255);
+        if (!inh || b > 64 || pay0 + 8 * (off + 8ull * b) > d.size) {
+          set_error(a.ctl, MS_ERR_FORMAT, hb);
+          b = 0;
+          off = 0;
+        }
+      } else {
+        b = (uint32_t)d.bw;
+        off = 8ull * b * hb;
+      }
+    }
+    if (tid == 0) cs->off_lo = off;
+    __syncthreads();
+    const uint64_t off_lo = cs->off_lo;
+    const uint64_t end = off + 8ull * b;
+    // blocks whose payload ends within one buffer (ends are monotone); a corrupt
+    // header makes an empty block and never stalls the loop
+    const bool fits = here && off >= off_lo && 8 * (end - off_lo) <= (uint64_t)kCtaBuf;
+    if (fits) cs->hdr[tid] = make_uint4((uint32_t)((off << 8) | b), (uint32_t)(off >> 24), (uint32_t)ref,
+                                        (uint32_t)(ref >> 32));
+    const int cnt = max(1, __syncthreads_count(fits));
+    const uint4 hl = cs->hdr[cnt - 1];
+    const uint64_t wl = (uint64_t)hl.x | (uint64_t)hl.y << 32;
+    // (a stale entry from a corrupt chain only shortens or clamps the copy)
+    const uint64_t bytes = min(8 * ((wl >> 8) + 8 * (wl & 255) - off_lo), (uint64_t)kCtaBuf);
+    const uint4* src = reinterpret_cast<const uint4*>(d.p + pay0 + 8 * off_lo);
+    for (uint32_t u = tid; u < (uint32_t)(bytes >> 4); u += blockDim.x) cp_async16(reinterpret_cast<uint4*>(cs->buf) + u, src + u);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    const uint64_t hi_blk = lo_blk + cnt;  // exclusive
+    if constexpr (kDelta) {
+      uint32_t pend = 0;
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        const uint64_t B = p[k] >> 9;
+        pend |= (uint32_t)(k < nv && B >= lo_blk && B < hi_blk) << k;
+      }
+      while (__ballot_sync(kFull, pend) != 0) {
+        uint64_t mb = ~0ull;
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+          if (pend & (1u << k)) mb = min(mb, p[k] >> 9);
+        const uint64_t B = warp_min(mb);
+        const uint4 h = cs->hdr[B - lo_blk];
+        const uint64_t w0 = (uint64_t)h.x | (uint64_t)h.y << 32, rr = (uint64_t)h.z | (uint64_t)h.w << 32;
+        const uint64_t boff = (w0 >> 8) - off_lo;
+        const int bb = (int)(w0 & 255);
+        uint64_t t[16];
+        if (8 * boff + 64ull * bb > bytes) {  // never read past the copy
+          if (lane == 0) set_error(a.ctl, MS_ERR_FORMAT, B);
+#pragma unroll
+          for (int k = 0; k < 16; k++) t[k] = 0;
+        } else {
+          read_lane_stream(reinterpret_cast<const uint16_t*>(cs->buf + 8 * boff), lane, bb, t);
+        }
+        uint64_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          sum += t[k];
+          t[k] = sum;
+        }
+        const uint64_t excl = warp_excl_scan(sum, lane) + rr;
+#pragma unroll
+        for (int k = 0; k < 16; k++) aux[swz(16 * lane + k)] = t[k] + excl;
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          if ((pend & (1u << k)) && (p[k] >> 9) == B) {
+            v[k] = aux[swz((int)(p[k] & 511))];
+            pend &= ~(1u << k);
+          }
+        }
+        __syncwarp();
+      }
+    } else {
+      const uint16_t* s16 = reinterpret_cast<const uint16_t*>(cs->buf);
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        const uint64_t B = p[k] >> 9;
+        if (k < nv && B >= lo_blk && B < hi_blk) {
+          const uint4 h = cs->hdr[B - lo_blk];
+          const uint64_t w0 = (uint64_t)h.x | (uint64_t)h.y << 32, rr = (uint64_t)h.z | (uint64_t)h.w << 32;
+          const uint64_t boff = (w0 >> 8) - off_lo;
+          const uint32_t bb = (uint32_t)(w0 & 255);
+          const uint64_t add = d.fmt == MS_FOR_BP ? rr : 0;
+          if (8 * boff + 64ull * bb > bytes) {  // never read past the copy
+            set_error(a.ctl, MS_ERR_FORMAT, B);
+          } else if (bb) {
+            const uint32_t r = (uint32_t)(p[k] & 511), j = r >> 4, kk = r & 15;
+            const uint32_t bit = kk * bb, q0 = bit >> 4, sh = bit & 15, nq = (sh + bb + 15) >> 4;
+            const uint32_t h0 = (uint32_t)(4 * boff) + 32 * q0 + j;  // halfword index in the piece
+            uint64_t w = 0, h4 = 0;
+#pragma unroll
+            for (uint32_t q = 0; q < 4; q++)
+              if (q < nq) w |= (uint64_t)s16[h0 + 32 * q] << (16 * q);
+            if (nq > 4) h4 = s16[h0 + 128];
+            const uint64_t x = (w >> sh) | (sh ? h4 << (64 - sh) : 0);
+            v[k] = (x & lowmask((int)bb)) + add;
+          } else {
+            v[k] = add;
+          }
+        }
+      }
+    }
+    __syncthreads();  // the next piece overwrites the buffer
+    lo_blk = hi_blk;
+  }
+  // positions in the uncompressed remainder (block formats) or the horizontal tail (static BP)
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    if (k < nv && (p[k] >> 9) >= nfull) {
+      if (blockfmt) {
+        const uint64_t at = pay0 + 8 * d.pwords + 8 * (p[k] - kBlock * d.nb);
+        v[k] = at + 8 <= d.size ? ldg64(d.p + at) : 0;
+      } else {
+        const uint64_t* tail = reinterpret_cast<const uint64_t*>(d.p + 64ull * d.bw * nfull);
+        const uint64_t bit = (p[k] - kBlock * nfull) * (uint64_t)d.bw;
+        const int sh = (int)(bit & 63);
+        uint64_t x = ldg64(tail + (bit >> 6)) >> sh;
+        if (sh + d.bw > 64) x |= ldg64(tail + (bit >> 6) + 1) << (64 - sh);
+        v[k] = x & lowmask(d.bw);
+      }
+    }
+  }
+  __syncthreads();
 }
 
 // Residual transform of a full block (Sec. 2.1): FOR subtracts the block minimum,
@@ -1266,14 +1339,23 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
   const uint64_t nch = (n_out + kBlock - 1) / kBlock;
   const uint64_t static_chunks = n_out / kBlock;
   const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
-  // chunk i of a warp: gw + i*W (interleaved), or, for project, a contiguous segment
-  // so that a warp's data accesses move forward through the data column
+  // chunk i of a warp: gw + i*W.  A project from compressed data gathers a CTA tile
+  // at a time: the CTA's warps take the 8 chunks of one tile together (tiles
+  // blockIdx.x, blockIdx.x + gridDim.x, ...) and every warp runs the CTA's tile
+  // count, since the gather synchronises the CTA.  A project from uncompressed data
+  // reads at random: each warp takes a contiguous segment of output chunks so that
+  // its reads move forward through the data column.
+  const bool cta_gather = kProject && c0.fmt != MS_UNCOMPR;
   const uint64_t seg = (nch + W - 1) / W;
-  const uint64_t first = kProject ? gw * seg : gw;
-  const uint64_t stride = kProject ? 1 : W;
-  const uint64_t count = kProject ? (first < nch ? min(seg, nch - first) : 0) : (gw < nch ? (nch - gw + W - 1) / W : 0);
+  const bool segmented = kProject && !cta_gather;
+  const uint64_t first = segmented ? gw * seg : gw, stride = segmented ? 1 : W;
+  const uint64_t count =
+      segmented ? (first < nch ? min(seg, nch - first) : 0) : (gw < nch ? (nch - gw + W - 1) / W : 0);
+  const uint64_t ntile = (nch + kWarps - 1) / kWarps;
+  const uint64_t loop_n =
+      cta_gather ? (blockIdx.x < ntile ? (ntile - blockIdx.x + gridDim.x - 1) / gridDim.x : 0) : count;
 
-  constexpr int D = (OP == OP_CALC || OP == OP_PROJECT_DELTA) ? kProdDepth2 : kProdDepth;
+  constexpr int D = (OP == OP_CALC || kProject) ? kProdDepth2 : kProdDepth;
   StreamSmem<D>* ring0 = nullptr;
   StreamSmem<D>* ring1 = nullptr;
   if constexpr (OP == OP_COMPRESS || OP == OP_DECOMPRESS || kProject) ring0 = &sm->s0;
@@ -1299,7 +1381,8 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
     }
   }
 
-  for (uint64_t i = 0; i < count; i++) {
+  auto* pcta = reinterpret_cast<typename ProducePlan<OP>::Cta*>(smem_raw + sizeof(Smem) * kWarps);
+  for (uint64_t i = 0; i < loop_n; i++) {
     const uint64_t g = first + i * stride;
     uint64_t v[16];
     int valid = 0;
@@ -1331,12 +1414,12 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
       } else if constexpr (OP == OP_PROJECT) {  // c0 = data, st0 streams the positions (c1)
         uint64_t p[16];
         valid = st0.decode(i, p, ctl);
-        if (!gather_staged(c0, p, valid, lane, v, sm->span, nullptr, ctl)) gather_random(a, c0, p, valid, lane, v);
+        if (cta_gather) gather_cta<false>(a, c0, p, valid, warp, lane, v, pcta, (uint64_t*)nullptr);
+        else gather_random(a, c0, p, valid, lane, v);
       } else {  // OP_PROJECT_DELTA
         uint64_t p[16];
         valid = st0.decode(i, p, ctl);
-        if (!gather_staged(c0, p, valid, lane, v, sm->span, sm->aux, ctl))
-          gather_delta_blocks(a, c0, p, valid, lane, v, sm->span, sm->aux);
+        gather_cta<true>(a, c0, p, valid, warp, lane, v, pcta, sm->aux);
       }
       __syncwarp();
     }

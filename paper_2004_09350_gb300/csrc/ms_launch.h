@@ -70,7 +70,7 @@ constexpr int kMapKernel[6] = {MS_K_COMPRESS, MS_K_DECOMPRESS, MS_K_PROJECT, MS_
 
 template <int OP>
 ms_status launch_map_impl(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
-  const size_t smem = sizeof(typename ProducePlan<OP>::Smem) * kWarps;
+  const size_t smem = sizeof(typename ProducePlan<OP>::Smem) * kWarps + ProducePlan<OP>::kCtaBytes;
   const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
   const int grid = grid_for(c, k_map<OP>, smem, tiles);
   ProfScope ps(c, kMapKernel[OP], s);
