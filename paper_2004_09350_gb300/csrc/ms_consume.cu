@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark(MarkArgs 
   const ColView c = view_of(a.in);
   const uint64_t lo = a.lo, span = a.span;
   const uint32_t negate = a.negate ? 0xffffu : 0u, live = a.empty ? 0u : 0xffffu;
-  cta_stream<kTileBuf>(c, sm, a.ctl, [&](uint64_t g, const uint64_t* v, int valid) {
+  cta_stream<kTileBuf>(c, sm, a.ctl, [&](uint64_t g, const uint64_t* v, int valid, bool narrow) {
     uint32_t m16 = 0;
     if (a.keybits) {
 #pragma unroll
@@ -26,6 +26,14 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark(MarkArgs 
         const bool hit = x < a.domain && ((__ldg(a.keybits + (x >> 5)) >> (x & 31)) & 1u);
         m16 |= (uint32_t)hit << k;
       }
+    } else if (narrow) {  // 32-bit compares
+      if (a.mode32 == 0) {
+#pragma unroll
+        for (int k = 0; k < 16; k++) m16 |= (uint32_t)((uint32_t)v[k] - a.lo32 <= a.span32) << k;
+      } else {
+        m16 = a.mode32 == 2 ? 0xffffu : 0u;
+      }
+      m16 = (m16 ^ negate) & live;
     } else {
 #pragma unroll
       for (int k = 0; k < 16; k++) m16 |= (uint32_t)(v[k] - lo <= span) << k;
@@ -110,7 +118,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_agg_sum(const 
   auto* sm = reinterpret_cast<TileSmem<kTileBuf>*>(smem_raw);
   const ColView c = view_of(in);
   uint64_t acc = 0;
-  cta_stream<kTileBuf>(c, sm, ctl, [&](uint64_t, const uint64_t* v, int) {
+  cta_stream<kTileBuf>(c, sm, ctl, [&](uint64_t, const uint64_t* v, int, bool) {
 #pragma unroll
     for (int k = 0; k < 16; k++) acc += v[k];  // zero past the column's end
   });
@@ -161,7 +169,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_build_keys(con
   const int lane = threadIdx.x & 31;
   auto* sm = reinterpret_cast<TileSmem<kTileBuf>*>(smem_raw);
   const ColView c = view_of(keys);
-  cta_stream<kTileBuf>(c, sm, ctl, [&](uint64_t, const uint64_t* v, int valid) {
+  cta_stream<kTileBuf>(c, sm, ctl, [&](uint64_t, const uint64_t* v, int valid, bool) {
 #pragma unroll
     for (int k = 0; k < 16; k++) {
       if (16 * lane + k < valid) {
@@ -185,7 +193,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_stats(const De
   __syncthreads();
   auto* sm = reinterpret_cast<TileSmem<kTileBuf>*>(smem_raw);
   const ColView c = view_of(in);
-  cta_stream<kTileBuf>(c, sm, ctl, [&](uint64_t, const uint64_t* v, int valid) {
+  cta_stream<kTileBuf>(c, sm, ctl, [&](uint64_t, const uint64_t* v, int valid, bool) {
     uint64_t mx = 0, mn = ~0ull, dmax = 0;
     uint32_t sorted = 0, runs = 0;
     const uint64_t prev_last = __shfl_up_sync(kFull, v[15], 1);

@@ -45,8 +45,10 @@ struct TileSmem {
   uint4 hdr[3][kClaim];  // the decoded claim, the scheduled claim, the next claim
 };
 
-// Calls body(g, v, valid) for every chunk g of c; v is zero past `valid`.  Every
-// thread of the CTA must call it (it synchronises the CTA).
+// Calls body(g, v, valid, narrow) for every chunk g of c; v is zero past `valid`,
+// and narrow says that every value of the chunk is below 2^32 (a block or static
+// width of at most 32 bits).  Every thread of the CTA must call it (it
+// synchronises the CTA).
 template <int BUF, class Body>
 MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body body) {
   static_assert(BUF >= 4096 && BUF % 4096 == 0, "buffer size");
@@ -161,6 +163,7 @@ MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body bo
     for (uint64_t k = da + warp; k < db; k += nwarps) {
       const int valid = (int)min((uint64_t)kBlock, c.n - k * kBlock);
       uint64_t v[16];
+      bool narrow = c.fmt == MS_STATIC_BP && c.bw <= 32;
       if (k < full) {
         uint32_t b;
         uint64_t off, ref = 0;
@@ -179,6 +182,7 @@ MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body bo
           b = (uint32_t)c.bw;
           at = sm->buf[dbi] + (uint64_t)fixed * k - dbase;
         }
+        narrow = (c.fmt == MS_DYN_BP || c.fmt == MS_STATIC_BP) && b <= 32;
         if (c.fmt == MS_UNCOMPR) {
           const uint4* st = reinterpret_cast<const uint4*>(at);
 #pragma unroll
@@ -229,7 +233,7 @@ MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body bo
 #pragma unroll
         for (int q = 0; q < 16; q++) v[q] = (16 * lane + q < valid && inside) ? ldg64(rawp + 16 * lane + q) : 0;
       }
-      body(k, v, valid);
+      body(k, v, valid, narrow);
     }
     __syncthreads();
   }
@@ -245,6 +249,10 @@ struct MarkArgs {
   // the predicate as one range test: hit = ((x - lo) <= span) != negate, never if empty
   uint64_t lo, span;
   uint32_t negate, empty;
+  // the same range restricted to x < 2^32, for chunks whose values all fit 32 bits:
+  // hit = (uint32(x - lo32) <= span32) != negate; mode32 1 = no x < 2^32 is in the
+  // range, 2 = every one is (negate and empty apply as above)
+  uint32_t lo32, span32, mode32;
   const uint32_t* keybits;  // semi-join: membership bitmap over the key domain
   uint64_t domain;
   uint16_t* bitmap;

@@ -58,6 +58,33 @@ void predicate_as_range(int cmp, uint64_t c1, uint64_t c2, MarkArgs* m) {
     case MS_GE: m->lo = c1; m->span = kMax - c1; break;
     default: m->lo = c1; m->span = c2 - c1; m->empty = c2 < c1; break;  // MS_BETWEEN
   }
+  // The range {x : (x - lo) mod 2^64 <= span} is a cyclic interval; its part below
+  // 2^32 is again one cyclic interval of the 32-bit values (or none, or all).
+  const uint64_t M = 0xffffffffull, lo = m->lo, span = m->span;
+  m->lo32 = 0;
+  m->span32 = 0;
+  m->mode32 = 0;
+  if (span == kMax) {  // every value
+    m->mode32 = 2;
+  } else if (lo + span >= lo) {  // no wrap: [lo, lo + span]
+    if (lo > M) {
+      m->mode32 = 1;
+    } else {
+      m->lo32 = (uint32_t)lo;
+      m->span32 = (uint32_t)(std::min(lo + span, M) - lo);
+    }
+  } else {  // wraps: [lo, 2^64) and [0, lo + span - 2^64]
+    const uint64_t hi = lo + span;  // mod 2^64
+    if (lo > M) {  // only [0, hi] reaches below 2^32
+      m->lo32 = 0;
+      m->span32 = (uint32_t)std::min(hi, M);
+    } else if (hi >= M || hi + 1 >= lo) {  // the two pieces cover [0, 2^32)
+      m->mode32 = 2;
+    } else {  // [lo, 2^32) and [0, hi]: the 32-bit interval from lo around to hi
+      m->lo32 = (uint32_t)lo;
+      m->span32 = (uint32_t)(hi - lo);  // mod 2^32
+    }
+  }
 }
 
 namespace {

@@ -143,6 +143,31 @@ def test_select_sparse_output_blocks(ctx, out_fmt):
     ctx.free(col)
 
 
+NARROW_CASES = [(ms.EQ, 5, 0), (ms.EQ, 1 << 33, 0), (ms.NE, 7, 0), (ms.NE, 1 << 40, 0), (ms.LT, 0, 0),
+                (ms.LT, 1 << 40, 0), (ms.LT, 1 << 19, 0), (ms.LE, (1 << 32) - 1, 0), (ms.GT, 2**64 - 1, 0),
+                (ms.GT, 1 << 32, 0), (ms.GT, 1000, 0), (ms.GE, 0, 0), (ms.GE, (1 << 32) - 5, 0),
+                (ms.BETWEEN, 9, 3), (ms.BETWEEN, 1 << 31, 1 << 33), (ms.BETWEEN, 1 << 33, 1 << 34),
+                (ms.BETWEEN, 100, 2**64 - 1), (ms.BETWEEN, 0, 2**64 - 1), (ms.BETWEEN, 1 << 10, 1 << 19)]
+
+
+@pytest.mark.parametrize("fmt", [ms.DYN_BP, ms.STATIC_BP, ms.FOR_BP])
+@pytest.mark.parametrize("case", NARROW_CASES, ids=lambda c: "%d-%d-%d" % c)
+def test_select_narrow_predicates(ctx, fmt, case):
+    """Blocks of at most 32 bits take the 32-bit form of the range test; constants
+    at and beyond 2^32, empty and full ranges, and negations must agree with the
+    64-bit definition."""
+    cmp, c1, c2 = case
+    n = 3 * 4096 + 77
+    x = synth.skewed_widths(51, n, widths=(1, 12, 20, 32))
+    x[::997] = np.uint64((1 << 32) - 1)
+    x[5] = np.uint64((1 << 32) - 5)
+    col, _ = gpu_col(ctx, x, fmt)
+    pos = ctx.select(col, cmp, c1, c2, fmt=ms.DELTA_BP)
+    assert_column(ctx, pos, oracle.select(x, cmp, c1, c2), ms.DELTA_BP)
+    ctx.free(pos)
+    ctx.free(col)
+
+
 def test_select_none_and_all(ctx):
     x = synth.uniform(5, 4096 * 4 + 17, 10, 20)
     col, _ = gpu_col(ctx, x, ms.FOR_BP)
