@@ -330,11 +330,16 @@ typedef struct {
                            0: width-specialised decoders */
   uint32_t schedule;    /* 0: each warp takes whole tiles from the work counter;
                            1: CTA b takes tiles b, b + grid, ... and its warps
-                           share each tile (one fragment per CTA at a time) */
+                           share each tile (one fragment per CTA at a time);
+                           2: CTA b takes 64-chunk claims b, b + grid, ... and
+                           copies runs of one fragment's chunks into two
+                           shared buffers of 8 KB x depth per column, which
+                           its warps decode (tile_chunks is not used) */
 } ms_batch_config;
 /* Supported (warps, depth, compact, schedule): schedule 0 with warps 4 or 8,
    depth 2..4, either decoder; schedule 1 with warps 4, 8 (depth 2 or 3) or 16
-   (depth 2) and the width-specialised decoders. */
+   (depth 2) and the width-specialised decoders; schedule 2 with warps 8, depth
+   2..4 and the width-specialised decoders. */
 
 /* ms_batch_run flags */
 #define MS_BATCH_ZERO 1u         /* zero d_sums[f0..f1) first (one memset) */

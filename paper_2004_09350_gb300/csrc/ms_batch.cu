@@ -28,6 +28,7 @@ MS_BATCH_DYNAMIC(MS_EXTERN, 2)
 MS_BATCH_DYNAMIC(MS_EXTERN, 3)
 MS_BATCH_DYNAMIC(MS_EXTERN, 4)
 MS_BATCH_STATIC(MS_EXTERN)
+MS_BATCH_CTA(MS_EXTERN)
 #undef MS_EXTERN
 
 // Host-built part of a fragment: the column slots and the predicate.
@@ -95,6 +96,10 @@ BatchLauncher batch_launcher(uint32_t warps, uint32_t depth, bool compact, uint3
   if (warps == W && depth == D) return &launch_batch_kernel<W, D, false, true>;
     MS_PICK(4, 2) MS_PICK(8, 2) MS_PICK(16, 2) MS_PICK(4, 3) MS_PICK(8, 3)
 #undef MS_PICK
+  } else if (schedule == 2 && !compact && warps == 8) {  // depth selects the buffers: 8 KB x depth per column
+    if (depth == 2) return &launch_batch_cta<16384, false>;
+    if (depth == 3) return &launch_batch_cta<24576, false>;
+    if (depth == 4) return &launch_batch_cta<32768, false>;
   }
   return nullptr;
 }

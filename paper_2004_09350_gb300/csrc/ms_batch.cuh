@@ -297,6 +297,176 @@ __global__ void __launch_bounds__(32 * WARPS) k_batch(BatchArgs a) {
   }
 }
 
+// ------------------------------------------------------ CTA-streamed schedule
+
+// Schedule 2: the CTA tile stream of the single-column consumers, extended to the
+// batch.  A CTA claims kBClaim consecutive chunks (claims b, b + gridDim.x, ...);
+// their directory records load one claim ahead.  Inside one fragment the x and y
+// payloads of consecutive packed chunks are contiguous, so the CTA copies a run of
+// chunks of one fragment (as many as fit in both buffers) with all its threads,
+// and its warps decode the run from shared memory while the next run loads.
+// Uncompressed chunks, remainders and static tails are read in place.
+constexpr int kBClaim = 64;
+
+template <int BUF>
+struct BatchCtaSmem {
+  uint8_t xbuf[2][BUF];
+  uint8_t ybuf[2][BUF];
+  ChunkRec rec[3][kBClaim];  // the decoded claim, the scheduled claim, the next claim
+};
+
+// end of a chunk's staged bytes (its start when it is read in place)
+MS_DEV uint64_t staged_end(const ChunkRec& r, int col) {
+  const uint32_t code = r.code[col];
+  const bool packed = ((code >> 8) & 15) == kKindPacked;
+  return r.addr[col] + (packed ? 64ull * (code & 255) : 0);
+}
+
+template <int BUF, bool kCompact>
+__global__ void __launch_bounds__(256) k_batch_cta(BatchArgs a) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  auto* sm = reinterpret_cast<BatchCtaSmem<BUF>*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+  const uint64_t span = a.c1 - a.c0;
+  const uint64_t nclaims = (span + kBClaim - 1) / kBClaim;
+  const ChunkRec* dir = a.dir + a.c0;
+  auto load_rec = [&](uint64_t claim, int rb) {
+    if (claim >= nclaims) return;
+    for (int u = tid; u < 4 * kBClaim; u += blockDim.x) {
+      const uint64_t g = claim * kBClaim + (u >> 2);
+      if (g < span)
+        cp_async16(reinterpret_cast<uint4*>(&sm->rec[rb][u >> 2]) + (u & 3),
+                   reinterpret_cast<const uint4*>(dir + g) + (u & 3));
+    }
+  };
+  uint64_t claim = blockIdx.x;
+  if (claim >= nclaims) return;
+  int rb = 0;
+  uint64_t cb = claim * kBClaim, ce = min(span, cb + kBClaim), g = cb;
+  load_rec(claim, 0);
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  load_rec(claim + gridDim.x, 1);
+  // the run in flight / being decoded: chunks [ga, gb) of claim (rb_s, cb_s), buffer bi
+  uint64_t ga = 0, gb = 0, cb_s = cb, x0 = 0, y0 = 0;
+  int rb_s = 0, bi = 0;
+  auto schedule = [&](int nbi) -> bool {
+    if (g >= ce) {  // next claim (its records landed with an earlier group)
+      claim += gridDim.x;
+      if (claim >= nclaims) return false;
+      rb = rb == 2 ? 0 : rb + 1;
+      cb = claim * kBClaim;
+      ce = min(span, cb + kBClaim);
+      g = cb;
+      load_rec(claim + gridDim.x, rb == 2 ? 0 : rb + 1);
+    }
+    const ChunkRec& r0 = sm->rec[rb][g - cb];
+    const uint32_t f0 = r0.frag;
+    const uint64_t sx = r0.addr[0], sy = r0.addr[1];
+    // chunks of the claim in g's fragment whose staged bytes end within both buffers
+    bool fits = false;
+    if ((uint64_t)tid < ce - g) {
+      const ChunkRec& r = sm->rec[rb][g + tid - cb];
+      fits = r.frag == f0 && staged_end(r, 0) - sx <= (uint64_t)BUF && staged_end(r, 1) - sy <= (uint64_t)BUF;
+    }
+    const uint64_t cnt = max(1, __syncthreads_count(fits));
+    const ChunkRec& rl = sm->rec[rb][g + cnt - 1 - cb];
+    const uint64_t bx = min(staged_end(rl, 0) - sx, (uint64_t)BUF) & ~15ull;
+    const uint64_t by = min(staged_end(rl, 1) - sy, (uint64_t)BUF) & ~15ull;
+    for (uint32_t u = tid; u < (uint32_t)(bx >> 4); u += blockDim.x)
+      cp_async16(reinterpret_cast<uint4*>(sm->xbuf[nbi]) + u, reinterpret_cast<const uint4*>(sx) + u);
+    for (uint32_t u = tid; u < (uint32_t)(by >> 4); u += blockDim.x)
+      cp_async16(reinterpret_cast<uint4*>(sm->ybuf[nbi]) + u, reinterpret_cast<const uint4*>(sy) + u);
+    ga = g;
+    gb = g + cnt;
+    cb_s = cb;
+    rb_s = rb;
+    x0 = sx;
+    y0 = sy;
+    g += cnt;
+    return true;
+  };
+  bool live = schedule(0);
+  cp_async_commit();
+  while (live) {
+    cp_async_wait<0>();
+    __syncthreads();
+    const uint64_t da = ga, db = gb, dcb = cb_s, dx0 = x0, dy0 = y0;
+    const int drb = rb_s, dbi = bi;
+    bi ^= 1;
+    live = schedule(bi);
+    cp_async_commit();
+    uint64_t acc = 0;
+    for (uint64_t k = da + warp; k < db; k += nwarps) {
+      const ChunkRec& r = sm->rec[drb][k - dcb];
+      const uint32_t meta = r.meta;
+      const int valid = (int)(meta & 1023);
+      const uint64_t lo = r.lo, pspan = r.span;
+      uint32_t m16 = 0;
+#pragma unroll 1
+      for (int col = 0; col < 2; col++) {
+        const uint32_t code = r.code[col];
+        const bool packed = ((code >> 8) & 15) == kKindPacked;
+        const uint8_t* base = col ? sm->ybuf[dbi] : sm->xbuf[dbi];
+        const uint64_t start = col ? dy0 : dx0;
+        // a staged chunk lies inside the copied run: its bytes were checked against
+        // the buffer when the run was cut
+        const bool staged = packed && r.addr[col] >= start && r.addr[col] + 64ull * (code & 255) - start <= BUF;
+        uint64_t v[16];
+        if (staged) {
+          decode_rec<kCompact>(r.addr[col], r.ref[col], code, valid,
+                               reinterpret_cast<const uint16_t*>(base + (r.addr[col] - start)), lane, v);
+        } else {
+          // in place: a raw chunk, or (never for a consistent directory) a packed one outside the run
+          decode_rec<kCompact>(r.addr[col], r.ref[col], code, valid, reinterpret_cast<const uint16_t*>(r.addr[col]),
+                               lane, v);
+        }
+        if (col == 0) {
+#pragma unroll
+          for (int q = 0; q < 16; q++) m16 |= (uint32_t)(v[q] - lo <= pspan) << q;
+          const int first = 16 * lane;
+          m16 = (m16 ^ ((meta >> 16) & 1 ? 0xffffu : 0u)) & ((meta >> 17) & 1 ? 0u : 0xffffu) &
+                (valid >= first + 16 ? 0xffffu : (valid > first ? (1u << (valid - first)) - 1u : 0u));
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; q++)
+            if ((m16 >> q) & 1u) acc += v[q];
+        }
+      }
+    }
+    // every chunk of a run belongs to one fragment
+    const uint64_t t = warp_sum(acc);
+    if (lane == 0 && t && da + warp < db)
+      atomicAdd(a.sums + sm->rec[drb][da - dcb].frag, (unsigned long long)t);
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
+template <int BUF, bool kCompact>
+ms_status launch_batch_cta(ms_ctx* c, const BatchArgs& a, uint32_t ctas_per_sm, cudaStream_t s) {
+  static int occ_cache[16];
+  const size_t smem = sizeof(BatchCtaSmem<BUF>);
+  const int dev = c->device;
+  int occ = (dev >= 0 && dev < 16) ? occ_cache[dev] : 0;
+  if (occ == 0) {
+    if (cuda_status(cudaFuncSetAttribute(k_batch_cta<BUF, kCompact>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem)) != MS_OK)
+      return MS_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_cta<BUF, kCompact>, 256, smem) != cudaSuccess ||
+        occ < 1)
+      occ = 1;
+    if (dev >= 0 && dev < 16) occ_cache[dev] = occ;
+  }
+  if (a.ntiles == 0) return MS_OK;
+  if (ctas_per_sm) occ = std::min<int>(occ, (int)ctas_per_sm);
+  const uint64_t claims = cdiv(a.c1 - a.c0, kBClaim);
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)occ * (uint64_t)c->sms, claims));
+  k_batch_cta<BUF, kCompact><<<grid, 256, smem, s>>>(a);
+  return cuda_status(cudaGetLastError());
+}
+
 // Launches k_batch<WARPS, D, kCompact> over a.ntiles tiles; grid capped at the
 // resident CTAs (ctas_per_sm per SM when nonzero).  With a.ntiles == 0 it only sets
 // the kernel's shared-memory attribute and caches its occupancy (done before a
@@ -346,6 +516,10 @@ BatchLauncher batch_launcher(uint32_t warps, uint32_t depth, bool compact, uint3
 #define MS_BATCH_DYNAMIC(X, D) \
   X template ms_status MS_BATCH_LAUNCHER(4, D, false, false) X template ms_status MS_BATCH_LAUNCHER(8, D, false, false) \
   X template ms_status MS_BATCH_LAUNCHER(4, D, true, false) X template ms_status MS_BATCH_LAUNCHER(8, D, true, false)
+#define MS_BATCH_CTA(X)                                                                          \
+  X template ms_status launch_batch_cta<16384, false>(ms_ctx*, const BatchArgs&, uint32_t, cudaStream_t); \
+  X template ms_status launch_batch_cta<24576, false>(ms_ctx*, const BatchArgs&, uint32_t, cudaStream_t); \
+  X template ms_status launch_batch_cta<32768, false>(ms_ctx*, const BatchArgs&, uint32_t, cudaStream_t);
 // static schedule: width-specialised decoders, warps {4, 8, 16} x depth {2, 3}
 #define MS_BATCH_STATIC(X)                                                                                        \
   X template ms_status MS_BATCH_LAUNCHER(4, 2, false, true) X template ms_status MS_BATCH_LAUNCHER(8, 2, false, true) \

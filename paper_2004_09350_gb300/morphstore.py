@@ -45,7 +45,8 @@ class KernelTime(ctypes.Structure):
 class BatchConfig(ctypes.Structure):
     """ms_batch_config: warps per CTA, chunks in flight per warp, chunks per tile
     (power of two), CTAs per SM (0 = as many as fit), compact decoder flag,
-    schedule (0 = tiles to warps from a work counter, 1 = tiles round-robin to CTAs)."""
+    schedule (0 = tiles to warps from a work counter, 1 = tiles round-robin to CTAs,
+    2 = runs of chunks streamed through CTA-wide shared-memory buffers)."""
     _fields_ = [("warps", ctypes.c_uint32), ("depth", ctypes.c_uint32), ("tile_chunks", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("compact", ctypes.c_uint32), ("schedule", ctypes.c_uint32)]
 
@@ -59,8 +60,10 @@ class BatchConfig(ctypes.Structure):
 
 DEFAULT_BATCH_CONFIG = (8, 2, 32, 0, 0, 1)
 # (warps, depth, compact, schedule) combinations the library is built with
+# (schedule 2 streams runs of chunks through CTA-wide buffers of 8 KB x depth per column)
 BATCH_VARIANTS = tuple([(w, d, c, 0) for w in (4, 8) for d in (2, 3, 4) for c in (0, 1)] +
-                       [(4, 2, 0, 1), (8, 2, 0, 1), (16, 2, 0, 1), (4, 3, 0, 1), (8, 3, 0, 1)])
+                       [(4, 2, 0, 1), (8, 2, 0, 1), (16, 2, 0, 1), (4, 3, 0, 1), (8, 3, 0, 1)] +
+                       [(8, 2, 0, 2), (8, 3, 0, 2), (8, 4, 0, 2)])
 BATCH_ZERO, BATCH_PER_FRAGMENT = 1, 2
 
 

@@ -168,7 +168,7 @@ def test_errors_are_reported(ctx, batch):
     sums = torch.zeros(b.n, dtype=torch.int64, device=ctx.device)
     for cfg in ((6, 3, 32, 0, 0, 0), (8, 5, 32, 0, 0, 0), (8, 4, 4, 0, 0, 0), (8, 3, 24, 0, 0, 0),
                 (8, 3, 2048, 0, 0, 0), (8, 3, 32, 0, 2, 0), (16, 2, 8, 0, 0, 1), (16, 3, 64, 0, 0, 1),
-                (8, 2, 64, 0, 1, 1), (8, 2, 64, 0, 0, 2)):
+                (8, 2, 64, 0, 1, 1), (8, 2, 64, 0, 0, 3), (4, 2, 64, 0, 0, 2), (8, 2, 64, 0, 1, 2)):
         with pytest.raises(ms.MSError) as e:
             b.run(sums, cfg=cfg)
         assert e.value.code == ms.MS_ERR_INVALID_ARG
