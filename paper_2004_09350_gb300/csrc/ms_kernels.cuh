@@ -355,13 +355,6 @@ struct SmemSingle {
 struct SmemPair {
   StreamSmem<kProdDepth2> s0, s1;
 };
-struct SmemProject {
-  StreamSmem<kProdDepth2> s0;  // positions
-  StreamSmem<kProdDepth> s1;   // data blocks gathered densely
-  uint64_t aux[kBlock];        // one decoded data block
-  uint32_t list[kBlock];       // data blocks to decode, relative to the first one
-  uint16_t runs[32];           // run-start mask per lane
-};
 struct SmemProjectRandom {
   StreamSmem<kProdDepth2> s0;  // positions
 };
@@ -416,13 +409,6 @@ struct ProducePlan {
   static constexpr size_t kCtaBytes = (OP == OP_PROJECT_DELTA || OP == OP_PROJECT) ? sizeof(Cta) : 0;
 };
 
-// Direct-offset kernel (k_produce, the no-allocation path) keeps the list-based
-// project layout.
-template <int OP>
-struct DirectPlan {
-  using Smem = typename std::conditional<OP == OP_PROJECT, SmemProject, typename ProducePlan<OP>::Smem>::type;
-};
-
 // Output length of the operator (device-side, may depend on previous kernels).
 template <int OP>
 MS_DEV uint64_t produce_n(const ProduceArgs& a) {
@@ -435,165 +421,6 @@ MS_DEV uint64_t produce_n(const ProduceArgs& a) {
 
 MS_DEV uint64_t arith(int op, uint64_t x, uint64_t y) {
   return op == MS_ADD ? x + y : op == MS_SUB ? x - y : x * y;
-}
-
-// Runs a nested chunk stream over data blocks lo..lo+count-1 and calls
-// body(block, v) for each decoded block (all values valid for full blocks).
-template <int D, class Body>
-MS_DEV void stream_blocks(const ColView& c, uint64_t lo, uint64_t count, StreamSmem<D>* sm, int lane, DevCtl* ctl,
-                          Body body) {
-  ChunkStream<D> cs{c, lo, 1, count, sm, lane};
-  if (count == 0) return;
-  cs.prologue();
-  for (int j = 0; j < D - 1; j++) {
-    cs.prologue_step(j);
-    cp_async_commit();
-  }
-  for (uint64_t i = 0; i < count; i++) {
-    cp_async_wait<D - 2>();
-    __syncwarp();
-    cs.step(i);
-    cp_async_commit();
-    uint64_t t[16];
-    cs.decode(i, t, ctl);
-    body(cs.chunk(i), t);
-    __syncwarp();
-  }
-  cp_async_wait<0>();
-  __syncwarp();
-}
-
-// Decodes the data blocks lo + list[0..count) with a prefetching chunk stream and,
-// after each block, fills v[k] for the pending positions inside it (gathered from
-// the block decoded into sm->aux).  One decode site per kernel keeps the
-// width-specialised decoder's code footprint small.
-template <class Smem>
-MS_DEV void gather_listed(const ColView& d, uint64_t lo, uint64_t count, const uint64_t p[16], uint32_t& pending,
-                          uint64_t v[16], int lane, Smem* sm, DevCtl* ctl) {
-  constexpr int D = kProdDepth;
-  ChunkStream<D> cs{d, lo, 1, count, &sm->s1, lane};
-  cs.list = sm->list;
-  if (count == 0) return;
-  cs.prologue();
-  for (int j = 0; j < D - 1; j++) {
-    cs.prologue_step(j);
-    cp_async_commit();
-  }
-  for (uint64_t i = 0; i < count; i++) {
-    cp_async_wait<D - 2>();
-    __syncwarp();
-    cs.step(i);
-    cp_async_commit();
-    {
-      uint64_t t[16];
-      cs.decode(i, t, ctl);
-#pragma unroll
-      for (int k = 0; k < 16; k++) sm->aux[swz(16 * lane + k)] = t[k];
-    }
-    __syncwarp();
-    const uint64_t B = cs.chunk(i);
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-      if ((pending & (1u << k)) && p[k] / kBlock == B) {
-        v[k] = sm->aux[swz((int)(p[k] % kBlock))];
-        pending &= ~(1u << k);
-      }
-    }
-    __syncwarp();
-  }
-  cp_async_wait<0>();
-  __syncwarp();
-}
-
-// project core for one output chunk: positions p (lane-blocked) -> values v.
-// Sorted positions fall into runs, one per touched data block.  Blocks with a long
-// run (every run for DELTA data, whose values need the block's prefix sum) are
-// decoded once with a prefetching stream and gathered from shared memory.  The
-// remaining positions are random reads through the header directory (Sec. 4.2
-// random access, extended to the dynamic formats).
-template <class Smem>
-MS_DEV void project_gather(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
-                           uint64_t v[16], Smem* sm) {
-  uint32_t pending = 0;
-  bool sorted = true;
-#pragma unroll
-  for (int k = 0; k < 16; k++) {
-    v[k] = 0;
-    if (16 * lane + k < valid) {
-      if (p[k] < d.n) {
-        pending |= 1u << k;
-      } else {
-        set_error(a.ctl, MS_ERR_OUT_OF_RANGE, p[k]);
-      }
-      if (k > 0 && p[k] < p[k - 1]) sorted = false;
-    }
-  }
-  const uint64_t prev_last = __shfl_up_sync(kFull, p[15], 1);
-  if (lane > 0 && 16 * lane < valid && p[0] < prev_last) sorted = false;
-  bool runs_pass = __all_sync(kFull, sorted);
-  const bool delta = d.fmt == MS_DELTA_BP;
-  // Each pass lists data blocks to decode: the sorted case lists every block with a
-  // long run in one pass; unsorted positions into DELTA data list one distinct
-  // block per pass (ascending).
-  while (__ballot_sync(kFull, pending) != 0) {
-    uint64_t lo;
-    uint32_t total;
-    if (runs_pass) {
-      runs_pass = false;
-      // pending slots are a prefix of each lane's slots (sorted; out-of-range ones come last)
-      lo = warp_min((pending & 1u) ? p[0] / kBlock : ~0ull);
-      uint32_t starts = 0;
-      const uint64_t prevb = __shfl_up_sync(kFull, p[15] / kBlock, 1);
-#pragma unroll
-      for (int k = 0; k < 16; k++) {
-        const uint64_t bk = p[k] / kBlock;
-        if ((pending & (1u << k)) && (k == 0 ? (lane == 0 || bk != prevb) : bk != p[k - 1] / kBlock))
-          starts |= 1u << k;
-      }
-      sm->runs[lane] = (uint16_t)starts;
-      const uint32_t lanes_with = __ballot_sync(kFull, starts != 0);
-      __syncwarp();
-      const uint32_t min_run = delta ? 1u : (d.fmt == MS_UNCOMPR ? 128u : 8u);
-      uint32_t dense_here = 0;
-#pragma unroll
-      for (int k = 0; k < 16; k++) {
-        if (starts & (1u << k)) {
-          const uint32_t later = starts & ~((2u << k) - 1u);
-          int next;
-          if (later) {
-            next = 16 * lane + __ffs(later) - 1;
-          } else {
-            const uint32_t nl = lanes_with & ~((2u << lane) - 1u);
-            next = nl ? 16 * (__ffs(nl) - 1) + __ffs(sm->runs[__ffs(nl) - 1]) - 1 : valid;
-          }
-          if ((uint32_t)(next - (16 * lane + k)) >= min_run) dense_here |= 1u << k;
-        }
-      }
-      const uint32_t nd = __popc(dense_here);
-      const uint32_t at = warp_excl_scan32(nd, lane);
-      total = __shfl_sync(kFull, at + nd, 31);
-      uint32_t o = at;
-#pragma unroll
-      for (int k = 0; k < 16; k++)
-        if (dense_here & (1u << k)) sm->list[o++] = (uint32_t)(p[k] / kBlock - lo);
-    } else if (delta) {
-      uint64_t mb = ~0ull;
-#pragma unroll
-      for (int k = 0; k < 16; k++)
-        if (pending & (1u << k)) mb = min(mb, p[k] / kBlock);
-      lo = warp_min(mb);
-      total = 1;
-      if (lane == 0) sm->list[0] = 0;
-    } else {
-      break;
-    }
-    __syncwarp();
-    gather_listed(d, lo, total, p, pending, v, lane, sm, a.ctl);
-  }
-  // short runs or unsorted positions: random reads (never DELTA: its runs are all listed)
-#pragma unroll
-  for (int k = 0; k < 16; k++)
-    if (pending & (1u << k)) v[k] = read_at(d, p[k]);
 }
 
 // project core for DELTA data when the positions are unsorted or spread over
@@ -1025,9 +852,13 @@ MS_DEV int encode_block(int fmt, uint64_t v[16], int lane, uint64_t* ref_out) {
   return bw64(warp_or(o));
 }
 
+// Direct-offset producer of the allocation-free compress path: payload offsets come
+// from a decoupled look-back inside the kernel instead of a placement pass.
 template <int OP>
 __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_produce(ProduceArgs a) {
-  using Smem = typename DirectPlan<OP>::Smem;
+  static_assert(OP == OP_COMPRESS || OP == OP_DECOMPRESS || OP == OP_CALC || OP == OP_EMIT,
+                "k_produce has no project path");
+  using Smem = typename ProducePlan<OP>::Smem;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ uint64_t s_words[kWarps];
   __shared__ uint64_t s_excl;
@@ -1042,8 +873,8 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_produ
 
   ColView c0{}, c1{};
   if (OP == OP_COMPRESS) c0 = view_raw(a.raw_in, a.raw_n);
-  if (OP == OP_DECOMPRESS || OP == OP_CALC || OP == OP_PROJECT) c0 = view_of(a.in0);
-  if ((OP == OP_CALC || OP == OP_PROJECT) && a.in1) c1 = view_of(a.in1);
+  if (OP == OP_DECOMPRESS || OP == OP_CALC) c0 = view_of(a.in0);
+  if (OP == OP_CALC && a.in1) c1 = view_of(a.in1);
   const uint64_t n_out = produce_n<OP>(a);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (OP == OP_DECOMPRESS && a.in0->n > a.raw_cap) set_error(ctl, MS_ERR_INVALID_ARG, a.in0->n);
@@ -1059,7 +890,7 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_produ
   const uint64_t first = (uint64_t)blockIdx.x * kWarps + warp, stride = kWarps * G;
 
   // input streams: chunk i of a warp is first + i*stride, for every tile of the CTA
-  constexpr int D = (OP == OP_CALC || OP == OP_PROJECT) ? kProdDepth2 : kProdDepth;
+  constexpr int D = OP == OP_CALC ? kProdDepth2 : kProdDepth;
   StreamSmem<D>* ring0 = nullptr;
   StreamSmem<D>* ring1 = nullptr;
   if constexpr (OP == OP_COMPRESS || OP == OP_DECOMPRESS) ring0 = &sm->s0;
@@ -1067,9 +898,7 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_produ
     ring0 = &sm->s0;
     ring1 = &sm->s1;
   }
-  if constexpr (OP == OP_PROJECT) ring0 = &sm->s0;
-  const ColView main_col = (OP == OP_PROJECT) ? c1 : c0;
-  ChunkStream<D> st0{main_col, first, stride, (OP == OP_EMIT) ? 0 : my_tiles, ring0, lane};
+  ChunkStream<D> st0{c0, first, stride, (OP == OP_EMIT) ? 0 : my_tiles, ring0, lane};
   ChunkStream<D> st1{c1, first, stride, (OP == OP_CALC && a.in1) ? my_tiles : 0, ring1, lane};
   if (OP != OP_EMIT && my_tiles) {
     for (int i = 0; i < D; i++) {
@@ -1120,10 +949,6 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_produ
 #pragma unroll
           for (int k = 0; k < 16; k++) v[k] = arith(a.arith, v[k], a.scalar);
         }
-      } else {  // OP_PROJECT: c0 = data, st0 streams the positions (c1)
-        uint64_t p[16];
-        valid = st0.decode(i, p, ctl);
-        project_gather(a, c0, p, valid, lane, v, sm);
       }
       __syncwarp();
     }
