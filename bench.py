@@ -51,11 +51,13 @@ def parse():
     ap.add_argument("--seed", type=int, default=2020)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["sweep-plan", "star", "selector", "batch"], default="sweep-plan",
+    ap.add_argument("--workload", choices=["sweep-plan", "star", "selector", "batch", "kernel"], default="sweep-plan",
                     help="sweep-plan: the 2^28-row select/project/calc/sum plan (default); "
                          "star: the star-schema plan on a 6e8-row fact table; "
                          "selector: train the learned format selector on engine traces and judge it; "
-                         "batch: 4096 select->project->agg_sum fragments in one persistent launch")
+                         "batch: 4096 select->project->agg_sum fragments in one persistent launch; "
+                         "kernel: one operator of the plan alone (--kernel), the case the ncu summaries use")
+    ap.add_argument("--kernel", choices=["agg_sum", "select", "project"], default="agg_sum")
     ap.add_argument("--selector-items", type=int, default=3000)
     ap.add_argument("--fragments", type=int, default=4096)
     ap.add_argument("--batch-max-log2", type=float, default=24.0)
@@ -847,8 +849,55 @@ def bench_batch(args):
     }
 
 
+# ------------------------------------------------------------ one kernel
+
+def bench_kernel(args):
+    """One operator of the plan on the plan's columns (X dynamic BP, K DELTA, positions
+    of X < c at 10% as DELTA), built with bench.py's own generators at --rows: 3 warm-up
+    and --steps timed calls, per-kernel CUDA-event times.  This is the case the
+    profiles' ncu captures run (a few launches on a column larger than L2)."""
+    import torch
+    from paper_2004_09350_gb300 import morphstore as ms
+
+    n = args.rows
+    x, k, c = make_inputs(n, args.seed, args.selectivity)
+    dev = torch.device("cuda", 0)
+    ctx = ms.Ctx(0, arena_bytes=int(2.5 * 8 * n) + (1 << 30), max_rows=n)
+    cx = ctx.compress(ms.as_device_u64(x, dev), ms.DYN_BP)
+    ck = ctx.compress(ms.as_device_u64(k, dev), ms.DELTA_BP)
+    res = torch.zeros(1, dtype=torch.int64, device=dev)
+    pos = ctx.select(cx, ms.LT, c, fmt=ms.DELTA_BP) if args.kernel == "project" else None
+
+    def once():
+        if args.kernel == "agg_sum":
+            ctx.agg_sum(cx, out=res)
+        elif args.kernel == "select":
+            ctx.free(ctx.select(cx, ms.LT, c, fmt=ms.DELTA_BP))
+        else:
+            ctx.free(ctx.project(cx, pos, fmt=ms.DYN_BP))
+            ctx.free(ctx.project(ck, pos, fmt=ms.DELTA_BP))
+    for _ in range(3):
+        once()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    for _ in range(args.steps):
+        once()
+    prof = ctx.profile_collect()
+    ctx.check(what="kernel workload")
+    out = {"workload": "kernel", "kernel": args.kernel, "rows": n,
+           "bytes": {"X": ctx.info(cx)["size_bytes"], "K": ctx.info(ck)["size_bytes"]},
+           "ms_per_launch": {kk: round(v[1] / v[0], 4) for kk, v in prof.items()}}
+    if pos is not None:
+        out["positions"] = ctx.info(pos)["n"]
+    ctx.close()
+    return out
+
+
 def main():
     args = parse()
+    if args.workload == "kernel" and args.impl == "ours":
+        print(json.dumps(bench_kernel(args)))
+        return
     if args.workload == "batch" and args.impl == "ours":
         print(json.dumps(bench_batch(args)))
         return
