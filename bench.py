@@ -253,6 +253,22 @@ def measured_traffic(kernel):
     return e.get("dram_bytes_per_launch")
 
 
+def max_over_ranks(x, world, device=None):
+    """The largest x over all ranks (the slowest replica sets the job's step time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rows_per_s(world, rows, ms_step):
+    """Whole-job throughput: every replica processes `rows` per step."""
+    return world * rows / (ms_step * 1e-3)
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -329,11 +345,7 @@ def bench_ours(args):
             torch.cuda.synchronize()
         ck_info = clocks.stop() if clocks else None
         ctx.check(what=f"{label} timed steps")
-        ms_step = t0.elapsed_time(t1) / args.steps
-        if world > 1:
-            tt = torch.tensor([ms_step], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms_step = float(tt.item())
+        ms_step = max_over_ranks(t0.elapsed_time(t1) / args.steps, world, dev)
         got = int(ms.to_numpy_u64(res)[0])
         out[label] = dict(ms_step=ms_step, sizes=sizes, m=m, prof=prof, clocks=ck_info, sum=got,
                           footprint=int(sum(sizes.values())), arena_peak=int(high - (base_use - 0)))
@@ -394,13 +406,9 @@ def bench_ours(args):
         for _ in range(args.steps):
             e2e_step()
         barrier()
-        e2e_ms = (time.perf_counter() - t) * 1e3 / args.steps
-        if world > 1:
-            tt = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_ms = float(tt.item())
+        e2e_ms = max_over_ranks((time.perf_counter() - t) * 1e3 / args.steps, world, dev)
         assert int(hres.numpy().view(np.uint64)[0]) == comp["sum"]
-        e2e = {"value": world * n / (e2e_ms * 1e-3), "unit": "rows/s",
+        e2e = {"value": job_rows_per_s(world, n, e2e_ms), "unit": "rows/s",
                "h2d_bytes_per_step": int(hx.numel() + hk.numel()), "d2h_bytes_per_step": 8,
                "ms_per_step": round(e2e_ms, 3)}
 
@@ -416,7 +424,7 @@ def bench_ours(args):
     unc = out["uncompressed"]
     line = {
         "metric": METRIC,
-        "value": world * n / (comp["ms_step"] * 1e-3),
+        "value": job_rows_per_s(world, n, comp["ms_step"]),
         "unit": "rows/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -440,7 +448,7 @@ def bench_ours(args):
                      "alg_bytes_per_launch": per_kernel[dom]["alg_bytes"]},
         "per_kernel": per_kernel,
         "plan_GBps": round(plan_bytes / (comp["ms_step"] * 1e-3) / 1e9, 1),
-        "uncompressed": {"value": world * n / (unc["ms_step"] * 1e-3), "ms_per_step": round(unc["ms_step"], 4),
+        "uncompressed": {"value": job_rows_per_s(world, n, unc["ms_step"]), "ms_per_step": round(unc["ms_step"], 4),
                          "footprint_bytes": unc["footprint"], "arena_peak_bytes": unc["arena_peak"]},
         "compressed": {"footprint_bytes": comp["footprint"], "arena_peak_bytes": comp["arena_peak"],
                        "sizes": comp["sizes"]},
