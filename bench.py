@@ -331,12 +331,15 @@ def bench_ours(args):
                 free_all(ctx, run_plan(ctx, cx, ck, c, fm, res))
         barrier()
         ctx.profile(True)
-        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0.record()
-        for _ in range(args.steps):
+        # one event between consecutive steps: the mean over the whole region and the best step
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs[0].record()
+        for i in range(args.steps):
             free_all(ctx, run_plan(ctx, cx, ck, c, fm, res))
-        t1.record()
+            evs[i + 1].record()
+        t0, t1 = evs[0], evs[-1]
         barrier()
+        best_ms = min(evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps))
         prof = ctx.profile_collect()
         ctx.profile(False)
         if clocks:
@@ -347,7 +350,7 @@ def bench_ours(args):
         ctx.check(what=f"{label} timed steps")
         ms_step = max_over_ranks(t0.elapsed_time(t1) / args.steps, world, dev)
         got = int(ms.to_numpy_u64(res)[0])
-        out[label] = dict(ms_step=ms_step, sizes=sizes, m=m, prof=prof, clocks=ck_info, sum=got,
+        out[label] = dict(ms_step=ms_step, best_ms=best_ms, sizes=sizes, m=m, prof=prof, clocks=ck_info, sum=got,
                           footprint=int(sum(sizes.values())), arena_peak=int(high - (base_use - 0)))
         ctx.free(ck)
         ctx.free(cx)
@@ -430,6 +433,7 @@ def bench_ours(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": round(comp["ms_step"], 4),
+        "ms_per_step_best": round(comp["best_ms"], 4),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -449,6 +453,7 @@ def bench_ours(args):
         "per_kernel": per_kernel,
         "plan_GBps": round(plan_bytes / (comp["ms_step"] * 1e-3) / 1e9, 1),
         "uncompressed": {"value": job_rows_per_s(world, n, unc["ms_step"]), "ms_per_step": round(unc["ms_step"], 4),
+                         "ms_per_step_best": round(unc["best_ms"], 4),
                          "footprint_bytes": unc["footprint"], "arena_peak_bytes": unc["arena_peak"]},
         "compressed": {"footprint_bytes": comp["footprint"], "arena_peak_bytes": comp["arena_peak"],
                        "sizes": comp["sizes"]},

@@ -376,6 +376,16 @@ ms_status ms_graph_launch(ms_graph *g, void *stream);
 ms_status ms_graph_destroy(ms_graph *g);
 ms_status ms_batch_destroy(ms_batch *b);
 
+/* ------------------------------------------------------------- self-test */
+
+/* Failure-detection self-test: one bounded device-side wait that nothing ever
+   satisfies (a look-back whose predecessor tile never publishes).  The wait gives
+   up after its iteration limit (about 2^20 polls with back-off), records
+   MS_ERR_TIMEOUT in the device error word and returns.  Nothing faults or traps;
+   the context stays usable, and the next ms_get_error returns MS_ERR_TIMEOUT.
+   Uses the context's scratch; asynchronous on `stream`. */
+ms_status ms_selftest_wait_timeout(ms_ctx *ctx, void *stream);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Kernels of the library, as reported by ms_profile_collect. */

@@ -16,7 +16,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _HDR = os.path.join(_HERE, "oracle.h")
-_LIB = os.path.join(_HERE, "liboracle.so")
+# ORACLE_LIB names a prebuilt oracle library to load instead (a sanitizer build in the tests)
+_LIB = os.environ.get("ORACLE_LIB") or os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -50,7 +51,8 @@ def build(force: bool = False) -> str:
 def _load():
     global _lib
     if _lib is None:
-        build()
+        if not os.environ.get("ORACLE_LIB"):
+            build()
         lib = ctypes.CDLL(_LIB)
         u64, i32, p = ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
         sig = {

@@ -143,6 +143,7 @@ extern "C" {
 
 ms_status ms_batch_create(ms_ctx* c, uint32_t n, ms_column* const* x, ms_column* const* y, const int32_t* cmp,
                           const uint64_t* c1, const uint64_t* c2, ms_batch** out, void* stream) {
+  MS_TRACE();
   if (!c || !out || !x || !y || !cmp || !c1 || n == 0) return MS_ERR_INVALID_ARG;
   *out = nullptr;
   std::vector<BatchInit> init(n);
@@ -222,6 +223,7 @@ ms_status ms_batch_info(const ms_batch* b, uint64_t* rows, uint64_t* chunks, uin
 
 ms_status ms_batch_run(ms_batch* b, uint32_t f0, uint32_t f1, const ms_batch_config* cfg_in, uint32_t flags,
                        uint64_t* d_sums, void* stream) {
+  MS_TRACE();
   if (!b || !d_sums || f0 > f1 || f1 > b->n || (flags & ~(MS_BATCH_ZERO | MS_BATCH_PER_FRAGMENT)))
     return MS_ERR_INVALID_ARG;
   const ms_batch_config cfg = cfg_in ? *cfg_in : ms_batch_config{8, 2, 32, 0, 0, 1};
@@ -245,6 +247,7 @@ ms_status ms_batch_run(ms_batch* b, uint32_t f0, uint32_t f1, const ms_batch_con
 
 ms_status ms_batch_graph(ms_batch* b, uint32_t f0, uint32_t f1, const ms_batch_config* cfg, uint32_t flags,
                          uint64_t* d_sums, ms_graph** out) {
+  MS_TRACE();
   if (!b || !out) return MS_ERR_INVALID_ARG;
   *out = nullptr;
   const ms_batch_config conf = cfg ? *cfg : ms_batch_config{8, 2, 32, 0, 0, 1};
@@ -276,6 +279,7 @@ ms_status ms_batch_graph(ms_batch* b, uint32_t f0, uint32_t f1, const ms_batch_c
 }
 
 ms_status ms_graph_launch(ms_graph* g, void* stream) {
+  MS_TRACE();
   if (!g) return MS_ERR_INVALID_ARG;
   return cuda_status(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
 }

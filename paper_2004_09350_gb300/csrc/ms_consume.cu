@@ -162,6 +162,18 @@ __global__ void __launch_bounds__(32 * kPairWarps, 4) k_group_sum(const DevMeta*
     if (hist[k]) atomicAdd(reinterpret_cast<unsigned long long*>(sums) + k, hist[k]);
 }
 
+// Failure-detection self-test: tile 1 of a look-back whose tile 0 never publishes.
+__global__ void k_selftest_wait(uint64_t* status, DevCtl* ctl) {
+  lookback(status, 1, 0, threadIdx.x & 31, ctl);
+}
+
+ms_status launch_selftest_wait(ms_ctx* c, cudaStream_t s) {
+  uint64_t* status = reinterpret_cast<uint64_t*>(c->work);
+  if (cuda_status(cudaMemsetAsync(status, 0, 2 * sizeof(uint64_t), s)) != MS_OK) return MS_ERR_CUDA;
+  k_selftest_wait<<<1, 32, 0, s>>>(status, c->ctl);
+  return cuda_status(cudaGetLastError());
+}
+
 // Semi-join build side: set bit key for every key of the build column.
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_build_keys(const DevMeta* keys, uint64_t domain,
                                                                              uint32_t* bits, DevCtl* ctl) {

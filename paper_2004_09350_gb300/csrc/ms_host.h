@@ -5,6 +5,8 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "morphstore.h"
 #include "ms_device.cuh"
 
@@ -58,6 +60,16 @@ ms_column* new_arena_column(ms_ctx* c, int fmt, int bw, uint64_t n_max);
 void drop_new_column(ms_ctx* c, ms_column* col);
 // Makes sure the scratch area holds at least `bytes`; synchronises when it grows.
 ms_status ensure_work(ms_ctx* c, uint64_t bytes);
+
+// An NVTX range around one entry point (visible to nsys and to ncu's --nvtx filters;
+// a no-op without a tool attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define MS_TRACE() ::ms::NvtxRange ms_trace_range_(__func__)
 
 // Brackets one kernel launch with profiling events when profiling is on.
 class ProfScope {

@@ -45,6 +45,7 @@ ms_status launch_group_sum(ms_ctx* c, const DevMeta* gid, const DevMeta* val, ui
 ms_status launch_build_keys(ms_ctx* c, const DevMeta* keys, uint64_t domain, uint32_t* bits, uint64_t n_max,
                             cudaStream_t s);
 ms_status launch_stats(ms_ctx* c, const DevMeta* in, uint64_t* d_stats, uint64_t n_max, cudaStream_t s);
+ms_status launch_selftest_wait(ms_ctx* c, cudaStream_t s);
 
 // producers (ms_map_*.cu): one warp-independent k_map<OP> launch
 template <int OP>

@@ -180,6 +180,7 @@ using namespace ms;
 extern "C" {
 
 ms_status ms_mlp_forward(const float* d_params, const float* d_x, uint64_t n, float* d_y, void* stream) {
+  MS_TRACE();
   if (!d_params || (n && (!d_x || !d_y))) return MS_ERR_INVALID_ARG;
   if (n == 0) return MS_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -194,6 +195,7 @@ ms_status ms_mlp_forward(const float* d_params, const float* d_x, uint64_t n, fl
 ms_status ms_mlp_loss_grad(const float* d_params, const float* d_x, const float* d_y, const float* d_mask,
                            uint64_t n, float inv_count, float* d_grad, float* d_loss, float* d_partials,
                            uint64_t partials_floats, void* stream) {
+  MS_TRACE();
   if (!d_params || !d_grad || !d_loss || !d_partials || (n && (!d_x || !d_y || !d_mask))) return MS_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int grid = mlp_grid(std::max<uint64_t>(n, 1));
@@ -210,6 +212,7 @@ ms_status ms_mlp_loss_grad(const float* d_params, const float* d_x, const float*
 
 ms_status ms_mlp_adam(float* d_params, const float* d_grad, float* d_m, float* d_v, uint64_t step, float lr,
                       float beta1, float beta2, float eps, void* stream) {
+  MS_TRACE();
   if (!d_params || !d_grad || !d_m || !d_v || step == 0) return MS_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double p1 = 1.0, p2 = 1.0;

@@ -135,6 +135,7 @@ extern "C" {
 
 ms_status ms_compress(ms_ctx* c, const uint64_t* d_in, uint64_t n, int fmt, int bw, ms_column** out,
                       void* stream) {
+  MS_TRACE();
   if (!c || !out || (!d_in && n) || !valid_format(fmt, bw)) return MS_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(d_in) % 16) return MS_ERR_INVALID_ARG;
   *out = nullptr;
@@ -149,6 +150,7 @@ ms_status ms_compress(ms_ctx* c, const uint64_t* d_in, uint64_t n, int fmt, int 
 }
 
 ms_status ms_decompress(ms_ctx* c, const ms_column* col, uint64_t* d_out, uint64_t cap, void* stream) {
+  MS_TRACE();
   if (!c || !owned(c, col) || (!d_out && cap)) return MS_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(d_out) % 16) return MS_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -163,6 +165,7 @@ ms_status ms_decompress(ms_ctx* c, const ms_column* col, uint64_t* d_out, uint64
 
 ms_status ms_select(ms_ctx* c, const ms_column* in, int cmp, uint64_t c1, uint64_t c2, int fmt, int bw,
                     ms_column** out, void* stream) {
+  MS_TRACE();
   if (!c || !out || !owned(c, in) || !valid_format(fmt, bw) || cmp < MS_EQ || cmp > MS_BETWEEN)
     return MS_ERR_INVALID_ARG;
   *out = nullptr;
@@ -181,6 +184,7 @@ ms_status ms_select(ms_ctx* c, const ms_column* in, int cmp, uint64_t c1, uint64
 
 ms_status ms_project(ms_ctx* c, const ms_column* data, const ms_column* pos, int fmt, int bw,
                      ms_column** out, void* stream) {
+  MS_TRACE();
   if (!c || !out || !owned(c, data) || !owned(c, pos) || !valid_format(fmt, bw)) return MS_ERR_INVALID_ARG;
   *out = nullptr;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -198,6 +202,7 @@ ms_status ms_project(ms_ctx* c, const ms_column* data, const ms_column* pos, int
 
 ms_status ms_calc(ms_ctx* c, int op, const ms_column* x, const ms_column* y, uint64_t scalar, int fmt,
                   int bw, ms_column** out, void* stream) {
+  MS_TRACE();
   if (!c || !out || !owned(c, x) || (y && !owned(c, y)) || !valid_format(fmt, bw) || op < MS_ADD ||
       op > MS_MUL)
     return MS_ERR_INVALID_ARG;
@@ -216,6 +221,7 @@ ms_status ms_calc(ms_ctx* c, int op, const ms_column* x, const ms_column* y, uin
 }
 
 ms_status ms_agg_sum(ms_ctx* c, const ms_column* in, uint64_t* d_result, void* stream) {
+  MS_TRACE();
   if (!c || !owned(c, in) || !d_result) return MS_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cuda_status(cudaMemsetAsync(d_result, 0, 8, s)) != MS_OK) return MS_ERR_CUDA;
@@ -224,6 +230,7 @@ ms_status ms_agg_sum(ms_ctx* c, const ms_column* in, uint64_t* d_result, void* s
 
 ms_status ms_group_sum(ms_ctx* c, const ms_column* gid, const ms_column* val, uint64_t G, uint64_t* d_sums,
                        void* stream) {
+  MS_TRACE();
   if (!c || !owned(c, gid) || !owned(c, val) || (!d_sums && G)) return MS_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (G && cuda_status(cudaMemsetAsync(d_sums, 0, 8 * G, s)) != MS_OK) return MS_ERR_CUDA;
@@ -233,6 +240,7 @@ ms_status ms_group_sum(ms_ctx* c, const ms_column* gid, const ms_column* val, ui
 
 ms_status ms_semijoin(ms_ctx* c, const ms_column* probe, const ms_column* keys, uint64_t domain, int fmt,
                       int bw, ms_column** out, void* stream) {
+  MS_TRACE();
   if (!c || !out || !owned(c, probe) || !owned(c, keys) || !valid_format(fmt, bw) || domain == 0)
     return MS_ERR_INVALID_ARG;
   *out = nullptr;
@@ -254,10 +262,17 @@ ms_status ms_semijoin(ms_ctx* c, const ms_column* probe, const ms_column* keys, 
 }
 
 ms_status ms_column_stats(ms_ctx* c, const ms_column* col, uint64_t* d_stats, void* stream) {
+  MS_TRACE();
   if (!c || !owned(c, col) || !d_stats) return MS_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cuda_status(cudaMemsetAsync(d_stats, 0, 8 * MS_STATS_WORDS, s)) != MS_OK) return MS_ERR_CUDA;
   return launch_stats(c, c->metas + col->slot, d_stats, col->n_max, s);
+}
+
+ms_status ms_selftest_wait_timeout(ms_ctx* c, void* stream) {
+  MS_TRACE();
+  if (!c) return MS_ERR_INVALID_ARG;
+  return launch_selftest_wait(c, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -125,6 +125,7 @@ def load() -> ctypes.CDLL:
         "ms_graph_launch": [p, p],
         "ms_graph_destroy": [p],
         "ms_batch_destroy": [p],
+        "ms_selftest_wait_timeout": [p, p],
     })
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -274,6 +275,11 @@ class Ctx:
         _check(load().ms_arena_reset_high_water(self.h, _stream_handle(stream)), "reset_high_water")
 
     # ---------------------------------------------------------- statistics
+    def selftest_wait_timeout(self, stream=None):
+        """Run one device wait that nothing satisfies; it must give up with
+        MS_ERR_TIMEOUT in the error word (read it with get_error)."""
+        _check(load().ms_selftest_wait_timeout(self.h, _stream_handle(stream)), "ms_selftest_wait_timeout")
+
     def column_stats(self, col: Column, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """ms_column_stats into an int64 device tensor of STATS_WORDS words."""
         if out is None:

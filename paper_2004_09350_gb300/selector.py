@@ -24,6 +24,7 @@ All choices change formats only; every result stays bit-exact.
 """
 from __future__ import annotations
 
+import json
 import math
 
 import numpy as np
@@ -142,6 +143,33 @@ class Selector:
                 hist.append((step, float(loss.item())))
         self.loss_history = hist
         return hist
+
+    # --------------------------------------------------------- checkpoint
+    def save(self, prefix: str) -> None:
+        """Writes the network as <prefix>.bin (MS_MLP_PARAMS little-endian fp32 in the
+        packed layout of include/morphstore.h) and <prefix>.json (target scaling,
+        loss history)."""
+        theta = self.params.detach().to("cpu", torch.float32).numpy().astype("<f4")
+        theta.tofile(prefix + ".bin")
+        meta = {"params": int(theta.size), "layout": "W1[16][64] b1[64] W2[64][64] b2[64] W3[64][10] b3[10]",
+                "mu": [float(v) for v in self.mu], "sd": [float(v) for v in self.sd],
+                "loss_history": [[int(a), float(b)] for a, b in self.loss_history]}
+        with open(prefix + ".json", "w") as f:
+            json.dump(meta, f, indent=1)
+
+    @classmethod
+    def load(cls, prefix: str, device) -> "Selector":
+        with open(prefix + ".json") as f:
+            meta = json.load(f)
+        theta = np.fromfile(prefix + ".bin", dtype="<f4")
+        if theta.size != ms.MLP_PARAMS or meta.get("params") != ms.MLP_PARAMS:
+            raise ValueError("not a selector checkpoint: wrong parameter count")
+        sel = cls(device)
+        sel.params = torch.from_numpy(theta.astype(np.float32)).to(device)
+        sel.mu = np.asarray(meta["mu"], dtype=np.float32)
+        sel.sd = np.asarray(meta["sd"], dtype=np.float32)
+        sel.loss_history = [tuple(v) for v in meta.get("loss_history", [])]
+        return sel
 
     def predict(self, X: np.ndarray) -> np.ndarray:
         x = torch.from_numpy(np.ascontiguousarray(X, np.float32)).to(self.device)
