@@ -13,7 +13,8 @@ value = logical input rows per second of the compressed pipeline (whole job).
 roofline = the dominant kernel's algorithmic bytes per launch / its mean launch
 time, against the measured HBM copy peak.  e2e = the same plan through the C
 ABI with the compressed base columns copied from pinned host memory every step
-and the sum read back.  cpu_baseline = the CPU oracle on a bounded sample of the
+and the sum read back (uncompressed.e2e: the uncompressed plan the same way, its
+base columns uncompressed).  cpu_baseline = the CPU oracle on a bounded sample of the
 same workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -381,10 +382,9 @@ def bench_ours(args):
     ach = per_kernel[dom]["alg_GBps"]
     plan_bytes = sum(v * per_kernel.get(kk, {"launches": 0})["launches"] / args.steps for kk, v in alg.items())
 
-    # ---- end to end through the C ABI from pinned host buffers
-    e2e = None
-    if not args.no_e2e:
-        fm = COMPRESSED
+    # ---- end to end through the C ABI from pinned host buffers: every step copies the
+    # plan's base columns in, in their format, runs the plan and reads the sum back
+    def e2e_run(fm):
         cx = ctx.compress(dx, fmt_id(fm["X"]))
         ck = ctx.compress(dk, fmt_id(fm["K"]))
         hx = torch.from_numpy(ctx.export_bytes(cx)).pin_memory()
@@ -409,11 +409,16 @@ def bench_ours(args):
         for _ in range(args.steps):
             e2e_step()
         barrier()
-        e2e_ms = max_over_ranks((time.perf_counter() - t) * 1e3 / args.steps, world, dev)
+        ms_e = max_over_ranks((time.perf_counter() - t) * 1e3 / args.steps, world, dev)
         assert int(hres.numpy().view(np.uint64)[0]) == comp["sum"]
-        e2e = {"value": job_rows_per_s(world, n, e2e_ms), "unit": "rows/s",
-               "h2d_bytes_per_step": int(hx.numel() + hk.numel()), "d2h_bytes_per_step": 8,
-               "ms_per_step": round(e2e_ms, 3)}
+        return {"value": job_rows_per_s(world, n, ms_e), "unit": "rows/s",
+                "h2d_bytes_per_step": int(hx.numel() + hk.numel()), "d2h_bytes_per_step": 8,
+                "ms_per_step": round(ms_e, 3)}
+
+    e2e = e2e_unc = None
+    if not args.no_e2e:
+        e2e = e2e_run(COMPRESSED)
+        e2e_unc = e2e_run(UNCOMPRESSED)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -453,7 +458,7 @@ def bench_ours(args):
         "per_kernel": per_kernel,
         "plan_GBps": round(plan_bytes / (comp["ms_step"] * 1e-3) / 1e9, 1),
         "uncompressed": {"value": job_rows_per_s(world, n, unc["ms_step"]), "ms_per_step": round(unc["ms_step"], 4),
-                         "ms_per_step_best": round(unc["best_ms"], 4),
+                         "ms_per_step_best": round(unc["best_ms"], 4), "e2e": e2e_unc,
                          "footprint_bytes": unc["footprint"], "arena_peak_bytes": unc["arena_peak"]},
         "compressed": {"footprint_bytes": comp["footprint"], "arena_peak_bytes": comp["arena_peak"],
                        "sizes": comp["sizes"]},
