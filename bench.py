@@ -240,9 +240,9 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel):
-    """dram bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel sources (else None)."""
+def measured_traffic(kernel, key="dram_bytes_per_launch"):
+    """A DRAM traffic figure (bytes per launch, or bytes per algorithmic byte) from the
+    committed ncu summary, if it was taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -251,7 +251,7 @@ def measured_traffic(kernel):
     e = t.get(kernel)
     if not e or e.get("source_digest") != source_digest():
         return None
-    return e.get("dram_bytes_per_launch")
+    return e.get(key)
 
 
 def max_over_ranks(x, world, device=None):
@@ -848,7 +848,9 @@ def bench_batch(args):
                    "l2": "inputs larger than L2 (no flush)", "launch": "one persistent launch in a CUDA graph"},
         "gb_per_s": info["bytes"] / (med * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                     "traffic": (None if measured_traffic("batch", "dram_per_algorithmic_byte") is None
+                                 else int(measured_traffic("batch", "dram_per_algorithmic_byte") * info["bytes"])),
                      "kernel": "k_batch", "kernel_ms": round(k_ms, 4)},
         "per_fragment_launches": {"ms_per_step": round(statistics.median(each), 3),
                                   "rows_per_s": rows / (statistics.median(each) * 1e-3),
