@@ -1,12 +1,19 @@
 // ms_kernels.cuh -- operator kernels of libms (sm_103a).
 //
-// Every operator is one or two persistent kernels that loop over 4096-value tiles
-// (8 warps x one 512-value chunk each).  Input blocks are decoded into lane
+// A warp owns one 512-value chunk at a time.  Input blocks are decoded into lane
 // registers, the operator core runs on the uncompressed values, and output blocks
 // are recompressed in shared memory before they are stored.  This is the
 // on-the-fly de/re-compression degree of Sec. 3.2 at block granularity: only
-// compressed bytes travel to and from device memory.  The payload offsets of
-// dynamically sized output blocks come from a decoupled look-back over tiles.
+// compressed bytes travel to and from device memory.
+//   * Consumers (mark, agg_sum, semi-join build, statistics) read their column
+//     through the CTA tile stream (cta_stream): runs of consecutive blocks copied
+//     into shared memory with all the CTA's threads, double-buffered.
+//   * Producers (k_map: compress, decompress, project, calc, emit) encode each
+//     output block into a stage slot; a placement pass (ms_place.cu) turns the
+//     block widths into payload offsets with a decoupled look-back and moves the
+//     payloads into place.  Project gathers a CTA tile of sorted positions from
+//     the data blocks they span, staged the same way (gather_cta).
+//   * k_produce is the direct-offset variant of the allocation-free compress path.
 #pragma once
 #include <type_traits>
 
