@@ -378,10 +378,17 @@ template <int kCtaBuf>
 struct ProjectCta {
   static constexpr int kBuf = kCtaBuf;
   uint8_t buf[kCtaBuf];
-  uint4 hdr[kCtaHdr];  // {(payload word offset << 8) | b, reference} of the piece's blocks
+  // per block of the piece: {halfword offset of its payload in buf, width b, mask of
+  // b bits (low word, high word)}; the value extraction reads up to 320 bytes past
+  // the end of buf, into hdr
+  uint4 hdr[kCtaHdr];
+  uint64_t ref[kCtaHdr];  // the blocks' reference values
+  static_assert(kCtaBuf % 16 == 0 && sizeof(uint4) * kCtaHdr >= 320, "extraction over-read must stay in hdr");
   uint64_t lo[kWarps], hi[kWarps];
   uint32_t ok[kWarps], nv[kWarps];
   uint64_t off_lo;
+  uint64_t mbar;   // completion barrier of the piece's bulk copy
+  uint32_t phase;  // its current phase parity
 };
 struct SmemEmit {
   uint32_t bits[kEmitSpan * 16];
@@ -395,6 +402,9 @@ struct SmemEmit {
 #endif
 #ifndef MS_PROJECT_CTA_BUF
 #define MS_PROJECT_CTA_BUF (152 * 1024)  // staged data blocks per CTA (DYN / FOR / static data)
+#endif
+#ifndef MS_PROJECT_BULK
+#define MS_PROJECT_BULK 1  // project copies its data pieces with the bulk-copy engine
 #endif
 #ifndef MS_PROJECT_DELTA_CTA_BUF
 #define MS_PROJECT_DELTA_CTA_BUF (96 * 1024)  // staged data blocks per CTA (DELTA data)
@@ -693,6 +703,13 @@ MS_DEV void gather_cta(const ProduceArgs& a, const ColView& d, const uint64_t p[
   const uint64_t nfull = blockfmt ? d.nb : d.n / kBlock;  // blocks with a packed payload
   const uint64_t pay0 = blockfmt ? 16 * d.nb : 0;
   const uint64_t last = min(B_hi, nfull - 1);
+  // Positions relative to the tile's first block fit 32 bits (the tile spans at most
+  // npos <= 4096 blocks), so the per-value work below is 32-bit.  Slots past the
+  // warp's valid count get ~0, whose block lies in no piece.
+  const uint64_t base = B_lo << 9;
+  uint32_t rel[16];
+#pragma unroll
+  for (int k = 0; k < 16; k++) rel[k] = k < nv ? (uint32_t)(p[k] - base) : ~0u;
   for (uint64_t lo_blk = B_lo; nfull > 0 && lo_blk <= last;) {
     // thread t: block lo_blk + t
     const uint64_t hb = lo_blk + tid;
@@ -706,7 +723,9 @@ MS_DEV void gather_cta(const ProduceArgs& a, const ColView& d, const uint64_t p[
         ref = inh ? ldg64(d.p + 16 * hb + 8) : 0;
         off = w0 >> 8;
         b = (uint32_t)(w0 & 255);
-        if (!inh || b > 64 || pay0 + 8 * (off + 8ull * b) > d.size) {
+        // every payload starts on an 8-word boundary (its predecessors are 8b words
+        // each); another offset is a corrupt chain and would misalign the copy
+        if (!inh || b > 64 || (off & 7) || pay0 + 8 * (off + 8ull * b) > d.size) {
           set_error(a.ctl, MS_ERR_FORMAT, hb);
           b = 0;
           off = 0;
@@ -723,43 +742,63 @@ MS_DEV void gather_cta(const ProduceArgs& a, const ColView& d, const uint64_t p[
     // blocks whose payload ends within one buffer (ends are monotone); a corrupt
     // header makes an empty block and never stalls the loop
     const bool fits = here && off >= off_lo && 8 * (end - off_lo) <= (uint64_t)kCtaBuf;
-    if (fits) cs->hdr[tid] = make_uint4((uint32_t)((off << 8) | b), (uint32_t)(off >> 24), (uint32_t)ref,
-                                        (uint32_t)(ref >> 32));
+    if (fits) {
+      cs->hdr[tid] = make_uint4((uint32_t)(4 * (off - off_lo)), b, b >= 32 ? ~0u : (1u << b) - 1u,
+                                b <= 32 ? 0u : (b >= 64 ? ~0u : (1u << (b - 32)) - 1u));
+      cs->ref[tid] = ref;
+    }
     const int cnt = max(1, __syncthreads_count(fits));
     const uint4 hl = cs->hdr[cnt - 1];
-    const uint64_t wl = (uint64_t)hl.x | (uint64_t)hl.y << 32;
-    // (a stale entry from a corrupt chain only shortens or clamps the copy)
-    const uint64_t bytes = min(8 * ((wl >> 8) + 8 * (wl & 255) - off_lo), (uint64_t)kCtaBuf);
-    const uint4* src = reinterpret_cast<const uint4*>(d.p + pay0 + 8 * off_lo);
-    for (uint32_t u = tid; u < (uint32_t)(bytes >> 4); u += blockDim.x) cp_async16(reinterpret_cast<uint4*>(cs->buf) + u, src + u);
+    // (a stale entry from a corrupt chain only shortens or clamps the copy, which
+    // never runs past the column's buffer)
+    const uint64_t at = pay0 + 8 * off_lo;
+    const uint64_t room = d.size > at ? d.size - at : 0;
+    uint32_t bytes = (uint32_t)min(min((uint64_t)(2ull * hl.x + 64ull * hl.y), (uint64_t)kCtaBuf), room) & ~15u;
+#if MS_PROJECT_BULK
+    // One thread hands the piece to the bulk-copy engine and the CTA waits on the
+    // barrier.  Payloads start on 64-byte boundaries of a 256-byte aligned column;
+    // a column that breaks this (it can only be corrupt) copies nothing.
+    if (reinterpret_cast<uintptr_t>(d.p + at) & 15) {
+      if (tid == 0) set_error(a.ctl, MS_ERR_FORMAT, lo_blk);
+      bytes = 0;
+    }
+    const uint32_t par = cs->phase;
+    if (bytes) {
+      if (tid == 0) {
+        mbar_expect_tx(&cs->mbar, bytes);
+        bulk_copy_g2s(cs->buf, d.p + at, bytes, &cs->mbar);
+      }
+      if (!mbar_wait(&cs->mbar, par) && tid == 0) set_error(a.ctl, MS_ERR_TIMEOUT, lo_blk);
+    }
+    __syncthreads();
+    if (tid == 0 && bytes) cs->phase = par ^ 1;
+#else
+    const uint4* src = reinterpret_cast<const uint4*>(d.p + at);
+    for (uint32_t u = tid; u < (bytes >> 4); u += blockDim.x) cp_async16(reinterpret_cast<uint4*>(cs->buf) + u, src + u);
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    const uint64_t hi_blk = lo_blk + cnt;  // exclusive
+#endif
+    const uint32_t lo_r = (uint32_t)(lo_blk - B_lo);  // the piece's first block, tile-relative
     if constexpr (kDelta) {
       uint32_t pend = 0;
 #pragma unroll
-      for (int k = 0; k < 16; k++) {
-        const uint64_t B = p[k] >> 9;
-        pend |= (uint32_t)(k < nv && B >= lo_blk && B < hi_blk) << k;
-      }
+      for (int k = 0; k < 16; k++) pend |= (uint32_t)((rel[k] >> 9) - lo_r < (uint32_t)cnt) << k;
       while (__ballot_sync(kFull, pend) != 0) {
-        uint64_t mb = ~0ull;
+        uint32_t mb = ~0u;
 #pragma unroll
         for (int k = 0; k < 16; k++)
-          if (pend & (1u << k)) mb = min(mb, p[k] >> 9);
-        const uint64_t B = warp_min(mb);
-        const uint4 h = cs->hdr[B - lo_blk];
-        const uint64_t w0 = (uint64_t)h.x | (uint64_t)h.y << 32, rr = (uint64_t)h.z | (uint64_t)h.w << 32;
-        const uint64_t boff = (w0 >> 8) - off_lo;
-        const int bb = (int)(w0 & 255);
+          if (pend & (1u << k)) mb = min(mb, rel[k] >> 9);
+        const uint32_t B = __reduce_min_sync(kFull, mb);
+        const uint4 h = cs->hdr[B - lo_r];
+        const uint64_t rr = cs->ref[B - lo_r];
         uint64_t t[16];
-        if (8 * boff + 64ull * bb > bytes) {  // never read past the copy
-          if (lane == 0) set_error(a.ctl, MS_ERR_FORMAT, B);
+        if (2 * h.x + 64 * h.y > bytes) {  // never read past the copy
+          if (lane == 0) set_error(a.ctl, MS_ERR_FORMAT, B_lo + B);
 #pragma unroll
           for (int k = 0; k < 16; k++) t[k] = 0;
         } else {
-          read_lane_stream(reinterpret_cast<const uint16_t*>(cs->buf + 8 * boff), lane, bb, t);
+          read_lane_stream(reinterpret_cast<const uint16_t*>(cs->buf) + h.x, lane, (int)h.y, t);
         }
         uint64_t sum = 0;
 #pragma unroll
@@ -773,56 +812,56 @@ MS_DEV void gather_cta(const ProduceArgs& a, const ColView& d, const uint64_t p[
         __syncwarp();
 #pragma unroll
         for (int k = 0; k < 16; k++) {
-          if ((pend & (1u << k)) && (p[k] >> 9) == B) {
-            v[k] = aux[swz((int)(p[k] & 511))];
+          if ((pend & (1u << k)) && (rel[k] >> 9) == B) {
+            v[k] = aux[swz((int)(rel[k] & 511))];
             pend &= ~(1u << k);
           }
         }
         __syncwarp();
       }
     } else {
+      // Value r of a block is bits [kk*b, kk*b + b) of lane stream j = r/16 (kk = r%16),
+      // and stream halfword i of lane j is payload halfword 32i + j.  Five halfwords
+      // cover a value of up to 64 bits at any of the 16 bit phases; the bits past the
+      // value are masked off.  The last of them may lie up to 320 bytes past the
+      // piece's end, which is still inside the shared buffer: `hdr` follows `buf`.
       const uint16_t* s16 = reinterpret_cast<const uint16_t*>(cs->buf);
+      const bool add_ref = d.fmt == MS_FOR_BP;
 #pragma unroll
       for (int k = 0; k < 16; k++) {
-        const uint64_t B = p[k] >> 9;
-        if (k < nv && B >= lo_blk && B < hi_blk) {
-          const uint4 h = cs->hdr[B - lo_blk];
-          const uint64_t w0 = (uint64_t)h.x | (uint64_t)h.y << 32, rr = (uint64_t)h.z | (uint64_t)h.w << 32;
-          const uint64_t boff = (w0 >> 8) - off_lo;
-          const uint32_t bb = (uint32_t)(w0 & 255);
-          const uint64_t add = d.fmt == MS_FOR_BP ? rr : 0;
-          if (8 * boff + 64ull * bb > bytes) {  // never read past the copy
-            set_error(a.ctl, MS_ERR_FORMAT, B);
-          } else if (bb) {
-            const uint32_t r = (uint32_t)(p[k] & 511), j = r >> 4, kk = r & 15;
-            const uint32_t bit = kk * bb, q0 = bit >> 4, sh = bit & 15, nq = (sh + bb + 15) >> 4;
-            const uint32_t h0 = (uint32_t)(4 * boff) + 32 * q0 + j;  // halfword index in the piece
-            uint64_t w = 0, h4 = 0;
-#pragma unroll
-            for (uint32_t q = 0; q < 4; q++)
-              if (q < nq) w |= (uint64_t)s16[h0 + 32 * q] << (16 * q);
-            if (nq > 4) h4 = s16[h0 + 128];
-            const uint64_t x = (w >> sh) | (sh ? h4 << (64 - sh) : 0);
-            v[k] = (x & lowmask((int)bb)) + add;
+        const uint32_t q = (rel[k] >> 9) - lo_r;
+        if (q < (uint32_t)cnt) {
+          const uint4 h = cs->hdr[q];
+          if (2 * h.x + 64 * h.y > bytes) {  // never read past the copy
+            set_error(a.ctl, MS_ERR_FORMAT, B_lo + lo_r + q);
           } else {
-            v[k] = add;
+            const uint32_t r = rel[k] & 511, bit = (r & 15) * h.y;
+            const uint32_t h0 = h.x + 32 * (bit >> 4) + (r >> 4);
+            const uint32_t w0 = (uint32_t)s16[h0] | (uint32_t)s16[h0 + 32] << 16;
+            const uint32_t w1 = (uint32_t)s16[h0 + 64] | (uint32_t)s16[h0 + 96] << 16;
+            const uint32_t w2 = s16[h0 + 128];
+            const uint32_t xl = __funnelshift_r(w0, w1, bit & 15) & h.z;
+            const uint32_t xh = __funnelshift_r(w1, w2, bit & 15) & h.w;
+            v[k] = ((uint64_t)xh << 32 | xl) + (add_ref ? cs->ref[q] : 0ull);
           }
         }
       }
     }
     __syncthreads();  // the next piece overwrites the buffer
-    lo_blk = hi_blk;
+    lo_blk += (uint64_t)cnt;
   }
   // positions in the uncompressed remainder (block formats) or the horizontal tail (static BP)
+  const uint32_t nfull_r = nfull > B_lo ? (uint32_t)min(nfull - B_lo, (uint64_t)1 << 23) : 0u;
 #pragma unroll
   for (int k = 0; k < 16; k++) {
-    if (k < nv && (p[k] >> 9) >= nfull) {
+    if (k < nv && (rel[k] >> 9) >= nfull_r) {
+      const uint64_t pk = base + rel[k];
       if (blockfmt) {
-        const uint64_t at = pay0 + 8 * d.pwords + 8 * (p[k] - kBlock * d.nb);
+        const uint64_t at = pay0 + 8 * d.pwords + 8 * (pk - kBlock * d.nb);
         v[k] = at + 8 <= d.size ? ldg64(d.p + at) : 0;
       } else {
         const uint64_t* tail = reinterpret_cast<const uint64_t*>(d.p + 64ull * d.bw * nfull);
-        const uint64_t bit = (p[k] - kBlock * nfull) * (uint64_t)d.bw;
+        const uint64_t bit = (pk - kBlock * nfull) * (uint64_t)d.bw;
         const int sh = (int)(bit & 63);
         uint64_t x = ldg64(tail + (bit >> 6)) >> sh;
         if (sh + d.bw > 64) x |= ldg64(tail + (bit >> 6) + 1) << (64 - sh);
@@ -1222,6 +1261,16 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
   }
 
   auto* pcta = reinterpret_cast<typename ProducePlan<OP>::Cta*>(smem_raw + sizeof(Smem) * kWarps);
+  if constexpr (kProject) {
+    // piece headers start zeroed: a slot that a corrupt chain skips then reads as an
+    // empty block at offset 0, never as an offset outside the buffer
+    for (int t = threadIdx.x; t < kCtaHdr; t += blockDim.x) pcta->hdr[t] = make_uint4(0, 0, 0, 0);
+    if (threadIdx.x == 0) {
+      mbar_init(&pcta->mbar, 1);
+      pcta->phase = 0;
+    }
+    __syncthreads();
+  }
   for (uint64_t i = 0; i < loop_n; i++) {
     const uint64_t g = first + i * stride;
     uint64_t v[16];
