@@ -109,6 +109,16 @@ MS_DEV void decode_rec(uint64_t addr, uint64_t ref, uint32_t code, int valid, co
     if (fmt == MS_FOR_BP) {
 #pragma unroll
       for (int k = 0; k < 16; k++) v[k] += ref;
+    } else if (fmt == MS_DELTA_BP && b <= 23) {  // 512 residuals < 2^23 sum below 2^32
+      uint32_t s = 0;
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        s += (uint32_t)v[k];
+        v[k] = s;
+      }
+      const uint64_t excl = (uint64_t)warp_excl_scan32(s, lane) + ref;
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] += excl;
     } else if (fmt == MS_DELTA_BP) {
       uint64_t s = 0;
 #pragma unroll

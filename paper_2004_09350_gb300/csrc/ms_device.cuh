@@ -390,6 +390,18 @@ MS_DEV int decode_chunk(const ColView& c, uint64_t g, int lane, uint64_t v[16], 
     if (c.fmt == MS_FOR_BP) {
 #pragma unroll
       for (int k = 0; k < 16; k++) v[k] += ref;
+    } else if (c.fmt == MS_DELTA_BP && b <= 23) {
+      // 512 residuals below 2^23 sum below 2^32: prefix sums in 32 bits (b is the
+      // block's width, so the warp branches together)
+      uint32_t s = 0;
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        s += (uint32_t)v[k];
+        v[k] = s;
+      }
+      const uint64_t excl = (uint64_t)warp_excl_scan32(s, lane) + ref;
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] += excl;
     } else if (c.fmt == MS_DELTA_BP) {
       uint64_t s = 0;
 #pragma unroll
@@ -590,6 +602,18 @@ MS_DEV int decode_staged(const ColView& c, uint64_t g, const uint64_t* hdr, cons
     if (c.fmt == MS_FOR_BP) {
 #pragma unroll
       for (int k = 0; k < 16; k++) v[k] += ref;
+    } else if (c.fmt == MS_DELTA_BP && b <= 23) {
+      // 512 residuals below 2^23 sum below 2^32: prefix sums in 32 bits (b is the
+      // block's width, so the warp branches together)
+      uint32_t s = 0;
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        s += (uint32_t)v[k];
+        v[k] = s;
+      }
+      const uint64_t excl = (uint64_t)warp_excl_scan32(s, lane) + ref;
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] += excl;
     } else if (c.fmt == MS_DELTA_BP) {
       uint64_t s = 0;
 #pragma unroll

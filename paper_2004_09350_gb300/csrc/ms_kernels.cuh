@@ -203,6 +203,16 @@ MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body bo
           if (c.fmt == MS_FOR_BP) {
 #pragma unroll
             for (int q = 0; q < 16; q++) v[q] += ref;
+          } else if (c.fmt == MS_DELTA_BP && b <= 23) {  // 32-bit prefix sums (see decode_staged)
+            uint32_t sum = 0;
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+              sum += (uint32_t)v[q];
+              v[q] = sum;
+            }
+            const uint64_t excl = (uint64_t)warp_excl_scan32(sum, lane) + ref;
+#pragma unroll
+            for (int q = 0; q < 16; q++) v[q] += excl;
           } else if (c.fmt == MS_DELTA_BP) {
             uint64_t sum = 0;
 #pragma unroll

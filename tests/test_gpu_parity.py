@@ -237,6 +237,53 @@ def test_project_position_formats_and_unsorted(ctx, data_fmt, pos_fmt):
     ctx.free(dcol)
 
 
+def delta_width_column(widths, tail=100, seed=5):
+    """Blocks of in-block differences at the given widths: even blocks take every
+    difference at its maximum 2^b - 1 (512 of them sum to just below 2^32 at b = 23),
+    odd ones random differences below 2^b with one at the maximum; block starts sit
+    near 2^64 so that the running values wrap."""
+    parts, v = [], np.uint64(2**64 - 5)
+    for i, b in enumerate(widths):
+        top = np.uint64((1 << b) - 1)
+        r = np.full(512, top, dtype=np.uint64) if i % 2 == 0 else synth.splitmix64(seed + i, 512) & top
+        r[0] = 0
+        r[1] = top
+        with np.errstate(over="ignore"):
+            blk = v + np.cumsum(r, dtype=np.uint64)
+        parts.append(blk)
+        v = synth.splitmix64(seed + 100 + i, 1)[0] | np.uint64(1 << 63)
+    parts.append(synth.splitmix64(seed + 999, tail))
+    return np.concatenate(parts)
+
+
+def test_delta_prefix_sums_at_the_32_bit_boundary(ctx):
+    """DELTA blocks of width <= 23 take 32-bit prefix sums, wider ones 64-bit: both
+    sides of that switch, at their largest sums, through every DELTA decoder (chunk
+    stream, CTA tile stream, project's block decode)."""
+    widths = [22, 23, 23, 24, 24, 31, 32, 33, 1, 0, 23, 63, 64, 23]
+    x = delta_width_column(widths)
+    ref = oracle.compress(ms.DELTA_BP, x)
+    hdr = ref.view(np.uint64)[: 2 * len(widths)].reshape(-1, 2)
+    assert [int(w) & 255 for w in hdr[:, 0]] == widths
+    col, _ = gpu_col(ctx, x, ms.DELTA_BP)
+    assert_column(ctx, col, x, ms.DELTA_BP)
+    assert int(ms.to_numpy_u64(ctx.agg_sum(col))[0]) == oracle.agg_sum(x)
+    ctx.check()
+    n = x.size
+    for pos in (np.arange(n, dtype=np.uint64), np.arange(3, n, 7, dtype=np.uint64),
+                np.sort(synth.uniform(6, 900, 0, n))):
+        pcol, _ = gpu_col(ctx, pos, ms.DELTA_BP)
+        for out_fmt in (ms.UNCOMPR, ms.DELTA_BP):
+            out = ctx.project(col, pcol, fmt=out_fmt)
+            assert_column(ctx, out, oracle.project(x, pos), out_fmt)
+            ctx.free(out)
+        ctx.free(pcol)
+    out = ctx.calc(ms.ADD, col, col, fmt=ms.DELTA_BP)
+    assert_column(ctx, out, oracle.calc(ms.ADD, x, x), ms.DELTA_BP)
+    ctx.free(out)
+    ctx.free(col)
+
+
 # -------------------------------------------------------------------- calc
 
 @pytest.mark.parametrize("fa,fb", [(f, f) for f in FMTS] + [(ms.DYN_BP, ms.DELTA_BP), (ms.UNCOMPR, ms.FOR_BP),
