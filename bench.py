@@ -25,6 +25,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -232,11 +233,18 @@ def cpu_baseline(x, k, c, target_s=15.0):
 # ---------------------------------------------------------------- helpers
 
 def source_digest():
+    """Digest of the kernel sources' code: comments, blank lines and layout are left
+    out, so that a comment edit keeps a committed traffic figure valid and any code
+    edit invalidates it."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2004_09350_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = "\n".join(" ".join(line.split()) for line in text.splitlines() if line.strip())
+        h.update(f.encode() + b"\0" + code.encode() + b"\0")
     return h.hexdigest()[:16]
 
 

@@ -645,7 +645,7 @@ MS_DEV int emit_gather(const ProduceArgs& a, uint64_t n_out, uint64_t g, int lan
 // Sorted positions of a whole CTA tile (8 consecutive output chunks) into DYN /
 // FOR / DELTA / static-BP data.  The data blocks the tile's positions span have
 // contiguous payloads, so the CTA copies them into shared memory in pieces of up
-// to kCtaBuf bytes with all its threads (coalesced 16-byte copies), and each warp
+// to kCtaBuf bytes (one bulk copy per piece, issued by one thread), and each warp
 // then takes its values from there: DYN / FOR / static values are cut out of their
 // blocks, DELTA blocks are decoded whole (prefix sums) into the warp's `aux`.  A
 // random read per position would instead touch up to 32 scattered sectors per warp
