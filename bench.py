@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--workload", choices=["sweep-plan", "star", "selector", "batch", "kernel"], default="sweep-plan",
                     help="sweep-plan: the 2^28-row select/project/calc/sum plan (default); "
                          "star: the star-schema plan on a 6e8-row fact table; "
-                         "selector: train the learned format selector on engine traces and judge it; "
+                         "selector: train the learned format selector on engine traces and measure its regret; "
                          "batch: 4096 select->project->agg_sum fragments in one persistent launch; "
                          "kernel: one operator of the plan alone (--kernel), the case the ncu summaries use")
     ap.add_argument("--kernel", choices=["agg_sum", "select", "project"], default="agg_sum")

@@ -262,7 +262,7 @@ ms_status ms_compress_noalloc(const uint64_t *d_in, uint64_t n, int fmt, int sta
    log2 bytes per value and log2 nanoseconds per value of each of the five formats
    (outputs 0..4: size, 5..9: time, in ms_fmt order).  Labels come from the engine
    itself, by compressing every intermediate into every format (the exhaustive
-   try-all choice, which also judges the selector's regret).
+   try-all choice, against which the selector's regret is measured).
 
    Network: 16 -> 64 -> 64 -> 10, ReLU between layers, fp32.  Parameters are
    one packed array: W1[16][64], b1[64], W2[64][64], b2[64], W3[64][10], b3[10],

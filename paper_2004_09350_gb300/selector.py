@@ -12,8 +12,8 @@ learns such a model from traces the engine itself produces.
 * labels are, for each of the five formats, log2 bytes per value and log2
   nanoseconds per value of writing the column in that format and reading it
   once.  They are measured by compressing the intermediate into every format:
-  the exhaustive try-all-formats choice, which is also the judge of the
-  selector's regret;
+  the exhaustive try-all-formats choice, which is also the reference the
+  selector's regret is measured against;
 * the network (16 -> 64 -> 64 -> 10, ReLU, fp32) is trained with the library's
   own forward/backward and Adam kernels (``ms_mlp_*``);
 * a plan asks for formats before its intermediates exist: the plan runs once on a
