@@ -88,6 +88,8 @@ def make_inputs(rows, seed, sel):
     return x, k, c
 
 
+PLAN_WORKLOAD = ("select(X<c)->project(X,K)->calc(X'*K')->agg_sum on 2^28-row columns, "
+                 "X widths {3,8,16,27,40} per 512-block, K sorted gaps mean 4")
 COMPRESSED = {"X": "dyn_bp", "K": "delta_bp", "P": "delta_bp", "X'": "dyn_bp", "K'": "delta_bp", "Y": "dyn_bp"}
 UNCOMPRESSED = {k: "uncompr" for k in COMPRESSED}
 
@@ -453,8 +455,7 @@ def bench_ours(args):
         "dtype": "u64",
         "data": "synthetic (seeded SplitMix64)",
         "config": {
-            "workload": "select(X<c)->project(X,K)->calc(X'*K')->agg_sum on 2^28-row columns, "
-                        "X widths {3,8,16,27,40} per 512-block, K sorted gaps mean 4",
+            "workload": PLAN_WORKLOAD,
             "rows": n, "selectivity": round(comp["m"] / n, 5), "formats": COMPRESSED,
             "l2": "inputs larger than L2 (compressed X %.2f GB, K %.2f GB; uncompressed 2.1 GB each)"
                   % (comp["sizes"]["X"] / 1e9, comp["sizes"]["K"] / 1e9),
@@ -501,9 +502,12 @@ def bench_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot / args.steps * 1e3, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic (seeded SplitMix64)",
-            "config": {"workload": "same plan as the GPU arm on a prefix sample", "rows": rows},
+            "config": {"workload": PLAN_WORKLOAD, "rows": int(x.size),
+                       "selectivity": round(float(np.count_nonzero(x < np.uint64(c))) / max(x.size, 1), 5),
+                       "formats": COMPRESSED, "parallelism": "1 host core"},
             "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {rows} rows per step of the 2^28-row workload"},
+                             "sample": f"first {rows} rows of the {x.size}-row workload per step "
+                                       f"(the same plan and formats, single thread)"},
             "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
