@@ -29,10 +29,12 @@ CTAS_PER_SM = (0,)
 
 def candidates(variants=None, tiles=TILES, ctas=CTAS_PER_SM):
     """Every built (warps, depth, compact, schedule) variant with every tile size and
-    CTA cap that the variant accepts, as ms_batch_config tuples."""
+    CTA cap that the variant accepts, as ms_batch_config tuples: the work-counter
+    schedule (0) needs tiles of at least two pipeline depths, the per-CTA schedule (1)
+    at least one chunk per warp, the CTA-streamed schedule (2) takes any tile."""
     out = []
     for (w, d, c, s), t, k in itertools.product(variants or ms.BATCH_VARIANTS, tiles, ctas):
-        if (s == 0 and t >= 2 * d) or (s == 1 and t >= w):
+        if (s == 0 and t >= 2 * d) or (s == 1 and t >= w) or s == 2:
             out.append((w, d, t, k, c, s))
     return out
 
