@@ -60,6 +60,10 @@ def parse():
                          "batch: 4096 select->project->agg_sum fragments in one persistent launch; "
                          "kernel: one operator of the plan alone (--kernel), the case the ncu summaries use")
     ap.add_argument("--kernel", choices=["agg_sum", "select", "project"], default="agg_sum")
+    ap.add_argument("--width", type=int, default=0,
+                    help="kernel workload: every 512-block of X at this bit width (0: the plan's width mix)")
+    ap.add_argument("--x-format", choices=["uncompr", "static_bp", "dyn_bp", "delta_bp", "for_bp"], default="dyn_bp",
+                    help="kernel workload: the format X is stored in (static BP at X's largest width)")
     ap.add_argument("--selector-items", type=int, default=3000)
     ap.add_argument("--fragments", type=int, default=4096)
     ap.add_argument("--batch-max-log2", type=float, default=24.0)
@@ -891,11 +895,18 @@ def bench_kernel(args):
     import torch
     from paper_2004_09350_gb300 import morphstore as ms
 
+    from paper_2004_09350_gb300 import synth
+
     n = args.rows
     x, k, c = make_inputs(n, args.seed, args.selectivity)
+    if args.width:
+        x = synth.skewed_widths(args.seed, n, widths=(args.width,))
+        c = synth.value_at_rank(x, args.selectivity)
     dev = torch.device("cuda", 0)
     ctx = ms.Ctx(0, arena_bytes=int(2.5 * 8 * n) + (1 << 30), max_rows=n)
-    cx = ctx.compress(ms.as_device_u64(x, dev), ms.DYN_BP)
+    fx = fmt_id(args.x_format)
+    bw = max(1, int(x.max()).bit_length()) if fx == ms.STATIC_BP and x.size else 0
+    cx = ctx.compress(ms.as_device_u64(x, dev), fx, bw)
     ck = ctx.compress(ms.as_device_u64(k, dev), ms.DELTA_BP)
     res = torch.zeros(1, dtype=torch.int64, device=dev)
     pos = ctx.select(cx, ms.LT, c, fmt=ms.DELTA_BP) if args.kernel == "project" else None
@@ -916,7 +927,8 @@ def bench_kernel(args):
         once()
     prof = ctx.profile_collect()
     ctx.check(what="kernel workload")
-    out = {"workload": "kernel", "kernel": args.kernel, "rows": n,
+    out = {"workload": "kernel", "kernel": args.kernel, "rows": n, "x_format": args.x_format,
+           "x_width": args.width or "plan mix",
            "bytes": {"X": ctx.info(cx)["size_bytes"], "K": ctx.info(ck)["size_bytes"]},
            "ms_per_launch": {kk: round(v[1] / v[0], 4) for kk, v in prof.items()}}
     if pos is not None:
