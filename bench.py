@@ -225,6 +225,21 @@ def oracle_plan(x, k, c):
     return time.perf_counter() - t0, s
 
 
+def host_info():
+    """The host the CPU baseline ran on: CPU model (lscpu, else the platform) and core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return {"cpu": model or platform.processor() or platform.machine(), "cores": os.cpu_count()}
+
+
 def cpu_baseline(x, k, c, target_s=15.0):
     """Oracle on a bounded prefix sample sized for ~target_s seconds of CPU work."""
     probe = min(x.size, 1 << 15)
@@ -232,7 +247,7 @@ def cpu_baseline(x, k, c, target_s=15.0):
     rows = int(min(x.size, max(probe, probe * target_s / max(t, 1e-6))))
     rows -= rows % BLOCK
     t, _ = oracle_plan(x[:rows], k[:rows], c)
-    return {"value": rows / t, "unit": "rows/s", "cores": 1, "kind": "oracle",
+    return {"value": rows / t, "unit": "rows/s", "cores": 1, "host": host_info(), "kind": "oracle",
             "sample": f"first {rows} rows of X and K, same plan and formats, single thread ({t:.1f} s)"}
 
 
@@ -509,7 +524,7 @@ def bench_reference(args):
             "config": {"workload": PLAN_WORKLOAD, "rows": int(x.size),
                        "selectivity": round(float(np.count_nonzero(x < np.uint64(c))) / max(x.size, 1), 5),
                        "formats": COMPRESSED, "parallelism": "1 host core"},
-            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "host": host_info(), "kind": "oracle",
                              "sample": f"first {rows} rows of the {x.size}-row workload per step "
                                        f"(the same plan and formats, single thread)"},
             "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -592,7 +607,7 @@ def bench_star(args):
         f = {k: v[:rows].cpu().numpy().view(np.uint64) for k, v in fact.items()}
         d = {k: v.cpu().numpy().view(np.uint64) for k, v in dims.items()}
         t, _ = oracle_star_plan(f, d)
-        cpu = {"value": rows / t, "unit": "rows/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": rows / t, "unit": "rows/s", "cores": 1, "host": host_info(), "kind": "oracle",
                "sample": f"first {rows} fact rows, same plan on uncompressed arrays ({t:.1f} s)"}
     ctx.close()
     comp, unc = out["compressed"], out["uncompressed"]
@@ -878,7 +893,7 @@ def bench_batch(args):
                      "worst_ms": round(max(table.values()), 4), "candidates": len(table)},
         "selector": {"train_items": len(X), "setup_s": round(setup_sel_s, 1), "base_formats": counts},
         "parity": {"sampled_fragments": len(sample), "mismatches": mism, "all_launch_modes_agree": True},
-        "cpu_baseline": {"value": cpu_rows / cpu_t, "unit": "rows/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": cpu_rows / cpu_t, "unit": "rows/s", "cores": 1, "host": host_info(), "kind": "oracle",
                          "sample": f"{len(sample)} fragments ({cpu_rows} rows) through the oracle's "
                                    f"select, project and agg_sum ({cpu_t:.1f} s)"},
         "clocks": clk, "gpu_launches": len(one),
