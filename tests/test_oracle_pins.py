@@ -58,6 +58,20 @@ def test_layout_dyn_bp_hand_examples():
     assert oracle.compress(oracle.DYN_BP, x).tobytes() == want
 
 
+def test_layout_dyn_bp_two_blocks_hand_example():
+    """Header chain (block 1's payload starts 8 words in) and a value that straddles
+    two halfwords of its lane stream."""
+    assert "dyn_bp_two_blocks_chain_and_straddle" in {c["name"] for c in _gold("layout_examples.json")["cases"]}
+    x = np.zeros(1024, dtype=np.uint64)
+    x[0], x[528], x[549], x[1023] = 1, 5, 7, 6
+    p0, p1 = bytearray(64), bytearray(192)
+    p0[0] = 0x01
+    p1[2:4], p1[4:6], p1[68:70], p1[190:192] = b"\x05\x00", b"\x00\x80", b"\x03\x00", b"\x00\xc0"
+    want = _hex("0100000000000000 0000000000000000 0308000000000000 0000000000000000") + bytes(p0) + bytes(p1)
+    assert oracle.compress(oracle.DYN_BP, x).tobytes() == want
+    np.testing.assert_array_equal(oracle.decompress(oracle.DYN_BP, x.size, oracle.compress(oracle.DYN_BP, x)), x)
+
+
 def test_layout_for_bp_hand_example():
     x = 1000 + np.arange(512, dtype=np.uint64) % 4
     want = _hex("0200000000000000 e803000000000000") + b"\xe4" * 128
