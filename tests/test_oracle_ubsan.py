@@ -1,6 +1,7 @@
-"""The oracle built with UndefinedBehaviorSanitizer (CPU only): round trips of every
-format and width, edge lengths and every operator run without a sanitizer report
-(undefined shifts, overflow of signed values, out-of-bounds indexing of fixed arrays)."""
+"""The oracle built with UndefinedBehaviorSanitizer, and with AddressSanitizer (CPU
+only): round trips of every format and width, edge lengths and every operator run
+without a sanitizer report (undefined shifts, overflow of signed values, reads or
+writes outside a buffer)."""
 import os
 import shutil
 import subprocess
@@ -50,3 +51,25 @@ def test_oracle_under_ubsan(tmp_path):
     r = subprocess.run([sys.executable, "-c", SCRIPT], capture_output=True, text=True, env=env, timeout=600)
     assert r.returncode == 0 and "clean" in r.stdout, r.stderr[-3000:]
     assert "runtime error" not in r.stderr, r.stderr[-3000:]
+
+
+def test_oracle_under_asan(tmp_path):
+    """Out-of-bounds reads and writes of the oracle's buffers (heap and stack)."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc missing")
+    runtime = subprocess.run(["gcc", "-print-file-name=libasan.so"], capture_output=True, text=True).stdout.strip()
+    if not runtime or not os.path.exists(runtime):
+        pytest.skip("no ASan runtime")
+    lib = str(tmp_path / "liboracle_asan.so")
+    r = subprocess.run(["gcc", "-O1", "-g", "-std=c11", "-shared", "-fPIC", "-fsanitize=address",
+                        "-fno-omit-frame-pointer", "-o", lib, os.path.join(ROOT, "oracle", "oracle.c")],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("ASan build failed: " + r.stderr[-300:])
+    env = dict(os.environ, ORACLE_LIB=lib, LD_PRELOAD=os.path.realpath(runtime),
+               ASAN_OPTIONS="detect_leaks=0:halt_on_error=1")
+    r = subprocess.run([sys.executable, "-c", SCRIPT], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0 and "ERROR: AddressSanitizer" not in r.stderr and "clean" not in r.stdout:
+        pytest.skip("the interpreter does not start under the ASan runtime: " + r.stderr[-300:])
+    assert r.returncode == 0 and "clean" in r.stdout, r.stderr[-3000:]
+    assert "AddressSanitizer" not in r.stderr, r.stderr[-3000:]
