@@ -59,7 +59,8 @@ def parse():
                          "selector: train the learned format selector on engine traces and measure its regret; "
                          "batch: 4096 select->project->agg_sum fragments in one persistent launch; "
                          "kernel: one operator of the plan alone (--kernel), the case the ncu summaries use")
-    ap.add_argument("--kernel", choices=["agg_sum", "select", "project"], default="agg_sum")
+    ap.add_argument("--kernel", choices=["agg_sum", "select", "project", "compress", "decompress"],
+                    default="agg_sum")
     ap.add_argument("--width", type=int, default=0,
                     help="kernel workload: every 512-block of X at this bit width (0: the plan's width mix)")
     ap.add_argument("--x-format", choices=["uncompr", "static_bp", "dyn_bp", "delta_bp", "for_bp"], default="dyn_bp",
@@ -926,11 +927,17 @@ def bench_kernel(args):
     res = torch.zeros(1, dtype=torch.int64, device=dev)
     pos = ctx.select(cx, ms.LT, c, fmt=ms.DELTA_BP) if args.kernel == "project" else None
 
+    raw = ms.as_device_u64(x, dev) if args.kernel in ("compress", "decompress") else None
+
     def once():
         if args.kernel == "agg_sum":
             ctx.agg_sum(cx, out=res)
         elif args.kernel == "select":
             ctx.free(ctx.select(cx, ms.LT, c, fmt=ms.DELTA_BP))
+        elif args.kernel == "compress":  # X again, into a fresh arena column
+            ctx.free(ctx.compress(raw, fx, bw))
+        elif args.kernel == "decompress":  # X into a caller buffer
+            ctx.decompress(cx, out=raw)
         else:
             ctx.free(ctx.project(cx, pos, fmt=ms.DYN_BP))
             ctx.free(ctx.project(ck, pos, fmt=ms.DELTA_BP))
@@ -948,6 +955,12 @@ def bench_kernel(args):
            "ms_per_launch": {kk: round(v[1] / v[0], 4) for kk, v in prof.items()}}
     if pos is not None:
         out["positions"] = ctx.info(pos)["n"]
+    if args.kernel in ("compress", "decompress"):  # algorithmic bytes: 8n + bytes(col)
+        key = "compress" if args.kernel == "compress" else "decompress"
+        alg = 8 * n + out["bytes"]["X"]
+        ms_k = sum(v for kk, v in out["ms_per_launch"].items() if kk in (key, "place_scan", "place_copy"))
+        out["alg_bytes"] = alg
+        out["alg_GBps_with_placement"] = round(alg / (ms_k * 1e-3) / 1e9, 1) if ms_k else None
     ctx.close()
     return out
 
