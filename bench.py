@@ -563,7 +563,7 @@ def bench_star(args):
     dims = {k: ms.as_device_u64(v, dev) for k, v in synth.star_dims(args.seed + 1).items()}
     raw = {**fact, **dims}
     # arena: uncompressed base columns (7 fact columns) plus every intermediate
-    ctx = ms.Ctx(0, arena_bytes=8 * 8 * n + (4 << 30), max_rows=n)
+    ctx = ms.Ctx(0, arena_bytes=8 * 8 * n + 8 * n + (256 << 20), max_rows=n)
     out = {}
     for label, base_fm, fm in (("compressed", plans.STAR_BASE_COMPRESSED, plans.STAR_COMPRESSED),
                                ("uncompressed", plans.STAR_BASE_UNCOMPRESSED, plans.STAR_UNCOMPRESSED)):

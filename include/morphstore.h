@@ -246,8 +246,9 @@ ms_status ms_semijoin(ms_ctx *ctx, const ms_column *probe, const ms_column *buil
    about 33 KB) is a fixed device array in the library.  n above
    MS_NOALLOC_MAX_ROWS is rejected with MS_ERR_INVALID_ARG.
    The first call on a device (with that device current) looks the array's
-   device address up and caches it; make that first call before any stream
-   capture.  Every call shares the array: calls that
+   device address up, sets the kernel's attributes and caches both; this set-up
+   runs once per device even when several host threads make their first call
+   together.  Make that first call before any stream capture.  Every call shares the array: calls that
    overlap on the GPU (different streams or host threads) race and must be
    serialised by the caller.  No context is needed.  Asynchronous on `stream`. */
 ms_status ms_compress_noalloc(const uint64_t *d_in, uint64_t n, int fmt, int static_bw,

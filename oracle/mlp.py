@@ -5,7 +5,8 @@ L = inv_count * sum mask * (y_hat - y)^2.  Parameters are packed as W1[16][64],
 b1[64], W2[64][64], b2[64], W3[64][10], b3[10] (row-major, input index first),
 the layout of include/morphstore.h.  Backpropagation is written out layer by
 layer (chain rule), and tests/test_oracle_mlp.py pins it against central finite
-differences of the loss.
+differences of the loss.  The optimiser step is Adam (Kingma & Ba, ICLR 2015,
+Algorithm 1), pinned by a two-step example worked out by hand.
 """
 from __future__ import annotations
 
@@ -66,6 +67,21 @@ def loss_grad(theta, x, y, mask, inv_count):
     g["W1"] = x.T @ da1
     g["b1"] = da1.sum(axis=0)
     return L, pack(g)
+
+
+def adam_step(theta, grad, m, v, step, lr, beta1, beta2, eps):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) in fp64; returns new
+    (theta, m, v).  In the paper's order: the biased first and second moment
+    estimates are decayed and updated with the gradient, both are divided by their
+    bias corrections 1 - beta^t, and the parameters move by lr times the corrected
+    first moment over (the root of the corrected second moment plus eps)."""
+    g = np.asarray(grad, np.float64)
+    m_t = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v_t = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    m_hat = m_t / (1.0 - beta1 ** step)
+    v_hat = v_t / (1.0 - beta2 ** step)
+    theta_t = np.asarray(theta, np.float64) - lr * m_hat / (np.sqrt(v_hat) + eps)
+    return theta_t, m_t, v_t
 
 
 def init(seed: int) -> np.ndarray:

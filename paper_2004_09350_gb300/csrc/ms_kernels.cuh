@@ -399,6 +399,7 @@ struct ProjectCta {
   uint64_t off_lo;
   uint64_t mbar;   // completion barrier of the piece's bulk copy
   uint32_t phase;  // its current phase parity
+  uint32_t dead;   // a wait on the barrier gave up: no further copies into buf
 };
 struct SmemEmit {
   uint32_t bits[kEmitSpan * 16];
@@ -746,6 +747,12 @@ MS_DEV void gather_cta(const ProduceArgs& a, const ColView& d, const uint64_t p[
       }
     }
     if (tid == 0) cs->off_lo = off;
+#if MS_PROJECT_BULK
+    // Every thread's earlier generic-proxy accesses to buf (reads of the previous
+    // piece, a fallback tile's staging stores) are ordered before the async-proxy
+    // write of the bulk copy below: a proxy fence by each thread, then the barrier.
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+#endif
     __syncthreads();
     const uint64_t off_lo = cs->off_lo;
     const uint64_t end = off + 8ull * b;
@@ -772,15 +779,23 @@ MS_DEV void gather_cta(const ProduceArgs& a, const ColView& d, const uint64_t p[
       if (tid == 0) set_error(a.ctl, MS_ERR_FORMAT, lo_blk);
       bytes = 0;
     }
+    // After a wait that gave up, the CTA issues no further copy and decodes nothing
+    // from buf (a copy may still be landing there); the barrier phase stays as it was.
+    if (cs->dead) bytes = 0;
     const uint32_t par = cs->phase;
     if (bytes) {
       if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         mbar_expect_tx(&cs->mbar, bytes);
         bulk_copy_g2s(cs->buf, d.p + at, bytes, &cs->mbar);
       }
-      if (!mbar_wait(&cs->mbar, par) && tid == 0) set_error(a.ctl, MS_ERR_TIMEOUT, lo_blk);
+      if (!mbar_wait(&cs->mbar, par)) {
+        cs->dead = 1;
+        if (tid == 0) set_error(a.ctl, MS_ERR_TIMEOUT, lo_blk);
+      }
     }
     __syncthreads();
+    if (cs->dead) bytes = 0;
     if (tid == 0 && bytes) cs->phase = par ^ 1;
 #else
     const uint4* src = reinterpret_cast<const uint4*>(d.p + at);
@@ -1278,6 +1293,7 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
     if (threadIdx.x == 0) {
       mbar_init(&pcta->mbar, 1);
       pcta->phase = 0;
+      pcta->dead = 0;
     }
     __syncthreads();
   }

@@ -16,6 +16,7 @@
 // calls that overlap on the GPU (two streams, or two host threads) race on it.
 // Every GPU that loads this library holds the array until the process exits.
 #include <algorithm>
+#include <mutex>
 
 #include "ms_device.cuh"
 #include "ms_kernels.cuh"
@@ -33,8 +34,34 @@ constexpr size_t kScratchBytes = kCtlBytes + kMetaBytes + kStatusBytes;
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-uint8_t* g_scratch_addr[kMaxDevices];  // device address of the array, per device
-int g_sms[kMaxDevices];
+// Per-device set-up, done once under a once_flag (two host threads making their
+// first call on one device at the same time do not race): the array's device
+// address, the SM count, the kernel's shared-memory attribute and its occupancy.
+struct DeviceSetup {
+  std::once_flag once;
+  uint8_t* scratch = nullptr;
+  int grid_cap = 0;
+};
+DeviceSetup g_setup[kMaxDevices];
+constexpr size_t kProduceSmem = sizeof(typename ProducePlan<OP_COMPRESS>::Smem) * kWarps;
+
+void setup_device(int dev, DeviceSetup* d) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  int sms = 0, occ = 0;
+  if (e == cudaSuccess && !p) e = cudaErrorInvalidSymbol;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_produce<OP_COMPRESS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kProduceSmem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_produce<OP_COMPRESS>, kThreads, kProduceSmem);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // scratch stays null: every call on this device returns MS_ERR_CUDA
+    return;
+  }
+  d->grid_cap = std::max(occ, 1) * std::max(sms, 1);
+  d->scratch = static_cast<uint8_t*>(p);
+}
 
 // Resets the parts of the scratch that must start at zero and points the control
 // block at the caller's output buffer.
@@ -83,19 +110,10 @@ extern "C" ms_status ms_compress_noalloc(const uint64_t* d_in, uint64_t n, int f
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MS_ERR_CUDA;
   // one-time set-up per device, with that device current
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return MS_ERR_CUDA;
-    }
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-      return MS_ERR_CUDA;
-    g_sms[dev] = sms;
-    g_scratch_addr[dev] = static_cast<uint8_t*>(p);
-  }
-  uint8_t* scratch = g_scratch_addr[dev];
+  DeviceSetup* d = &g_setup[dev];
+  std::call_once(d->once, setup_device, dev, d);
+  if (!d->scratch) return MS_ERR_CUDA;
+  uint8_t* scratch = d->scratch;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const uint64_t tiles = std::max<uint64_t>(1, (n + kTile - 1) / kTile);
   k_noalloc_prepare<<<(unsigned)std::min<uint64_t>((tiles + 256) / 256, 64), 256, 0, s>>>(
@@ -110,16 +128,8 @@ extern "C" ms_status ms_compress_noalloc(const uint64_t* d_in, uint64_t n, int f
   a.fmt = fmt;
   a.bw = fmt == MS_STATIC_BP ? bw : 0;
   a.status = reinterpret_cast<uint64_t*>(scratch + kCtlBytes + kMetaBytes);
-  const size_t smem = sizeof(typename ProducePlan<OP_COMPRESS>::Smem) * kWarps;
-  if (cudaFuncSetAttribute(k_produce<OP_COMPRESS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return MS_ERR_CUDA;
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_produce<OP_COMPRESS>, kThreads, smem) != cudaSuccess ||
-      occ < 1)
-    occ = 1;
-  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)occ * g_sms[dev], tiles));
-  k_produce<OP_COMPRESS><<<grid, kThreads, smem, s>>>(a);
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)d->grid_cap, tiles));
+  k_produce<OP_COMPRESS><<<grid, kThreads, kProduceSmem, s>>>(a);
   if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
   k_noalloc_finish<<<1, 1, 0, s>>>(scratch, d_result);
   return cudaGetLastError() == cudaSuccess ? MS_OK : MS_ERR_CUDA;

@@ -50,6 +50,30 @@ def test_mlp_gradient_matches_reference(n):
     assert torch.equal(grad, grad2)
 
 
+@pytest.mark.parametrize("steps", [1, 5])
+def test_mlp_adam_matches_reference(steps):
+    # The library's Adam kernel (fp32) against the fp64 Adam of oracle/mlp.py, element by
+    # element after every step: parameters, first and second moments.  Each reference
+    # step starts from the GPU's current state, so fp32 rounding does not compound.
+    rng = np.random.default_rng(8)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV)
+    dth, dm, dv = t(mlp.init(9)), t(np.zeros(mlp.PARAMS)), t(np.zeros(mlp.PARAMS))
+    # the kernel takes its hyperparameters as fp32: the reference uses those exact values
+    lr, b1, b2, eps = (float(np.float32(a)) for a in (3e-3, 0.9, 0.999, 1e-8))
+    for step in range(1, steps + 1):
+        g = rng.normal(scale=10.0 ** float(rng.integers(-4, 2)), size=mlp.PARAMS).astype(np.float32)
+        before = [a.cpu().numpy().astype(np.float64) for a in (dth, dm, dv)]
+        want = mlp.adam_step(before[0], g, before[1], before[2], step, lr, b1, b2, eps)
+        ms.mlp_adam(dth, t(g), dm, dv, step, lr=lr, beta1=b1, beta2=b2, eps=eps)
+        torch.cuda.synchronize()
+        got = [a.cpu().numpy() for a in (dth, dm, dv)]
+        np.testing.assert_allclose(got[1], want[1], rtol=1e-6, atol=1e-30)
+        np.testing.assert_allclose(got[2], want[2], rtol=1e-6, atol=1e-30)
+        # theta moves by about lr per step: its error is bounded by fp32 rounding of theta
+        # plus a relative 1e-6 of the step
+        np.testing.assert_allclose(got[0], want[0], rtol=1e-6, atol=1e-6 * lr)
+
+
 def test_mlp_training_reduces_loss():
     x, _, _ = _data(2000, 5)
     # a learnable target: fixed random linear map of the features

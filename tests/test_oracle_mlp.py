@@ -60,3 +60,34 @@ def test_masked_targets_do_not_contribute():
     L2, g2 = mlp.loss_grad(theta, x, y2, m, 0.1)
     assert L1 == L2
     np.testing.assert_array_equal(g1, g2)
+
+
+def test_adam_two_steps_worked_by_hand():
+    # Kingma & Ba (2015), Algorithm 1, with beta1 = 9/10, beta2 = 999/1000, lr = 1/10,
+    # one parameter starting at 1 with gradients 1/2 and then -1/4.
+    #   t = 1: m = (1/10)(1/2) = 1/20, v = (1/1000)(1/4) = 1/4000,
+    #          m_hat = (1/20)/(1/10) = 1/2, v_hat = (1/4000)/(1/1000) = 1/4,
+    #          theta = 1 - (1/10)(1/2)/(1/2 + eps)            (a step of lr * sign(g))
+    #   t = 2: m = (9/10)(1/20) - (1/10)(1/4) = 1/50,
+    #          v = (999/1000)(1/4000) + (1/1000)(1/16) = 1249/4000000,
+    #          m_hat = (1/50)/(1 - 81/100) = 2/19,
+    #          v_hat = (1249/4000000)/(1 - 998001/1000000) = 1249/7996,
+    #          theta -= (1/10)(2/19)/(sqrt(1249/7996) + eps)
+    # Swapping beta1 and beta2, or dropping a bias correction, changes step 2.
+    # (fp64 evaluation: 1 - 0.9 is not exactly 1/10, so compare to ~1e-15.)
+    eps = 1e-8
+    th, m, v = mlp.adam_step(np.array([1.0]), np.array([0.5]), np.zeros(1), np.zeros(1), 1, 0.1, 0.9, 0.999, eps)
+    assert abs(m[0] - 1 / 20) < 1e-15 and abs(v[0] - 1 / 4000) < 1e-17
+    th1 = 1.0 - 0.1 * 0.5 / (0.5 + eps)
+    assert abs(th[0] - th1) < 1e-15
+    th, m, v = mlp.adam_step(th, np.array([-0.25]), m, v, 2, 0.1, 0.9, 0.999, eps)
+    assert abs(m[0] - 1 / 50) < 1e-15 and abs(v[0] - 1249 / 4000000) < 1e-17
+    th2 = th1 - 0.1 * (2 / 19) / (np.sqrt(1249 / 7996) + eps)
+    assert abs(th[0] - th2) < 1e-14, (th[0], th2)
+
+
+def test_adam_first_step_is_lr_times_sign_for_every_parameter():
+    # With zero moments, bias correction makes the first step lr * g / (|g| + eps).
+    g = np.array([3.0, -2e-3, 0.0, 7.5e4])
+    th, _, _ = mlp.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 1, 0.01, 0.8, 0.99, 1e-8)
+    np.testing.assert_allclose(th, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
