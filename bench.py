@@ -1,23 +1,29 @@
 #!/usr/bin/env python
 """Throughput of the on-the-fly morphing pipeline on one GB300 (or N replicas).
 
-Workload: two 2^28-row uint64 columns.  X has a bit width drawn per 512-value block
-from {3, 8, 16, 27, 40}.  K is sorted with geometric gaps of mean 4.  One step is
-the plan select(X < c) -> P; project(X, P) -> X'; project(K, P) -> K';
-calc(X' * K') -> Y; agg_sum(Y).  c is picked for about 10% selectivity.
-Compressed pipeline: X dynamic BP, K DELTA+BP, P DELTA+BP, X' dynamic BP,
-K' DELTA+BP, Y dynamic BP.  The same plan with every column uncompressed is
-timed beside it.
+Default workload (star): a star-schema plan over a 6e8-row fact table of uint64
+columns (foreign keys uniform over dimensions of 2.5e6, 2e5, 3e4 and 2556 rows,
+a date-sorted key, quantity, discount, revenue) and three dimension attributes.
+One step selects on two dimension attributes, semi-joins both into the fact
+table, selects discount and quantity ranges, projects, computes group ids and
+group-sums revenue into 105 groups.  Compressed pipeline: base columns dynamic
+BP (the sorted date key DELTA+BP), positions DELTA+BP, values dynamic BP.  The
+same plan with every column uncompressed is timed beside it.
 
-value = logical input rows per second of the compressed pipeline (whole job).
+value = fact rows per second of the compressed pipeline (whole job).
 roofline = the dominant kernel's algorithmic bytes per launch / its mean launch
 time, against the measured HBM copy peak.  e2e = the same plan through the C
-ABI with the compressed base columns copied from pinned host memory every step
-and the sum read back (uncompressed.e2e: the uncompressed plan the same way, its
-base columns uncompressed).  cpu_baseline = the CPU oracle on a bounded sample of the
-same workload.
+ABI with the base columns imported from pinned host memory every step in their
+format and the group sums read back (uncompressed.e2e: the uncompressed plan the
+same way).  cpu_baseline = the CPU oracle on a bounded prefix sample of the same
+workload.  Footprint: the sum of column sizes (base plus intermediates), and the
+device peak (base columns, the arena's high-water mark of intermediates and the
+context's work area).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Other workloads (--workload): sweep-plan (select(X<c) -> project X, K -> calc ->
+agg_sum on 2^28-row columns), selector, batch, kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 """
 from __future__ import annotations
 
@@ -48,14 +54,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--rows", type=int, default=1 << 28)
+    ap.add_argument("--rows", type=int, default=0,
+                    help="fact rows (star, default 6e8) or column rows (other workloads, default 2^28)")
     ap.add_argument("--selectivity", type=float, default=0.1)
     ap.add_argument("--seed", type=int, default=2020)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["sweep-plan", "star", "selector", "batch", "kernel"], default="sweep-plan",
-                    help="sweep-plan: the 2^28-row select/project/calc/sum plan (default); "
-                         "star: the star-schema plan on a 6e8-row fact table; "
+    ap.add_argument("--workload", choices=["star", "sweep-plan", "selector", "batch", "kernel"], default="star",
+                    help="star: the star-schema plan on a 6e8-row fact table (default); "
+                         "sweep-plan: the 2^28-row select/project/calc/sum plan; "
                          "selector: train the learned format selector on engine traces and measure its regret; "
                          "batch: 4096 select->project->agg_sum fragments in one persistent launch; "
                          "kernel: one operator of the plan alone (--kernel), the case the ncu summaries use")
@@ -71,6 +78,8 @@ def parse():
     ap.add_argument("--batch-train-items", type=int, default=400)
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
+    if not a.rows and a.workload != "star":
+        a.rows = 1 << 28
     return a
 
 
@@ -506,6 +515,8 @@ def bench_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return None
+    if args.workload == "star":
+        return bench_reference_star(args, world)
     x, k, c = make_inputs(args.rows, args.seed, args.selectivity)
     # each step runs the oracle on a bounded prefix so the whole run stays within minutes
     per_step_s = max(2.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
@@ -533,37 +544,186 @@ def bench_reference(args):
 
 # ------------------------------------------------------------- star plan
 
-def oracle_star_plan(fact, dims):
+STAR_WORKLOAD = ("star-schema plan on a 6e8-row fact table: select D1.c5 = 0 and D2.c25 < 15, semi-join fk1 "
+                 "and fk2, select 1 <= discount <= 3 and quantity < 25, project, calc, group_sum on 105 groups")
+
+
+def oracle_star_plan(fact, dims, codec=True):
+    """The star plan on the CPU oracle.  With codec=True every column passes through
+    the oracle's codec in the compressed pipeline's formats: the base columns are
+    decoded from their compressed bytes and every intermediate is encoded and
+    decoded again, as an engine with compressed intermediates does."""
     import oracle
     from paper_2004_09350_gb300 import plans, synth
+    fm = {k: int(v) for k, v in plans.STAR_COMPRESSED.items()}
+    fb = {k: int(v) for k, v in plans.STAR_BASE_COMPRESSED.items()}
+    packed = {k: oracle.compress(fb[k], v) for k, v in {**fact, **dims}.items()} if codec else None
     t0 = time.perf_counter()
-    s1 = oracle.select(dims["d1_c5"], oracle.EQ, 0)
-    s2 = oracle.select(dims["d2_c25"], oracle.LT, 15)
-    p1 = oracle.semijoin(fact["fk1"], s1, synth.DIM_SIZES[0])
-    q2 = oracle.semijoin(oracle.project(fact["fk2"], p1), s2, synth.DIM_SIZES[1])
-    p2 = oracle.project(p1, q2)
-    p3 = oracle.project(p2, oracle.select(oracle.project(fact["discount"], p2), oracle.BETWEEN, 1, 3))
-    p4 = oracle.project(p3, oracle.select(oracle.project(fact["quantity"], p3), oracle.LT, 25))
-    year = oracle.project(dims["date_year"], oracle.project(fact["fk_date"], p4))
-    c25 = oracle.project(dims["d2_c25"], oracle.project(fact["fk2"], p4))
-    gid = oracle.calc(oracle.ADD, oracle.calc(oracle.MUL, year, c=15), c25)
-    sums = oracle.group_sum(gid, oracle.project(fact["revenue"], p4), plans.STAR_GROUPS)
+    if codec:
+        src = {**fact, **dims}
+        b = {k: oracle.decompress(fb[k], src[k].size, packed[k]) for k in src}
+    else:
+        b = {**fact, **dims}
+
+    def inter(name, x):
+        return oracle.decompress(fm[name], x.size, oracle.compress(fm[name], x)) if codec else x
+
+    s1 = inter("S1", oracle.select(b["d1_c5"], oracle.EQ, 0))
+    s2 = inter("S2", oracle.select(b["d2_c25"], oracle.LT, 15))
+    p1 = inter("P1", oracle.semijoin(b["fk1"], s1, synth.DIM_SIZES[0]))
+    f2 = inter("F2", oracle.project(b["fk2"], p1))
+    q2 = inter("Q2", oracle.semijoin(f2, s2, synth.DIM_SIZES[1]))
+    p2 = inter("P2", oracle.project(p1, q2))
+    disc = inter("DISC", oracle.project(b["discount"], p2))
+    q3 = inter("Q3", oracle.select(disc, oracle.BETWEEN, 1, 3))
+    p3 = inter("P3", oracle.project(p2, q3))
+    qty = inter("QTY", oracle.project(b["quantity"], p3))
+    q4 = inter("Q4", oracle.select(qty, oracle.LT, 25))
+    p4 = inter("P4", oracle.project(p3, q4))
+    date = inter("DATE", oracle.project(b["fk_date"], p4))
+    year = inter("YEAR", oracle.project(b["date_year"], date))
+    f2b = inter("F2B", oracle.project(b["fk2"], p4))
+    c25 = inter("C25", oracle.project(b["d2_c25"], f2b))
+    g0 = inter("G0", oracle.calc(oracle.MUL, year, c=15))
+    gid = inter("GID", oracle.calc(oracle.ADD, g0, c25))
+    rev = inter("REV", oracle.project(b["revenue"], p4))
+    sums = oracle.group_sum(gid, rev, plans.STAR_GROUPS)
     return time.perf_counter() - t0, sums
 
 
+def star_host_sample(seed, rows):
+    """The first `rows` fact rows and the dimensions, generated on the host (the
+    same bits as the device generators)."""
+    from paper_2004_09350_gb300 import synth
+    return synth.star_fact(seed, rows), synth.star_dims(seed + 1)
+
+
+def star_cpu_sample_rows(seed, target_s):
+    """Fact rows of a prefix sample whose oracle star plan takes about target_s."""
+    probe = 1 << 18
+    f, d = star_host_sample(seed, probe)
+    t, _ = oracle_star_plan(f, d)
+    rows = int(probe * target_s / max(t, 1e-6))
+    return max(probe, rows - rows % BLOCK)
+
+
+def star_cpu_baseline(seed, n, target_s=15.0):
+    rows = min(n, star_cpu_sample_rows(seed, target_s))
+    f, d = star_host_sample(seed, rows)
+    t, _ = oracle_star_plan(f, d)
+    return {"value": rows / t, "unit": "rows/s", "cores": 1, "host": host_info(), "kind": "oracle",
+            "build": "gcc -O2, single thread, not pinned to a core",
+            "sample": f"first {rows} of the {n} fact rows, the same plan with every column passed through the "
+                      f"oracle's codec in the compressed pipeline's formats ({t:.1f} s)"}
+
+
+def _device_col_bytes(ctx, col):
+    return ctx.export_bytes(col, device=True)
+
+
+def project_touched_bytes(ctx, data, pos_t):
+    """Bytes of the data column's units that sorted positions pos_t (int64 device
+    tensor) touch: each touched 512-value block whole (header and payload) for the
+    block formats and static BP, each touched 32-byte sector of an uncompressed
+    column or of a block format's raw remainder."""
+    import torch
+    from paper_2004_09350_gb300 import morphstore as ms
+    if pos_t.numel() == 0:
+        return 0
+    meta = ctx.info(data)
+    n = meta["n"]
+    if data.fmt == ms.UNCOMPR:
+        return 32 * int(torch.unique_consecutive(pos_t >> 2).numel())
+    if data.fmt == ms.STATIC_BP:
+        full = n // BLOCK
+        g = torch.unique_consecutive(pos_t >> 9)
+        blk = int((g < full).sum())
+        tail = pos_t[pos_t >= full * BLOCK]
+        tail_sect = int(torch.unique_consecutive((tail - full * BLOCK) * meta["static_bw"] // 256).numel())
+        return 64 * meta["static_bw"] * blk + 32 * tail_sect
+    nb = meta["n_blocks"]
+    raw = _device_col_bytes(ctx, data)
+    hdr = raw[: 16 * nb].view(torch.int64).view(-1, 2)[:, 0] if nb else torch.zeros(0, dtype=torch.int64,
+                                                                                      device=pos_t.device)
+    g = torch.unique_consecutive(pos_t >> 9)
+    gm = g[g < nb]
+    b = (hdr[gm] & 255) if nb else gm
+    rem = pos_t[pos_t >= nb * BLOCK]
+    rem_sect = int(torch.unique_consecutive((rem - nb * BLOCK) >> 2).numel()) if rem.numel() else 0
+    return int(16 * gm.numel() + 64 * int(b.sum())) + 32 * rem_sect
+
+
+def star_kernel_bytes(ctx, trace):
+    """Algorithmic bytes of one step of the star plan, per kernel (the operator
+    definitions of the measurement plan; bytes(c) = physical column size):
+      select    mark: bytes(in) + n/8 (match bitmap) + 4 per 512-row chunk (counts)
+                emit: n/8 + 8 per chunk (offsets) + bytes(out)
+      semijoin  build_keys: bytes(keys) + D/8;  mark: bytes(probe) + D/8 (key bitmap
+                read) + n/8 + 4 per chunk;  emit as for select
+      project   bytes(pos) + the data units the positions touch + bytes(out)
+      calc      bytes(a) + bytes(b) + bytes(out);  group_sum  bytes(gid) + bytes(val) + 8G
+    Scan and placement kernels move only bookkeeping and have no algorithmic bytes."""
+    size = {}
+
+    def sz(c):
+        k = id(c)
+        if k not in size:
+            size[k] = ctx.info(c)
+        return size[k]
+
+    kb = {}
+
+    def add(k, v):
+        kb[k] = kb.get(k, 0) + int(v)
+
+    for op, name, ins, out, extra in trace:
+        if op in ("select", "semijoin"):
+            n = sz(ins[0])["n"]
+            nch = -(-n // BLOCK)
+            bitmap = n // 8
+            add("mark", sz(ins[0])["size_bytes"] + bitmap + 4 * nch)
+            add("emit", bitmap + 8 * nch + sz(out)["size_bytes"])
+            if op == "semijoin":
+                add("build_keys", sz(ins[1])["size_bytes"] + -(-extra // 8))
+                add("mark", -(-extra // 8))
+        elif op == "project":
+            pos_t = ctx.decompress(ins[1])
+            add("project", sz(ins[1])["size_bytes"] + project_touched_bytes(ctx, ins[0], pos_t)
+                + sz(out)["size_bytes"])
+            del pos_t
+        elif op == "calc":
+            add("calc", sum(sz(c)["size_bytes"] for c in ins) + sz(out)["size_bytes"])
+        elif op == "group_sum":
+            add("group_sum", sum(sz(c)["size_bytes"] for c in ins) + 8 * extra)
+    return kb
+
+
 def bench_star(args):
+    """The star-schema plan at 6e8 fact rows (the default workload)."""
     import torch
     from paper_2004_09350_gb300 import morphstore as ms
     from paper_2004_09350_gb300 import plans, synth
 
-    n = args.rows if args.rows != (1 << 28) else 600_000_000
-    dev = torch.device("cuda", 0)
+    world, rank, local = dist_setup(args)
+    n = args.rows or 600_000_000
+    dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
     fact = synth.star_fact_torch(args.seed, n, dev)
     dims = {k: ms.as_device_u64(v, dev) for k, v in synth.star_dims(args.seed + 1).items()}
     raw = {**fact, **dims}
-    # arena: uncompressed base columns (7 fact columns) plus every intermediate
-    ctx = ms.Ctx(0, arena_bytes=8 * 8 * n + 8 * n + (256 << 20), max_rows=n)
+    # arena: the base columns (uncompressed: 7 fact columns of 8 bytes) plus every
+    # intermediate of one step (at most 8 bytes a fact row in the uncompressed plan)
+    ctx = ms.Ctx(local, arena_bytes=8 * 8 * n + 8 * n + (256 << 20), max_rows=n)
     out = {}
     for label, base_fm, fm in (("compressed", plans.STAR_BASE_COMPRESSED, plans.STAR_COMPRESSED),
                                ("uncompressed", plans.STAR_BASE_UNCOMPRESSED, plans.STAR_UNCOMPRESSED)):
@@ -576,53 +736,173 @@ def bench_star(args):
             plans.free_lifo(ctx, cols)
         use0, _ = ctx.arena_usage()
         ctx.reset_high_water()
-        _, cols = plans.star_plan(ctx, base, fm, out=res)
+        trace = []
+        _, cols = plans.star_plan(ctx, base, fm, out=res, trace=trace)
         inter_bytes = plans.footprint(ctx, cols)
         _, high = ctx.arena_usage()
+        kb = star_kernel_bytes(ctx, trace) if label == "compressed" else None
         plans.free_lifo(ctx, cols)
-        torch.cuda.synchronize()
+        del trace
+        ctx.check(what=f"star {label} sizing step")
+        barrier()
+        clocks = Clocks(local) if label == "compressed" else None
+        if clocks:  # let the sampler see load before the timed region
+            w0 = time.perf_counter()
+            while time.perf_counter() - w0 < 0.3:
+                _, cols = plans.star_plan(ctx, base, fm, out=res)
+                plans.free_lifo(ctx, cols)
+                torch.cuda.synchronize()
+        barrier()
         ctx.profile(True)
-        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0.record()
-        for _ in range(args.steps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs[0].record()
+        for i in range(args.steps):
             _, cols = plans.star_plan(ctx, base, fm, out=res)
             plans.free_lifo(ctx, cols)
-        t1.record()
-        torch.cuda.synchronize()
+            evs[i + 1].record()
+        barrier()
         prof = ctx.profile_collect()
         ctx.profile(False)
-        ctx.check(what="star plan")
-        ms_step = t0.elapsed_time(t1) / args.steps
-        out[label] = {"ms_per_step": round(ms_step, 3), "rows_per_s": n / (ms_step * 1e-3),
-                      "base_bytes": base_bytes, "intermediate_bytes": inter_bytes,
+        if clocks:
+            w0 = time.perf_counter()
+            while time.perf_counter() - w0 < 0.3:
+                _, cols = plans.star_plan(ctx, base, fm, out=res)
+                plans.free_lifo(ctx, cols)
+                torch.cuda.synchronize()
+        ck_info = clocks.stop() if clocks else None
+        ctx.check(what=f"star {label} timed steps")
+        ms_step = max_over_ranks(evs[0].elapsed_time(evs[-1]) / args.steps, world, dev)
+        best = min(evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps))
+        out[label] = {"ms_per_step": round(ms_step, 4), "ms_per_step_best": round(best, 4),
+                      "rows_per_s": job_rows_per_s(world, n, ms_step),
+                      "base_bytes": int(base_bytes), "intermediate_bytes": int(inter_bytes),
+                      "footprint_bytes": int(base_bytes + inter_bytes),
                       "arena_peak_intermediates": int(high - use0),
-                      "footprint_bytes": base_bytes + inter_bytes,
-                      "sums": ms.to_numpy_u64(res).tolist(),
-                      "per_kernel_ms": {k: round(v[1] / args.steps, 3) for k, v in prof.items()}}
-        for c in reversed(list(base.values())):
-            ctx.free(c)
+                      "device_peak_bytes": int(base_bytes + (high - use0) + ctx.work_bytes()),
+                      "sums": ms.to_numpy_u64(res).tolist(), "prof": prof, "kernel_bytes": kb,
+                      "clocks": ck_info,
+                      "per_kernel_ms": {k: round(v[1] / args.steps, 4) for k, v in prof.items()}}
+        out[label]["_base"] = base
     assert out["compressed"]["sums"] == out["uncompressed"]["sums"], "star pipelines disagree"
-    cpu = None
-    if not args.no_cpu_baseline:
-        rows = min(n, 1 << 23)
-        f = {k: v[:rows].cpu().numpy().view(np.uint64) for k, v in fact.items()}
-        d = {k: v.cpu().numpy().view(np.uint64) for k, v in dims.items()}
-        t, _ = oracle_star_plan(f, d)
-        cpu = {"value": rows / t, "unit": "rows/s", "cores": 1, "host": host_info(), "kind": "oracle",
-               "sample": f"first {rows} fact rows, same plan on uncompressed arrays ({t:.1f} s)"}
-    ctx.close()
     comp, unc = out["compressed"], out["uncompressed"]
+
+    # ---- roofline of the dominant kernel of the compressed plan
+    per_kernel = {}
+    for kname, (launches, total) in comp["prof"].items():
+        alg = comp["kernel_bytes"].get(kname)
+        per_step_ms = total / args.steps
+        per_kernel[kname] = {"launches_per_step": launches // args.steps, "ms_per_step": round(per_step_ms, 4),
+                             "alg_bytes_per_step": alg,
+                             "alg_GBps": None if not alg else round(alg / (per_step_ms * 1e-3) / 1e9, 1)}
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_per_step"])
+    peak, peak_kind = peaks()
+    ach = per_kernel[dom]["alg_GBps"]
+    lps = max(per_kernel[dom]["launches_per_step"], 1)
+    plan_bytes = sum(v for v in comp["kernel_bytes"].values())
+
+    # ---- end to end through the C ABI: every step imports the base columns from
+    # pinned host memory in their format, runs the plan and reads the sums back
+    def e2e_run(label, base_fm, fm):
+        base = out[label]["_base"]
+        host = {k: torch.from_numpy(ctx.export_bytes(c)).pin_memory() for k, c in base.items()}
+        rows = {k: ctx.info(c)["n"] for k, c in base.items()}
+        hres = torch.zeros(plans.STAR_GROUPS, dtype=torch.int64).pin_memory()
+        res = torch.zeros(plans.STAR_GROUPS, dtype=torch.int64, device=dev)
+
+        def step():
+            imp = {k: ctx.import_bytes(base_fm[k], rows[k], host[k]) for k in base}
+            _, cols = plans.star_plan(ctx, imp, fm, out=res)
+            plans.free_lifo(ctx, cols)
+            hres.copy_(res, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            for c in reversed(list(imp.values())):
+                ctx.free(c)
+
+        for _ in range(args.warmup):
+            step()
+        barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        barrier()
+        ms_e = max_over_ranks((time.perf_counter() - t) * 1e3 / args.steps, world, dev)
+        assert hres.numpy().view(np.uint64).tolist() == comp["sums"], "end-to-end sums differ"
+        h2d = int(sum(h.numel() for h in host.values()))
+        del host
+        return {"value": job_rows_per_s(world, n, ms_e), "unit": "rows/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 8 * plans.STAR_GROUPS, "ms_per_step": round(ms_e, 3)}
+
+    e2e = e2e_unc = None
+    if not args.no_e2e:
+        e2e = e2e_run("compressed", plans.STAR_BASE_COMPRESSED, plans.STAR_COMPRESSED)
+        e2e_unc = e2e_run("uncompressed", plans.STAR_BASE_UNCOMPRESSED, plans.STAR_UNCOMPRESSED)
+    for label in ("uncompressed", "compressed"):
+        for c in reversed(list(out[label].pop("_base").values())):
+            ctx.free(c)
+    ctx.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = star_cpu_baseline(args.seed, n)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return None
+    clocks = comp.get("clocks")
+    launches = int(sum(p["launches_per_step"] for p in per_kernel.values()) * args.steps)
     for v in (comp, unc):
-        v.pop("sums")
-    return {"metric": METRIC, "workload": "star", "value": comp["rows_per_s"], "unit": "rows/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": comp["ms_per_step"],
-            "higher_is_better": True, "dtype": "u64", "data": "synthetic (seeded SplitMix64, generated on the GPU)",
-            "config": {"workload": "star-schema plan: 2 dimension selects, 2 semi-joins, 2 range selects, "
-                                   "projects, calc, 105-group sum", "fact_rows": n},
-            "compressed": comp, "uncompressed": unc,
-            "speedup_vs_uncompressed": round(unc["ms_per_step"] / comp["ms_per_step"], 3),
-            "footprint_ratio": round(comp["footprint_bytes"] / unc["footprint_bytes"], 4),
-            "cpu_baseline": cpu}
+        for k in ("sums", "prof", "kernel_bytes", "clocks"):
+            v.pop(k, None)
+    return {
+        "metric": METRIC, "value": comp["rows_per_s"], "unit": "rows/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": comp["ms_per_step"],
+        "ms_per_step_best": comp["ms_per_step_best"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded SplitMix64, generated on the GPU)",
+        "config": {"workload": STAR_WORKLOAD, "fact_rows": n, "dimension_rows": list(synth.DIM_SIZES),
+                   "formats": "base: fk_date DELTA+BP, other columns dynamic BP; positions DELTA+BP, values "
+                              "dynamic BP",
+                   "l2": "inputs larger than L2 (compressed fact columns %.2f GB)" % (comp["base_bytes"] / 1e9),
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": None if ach is None else round(ach / peak, 4), "peak_kind": peak_kind,
+                     "traffic": measured_traffic("star_" + dom),
+                     "alg_bytes_per_launch": None if not per_kernel[dom]["alg_bytes_per_step"]
+                     else int(per_kernel[dom]["alg_bytes_per_step"] / lps),
+                     "launches_per_step": lps},
+        "per_kernel": per_kernel,
+        "plan_alg_GBps": round(plan_bytes / (comp["ms_per_step"] * 1e-3) / 1e9, 1),
+        "compressed": comp, "uncompressed": dict(unc, e2e=e2e_unc),
+        "speedup_vs_uncompressed": round(unc["ms_per_step"] / comp["ms_per_step"], 3),
+        "footprint_ratio": round(comp["footprint_bytes"] / unc["footprint_bytes"], 4),
+        "device_peak_ratio": round(comp["device_peak_bytes"] / unc["device_peak_bytes"], 4),
+        "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+    }
+
+
+def bench_reference_star(args, world):
+    """Reference arm of the star workload: the oracle as it stands, on one host core,
+    each step a bounded prefix sample of the same fact table."""
+    n = args.rows or 600_000_000
+    per_step_s = max(2.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
+    rows = min(n, star_cpu_sample_rows(args.seed, per_step_s))
+    f, d = star_host_sample(args.seed, rows)
+    fw, dw = star_host_sample(args.seed, 1 << 16)
+    for _ in range(args.warmup):
+        oracle_star_plan(fw, dw)
+    times = [oracle_star_plan(f, d)[0] for _ in range(args.steps)]
+    tot = sum(times)
+    value = rows * args.steps / tot
+    from paper_2004_09350_gb300 import synth
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (seeded SplitMix64)",
+            "config": {"workload": STAR_WORKLOAD, "fact_rows": n, "dimension_rows": list(synth.DIM_SIZES),
+                       "parallelism": "1 host core"},
+            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "host": host_info(), "kind": "oracle",
+                             "build": "gcc -O2, single thread, not pinned to a core",
+                             "sample": f"first {rows} of the {n} fact rows per step, the same plan with every "
+                                       f"column passed through the oracle's codec in the compressed formats"},
+            "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 # ------------------------------------------------------- learned selector
@@ -976,10 +1256,12 @@ def main():
     if args.workload == "selector" and args.impl == "ours":
         print(json.dumps(bench_selector(args)))
         return
-    if args.workload == "star" and args.impl == "ours":
-        print(json.dumps(bench_star(args)))
-        return
-    line = bench_reference(args) if args.impl == "reference" else bench_ours(args)
+    if args.impl == "reference":
+        line = bench_reference(args)
+    elif args.workload == "star":
+        line = bench_star(args)
+    else:
+        line = bench_ours(args)
     if line is not None:
         print(json.dumps(line))
 

@@ -149,6 +149,12 @@ const char *ms_cuda_error_string(int code);
 ms_status ms_arena_usage(ms_ctx *ctx, uint64_t *in_use, uint64_t *high_water,
                          void *stream);
 ms_status ms_arena_reset_high_water(ms_ctx *ctx, void *stream);
+/* Bytes of the context's work area: the scratch its operators carve for
+   look-back status words, match bitmaps, per-chunk offsets and key bitmaps.  It
+   is allocated on demand and grows with the longest column seen; together with
+   the arena's high-water mark it is the device memory a plan needs beyond its
+   base columns.  0 for a NULL context.  No synchronisation. */
+uint64_t ms_work_bytes(const ms_ctx *ctx);
 
 /* ---------------------------------------------------------------- columns */
 

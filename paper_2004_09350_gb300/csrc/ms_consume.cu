@@ -5,9 +5,9 @@
 
 namespace ms {
 
-// Mark kernel of select / semi-join: every warp streams its own chunks (no block
-// barrier, no look-back) and writes per 512-row chunk a 512-bit match bitmap
-// (lane j's 16 rows -> halfword j) and the chunk's match count.
+// Mark kernel of select: the CTA streams its claims of the column (cta_stream) and
+// writes per 512-row chunk a 512-bit match bitmap (lane j's 16 rows -> halfword j)
+// and the chunk's match count.
 
 
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark(MarkArgs a) {
@@ -19,14 +19,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark(MarkArgs 
   const uint32_t negate = a.negate ? 0xffffu : 0u, live = a.empty ? 0u : 0xffffu;
   cta_stream<kTileBuf>(c, sm, a.ctl, [&](uint64_t g, const uint64_t* v, int valid, bool narrow) {
     uint32_t m16 = 0;
-    if (a.keybits) {
-#pragma unroll
-      for (int k = 0; k < 16; k++) {
-        const uint64_t x = v[k];
-        const bool hit = x < a.domain && ((__ldg(a.keybits + (x >> 5)) >> (x & 31)) & 1u);
-        m16 |= (uint32_t)hit << k;
-      }
-    } else if (narrow) {  // 32-bit compares
+    if (narrow) {  // 32-bit compares
       if (a.mode32 == 0) {
 #pragma unroll
         for (int k = 0; k < 16; k++) m16 |= (uint32_t)((uint32_t)v[k] - a.lo32 <= a.span32) << k;
@@ -46,6 +39,59 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark(MarkArgs 
     const uint32_t cnt = __reduce_add_sync(kFull, (uint32_t)__popc(m16));
     if (lane == 0) a.counts[g] = cnt;
   });
+}
+
+// Semi-join probe with the key bitmap in shared memory.  A bitmap of the whole key
+// domain is up to D/8 bytes (312 KB for 2.5e6 keys): too big for one CTA's shared
+// memory, and read at random from L2 it leaves the probe latency-bound.  So the
+// grid is cut into groups; CTA b belongs to group b % groups, holds that group's
+// slice of the bitmap in shared memory and takes claims b / groups, b / groups +
+// grid / groups, ...  The CTAs of one claim read the same probe data at about the
+// same time (one HBM read, the rest L2 hits), and each marks only the keys of its
+// slice.  With one group the matches and counts are written as in k_mark; with
+// several, the groups OR their matches into a zeroed bitmap and the scan counts
+// the bits.
+constexpr int kKeyTileBuf = 16384;
+constexpr size_t kKeyTileSmemBytes = sizeof(TileSmem<kKeyTileBuf>);
+
+__global__ void __launch_bounds__(kTileThreads, 1) k_mark_keys(MarkArgs a) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int lane = threadIdx.x & 31;
+  auto* sm = reinterpret_cast<TileSmem<kKeyTileBuf>*>(smem_raw);
+  uint32_t* kb = reinterpret_cast<uint32_t*>(smem_raw + kKeyTileSmemBytes);
+  const uint32_t G = a.groups, grp = blockIdx.x % G;
+  const uint64_t total_words = (a.domain + 31) / 32;
+  const uint64_t w0 = (uint64_t)grp * a.group_words;
+  const uint32_t nw = (uint32_t)(w0 < total_words ? min((uint64_t)a.group_words, total_words - w0) : 0);
+  for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) kb[i] = __ldg(a.keybits + w0 + i);
+  __syncthreads();
+  const uint64_t lo = 32 * w0, span = 32ull * nw;  // keys [lo, lo + span) of the domain
+  const ColView c = view_of(a.in);
+  const uint64_t cstride = max(1u, gridDim.x / G);
+  if (blockIdx.x / G >= cstride) return;  // a partial group at the end of the grid
+  uint32_t* bm32 = reinterpret_cast<uint32_t*>(a.bitmap);
+  cta_stream<kKeyTileBuf>(
+      c, sm, a.ctl,
+      [&](uint64_t g, const uint64_t* v, int valid, bool) {
+        uint32_t m16 = 0;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          const uint64_t r = v[k] - lo;  // keys >= domain lie past every slice
+          const bool hit = r < span && v[k] < a.domain && ((kb[r >> 5] >> (r & 31)) & 1u);
+          m16 |= (uint32_t)hit << k;
+        }
+        const int first = 16 * lane;
+        m16 &= valid >= first + 16 ? 0xffffu : (valid > first ? (1u << (valid - first)) - 1u : 0u);
+        if (G == 1) {
+          a.bitmap[g * 32 + lane] = (uint16_t)m16;
+          const uint32_t cnt = __reduce_add_sync(kFull, (uint32_t)__popc(m16));
+          if (lane == 0) a.counts[g] = cnt;
+        } else {
+          const uint32_t pair = m16 | (__shfl_down_sync(kFull, m16, 1) << 16);
+          if (!(lane & 1) && pair) atomicOr(bm32 + g * 16 + (lane >> 1), pair);
+        }
+      },
+      blockIdx.x / G, cstride);
 }
 
 // Exclusive scan of the per-chunk match counts (decoupled look-back over tiles of
@@ -73,7 +119,20 @@ __global__ void __launch_bounds__(kThreads) k_scan_counts(ScanArgs a) {
     uint32_t sum = 0;
 #pragma unroll
     for (int k = 0; k < kPer; k++) {
-      cnt[k] = (g0 + k < nch) ? a.counts[g0 + k] : 0;
+      if (a.bitmap) {
+        uint32_t c = 0;
+        if (g0 + k < nch) {
+          const uint4* w = reinterpret_cast<const uint4*>(a.bitmap) + 4 * (g0 + k);
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const uint4 u = w[q];
+            c += __popc(u.x) + __popc(u.y) + __popc(u.z) + __popc(u.w);
+          }
+        }
+        cnt[k] = c;
+      } else {
+        cnt[k] = (g0 + k < nch) ? a.counts[g0 + k] : 0;
+      }
       sum += cnt[k];
     }
     const uint32_t texcl = warp_excl_scan32(sum, lane);
@@ -265,11 +324,31 @@ ms_status launch_stats(ms_ctx* c, const DevMeta* in, uint64_t* d_stats, uint64_t
   return cuda_status(cudaGetLastError());
 }
 
+// Shared memory the key bitmap of a semi-join probe may take per CTA.
+constexpr size_t kKeySmemBudget = 224 * 1024 - kKeyTileSmemBytes;
+
 ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max, cudaStream_t s) {
   a.bitmap = w.bitmap;
   a.counts = w.counts;
-  const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
-  {
+  bool bitmap_counts = false;
+  if (a.keybits) {  // semi-join probe: key bitmap in shared memory, in slices if needed
+    const uint64_t words = cdiv(a.domain, 32);
+    const uint64_t groups = cdiv(4 * words, kKeySmemBudget);
+    a.groups = (uint32_t)groups;
+    a.group_words = (uint32_t)cdiv(words, groups);
+    const size_t smem = kKeyTileSmemBytes + 4 * (size_t)a.group_words;
+    const uint64_t claims = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kClaim);
+    int grid = grid_for(c, k_mark_keys, smem, claims * groups, kTileThreads);
+    grid = std::max<int>((int)groups, grid - grid % (int)groups);  // whole groups
+    if (groups > 1) {
+      bitmap_counts = true;
+      if (cuda_status(cudaMemsetAsync(w.bitmap, 0, 64 * cdiv(std::max<uint64_t>(n_max, 1), kBlock), s)) != MS_OK)
+        return MS_ERR_CUDA;
+    }
+    ProfScope ps(c, MS_K_MARK, s);
+    k_mark_keys<<<grid, kTileThreads, smem, s>>>(a);
+    if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
+  } else {
     const int grid = tile_grid(c, k_mark, n_max);
     ProfScope ps(c, MS_K_MARK, s);
     k_mark<<<grid, kTileThreads, kTileSmemBytes, s>>>(a);
@@ -279,6 +358,7 @@ ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max
   sa.in = a.in;
   sa.ctl = c->ctl;
   sa.counts = w.counts;
+  sa.bitmap = bitmap_counts ? reinterpret_cast<const uint32_t*>(w.bitmap) : nullptr;
   sa.coff = w.coff;
   sa.bstart = w.bstart;
   sa.status = w.status;

@@ -231,6 +231,8 @@ ms_status ms_get_error(ms_ctx* c, void* stream) {
 
 uint64_t ms_last_error_info(ms_ctx* c) { return c ? c->last_err_info : 0; }
 
+uint64_t ms_work_bytes(const ms_ctx* c) { return c ? c->work_cap : 0; }
+
 ms_status ms_arena_usage(ms_ctx* c, uint64_t* in_use, uint64_t* high, void* stream) {
   if (!c) return MS_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -56,8 +56,11 @@ struct TileSmem {
 // and narrow says that every value of the chunk is below 2^32 (a block or static
 // width of at most 32 bits).  Every thread of the CTA must call it (it
 // synchronises the CTA).
+// The CTA takes claims claim0, claim0 + cstride, ... (by default blockIdx.x and
+// gridDim.x).
 template <int BUF, class Body>
-MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body body) {
+MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body body, uint64_t claim0 = ~0ull,
+                       uint64_t cstride = 0) {
   static_assert(BUF >= 4096 && BUF % 4096 == 0, "buffer size");
   const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
   const uint64_t nch = (c.n + kBlock - 1) / kBlock;
@@ -101,7 +104,11 @@ MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body bo
     return 8 * off;
   };
 
-  uint64_t claim = blockIdx.x;
+  if (claim0 == ~0ull) {
+    claim0 = blockIdx.x;
+    cstride = gridDim.x;
+  }
+  uint64_t claim = claim0;
   if (claim >= nclaims) return;
   int hb = 0;
   uint64_t cb = claim * kClaim, ce = min(nch, cb + kClaim), g = cb;
@@ -109,7 +116,7 @@ MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body bo
   cp_async_commit();
   cp_async_wait<0>();
   __syncthreads();
-  load_hdr(claim + gridDim.x, 1);  // one claim ahead (header buffers rotate 0, 1, 2)
+  load_hdr(claim + cstride, 1);  // one claim ahead (header buffers rotate 0, 1, 2)
   // the sub-tile in flight / being decoded: chunks [ga, gb) of claim (hb_s, cb_s) in buffer bi
   uint64_t ga = 0, gb = 0, base = 0, cb_s = cb;
   int hb_s = 0, bi = 0;
@@ -117,13 +124,13 @@ MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body bo
   // schedules the next sub-tile from the current claim into buffer nbi and issues its copy
   auto schedule = [&](int nbi) -> bool {
     if (g >= ce) {  // next claim (its headers landed with an earlier group)
-      claim += gridDim.x;
+      claim += cstride;
       if (claim >= nclaims) return false;
       hb = hb == 2 ? 0 : hb + 1;
       cb = claim * kClaim;
       ce = min(nch, cb + kClaim);
       g = cb;
-      load_hdr(claim + gridDim.x, hb == 2 ? 0 : hb + 1);
+      load_hdr(claim + cstride, hb == 2 ? 0 : hb + 1);
     }
     const uint64_t s0 = start_bytes(g, cb, hb);
     // chunks of the claim whose payload ends within one buffer from s0 (ends are monotone)
@@ -272,6 +279,11 @@ struct MarkArgs {
   uint32_t lo32, span32, mode32;
   const uint32_t* keybits;  // semi-join: membership bitmap over the key domain
   uint64_t domain;
+  // semi-join with the key bitmap in shared memory: the grid is cut into `groups`
+  // CTA groups; group r holds bitmap words [r*group_words, (r+1)*group_words) and
+  // marks the matches of keys in that range (OR-ed into a zeroed bitmap when
+  // groups > 1, and then the counts come from the scan)
+  uint32_t groups, group_words;
   uint16_t* bitmap;
   uint32_t* counts;
 };
@@ -283,6 +295,7 @@ struct ScanArgs {
   const DevMeta* in;
   DevCtl* ctl;
   const uint32_t* counts;
+  const uint32_t* bitmap;  // when set, a chunk's count is the population of its 16 bitmap words
   uint64_t* coff;
   uint64_t* bstart;
   uint64_t* status;
@@ -923,13 +936,261 @@ MS_DEV int encode_block(int fmt, uint64_t v[16], int lane, uint64_t* ref_out) {
   return bw64(warp_or(o));
 }
 
+// ------------------------------------------------ project cores (direct producer)
+
+// Values of a non-DELTA column at the warp's positions, read in place (Sec. 4.2
+// random access; the block header doubles as a directory for DYN / FOR).  `stage`
+// holds the warp's 512 positions (swizzled, index o = position o of the chunk) and
+// receives the values in their place; bit i of `ok` says that position lane + 32i
+// is valid and inside the column.  Lane t takes positions t, t + 32, ... (striped),
+// so with sorted positions the 32 lanes of one load read neighbouring values of
+// one block: the loads coalesce when positions are dense, and only the touched
+// sectors are read when they are sparse.  kGatherGroup positions at a time: their
+// header loads, then all their payload halfword loads, are in flight together.
+#ifndef MS_GATHER_GROUP
+#define MS_GATHER_GROUP 4
+#endif
+constexpr int kGatherGroup = MS_GATHER_GROUP;
+MS_DEV void gather_values(const ColView& d, uint64_t* stage, uint32_t ok, int lane) {
+  if (d.fmt == MS_UNCOMPR) {
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+      uint64_t x[8];
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const int i = 8 * half + u;
+        const uint64_t q = stage[swz(lane + 32 * i)];
+        x[u] = ((ok >> i) & 1u) ? ldg64(d.p + 8 * q) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u++) stage[swz(lane + 32 * (8 * half + u))] = x[u];
+    }
+    return;
+  }
+  const bool stat = d.fmt == MS_STATIC_BP;
+  const uint64_t nb = stat ? d.n / kBlock : d.nb;
+  const uint64_t pay0 = stat ? 0 : 16 * nb;
+  const uint64_t rem0 = stat ? 64ull * (uint64_t)d.bw * nb : 16 * nb + 8 * d.pwords;
+#pragma unroll
+  for (int half = 0; half < 16 / kGatherGroup; half++) {
+    uint64_t q[kGatherGroup], w0[kGatherGroup], ref[kGatherGroup];
+#pragma unroll
+    for (int u = 0; u < kGatherGroup; u++) {  // headers (or the fixed static width)
+      const int i = kGatherGroup * half + u;
+      q[u] = stage[swz(lane + 32 * i)];
+      const uint64_t g = q[u] >> 9;
+      const bool in = ((ok >> i) & 1u) && g < nb;
+      if (stat) {
+        w0[u] = ((8ull * (uint64_t)d.bw * g) << 8) | (uint64_t)d.bw;
+        ref[u] = 0;
+      } else if (in && 16 * (g + 1) <= d.size) {
+        const ulonglong2 h = __ldg(reinterpret_cast<const ulonglong2*>(d.p) + g);
+        w0[u] = h.x;
+        ref[u] = h.y;
+      } else {
+        w0[u] = 0;
+        ref[u] = 0;
+      }
+    }
+    uint32_t h[kGatherGroup][5];
+#pragma unroll
+    for (int u = 0; u < kGatherGroup; u++) {  // payload halfwords: up to five cover a value at any bit phase
+      const int i = kGatherGroup * half + u;
+      const uint64_t g = q[u] >> 9;
+      const int r = (int)(q[u] & 511);
+      const int b = (int)min((uint64_t)64, w0[u] & 255);
+      const uint64_t pay = pay0 + 8 * (w0[u] >> 8);
+      const bool in = ((ok >> i) & 1u) && g < nb && b > 0 && pay + 64ull * b <= d.size;
+      const int bit0 = (r & 15) * b;
+      const int nq = in ? (((bit0 & 15) + b + 15) >> 4) : 0;
+      const uint16_t* hw = reinterpret_cast<const uint16_t*>(d.p + (in ? pay : 0)) + 32 * (bit0 >> 4) + (r >> 4);
+#pragma unroll
+      for (int t = 0; t < 5; t++) h[u][t] = t < nq ? (uint32_t)__ldg(hw + 32 * t) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kGatherGroup; u++) {
+      const int i = kGatherGroup * half + u;
+      const uint64_t g = q[u] >> 9;
+      const int r = (int)(q[u] & 511);
+      const int b = (int)min((uint64_t)64, w0[u] & 255);
+      const int sh = ((r & 15) * b) & 15;
+      const uint64_t lo = (uint64_t)h[u][0] | ((uint64_t)h[u][1] << 16) | ((uint64_t)h[u][2] << 32) |
+                          ((uint64_t)h[u][3] << 48);
+      uint64_t v = ((lo >> sh) | (sh ? ((uint64_t)h[u][4] << (64 - sh)) : 0)) & lowmask(b);
+      v += ref[u];
+      if (g >= nb) {  // the raw remainder, or static BP's horizontal tail
+        if (stat) {
+          const uint64_t bit = (uint64_t)r * (uint64_t)d.bw;
+          const int s2 = (int)(bit & 63);
+          const uint64_t at = rem0 + 8 * (bit >> 6);
+          uint64_t y = at + 8 <= d.size ? ldg64(d.p + at) >> s2 : 0;
+          if (s2 + d.bw > 64 && at + 16 <= d.size) y |= ldg64(d.p + at + 8) << (64 - s2);
+          v = y & lowmask(d.bw);
+        } else {
+          const uint64_t at = rem0 + 8 * (uint64_t)r;
+          v = at + 8 <= d.size ? ldg64(d.p + at) : 0;
+        }
+      }
+      stage[swz(lane + 32 * i)] = ((ok >> i) & 1u) ? v : 0;
+    }
+  }
+}
+
+// project core, non-DELTA data: the warp's positions (lane-blocked, p[k] is output
+// value 16*lane + k) go to the warp's 4 KB stage, are gathered striped in place by
+// gather_values, and come back lane-blocked in v.  Positions >= n(data) raise
+// MS_ERR_OUT_OF_RANGE and give 0.
+MS_DEV void project_direct(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
+                           uint64_t v[16], uint64_t* stage) {
+#pragma unroll
+  for (int k = 0; k < 16; k++) stage[swz(16 * lane + k)] = p[k];
+  __syncwarp();
+  uint32_t ok = 0;
+#pragma unroll
+  for (int i = 0; i < 16; i++) {
+    const int o = lane + 32 * i;
+    const uint64_t q = stage[swz(o)];
+    const bool in = o < valid;
+    if (in && q >= d.n) set_error(a.ctl, MS_ERR_OUT_OF_RANGE, q);
+    ok |= (uint32_t)(in && q < d.n) << i;
+  }
+  gather_values(d, stage, ok, lane);
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 16; k++) v[k] = stage[swz(16 * lane + k)];
+  __syncwarp();
+}
+
+// Decodes block B (< nb) of a DELTA column straight from global memory (each lane
+// reads its own stream; a warp load covers 64 contiguous bytes) into lane
+// registers: residuals, then the in-lane prefix sums and one warp scan.
+MS_DEV void decode_delta_block(const ColView& d, uint64_t B, uint64_t w0, uint64_t ref, int lane, uint64_t t[16],
+                               DevCtl* ctl) {
+  int b = (int)(w0 & 255);
+  const uint64_t pay = 16 * d.nb + 8 * (w0 >> 8);
+  if (b > 64 || pay + 64ull * b > d.size) {
+    if (lane == 0) set_error(ctl, MS_ERR_FORMAT, B);
+    b = 0;
+  }
+  read_lane_stream(reinterpret_cast<const uint16_t*>(d.p + (b ? pay : 0)), lane, b, t);
+  if (b <= 23) {  // 512 residuals below 2^23 sum below 2^32
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      sum += (uint32_t)t[k];
+      t[k] = sum;
+    }
+    const uint64_t excl = (uint64_t)warp_excl_scan32(sum, lane) + ref;
+#pragma unroll
+    for (int k = 0; k < 16; k++) t[k] += excl;
+  } else {
+    uint64_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      sum += t[k];
+      t[k] = sum;
+    }
+    const uint64_t excl = warp_excl_scan(sum, lane) + ref;
+#pragma unroll
+    for (int k = 0; k < 16; k++) t[k] += excl;
+  }
+}
+
+// project core, DELTA data: values need their block's prefix sums, so every
+// distinct block the warp's positions touch is decoded once (in ascending order)
+// into `aux` and the positions in it are read from there.  A block of width 0 holds
+// 512 copies of its reference and is not decoded.  The positions wait in `stage`
+// (lane-private slots).  Works for unsorted positions.
+MS_DEV void project_delta(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
+                          uint64_t v[16], uint64_t* stage, uint64_t* aux) {
+  uint32_t pending = 0;
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    v[k] = 0;
+    stage[swz(16 * lane + k)] = p[k];
+    if (16 * lane + k < valid) {
+      if (p[k] < d.n) pending |= 1u << k;
+      else set_error(a.ctl, MS_ERR_OUT_OF_RANGE, p[k]);
+    }
+  }
+  while (__ballot_sync(kFull, pending) != 0) {
+    uint64_t mb = ~0ull;
+#pragma unroll
+    for (int k = 0; k < 16; k++)
+      if (pending & (1u << k)) mb = min(mb, stage[swz(16 * lane + k)] >> 9);
+    const uint64_t B = warp_min(mb);
+    if (B < d.nb) {
+      ulonglong2 h = make_ulonglong2(0, 0);
+      if (16 * (B + 1) <= d.size) h = __ldg(reinterpret_cast<const ulonglong2*>(d.p) + B);
+      else if (lane == 0) set_error(a.ctl, MS_ERR_FORMAT, B);
+      if ((h.x & 255) == 0) {  // flat block: every value is the reference
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          if ((pending & (1u << k)) && (stage[swz(16 * lane + k)] >> 9) == B) {
+            v[k] = h.y;
+            pending &= ~(1u << k);
+          }
+        }
+        continue;
+      }
+      uint64_t t[16];
+      decode_delta_block(d, B, h.x, h.y, lane, t, a.ctl);
+#pragma unroll
+      for (int k = 0; k < 16; k++) aux[swz(16 * lane + k)] = t[k];
+    } else {  // the raw remainder
+      const uint64_t at = 16 * d.nb + 8 * d.pwords;
+      const int rem = (int)(d.n - B * kBlock);
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        const int o = 16 * lane + k;
+        aux[swz(o)] = (o < rem && at + 8 * (uint64_t)(o + 1) <= d.size) ? ldg64(d.p + at + 8 * o) : 0;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const uint64_t q = stage[swz(16 * lane + k)];
+      if ((pending & (1u << k)) && (q >> 9) == B) {
+        v[k] = aux[swz((int)(q & 511))];
+        pending &= ~(1u << k);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Per-warp shared memory and occupancy of the direct-offset producer.
+struct DSmemSingle {
+  StreamSmem<kProdDepth> s0;
+};
+struct DSmemPair {
+  StreamSmem<kProdDepth2> s0, s1;
+};
+struct DSmemProject {
+  StreamSmem<kProdDepth2> s0;  // positions
+};
+struct DSmemProjectDelta {
+  StreamSmem<kProdDepth2> s0;  // positions
+  uint64_t aux[kBlock];        // the data block decoded last
+};
+template <int OP>
+struct DirectPlan {
+  using Smem = typename std::conditional<
+      OP == OP_CALC, DSmemPair,
+      typename std::conditional<
+          OP == OP_PROJECT, DSmemProject,
+          typename std::conditional<
+              OP == OP_PROJECT_DELTA, DSmemProjectDelta,
+              typename std::conditional<OP == OP_EMIT, SmemEmit, DSmemSingle>::type>::type>::type>::type;
+  static constexpr int kMinBlocks = 2;
+};
+
 // Direct-offset producer of the allocation-free compress path: payload offsets come
 // from a decoupled look-back inside the kernel instead of a placement pass.
 template <int OP>
-__global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_produce(ProduceArgs a) {
-  static_assert(OP == OP_COMPRESS || OP == OP_DECOMPRESS || OP == OP_CALC || OP == OP_EMIT,
-                "k_produce has no project path");
-  using Smem = typename ProducePlan<OP>::Smem;
+__global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produce(ProduceArgs a) {
+  using Smem = typename DirectPlan<OP>::Smem;
+  constexpr bool kProject = OP == OP_PROJECT || OP == OP_PROJECT_DELTA;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ uint64_t s_words[kWarps];
   __shared__ uint64_t s_excl;
@@ -944,11 +1205,11 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_produ
 
   ColView c0{}, c1{};
   if (OP == OP_COMPRESS) c0 = view_raw(a.raw_in, a.raw_n);
-  if (OP == OP_DECOMPRESS || OP == OP_CALC) c0 = view_of(a.in0);
-  if (OP == OP_CALC && a.in1) c1 = view_of(a.in1);
+  if (OP == OP_DECOMPRESS || OP == OP_CALC || kProject) c0 = view_of(a.in0);
+  if ((OP == OP_CALC || kProject) && a.in1) c1 = view_of(a.in1);
   const uint64_t n_out = produce_n<OP>(a);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (OP == OP_DECOMPRESS && a.in0->n > a.raw_cap) set_error(ctl, MS_ERR_INVALID_ARG, a.in0->n);
+    if (OP == OP_DECOMPRESS && raw && a.in0->n > a.raw_cap) set_error(ctl, MS_ERR_INVALID_ARG, a.in0->n);
     if (OP == OP_CALC && a.in1 && a.in0->n != a.in1->n) set_error(ctl, MS_ERR_INVALID_ARG, a.in1->n);
   }
   const int fmt = a.fmt, bw = a.bw;
@@ -961,15 +1222,16 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_produ
   const uint64_t first = (uint64_t)blockIdx.x * kWarps + warp, stride = kWarps * G;
 
   // input streams: chunk i of a warp is first + i*stride, for every tile of the CTA
-  constexpr int D = OP == OP_CALC ? kProdDepth2 : kProdDepth;
+  constexpr int D = (OP == OP_CALC || kProject) ? kProdDepth2 : kProdDepth;
   StreamSmem<D>* ring0 = nullptr;
   StreamSmem<D>* ring1 = nullptr;
-  if constexpr (OP == OP_COMPRESS || OP == OP_DECOMPRESS) ring0 = &sm->s0;
+  if constexpr (OP == OP_COMPRESS || OP == OP_DECOMPRESS || kProject) ring0 = &sm->s0;
   if constexpr (OP == OP_CALC) {
     ring0 = &sm->s0;
     ring1 = &sm->s1;
   }
-  ChunkStream<D> st0{c0, first, stride, (OP == OP_EMIT) ? 0 : my_tiles, ring0, lane};
+  // project streams its positions (c1); the data column (c0) is read in place
+  ChunkStream<D> st0{kProject ? c1 : c0, first, stride, (OP == OP_EMIT) ? 0 : my_tiles, ring0, lane};
   ChunkStream<D> st1{c1, first, stride, (OP == OP_CALC && a.in1) ? my_tiles : 0, ring1, lane};
   if (OP != OP_EMIT && my_tiles) {
     for (int i = 0; i < D; i++) {
@@ -1020,6 +1282,15 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_produ
 #pragma unroll
           for (int k = 0; k < 16; k++) v[k] = arith(a.arith, v[k], a.scalar);
         }
+      } else if constexpr (OP == OP_PROJECT) {
+        uint64_t p[16];
+        valid = st0.decode(i, p, ctl);
+        __syncwarp();
+        project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
+      } else if constexpr (OP == OP_PROJECT_DELTA) {
+        uint64_t p[16];
+        valid = st0.decode(i, p, ctl);
+        project_delta(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage), sm->aux);
       }
       __syncwarp();
     }

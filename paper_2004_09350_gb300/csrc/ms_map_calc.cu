@@ -8,4 +8,9 @@ ms_status launch_map<OP_CALC>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStr
   return launch_map_impl<OP_CALC>(c, a, n_max, s);
 }
 
+
+template <>
+ms_status launch_direct<OP_CALC>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
+  return launch_direct_impl<OP_CALC>(c, a, n_max, s);
+}
 }  // namespace ms

@@ -13,4 +13,14 @@ ms_status launch_map<OP_PROJECT_DELTA>(ms_ctx* c, ProduceArgs& a, uint64_t n_max
   return launch_map_impl<OP_PROJECT_DELTA>(c, a, n_max, s);
 }
 
+
+template <>
+ms_status launch_direct<OP_PROJECT>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
+  return launch_direct_impl<OP_PROJECT>(c, a, n_max, s);
+}
+
+template <>
+ms_status launch_direct<OP_PROJECT_DELTA>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
+  return launch_direct_impl<OP_PROJECT_DELTA>(c, a, n_max, s);
+}
 }  // namespace ms

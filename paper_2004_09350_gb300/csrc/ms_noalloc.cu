@@ -43,7 +43,7 @@ struct DeviceSetup {
   int grid_cap = 0;
 };
 DeviceSetup g_setup[kMaxDevices];
-constexpr size_t kProduceSmem = sizeof(typename ProducePlan<OP_COMPRESS>::Smem) * kWarps;
+constexpr size_t kProduceSmem = sizeof(typename DirectPlan<OP_COMPRESS>::Smem) * kWarps;
 
 void setup_device(int dev, DeviceSetup* d) {
   void* p = nullptr;

@@ -1,6 +1,9 @@
 // ms_ops.cu -- operator entry points of libms: argument checks, scratch layout and
 // the launch sequence of each operator.  Every launch is asynchronous on the
 // caller's stream.
+#include <stdlib.h>
+#include <string.h>
+
 #include <algorithm>
 
 #include "ms_launch.h"
@@ -92,8 +95,18 @@ namespace {
 bool owned(ms_ctx* c, const ms_column* col) { return col && col->ctx == c && !col->freed; }
 
 
-// Launches k_map<OP> into a new arena column and, for block formats, places the
-// staged blocks.
+// MS_PRODUCER=map selects the staged producers (k_map + placement) instead of the
+// direct-offset ones, for comparison.
+bool use_staged_producers() {
+  static const bool on = [] {
+    const char* e = getenv("MS_PRODUCER");
+    return e && strcmp(e, "map") == 0;
+  }();
+  return on;
+}
+
+// Launches the producer of OP into a new arena column: k_produce<OP>, which places
+// every output block itself, or k_map<OP> followed by the placement pass.
 template <int OP>
 ms_status produce_column(ms_ctx* c, ProduceArgs& a, const Work& w, uint64_t n_max, int fmt, int bw,
                          ms_column** out, cudaStream_t s) {
@@ -105,8 +118,14 @@ ms_status produce_column(ms_ctx* c, ProduceArgs& a, const Work& w, uint64_t n_ma
   a.bw = fmt == MS_STATIC_BP ? bw : 0;
   a.stage = w.stage;
   a.stage_meta = w.stage_meta;
-  ms_status st = launch_map<OP>(c, a, n_max, s);
-  if (st == MS_OK && fmt >= MS_DYN_BP) st = launch_place(c, w, a.out_meta, n_max, s);
+  a.status = w.status2;
+  ms_status st;
+  if (use_staged_producers()) {
+    st = launch_map<OP>(c, a, n_max, s);
+    if (st == MS_OK && fmt >= MS_DYN_BP) st = launch_place(c, w, a.out_meta, n_max, s);
+  } else {
+    st = launch_direct<OP>(c, a, n_max, s);
+  }
   if (st != MS_OK) {
     drop_new_column(c, col);
     return st;
@@ -160,7 +179,8 @@ ms_status ms_decompress(ms_ctx* c, const ms_column* col, uint64_t* d_out, uint64
   a.raw_out = d_out;
   a.raw_cap = cap;
   a.fmt = MS_UNCOMPR;
-  return launch_map<OP_DECOMPRESS>(c, a, std::min(col->n_max, cap), s);
+  if (use_staged_producers()) return launch_map<OP_DECOMPRESS>(c, a, std::min(col->n_max, cap), s);
+  return launch_direct<OP_DECOMPRESS>(c, a, std::min(col->n_max, cap), s);
 }
 
 ms_status ms_select(ms_ctx* c, const ms_column* in, int cmp, uint64_t c1, uint64_t c2, int fmt, int bw,

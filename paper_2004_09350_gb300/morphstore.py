@@ -145,6 +145,8 @@ def load() -> ctypes.CDLL:
     lib.ms_last_error_info.restype = u64
     lib.ms_column_max_rows.argtypes = [p]
     lib.ms_column_max_rows.restype = u64
+    lib.ms_work_bytes.argtypes = [p]
+    lib.ms_work_bytes.restype = u64
     _lib = lib
     return lib
 
@@ -271,6 +273,10 @@ class Ctx:
                "ms_arena_usage")
         return a.value, b.value
 
+    def work_bytes(self) -> int:
+        """Bytes of the context's work area (ms_work_bytes)."""
+        return int(load().ms_work_bytes(self.h))
+
     def reset_high_water(self, stream=None):
         _check(load().ms_arena_reset_high_water(self.h, _stream_handle(stream)), "reset_high_water")
 
@@ -320,12 +326,20 @@ class Ctx:
         del keep
         return self._new(out, fmt, bw)
 
-    def export_bytes(self, col: Column, stream=None) -> np.ndarray:
+    def export_bytes(self, col: Column, stream=None, device: bool = False):
+        """The column's bytes: a host numpy uint8 array, or a uint8 tensor on the
+        context's device when device=True."""
         meta = self.info(col, stream)
-        buf = np.zeros(max(meta["size_bytes"], 1), dtype=np.uint8)
+        n = max(meta["size_bytes"], 1)
+        if device:
+            buf = torch.empty(n, dtype=torch.uint8, device=self.device)
+            ptr = buf.data_ptr()
+        else:
+            buf = np.zeros(n, dtype=np.uint8)
+            ptr = buf.ctypes.data
         got = ctypes.c_uint64()
-        _check(load().ms_column_export(self.h, col.ptr, ctypes.c_void_p(buf.ctypes.data), buf.size,
-                                       ctypes.byref(got), _stream_handle(stream)), "ms_column_export")
+        _check(load().ms_column_export(self.h, col.ptr, ctypes.c_void_p(ptr), n, ctypes.byref(got),
+                                       _stream_handle(stream)), "ms_column_export")
         return buf[: got.value]
 
     def info(self, col: Column, stream=None) -> dict:

@@ -50,7 +50,7 @@ STAR_BASE_COMPRESSED = {"fk1": ms.DYN_BP, "fk2": ms.DYN_BP, "fk3": ms.DYN_BP, "f
 STAR_BASE_UNCOMPRESSED = {k: ms.UNCOMPR for k in STAR_BASE_COMPRESSED}
 
 
-def star_plan(ctx, base, fm, out=None):
+def star_plan(ctx, base, fm, out=None, trace=None):
     """Star-schema plan: select on two dimensions, semi-join them into the fact
     table, select on discount and quantity ranges, project, and group-sum revenue
     by (year, c25):
@@ -59,34 +59,42 @@ def star_plan(ctx, base, fm, out=None):
       P1 = fact rows with fk1 in S1; P2 = P1 rows with fk2 in S2
       P3 = P2 rows with 1 <= discount <= 3; P4 = P3 rows with quantity < 25
       gid = year(fk_date) * 15 + D2.c25[fk2]; result[g] = sum of revenue per gid
+
+    trace, when a list, receives one record per operator: (op, output name,
+    input columns, output column, key domain or group count).
     """
     from .synth import DIM_SIZES
     cols = []
 
-    def keep(c):
+    def keep(op, name, ins, c, extra=0):
         cols.append(c)
+        if trace is not None:
+            trace.append((op, name, ins, c, extra))
         return c
 
-    s1 = keep(ctx.select(base["d1_c5"], ms.EQ, 0, fmt=fm["S1"]))
-    s2 = keep(ctx.select(base["d2_c25"], ms.LT, 15, fmt=fm["S2"]))
-    p1 = keep(ctx.semijoin(base["fk1"], s1, DIM_SIZES[0], fmt=fm["P1"]))
-    f2 = keep(ctx.project(base["fk2"], p1, fmt=fm["F2"]))
-    q2 = keep(ctx.semijoin(f2, s2, DIM_SIZES[1], fmt=fm["Q2"]))
-    p2 = keep(ctx.project(p1, q2, fmt=fm["P2"]))
-    disc = keep(ctx.project(base["discount"], p2, fmt=fm["DISC"]))
-    q3 = keep(ctx.select(disc, ms.BETWEEN, 1, 3, fmt=fm["Q3"]))
-    p3 = keep(ctx.project(p2, q3, fmt=fm["P3"]))
-    qty = keep(ctx.project(base["quantity"], p3, fmt=fm["QTY"]))
-    q4 = keep(ctx.select(qty, ms.LT, 25, fmt=fm["Q4"]))
-    p4 = keep(ctx.project(p3, q4, fmt=fm["P4"]))
-    date = keep(ctx.project(base["fk_date"], p4, fmt=fm["DATE"]))
-    year = keep(ctx.project(base["date_year"], date, fmt=fm["YEAR"]))
-    f2b = keep(ctx.project(base["fk2"], p4, fmt=fm["F2B"]))
-    c25 = keep(ctx.project(base["d2_c25"], f2b, fmt=fm["C25"]))
-    g0 = keep(ctx.calc(ms.MUL, year, None, c=15, fmt=fm["G0"]))
-    gid = keep(ctx.calc(ms.ADD, g0, c25, fmt=fm["GID"]))
-    rev = keep(ctx.project(base["revenue"], p4, fmt=fm["REV"]))
+    b = base
+    s1 = keep("select", "S1", [b["d1_c5"]], ctx.select(b["d1_c5"], ms.EQ, 0, fmt=fm["S1"]))
+    s2 = keep("select", "S2", [b["d2_c25"]], ctx.select(b["d2_c25"], ms.LT, 15, fmt=fm["S2"]))
+    p1 = keep("semijoin", "P1", [b["fk1"], s1], ctx.semijoin(b["fk1"], s1, DIM_SIZES[0], fmt=fm["P1"]), DIM_SIZES[0])
+    f2 = keep("project", "F2", [b["fk2"], p1], ctx.project(b["fk2"], p1, fmt=fm["F2"]))
+    q2 = keep("semijoin", "Q2", [f2, s2], ctx.semijoin(f2, s2, DIM_SIZES[1], fmt=fm["Q2"]), DIM_SIZES[1])
+    p2 = keep("project", "P2", [p1, q2], ctx.project(p1, q2, fmt=fm["P2"]))
+    disc = keep("project", "DISC", [b["discount"], p2], ctx.project(b["discount"], p2, fmt=fm["DISC"]))
+    q3 = keep("select", "Q3", [disc], ctx.select(disc, ms.BETWEEN, 1, 3, fmt=fm["Q3"]))
+    p3 = keep("project", "P3", [p2, q3], ctx.project(p2, q3, fmt=fm["P3"]))
+    qty = keep("project", "QTY", [b["quantity"], p3], ctx.project(b["quantity"], p3, fmt=fm["QTY"]))
+    q4 = keep("select", "Q4", [qty], ctx.select(qty, ms.LT, 25, fmt=fm["Q4"]))
+    p4 = keep("project", "P4", [p3, q4], ctx.project(p3, q4, fmt=fm["P4"]))
+    date = keep("project", "DATE", [b["fk_date"], p4], ctx.project(b["fk_date"], p4, fmt=fm["DATE"]))
+    year = keep("project", "YEAR", [b["date_year"], date], ctx.project(b["date_year"], date, fmt=fm["YEAR"]))
+    f2b = keep("project", "F2B", [b["fk2"], p4], ctx.project(b["fk2"], p4, fmt=fm["F2B"]))
+    c25 = keep("project", "C25", [b["d2_c25"], f2b], ctx.project(b["d2_c25"], f2b, fmt=fm["C25"]))
+    g0 = keep("calc", "G0", [year], ctx.calc(ms.MUL, year, None, c=15, fmt=fm["G0"]))
+    gid = keep("calc", "GID", [g0, c25], ctx.calc(ms.ADD, g0, c25, fmt=fm["GID"]))
+    rev = keep("project", "REV", [b["revenue"], p4], ctx.project(b["revenue"], p4, fmt=fm["REV"]))
     res = ctx.group_sum(gid, rev, STAR_GROUPS, out=out)
+    if trace is not None:
+        trace.append(("group_sum", "RESULT", [gid, rev], None, STAR_GROUPS))
     return res, cols
 
 

@@ -55,23 +55,32 @@ def test_mlp_adam_matches_reference(steps):
     # The library's Adam kernel (fp32) against the fp64 Adam of oracle/mlp.py, element by
     # element after every step: parameters, first and second moments.  Each reference
     # step starts from the GPU's current state, so fp32 rounding does not compound.
+    # Tolerance: the fp32 rounding bound of each update.  m = b1*m + (1-b1)*g can
+    # cancel, so its bound is relative to the two terms, not to the result:
+    # |err| <= 3 * 2^-24 * (|b1*m| + |(1-b1)*g|); v has no cancellation (2^-22
+    # relative); theta - step rounds once and the step carries about a dozen
+    # roundings (the fp32 bias corrections, divisions, square root, products):
+    # 2^-23*|theta| + 12*2^-24*|step|.
     rng = np.random.default_rng(8)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV)
     dth, dm, dv = t(mlp.init(9)), t(np.zeros(mlp.PARAMS)), t(np.zeros(mlp.PARAMS))
     # the kernel takes its hyperparameters as fp32: the reference uses those exact values
     lr, b1, b2, eps = (float(np.float32(a)) for a in (3e-3, 0.9, 0.999, 1e-8))
+    u = 2.0 ** -24
     for step in range(1, steps + 1):
         g = rng.normal(scale=10.0 ** float(rng.integers(-4, 2)), size=mlp.PARAMS).astype(np.float32)
-        before = [a.cpu().numpy().astype(np.float64) for a in (dth, dm, dv)]
-        want = mlp.adam_step(before[0], g, before[1], before[2], step, lr, b1, b2, eps)
+        th0, m0, v0 = [a.cpu().numpy().astype(np.float64) for a in (dth, dm, dv)]
+        want = mlp.adam_step(th0, g, m0, v0, step, lr, b1, b2, eps)
         ms.mlp_adam(dth, t(g), dm, dv, step, lr=lr, beta1=b1, beta2=b2, eps=eps)
         torch.cuda.synchronize()
-        got = [a.cpu().numpy() for a in (dth, dm, dv)]
-        np.testing.assert_allclose(got[1], want[1], rtol=1e-6, atol=1e-30)
-        np.testing.assert_allclose(got[2], want[2], rtol=1e-6, atol=1e-30)
-        # theta moves by about lr per step: its error is bounded by fp32 rounding of theta
-        # plus a relative 1e-6 of the step
-        np.testing.assert_allclose(got[0], want[0], rtol=1e-6, atol=1e-6 * lr)
+        got = [a.cpu().numpy().astype(np.float64) for a in (dth, dm, dv)]
+        g64 = g.astype(np.float64)
+        bound_m = 3 * u * (np.abs(b1 * m0) + np.abs((1 - b1) * g64)) + 1e-38
+        assert (np.abs(got[1] - want[1]) <= bound_m).all(), np.max(np.abs(got[1] - want[1]) / bound_m)
+        np.testing.assert_allclose(got[2], want[2], rtol=4 * u, atol=1e-38)
+        step_size = np.abs(th0 - want[0])
+        bound_t = 2 * u * np.abs(want[0]) + 12 * u * step_size + 1e-38
+        assert (np.abs(got[0] - want[0]) <= bound_t).all(), np.max(np.abs(got[0] - want[0]) / bound_t)
 
 
 def test_mlp_training_reduces_loss():
