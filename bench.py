@@ -722,8 +722,9 @@ def bench_star(args):
     dims = {k: ms.as_device_u64(v, dev) for k, v in synth.star_dims(args.seed + 1).items()}
     raw = {**fact, **dims}
     # arena: the base columns (uncompressed: 7 fact columns of 8 bytes) plus every
-    # intermediate of one step (at most 8 bytes a fact row in the uncompressed plan)
-    ctx = ms.Ctx(local, arena_bytes=8 * 8 * n + 8 * n + (256 << 20), max_rows=n)
+    # intermediate of one step (at most 8 bytes a fact row in the uncompressed plan), and
+    # the compressed base columns, which stay for the end-to-end runs (12 bytes a row)
+    ctx = ms.Ctx(local, arena_bytes=8 * 8 * n + 8 * n + 12 * n + (256 << 20), max_rows=n)
     out = {}
     for label, base_fm, fm in (("compressed", plans.STAR_BASE_COMPRESSED, plans.STAR_COMPRESSED),
                                ("uncompressed", plans.STAR_BASE_UNCOMPRESSED, plans.STAR_UNCOMPRESSED)):
@@ -804,7 +805,7 @@ def bench_star(args):
     # pinned host memory in their format, runs the plan and reads the sums back
     def e2e_run(label, base_fm, fm):
         base = out[label]["_base"]
-        host = {k: torch.from_numpy(ctx.export_bytes(c)).pin_memory() for k, c in base.items()}
+        host = {k: ctx.export_bytes(c, pinned=True) for k, c in base.items()}
         rows = {k: ctx.info(c)["n"] for k, c in base.items()}
         hres = torch.zeros(plans.STAR_GROUPS, dtype=torch.int64).pin_memory()
         res = torch.zeros(plans.STAR_GROUPS, dtype=torch.int64, device=dev)

@@ -191,6 +191,15 @@ ms_status ms_compress(ms_ctx *ctx, const uint64_t *d_in, uint64_t n, int fmt,
 ms_status ms_decompress(ms_ctx *ctx, const ms_column *col, uint64_t *d_out,
                         uint64_t cap, void *stream);
 
+/* morph (Sec. 3.2, "On-the-Fly Morphing"): the column's values as a new column in
+   out_fmt, with no uncompressed intermediate in device memory.  Each 512-value
+   block is decoded into registers and re-encoded in out_fmt by the same warp (a
+   direct morphing algorithm for every ordered pair of formats: n^2 - n = 20 of
+   them, and the identity).  MS_ERR_VALUE_TOO_WIDE (device) for a value wider than
+   out_static_bw under MS_STATIC_BP. */
+ms_status ms_morph(ms_ctx *ctx, const ms_column *col, int out_fmt, int out_static_bw,
+                   ms_column **out, void *stream);
+
 /* select (Sec. 5.1 "Single Operator"): ascending 0-based positions i with
    x_i <cmp> c1 (MS_BETWEEN: c1 <= x_i <= c2), as a new column in out_fmt. */
 ms_status ms_select(ms_ctx *ctx, const ms_column *in, int cmp, uint64_t c1,

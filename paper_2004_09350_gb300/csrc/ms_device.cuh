@@ -747,12 +747,23 @@ MS_DEV void publish(uint64_t* st, uint64_t flag_val) {
   *reinterpret_cast<volatile uint64_t*>(st) = flag_val;
 }
 
+// First half of a split look-back: publish tile's aggregate (its inclusive prefix if
+// it is tile 0).  Executed by one whole warp.
+MS_DEV void lookback_publish(uint64_t* status, uint64_t tile, uint64_t agg, int lane) {
+  if (lane == 0) publish(status + tile, (tile == 0 ? MS_FLAG_PRE : MS_FLAG_AGG) | agg);
+}
+
+// Second half: wait for the predecessors, publish the inclusive prefix and return the
+// exclusive prefix (the aggregate was published by lookback_publish).
+MS_DEV uint64_t lookback_resolve(uint64_t* status, uint64_t tile, uint64_t agg, int lane, DevCtl* ctl);
+
 MS_DEV uint64_t lookback(uint64_t* status, uint64_t tile, uint64_t agg, int lane, DevCtl* ctl) {
-  if (tile == 0) {
-    if (lane == 0) publish(status, MS_FLAG_PRE | agg);
-    return 0;
-  }
-  if (lane == 0) publish(status + tile, MS_FLAG_AGG | agg);
+  lookback_publish(status, tile, agg, lane);
+  return lookback_resolve(status, tile, agg, lane, ctl);
+}
+
+MS_DEV uint64_t lookback_resolve(uint64_t* status, uint64_t tile, uint64_t agg, int lane, DevCtl* ctl) {
+  if (tile == 0) return 0;
   uint64_t excl = 0;
   int64_t hi = (int64_t)tile - 1;
   uint32_t spins = 0;

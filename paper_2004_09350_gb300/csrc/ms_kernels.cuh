@@ -1192,7 +1192,8 @@ __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produc
   using Smem = typename DirectPlan<OP>::Smem;
   constexpr bool kProject = OP == OP_PROJECT || OP == OP_PROJECT_DELTA;
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  __shared__ uint64_t s_words[kWarps];
+  __shared__ uint64_t s_words[2][kWarps];  // by tile parity: payload words of each warp's block
+  __shared__ uint64_t s_agg[2];
   __shared__ uint64_t s_excl;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Smem* sm = reinterpret_cast<Smem*>(smem_raw) + warp;
@@ -1248,6 +1249,59 @@ __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produc
     }
   }
 
+  // A block-format tile is published and stored one iteration late: after encoding
+  // tile i the CTA publishes its aggregate (payload words) and moves on; the
+  // look-back of tile i and the store of its blocks from the stage slots happen at
+  // the top of iteration i + 1, before that iteration's prefetch refills the slot.
+  // By then the tile's predecessors have had a whole tile's time to publish, so the
+  // look-back rarely waits.  Per warp, the pending block: its stage, width,
+  // reference, valid count and chunk.
+  bool pend = false;
+  uint64_t pend_tile = 0, pend_g = 0, pend_ref = 0;
+  int pend_b = 0, pend_valid = 0, par = 0;
+  uint16_t* pend_stage = nullptr;
+  auto finish = [&]() {  // every thread of the CTA calls it
+    if (warp == 0) {
+      const uint64_t agg = s_agg[par];
+      const uint64_t ex = lookback_resolve(a.status, pend_tile, agg, lane, ctl);
+      if (lane == 0) {
+        s_excl = ex;
+        if (pend_tile == ntiles - 1) ctl->op_words = ex + agg;
+      }
+    }
+    __syncthreads();
+    if (pend_valid > 0) {
+      uint64_t off = s_excl;
+      for (int w = 0; w < warp; w++) off += s_words[par][w];
+      if (pend_valid == kBlock) {
+        const uint64_t pay = 16 * nb_out + 8 * off;
+        if (16 * (pend_g + 1) <= avail && pay + 64ull * pend_b <= avail) {
+          if (lane == 0) {
+            uint64_t* h = reinterpret_cast<uint64_t*>(base) + 2 * pend_g;
+            h[0] = (off << 8) | (uint64_t)pend_b;
+            h[1] = pend_ref;
+          }
+          uint4* dst = reinterpret_cast<uint4*>(base + pay);
+          const uint4* src = reinterpret_cast<const uint4*>(pend_stage);
+          for (int t = lane; t < 4 * pend_b; t += 32) dst[t] = src[t];
+        } else if (lane == 0) {
+          set_error(ctl, MS_ERR_NOMEM, pend_g);
+        }
+      } else {  // remainder: raw values behind the whole payload
+        const uint64_t rem = 16 * nb_out + 8 * off;
+        if (rem + 8ull * pend_valid <= avail) {
+          uint64_t* dst = reinterpret_cast<uint64_t*>(base + rem);
+          const uint64_t* src = reinterpret_cast<const uint64_t*>(pend_stage);
+          for (int t = lane; t < pend_valid; t += 32) dst[t] = src[t];
+        } else if (lane == 0) {
+          set_error(ctl, MS_ERR_NOMEM, pend_g);
+        }
+      }
+    }
+    __syncwarp();
+    pend = false;
+  };
+
   for (uint64_t i = 0; i < my_tiles; i++) {
     const uint64_t tile = blockIdx.x + i * G;
     const uint64_t g = tile * kWarps + warp;
@@ -1255,6 +1309,7 @@ __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produc
     int valid = 0;
     uint16_t* out_stage;
     if constexpr (OP == OP_EMIT) {
+      if (pend) finish();  // its stage (sm->out) is reused below
       out_stage = sm->out;
       if (g < nch) valid = emit_gather(a, n_out, g, lane, v, sm);
       else {
@@ -1264,6 +1319,7 @@ __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produc
     } else {
       cp_async_wait<D - 2>();
       __syncwarp();
+      if (pend) finish();  // before step(i) refills the pending tile's slot
       st0.step(i);
       st1.step(i);
       cp_async_commit();
@@ -1294,16 +1350,40 @@ __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produc
       }
       __syncwarp();
     }
-    // ---- encode into the warp's output stage
-    int b = 0;
-    uint64_t ref = 0, words = 0;
     if (blockfmt) {
+      // ---- encode into the warp's stage (the remainder as raw values) and publish
+      // the tile's aggregate; the look-back and the store wait for the next iteration
+      int b = 0;
+      uint64_t ref = 0;
       if (valid == kBlock) {
         b = encode_block(fmt, v, lane, &ref);
         write_lane_stream(out_stage, lane, b, v);
-        words = 8ull * b;
+      } else if (valid > 0) {
+        uint64_t* st64 = reinterpret_cast<uint64_t*>(out_stage);
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+          if (16 * lane + k < valid) st64[16 * lane + k] = v[k];
       }
-    } else if (fmt == MS_STATIC_BP && valid > 0) {
+      par = (int)(i & 1);
+      if (lane == 0) s_words[par][warp] = valid == kBlock ? 8ull * b : 0;
+      __syncthreads();
+      if (warp == 0) {
+        const uint64_t agg = warp_sum(lane < kWarps ? s_words[par][lane] : 0);
+        if (lane == 0) s_agg[par] = agg;
+        lookback_publish(a.status, tile, agg, lane);
+      }
+      __syncwarp();
+      pend = true;
+      pend_tile = tile;
+      pend_g = g;
+      pend_b = b;
+      pend_ref = ref;
+      pend_valid = valid;
+      pend_stage = out_stage;
+      continue;
+    }
+    // ---- fixed-offset formats: encode and store in place
+    if (fmt == MS_STATIC_BP && valid > 0) {
       uint64_t o = 0;
 #pragma unroll
       for (int k = 0; k < 16; k++) o |= (16 * lane + k < valid) ? v[k] : 0;
@@ -1314,6 +1394,15 @@ __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produc
       for (int k = 0; k < 16; k++) v[k] &= mask;
       if (g < static_chunks) {
         write_lane_stream(out_stage, lane, bw, v);
+        __syncwarp();
+        const uint64_t pay = 64ull * bw * g;
+        if (pay + 64ull * bw <= avail) {
+          uint4* dst = reinterpret_cast<uint4*>(base + pay);
+          const uint4* src = reinterpret_cast<const uint4*>(out_stage);
+          for (int t = lane; t < 4 * bw; t += 32) dst[t] = src[t];
+        } else if (lane == 0) {
+          set_error(ctl, MS_ERR_NOMEM, g);
+        }
       } else {  // horizontal tail
         uint32_t* w32 = reinterpret_cast<uint32_t*>(out_stage);
         for (int t = lane; t < 1024; t += 32) w32[t] = 0;
@@ -1323,12 +1412,12 @@ __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produc
           const int t = 16 * lane + k;
           if (t < valid && v[k]) {
             const uint64_t bit = (uint64_t)t * bw;
-            const int s = (int)(bit & 31);
+            const int sh = (int)(bit & 31);
             const uint64_t x = v[k];
             int wi = (int)(bit >> 5);
-            atomicOr(w32 + wi, (uint32_t)(x << s));
-            uint64_t rest = (s == 0) ? (x >> 32) : (x >> (32 - s));
-            int have = 32 - s;
+            atomicOr(w32 + wi, (uint32_t)(x << sh));
+            uint64_t rest = (sh == 0) ? (x >> 32) : (x >> (32 - sh));
+            int have = 32 - sh;
             while (have < bw && rest) {
               atomicOr(w32 + (++wi), (uint32_t)rest);
               rest >>= 32;
@@ -1336,103 +1425,45 @@ __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produc
             }
           }
         }
-      }
-      __syncwarp();
-    }
-    if (blockfmt) {
-      if (lane == 0) s_words[warp] = words;
-      __syncthreads();
-      if (warp == 0) {
-        const uint64_t agg = warp_sum(lane < kWarps ? s_words[lane] : 0);
-        const uint64_t ex = lookback(a.status, tile, agg, lane, ctl);
-        if (lane == 0) {
-          s_excl = ex;
-          if (tile == ntiles - 1) ctl->op_words = ex + agg;
-        }
-      }
-      __syncthreads();
-    }
-    // ---- store
-    if (valid > 0) {
-      if (blockfmt) {
-        uint64_t off = s_excl;
-        for (int w = 0; w < warp; w++) off += s_words[w];
-        if (valid == kBlock) {
-          const uint64_t pay = 16 * nb_out + 8 * off;
-          if (16 * (g + 1) <= avail && pay + 64ull * b <= avail) {
-            if (lane == 0) {
-              uint64_t* h = reinterpret_cast<uint64_t*>(base) + 2 * g;
-              h[0] = (off << 8) | (uint64_t)b;
-              h[1] = ref;
-            }
-            uint4* dst = reinterpret_cast<uint4*>(base + pay);
-            const uint4* src = reinterpret_cast<const uint4*>(out_stage);
-            for (int t = lane; t < 4 * b; t += 32) dst[t] = src[t];
-          } else if (lane == 0) {
-            set_error(ctl, MS_ERR_NOMEM, g);
-          }
-        } else {  // remainder: raw values behind the whole payload
-          const uint64_t rem = 16 * nb_out + 8 * off;
-          if (rem + 8ull * valid <= avail) {
-            uint64_t* dst = reinterpret_cast<uint64_t*>(base + rem);
-#pragma unroll
-            for (int k = 0; k < 16; k++)
-              if (16 * lane + k < valid) dst[16 * lane + k] = v[k];
-          } else if (lane == 0) {
-            set_error(ctl, MS_ERR_NOMEM, g);
-          }
-        }
-      } else if (fmt == MS_STATIC_BP) {
-        if (g < static_chunks) {
-          const uint64_t pay = 64ull * bw * g;
-          if (pay + 64ull * bw <= avail) {
-            uint4* dst = reinterpret_cast<uint4*>(base + pay);
-            const uint4* src = reinterpret_cast<const uint4*>(out_stage);
-            for (int t = lane; t < 4 * bw; t += 32) dst[t] = src[t];
-          } else if (lane == 0) {
-            set_error(ctl, MS_ERR_NOMEM, g);
-          }
-        } else {
-          const uint64_t pay = 64ull * bw * static_chunks;
-          const int nw = (int)(((uint64_t)valid * bw + 63) / 64);
-          if (pay + 8ull * nw <= avail) {
-            uint64_t* dst = reinterpret_cast<uint64_t*>(base + pay);
-            const uint64_t* src = reinterpret_cast<const uint64_t*>(out_stage);
-            for (int t = lane; t < nw; t += 32) dst[t] = src[t];
-          } else if (lane == 0) {
-            set_error(ctl, MS_ERR_NOMEM, g);
-          }
-        }
-      } else {  // uncompressed output (arena column or caller buffer)
-        const uint64_t pay = 8ull * kBlock * g;
-        if (pay + 8ull * valid <= avail) {
+        __syncwarp();
+        const uint64_t pay = 64ull * bw * static_chunks;
+        const int nw = (int)(((uint64_t)valid * bw + 63) / 64);
+        if (pay + 8ull * nw <= avail) {
           uint64_t* dst = reinterpret_cast<uint64_t*>(base + pay);
-          if (valid == kBlock) {
-            uint4* stg = reinterpret_cast<uint4*>(out_stage);
-#pragma unroll
-            for (int cc = 0; cc < 8; cc++)
-              stg[lane * 8 + (cc ^ (lane & 7))] =
-                  make_uint4((uint32_t)v[2 * cc], (uint32_t)(v[2 * cc] >> 32), (uint32_t)v[2 * cc + 1],
-                             (uint32_t)(v[2 * cc + 1] >> 32));
-            __syncwarp();
-#pragma unroll
-            for (int it = 0; it < 8; it++) {
-              const int ci = lane + 32 * it, L = ci >> 3, cc = ci & 7;
-              reinterpret_cast<uint4*>(dst)[ci] = stg[L * 8 + (cc ^ (L & 7))];
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < 16; k++)
-              if (16 * lane + k < valid) dst[16 * lane + k] = v[k];
-          }
+          const uint64_t* src = reinterpret_cast<const uint64_t*>(out_stage);
+          for (int t = lane; t < nw; t += 32) dst[t] = src[t];
         } else if (lane == 0) {
           set_error(ctl, MS_ERR_NOMEM, g);
         }
       }
+    } else if (fmt == MS_UNCOMPR && valid > 0) {  // arena column or caller buffer
+      const uint64_t pay = 8ull * kBlock * g;
+      if (pay + 8ull * valid <= avail) {
+        uint64_t* dst = reinterpret_cast<uint64_t*>(base + pay);
+        if (valid == kBlock) {
+          uint4* stg = reinterpret_cast<uint4*>(out_stage);
+#pragma unroll
+          for (int cc = 0; cc < 8; cc++)
+            stg[lane * 8 + (cc ^ (lane & 7))] = make_uint4((uint32_t)v[2 * cc], (uint32_t)(v[2 * cc] >> 32),
+                                                          (uint32_t)v[2 * cc + 1], (uint32_t)(v[2 * cc + 1] >> 32));
+          __syncwarp();
+#pragma unroll
+          for (int it = 0; it < 8; it++) {
+            const int ci = lane + 32 * it, L = ci >> 3, cc = ci & 7;
+            reinterpret_cast<uint4*>(dst)[ci] = stg[L * 8 + (cc ^ (L & 7))];
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; k++)
+            if (16 * lane + k < valid) dst[16 * lane + k] = v[k];
+        }
+      } else if (lane == 0) {
+        set_error(ctl, MS_ERR_NOMEM, g);
+      }
     }
     __syncwarp();
-    if (blockfmt) __syncthreads();
   }
+  if (pend) finish();
   cp_async_wait<0>();
 
   // ---- epilogue: the last CTA to finish describes the output column and moves

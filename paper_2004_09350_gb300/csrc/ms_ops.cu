@@ -183,6 +183,20 @@ ms_status ms_decompress(ms_ctx* c, const ms_column* col, uint64_t* d_out, uint64
   return launch_direct<OP_DECOMPRESS>(c, a, std::min(col->n_max, cap), s);
 }
 
+ms_status ms_morph(ms_ctx* c, const ms_column* col, int fmt, int bw, ms_column** out, void* stream) {
+  MS_TRACE();
+  if (!c || !out || !owned(c, col) || !valid_format(fmt, bw)) return MS_ERR_INVALID_ARG;
+  *out = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Work w;
+  ms_status st = carve(c, col->n_max, 0, &w, s);
+  if (st != MS_OK) return st;
+  ProduceArgs a{};
+  a.in0 = c->metas + col->slot;
+  a.raw_cap = ~0ull;
+  return produce_column<OP_DECOMPRESS>(c, a, w, col->n_max, fmt, bw, out, s);
+}
+
 ms_status ms_select(ms_ctx* c, const ms_column* in, int cmp, uint64_t c1, uint64_t c2, int fmt, int bw,
                     ms_column** out, void* stream) {
   MS_TRACE();

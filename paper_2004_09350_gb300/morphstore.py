@@ -105,6 +105,7 @@ def load() -> ctypes.CDLL:
         "ms_column_free": [p, p, p],
         "ms_compress": [p, p, u64, i32, i32, pp, p],
         "ms_decompress": [p, p, p, u64, p],
+        "ms_morph": [p, p, i32, i32, pp, p],
         "ms_select": [p, p, i32, u64, u64, i32, i32, pp, p],
         "ms_project": [p, p, p, i32, i32, pp, p],
         "ms_calc": [p, i32, p, p, u64, i32, i32, pp, p],
@@ -326,13 +327,14 @@ class Ctx:
         del keep
         return self._new(out, fmt, bw)
 
-    def export_bytes(self, col: Column, stream=None, device: bool = False):
-        """The column's bytes: a host numpy uint8 array, or a uint8 tensor on the
-        context's device when device=True."""
+    def export_bytes(self, col: Column, stream=None, device: bool = False, pinned: bool = False):
+        """The column's bytes: a host numpy uint8 array, a uint8 tensor on the
+        context's device (device=True) or a pinned host uint8 tensor (pinned=True)."""
         meta = self.info(col, stream)
         n = max(meta["size_bytes"], 1)
-        if device:
-            buf = torch.empty(n, dtype=torch.uint8, device=self.device)
+        if device or pinned:
+            buf = torch.empty(n, dtype=torch.uint8, device=self.device) if device else \
+                torch.empty(n, dtype=torch.uint8, pin_memory=True)
             ptr = buf.data_ptr()
         else:
             buf = np.zeros(n, dtype=np.uint8)
@@ -367,6 +369,12 @@ class Ctx:
         _check(load().ms_decompress(self.h, col.ptr, ctypes.c_void_p(out.data_ptr()), out.numel(),
                                     _stream_handle(stream)), "ms_decompress")
         return out
+
+    def morph(self, col: Column, fmt: int, bw: int = 0, stream=None) -> Column:
+        """ms_morph: the column's values in another format, block by block in registers."""
+        out = ctypes.c_void_p()
+        _check(load().ms_morph(self.h, col.ptr, fmt, bw, ctypes.byref(out), _stream_handle(stream)), "ms_morph")
+        return self._new(out, fmt, bw)
 
     def select(self, col: Column, cmp: int, c1: int, c2: int = 0, fmt: int = UNCOMPR, bw: int = 0,
                stream=None) -> Column:
