@@ -927,7 +927,7 @@ def plan_time(ctx, cx, ck, c, fm, res, reps=3):
 def bench_selector(args):
     import torch
     from paper_2004_09350_gb300 import morphstore as ms
-    from paper_2004_09350_gb300 import selector, synth
+    from paper_2004_09350_gb300 import plans, selector, synth
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
@@ -971,22 +971,18 @@ def bench_selector(args):
     free_all(ctx, cols)
     for col in (sk, sx):
         ctx.free(col)
-    plan_formats = (ms.UNCOMPR, ms.DYN_BP, ms.DELTA_BP, ms.FOR_BP)
-    picks = {name: int(sel.choose(feats[name], "time", allowed=plan_formats)[0]) for name in PLAN_INTERMEDIATES}
+    picks = {name: int(sel.choose(feats[name], "time", allowed=plans.PLAN_CANDIDATES)[0])
+             for name in PLAN_INTERMEDIATES}
     fm_sel = {name: ms.FORMAT_NAMES[picks[name]] for name in PLAN_INTERMEDIATES}
-    # greedy per-intermediate runtime search (Sec. 5.2): one intermediate at a time,
-    # try every format, keep the fastest, move on
-    fm_g = dict(COMPRESSED)
-    for name in PLAN_INTERMEDIATES:
-        best = None
-        for f in ms.FORMAT_NAMES:
-            if f == "static_bp":
-                continue  # static BP needs a width known only after the intermediate exists
-            trial = dict(fm_g, **{name: f})
-            t = plan_time(ctx, cx, ck, c, trial, res)
-            if best is None or t < best[0]:
-                best = (t, f)
-        fm_g[name] = best[1]
+    # greedy per-intermediate runtime search (Sec. 5.2) over the plan's intermediates
+    # (plans.greedy_formats; static BP is not a candidate: its width must be known
+    # before the intermediate exists)
+    run = lambda fm: plans.select_project_calc_sum(  # noqa: E731
+        ctx, cx, ck, c, {k2: fmt_id(v) for k2, v in fm.items()}, out=res)
+    names_fm = {k2: v for k2, v in COMPRESSED.items() if k2 in PLAN_INTERMEDIATES}
+    g_fm, _, _ = plans.greedy_formats(ctx, run, PLAN_INTERMEDIATES,
+                                      {k2: fmt_id(v) for k2, v in names_fm.items()}, "time", reps=3)
+    fm_g = dict(COMPRESSED, **{k2: ms.FORMAT_NAMES[v] for k2, v in g_fm.items()})
     t_sel = plan_time(ctx, cx, ck, c, dict(COMPRESSED, **fm_sel), res, reps=10)
     t_greedy = plan_time(ctx, cx, ck, c, fm_g, res, reps=10)
     t_fixed = plan_time(ctx, cx, ck, c, COMPRESSED, res, reps=10)

@@ -191,6 +191,18 @@ ms_status ms_compress(ms_ctx *ctx, const uint64_t *d_in, uint64_t n, int fmt,
 ms_status ms_decompress(ms_ctx *ctx, const ms_column *col, uint64_t *d_out,
                         uint64_t cap, void *stream);
 
+/* specialized select (Sec. 3.2, "Specialized Operators"): the positions ms_select
+   returns, computed on the compressed representation.  Only for inputs in
+   MS_DYN_BP, MS_FOR_BP, MS_DELTA_BP or MS_STATIC_BP (MS_ERR_FORMAT otherwise, at
+   once).  A block whose header bounds its values wholly inside or outside the
+   predicate's range is decided from its 16-byte header without reading or
+   decoding its payload; the others are compared in the residual domain as they
+   are unpacked (the predicate is shifted by the block's reference once, so FOR
+   and DELTA references are never added back, and b <= 32 compares in 32 bits). */
+ms_status ms_select_packed(ms_ctx *ctx, const ms_column *in, int cmp, uint64_t c1,
+                           uint64_t c2, int out_fmt, int out_static_bw, ms_column **out,
+                           void *stream);
+
 /* morph (Sec. 3.2, "On-the-Fly Morphing"): the column's values as a new column in
    out_fmt, with no uncompressed intermediate in device memory.  Each 512-value
    block is decoded into registers and re-encoded in out_fmt by the same warp (a
@@ -421,7 +433,8 @@ typedef enum {
   MS_K_PLACE_COPY = 12, /* block-format outputs: payload placement */
   MS_K_STATS = 13,      /* column statistics for the format selector */
   MS_K_BATCH = 14,      /* batched select -> project -> agg_sum fragments */
-  MS_K_COUNT = 15
+  MS_K_SELECT_PACKED = 15, /* specialized select on packed codes -> match bitmap */
+  MS_K_COUNT = 16
 } ms_kernel;
 
 typedef struct {

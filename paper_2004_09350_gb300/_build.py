@@ -18,6 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libms.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["ms_host.cu", "ms_ops.cu", "ms_noalloc.cu", "ms_consume.cu", "ms_place.cu", "ms_map_codec.cu",
+           "ms_select_packed.cu",
            "ms_map_project.cu", "ms_map_calc.cu", "ms_map_emit.cu", "ms_mlp.cu",
            "ms_batch.cu", "ms_batch_d2.cu", "ms_batch_d3.cu", "ms_batch_d4.cu",
            "ms_batch_static.cu"]

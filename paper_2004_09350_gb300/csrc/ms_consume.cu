@@ -1,6 +1,9 @@
 // ms_consume.cu -- consuming kernels (no output column): the select / semi-join
 // mark step and its count scan, agg_sum, group_sum and the semi-join build side,
 // plus their launchers.
+#include <stdlib.h>
+#include <string.h>
+
 #include "ms_launch.h"
 
 namespace ms {
@@ -10,16 +13,24 @@ namespace ms {
 // and the chunk's match count.
 
 
-__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark(MarkArgs a) {
+template <int BUF>
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark_t(MarkArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31;
-  auto* sm = reinterpret_cast<TileSmem<kTileBuf>*>(smem_raw);
+  auto* sm = reinterpret_cast<TileSmem<BUF>*>(smem_raw);
   const ColView c = view_of(a.in);
   const uint64_t lo = a.lo, span = a.span;
   const uint32_t negate = a.negate ? 0xffffu : 0u, live = a.empty ? 0u : 0xffffu;
-  cta_stream<kTileBuf>(c, sm, a.ctl, [&](uint64_t g, const uint64_t* v, int valid, bool narrow) {
+  cta_stream<BUF>(c, sm, a.ctl, [&](uint64_t g, const uint64_t* v, int valid, bool narrow) {
     uint32_t m16 = 0;
-    if (narrow) {  // 32-bit compares
+    if (a.keybits) {  // semi-join probe against a key bitmap read through the caches
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        const uint64_t x = v[k];
+        const bool hit = x < a.domain && ((__ldg(a.keybits + (x >> 5)) >> (x & 31)) & 1u);
+        m16 |= (uint32_t)hit << k;
+      }
+    } else if (narrow) {  // 32-bit compares
       if (a.mode32 == 0) {
 #pragma unroll
         for (int k = 0; k < 16; k++) m16 |= (uint32_t)((uint32_t)v[k] - a.lo32 <= a.span32) << k;
@@ -40,6 +51,13 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark(MarkArgs 
     if (lane == 0) a.counts[g] = cnt;
   });
 }
+
+// k_mark: the tile stream's usual 2 x 32 KB buffers.  k_mark_l1: 2 x 8 KB buffers
+// and a small shared-memory carve-out, so that most of the SM's unified L1 caches
+// the key bitmap of a semi-join probe.
+constexpr auto k_mark = k_mark_t<kTileBuf>;
+constexpr int kMarkL1Buf = 8192;
+constexpr auto k_mark_l1 = k_mark_t<kMarkL1Buf>;
 
 // Semi-join probe with the key bitmap in shared memory.  A bitmap of the whole key
 // domain is up to D/8 bytes (312 KB for 2.5e6 keys): too big for one CTA's shared
@@ -331,9 +349,24 @@ ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max
   a.bitmap = w.bitmap;
   a.counts = w.counts;
   bool bitmap_counts = false;
-  if (a.keybits) {  // semi-join probe: key bitmap in shared memory, in slices if needed
-    const uint64_t words = cdiv(a.domain, 32);
-    const uint64_t groups = cdiv(4 * words, kKeySmemBudget);
+  const uint64_t words = a.keybits ? cdiv(a.domain, 32) : 0;
+  const uint64_t groups = a.keybits ? cdiv(4 * words, kKeySmemBudget) : 0;
+  // a key bitmap that fits one CTA's shared memory is probed there; a larger one
+  // through the caches (MS_SEMIJOIN=smem: in slices over CTA groups; =l1: with a
+  // small shared-memory carve-out so that L1 holds more of it)
+  static const int large_mode = [] {
+    const char* e = getenv("MS_SEMIJOIN");
+    return !e ? 0 : (strcmp(e, "smem") == 0 ? 1 : (strcmp(e, "l1") == 0 ? 2 : 0));
+  }();
+  if (a.keybits && groups > 1 && large_mode == 2) {
+    const size_t smem = sizeof(TileSmem<kMarkL1Buf>);
+    cudaFuncSetAttribute(k_mark_l1, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
+    const int grid = grid_for(c, k_mark_l1, smem,
+                              cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kClaim), kTileThreads);
+    ProfScope ps(c, MS_K_MARK, s);
+    k_mark_l1<<<grid, kTileThreads, smem, s>>>(a);
+    if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
+  } else if (a.keybits && (groups == 1 || large_mode == 1)) {  // key bitmap in shared memory
     a.groups = (uint32_t)groups;
     a.group_words = (uint32_t)cdiv(words, groups);
     const size_t smem = kKeyTileSmemBytes + 4 * (size_t)a.group_words;
@@ -348,12 +381,17 @@ ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max
     ProfScope ps(c, MS_K_MARK, s);
     k_mark_keys<<<grid, kTileThreads, smem, s>>>(a);
     if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
-  } else {
+  } else {  // select, or a large key bitmap read through L2
     const int grid = tile_grid(c, k_mark, n_max);
     ProfScope ps(c, MS_K_MARK, s);
     k_mark<<<grid, kTileThreads, kTileSmemBytes, s>>>(a);
     if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
   }
+  return launch_scan(c, a, w, n_max, bitmap_counts, s);
+}
+
+ms_status launch_scan(ms_ctx* c, const MarkArgs& a, const Work& w, uint64_t n_max, bool bitmap_counts,
+                      cudaStream_t s) {
   ScanArgs sa{};
   sa.in = a.in;
   sa.ctl = c->ctl;

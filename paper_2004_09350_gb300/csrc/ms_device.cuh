@@ -764,18 +764,37 @@ MS_DEV uint64_t lookback(uint64_t* status, uint64_t tile, uint64_t agg, int lane
 
 MS_DEV uint64_t lookback_resolve(uint64_t* status, uint64_t tile, uint64_t agg, int lane, DevCtl* ctl) {
   if (tile == 0) return 0;
+  // Each round reads a window of 256 predecessors, 8 consecutive ones per lane (lane
+  // l: tiles hi - 8l - j, j = 0..7, newest first), so a look-back that has to walk
+  // back over a whole round of CTAs (tiles whose inclusive prefix is not out yet)
+  // takes one or two memory round trips instead of one per 32 tiles.
+  constexpr int kPer = 8;
   uint64_t excl = 0;
   int64_t hi = (int64_t)tile - 1;
   uint32_t spins = 0;
   while (true) {
-    const int64_t t = hi - lane;
-    uint64_t s = t >= 0 ? *reinterpret_cast<volatile uint64_t*>(status + t) : MS_FLAG_PRE;
-    const uint32_t flag = (uint32_t)(s >> 62);
-    const uint32_t pre = __ballot_sync(kFull, flag == 2);
-    const uint32_t none = __ballot_sync(kFull, flag == 0);
+    uint64_t st[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; j++) {
+      const int64_t t = hi - kPer * lane - j;
+      st[j] = t >= 0 ? *reinterpret_cast<volatile uint64_t*>(status + t) : MS_FLAG_PRE;
+    }
+    int jp = kPer;  // the lane's newest inclusive prefix
+    bool lnone = false;
+    uint64_t lsum = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; j++) {
+      if (jp == kPer) {
+        const uint32_t f = (uint32_t)(st[j] >> 62);
+        lnone |= f == 0;
+        lsum += st[j] & MS_VAL_MASK;
+        if (f == 2) jp = j;
+      }
+    }
+    const uint32_t pre = __ballot_sync(kFull, jp < kPer);
     const int first = pre ? __ffs(pre) - 1 : 31;
     const uint32_t need = first == 31 ? kFull : ((2u << first) - 1u);
-    if (none & need) {
+    if (__ballot_sync(kFull, lnone) & need) {
       if (++spins > kSpinLimit) {
         if (lane == 0) set_error(ctl, MS_ERR_TIMEOUT, tile);
         break;
@@ -784,9 +803,9 @@ MS_DEV uint64_t lookback_resolve(uint64_t* status, uint64_t tile, uint64_t agg, 
       continue;
     }
     __threadfence();
-    excl += warp_sum(lane <= first ? (s & MS_VAL_MASK) : 0);
+    excl += warp_sum(lane <= first ? lsum : 0);
     if (pre) break;
-    hi -= 32;
+    hi -= 32 * kPer;
   }
   if (lane == 0) publish(status + tile, MS_FLAG_PRE | (excl + agg));
   return excl;

@@ -411,7 +411,7 @@ const char* ms_kernel_name(int k) {
   static const char* names[MS_K_COUNT] = {"mark",      "emit",       "compress", "decompress",
                                           "project",   "calc",       "agg_sum",  "group_sum",
                                           "build_keys", "validate",  "scan",     "place_scan",
-                                          "place_copy", "stats",      "batch"};
+                                          "place_copy", "stats",      "batch",    "select_packed"};
   return (k >= 0 && k < MS_K_COUNT) ? names[k] : "?";
 }
 

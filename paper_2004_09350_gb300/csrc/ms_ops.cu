@@ -216,6 +216,26 @@ ms_status ms_select(ms_ctx* c, const ms_column* in, int cmp, uint64_t c1, uint64
   return emit_positions(c, w, in->n_max, fmt, bw, out, s);
 }
 
+ms_status ms_select_packed(ms_ctx* c, const ms_column* in, int cmp, uint64_t c1, uint64_t c2, int fmt, int bw,
+                           ms_column** out, void* stream) {
+  MS_TRACE();
+  if (!c || !out || !owned(c, in) || !valid_format(fmt, bw) || cmp < MS_EQ || cmp > MS_BETWEEN)
+    return MS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (in->fmt == MS_UNCOMPR) return MS_ERR_FORMAT;  // nothing packed to work on
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Work w;
+  ms_status st = carve(c, in->n_max, 0, &w, s);
+  if (st != MS_OK) return st;
+  MarkArgs m{};
+  m.in = c->metas + in->slot;
+  m.ctl = c->ctl;
+  predicate_as_range(cmp, c1, c2, &m);
+  st = launch_select_packed(c, m, w, in->n_max, s);
+  if (st != MS_OK) return st;
+  return emit_positions(c, w, in->n_max, fmt, bw, out, s);
+}
+
 ms_status ms_project(ms_ctx* c, const ms_column* data, const ms_column* pos, int fmt, int bw,
                      ms_column** out, void* stream) {
   MS_TRACE();

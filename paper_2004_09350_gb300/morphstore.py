@@ -107,6 +107,7 @@ def load() -> ctypes.CDLL:
         "ms_decompress": [p, p, p, u64, p],
         "ms_morph": [p, p, i32, i32, pp, p],
         "ms_select": [p, p, i32, u64, u64, i32, i32, pp, p],
+        "ms_select_packed": [p, p, i32, u64, u64, i32, i32, pp, p],
         "ms_project": [p, p, p, i32, i32, pp, p],
         "ms_calc": [p, i32, p, p, u64, i32, i32, pp, p],
         "ms_agg_sum": [p, p, p, p],
@@ -301,9 +302,9 @@ class Ctx:
 
     def profile_collect(self) -> dict:
         """{kernel name: (launches, total device ms)} since the last collect (synchronises)."""
-        arr = (KernelTime * 16)()
+        arr = (KernelTime * 32)()
         n = ctypes.c_int()
-        _check(load().ms_profile_collect(self.h, arr, 16, ctypes.byref(n)), "ms_profile_collect")
+        _check(load().ms_profile_collect(self.h, arr, 32, ctypes.byref(n)), "ms_profile_collect")
         lib = load()
         return {lib.ms_kernel_name(arr[i].kernel).decode(): (arr[i].launches, arr[i].total_ms)
                 for i in range(n.value)}
@@ -369,6 +370,14 @@ class Ctx:
         _check(load().ms_decompress(self.h, col.ptr, ctypes.c_void_p(out.data_ptr()), out.numel(),
                                     _stream_handle(stream)), "ms_decompress")
         return out
+
+    def select_packed(self, col: Column, cmp: int, c1: int, c2: int = 0, fmt: int = UNCOMPR, bw: int = 0,
+                      stream=None) -> Column:
+        """ms_select_packed: the specialized select on a packed (block or static BP) column."""
+        out = ctypes.c_void_p()
+        _check(load().ms_select_packed(self.h, col.ptr, cmp, c1, c2, fmt, bw, ctypes.byref(out),
+                                       _stream_handle(stream)), "ms_select_packed")
+        return self._new(out, fmt, bw)
 
     def morph(self, col: Column, fmt: int, bw: int = 0, stream=None) -> Column:
         """ms_morph: the column's values in another format, block by block in registers."""

@@ -106,3 +106,88 @@ def free_lifo(ctx, cols):
 def footprint(ctx, cols) -> int:
     """Sum of the physical sizes of the given columns (synchronises)."""
     return sum(ctx.info(c)["size_bytes"] for c in cols)
+
+
+# --------------------------------------------- plan-level format choice
+
+# Formats an intermediate may take when the choice is made before it exists: static
+# BP needs its width up front, so it is left to the selector's sampled statistics.
+PLAN_CANDIDATES = (ms.UNCOMPR, ms.DYN_BP, ms.DELTA_BP, ms.FOR_BP)
+PLAN_OBJECTIVES = ("time", "size")
+
+
+def plan_cost(ctx, run, fm, objective="time", reps=3):
+    """Cost of one format combination of a plan.  run(fm) enqueues the plan and
+    returns (result, intermediates in allocation order).  objective "time": mean
+    device milliseconds of `reps` runs after one warm-up run (CUDA events on the
+    current stream); "size": the sum of the intermediates' physical sizes (the
+    paper's footprint measure, Sec. 5.2).  Every run frees its intermediates."""
+    import torch
+    _, cols = run(fm)
+    if objective == "size":
+        cost = footprint(ctx, cols)
+        free_lifo(ctx, cols)
+        return float(cost)
+    free_lifo(ctx, cols)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(reps):
+        _, cols = run(fm)
+        free_lifo(ctx, cols)
+    t1.record()
+    t1.synchronize()
+    return t0.elapsed_time(t1) / reps
+
+
+def greedy_formats(ctx, run, names, start, objective="time", candidates=PLAN_CANDIDATES, reps=3, cost=None):
+    """Greedy per-intermediate format search over a whole plan (Sec. 5.2,
+    "Determining a good format combination"): the intermediates are visited once,
+    in plan order; for each, every candidate format is tried with all others held
+    fixed, and the cheapest is kept before moving on.  Returns (formats, cost of
+    the final combination, number of plan evaluations).  `cost(fm)` overrides the
+    measurement (plan_cost by default)."""
+    if objective not in PLAN_OBJECTIVES:
+        raise ValueError(f"objective must be one of {PLAN_OBJECTIVES}")
+    measure = cost or (lambda fm: plan_cost(ctx, run, fm, objective, reps))
+    fm = dict(start)
+    evals, best_cost = 0, None
+    for name in names:
+        best = None
+        for f in candidates:
+            trial = dict(fm, **{name: f})
+            c = measure(trial)
+            evals += 1
+            if best is None or c < best[0]:
+                best = (c, f)
+        fm[name] = best[1]
+        best_cost = best[0]
+    return fm, best_cost, evals
+
+
+def selector_formats(ctx, selector, run_sample, names, ops, objective="time", candidates=PLAN_CANDIDATES,
+                     n_scale=1.0, random_reads=()):
+    """Formats chosen by the learned selector (selector.Selector) before the plan
+    runs: run_sample(fm) runs the plan once on a prefix sample with every
+    intermediate uncompressed; each intermediate's statistics (ms_column_stats),
+    scaled to the full length by n_scale, give its features, and the selector picks
+    the format it predicts cheapest for the objective.  ops[name] is the producing
+    operator ("select", "project", "calc", "semijoin"); names in random_reads are
+    read at random by a later project."""
+    from . import selector as sel_mod
+    fm0 = {name: ms.UNCOMPR for name in names}
+    _, cols = run_sample(fm0)
+    feats = []
+    for name, col in zip(names, cols):
+        feats.append(sel_mod.column_features(ctx, col, ops[name], name in random_reads, n_scale))
+    free_lifo(ctx, cols)
+    picks = selector.choose(__import__("numpy").stack(feats), objective, allowed=candidates)
+    return {name: int(p) for name, p in zip(names, picks)}
+
+
+STAR_NAMES = tuple(STAR_COMPRESSED)  # the star plan's intermediates in plan order
+STAR_OPS = {"S1": "select", "S2": "select", "P1": "semijoin", "F2": "project", "Q2": "semijoin", "P2": "project",
+            "DISC": "project", "Q3": "select", "P3": "project", "QTY": "project", "Q4": "select", "P4": "project",
+            "DATE": "project", "YEAR": "project", "F2B": "project", "C25": "project", "G0": "calc", "GID": "calc",
+            "REV": "project"}
+# intermediates a later project reads at random (the position lists projected through)
+STAR_RANDOM_READS = ("P1", "P2", "P3")

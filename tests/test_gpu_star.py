@@ -108,3 +108,28 @@ def test_star_plan_intermediates_match_oracle(base_fm, fm):
             code = ctx.get_error()
             assert code == ms.MS_OK, f"device error {code} (info {ctx.last_error_info()}) by {name}"
             np.testing.assert_array_equal(ms.to_numpy_u64(ctx.decompress(got[name])), want[name], err_msg=name)
+
+
+@pytest.mark.parametrize("objective", ["size", "time"])
+def test_greedy_plan_formats_keep_results_and_meet_their_objective(objective):
+    """Plan-level format choice (Sec. 5.2): the greedy per-intermediate search over the
+    star plan's 19 intermediates changes formats only (the sums stay the oracle's),
+    and its combination costs no more than the starting one under its objective."""
+    n = (1 << 18) + 5
+    fact = synth.star_fact(9, n)
+    dims = synth.star_dims(10)
+    want, _ = oracle_star(fact, dims)
+    with ms.Ctx(0, arena_bytes=1 << 30, max_rows=1 << 20) as ctx:
+        base = {k: ctx.compress(ms.as_device_u64(v, ctx.device), plans.STAR_BASE_COMPRESSED[k])
+                for k, v in {**fact, **dims}.items()}
+        run = lambda fm: plans.star_plan(ctx, base, fm)  # noqa: E731
+        start = dict(plans.STAR_COMPRESSED)
+        c0 = plans.plan_cost(ctx, run, start, objective, reps=2)
+        fm, c, evals = plans.greedy_formats(ctx, run, plans.STAR_NAMES, start, objective, reps=2)
+        assert evals == len(plans.STAR_NAMES) * len(plans.PLAN_CANDIDATES)
+        if objective == "size":  # sizes are deterministic: the search can only improve
+            assert c <= c0 and plans.plan_cost(ctx, run, fm, "size") == c
+        res, cols = run(fm)
+        ctx.check(what="greedy formats")
+        np.testing.assert_array_equal(ms.to_numpy_u64(res), want)
+        plans.free_lifo(ctx, cols)
