@@ -66,8 +66,11 @@ def parse():
                          "selector: train the learned format selector on engine traces and measure its regret; "
                          "batch: 4096 select->project->agg_sum fragments in one persistent launch; "
                          "kernel: one operator of the plan alone (--kernel), the case the ncu summaries use")
-    ap.add_argument("--kernel", choices=["agg_sum", "select", "project", "compress", "decompress"],
-                    default="agg_sum")
+    ap.add_argument("--kernel", choices=["agg_sum", "select", "select_packed", "project", "project_uniform",
+                                         "compress", "decompress"],
+                    default="agg_sum",
+                    help="project_uniform: project X at positions spread uniformly over the column "
+                         "(--selectivity of the rows), the access pattern of the star plan's projects")
     ap.add_argument("--width", type=int, default=0,
                     help="kernel workload: every 512-block of X at this bit width (0: the plan's width mix)")
     ap.add_argument("--x-format", choices=["uncompr", "static_bp", "dyn_bp", "delta_bp", "for_bp"], default="dyn_bp",
@@ -676,7 +679,7 @@ def star_kernel_bytes(ctx, trace):
     def add(k, v):
         kb[k] = kb.get(k, 0) + int(v)
 
-    for op, name, ins, out, extra in trace:
+    for op, name, ins, out, extra, _, _ in trace:
         if op in ("select", "semijoin"):
             n = sz(ins[0])["n"]
             nch = -(-n // BLOCK)
@@ -741,6 +744,8 @@ def bench_star(args):
         _, cols = plans.star_plan(ctx, base, fm, out=res, trace=trace)
         inter_bytes = plans.footprint(ctx, cols)
         _, high = ctx.arena_usage()
+        torch.cuda.synchronize()
+        op_ms = {rec[1]: round(rec[5].elapsed_time(rec[6]), 4) for rec in trace}
         kb = star_kernel_bytes(ctx, trace) if label == "compressed" else None
         plans.free_lifo(ctx, cols)
         del trace
@@ -781,7 +786,7 @@ def bench_star(args):
                       "arena_peak_intermediates": int(high - use0),
                       "device_peak_bytes": int(base_bytes + (high - use0) + ctx.work_bytes()),
                       "sums": ms.to_numpy_u64(res).tolist(), "prof": prof, "kernel_bytes": kb,
-                      "clocks": ck_info,
+                      "clocks": ck_info, "op_ms_sizing_step": op_ms,
                       "per_kernel_ms": {k: round(v[1] / args.steps, 4) for k, v in prof.items()}}
         out[label]["_base"] = base
     assert out["compressed"]["sums"] == out["uncompressed"]["sums"], "star pipelines disagree"
@@ -1203,6 +1208,9 @@ def bench_kernel(args):
     ck = ctx.compress(ms.as_device_u64(k, dev), ms.DELTA_BP)
     res = torch.zeros(1, dtype=torch.int64, device=dev)
     pos = ctx.select(cx, ms.LT, c, fmt=ms.DELTA_BP) if args.kernel == "project" else None
+    if args.kernel == "project_uniform":
+        u = ctx.compress(synth.uniform_torch(args.seed + 7, n, 0, 1 << 20, dev), ms.UNCOMPR)
+        pos = ctx.select(u, ms.LT, int(args.selectivity * (1 << 20)), fmt=ms.DELTA_BP)
 
     raw = ms.as_device_u64(x, dev) if args.kernel in ("compress", "decompress") else None
 
@@ -1211,6 +1219,10 @@ def bench_kernel(args):
             ctx.agg_sum(cx, out=res)
         elif args.kernel == "select":
             ctx.free(ctx.select(cx, ms.LT, c, fmt=ms.DELTA_BP))
+        elif args.kernel == "select_packed":
+            ctx.free(ctx.select_packed(cx, ms.LT, c, fmt=ms.DELTA_BP))
+        elif args.kernel == "project_uniform":
+            ctx.free(ctx.project(cx, pos, fmt=ms.DYN_BP))
         elif args.kernel == "compress":  # X again, into a fresh arena column
             ctx.free(ctx.compress(raw, fx, bw))
         elif args.kernel == "decompress":  # X into a caller buffer

@@ -1,9 +1,6 @@
 // ms_consume.cu -- consuming kernels (no output column): the select / semi-join
 // mark step and its count scan, agg_sum, group_sum and the semi-join build side,
 // plus their launchers.
-#include <stdlib.h>
-#include <string.h>
-
 #include "ms_launch.h"
 
 namespace ms {
@@ -59,16 +56,10 @@ constexpr auto k_mark = k_mark_t<kTileBuf>;
 constexpr int kMarkL1Buf = 8192;
 constexpr auto k_mark_l1 = k_mark_t<kMarkL1Buf>;
 
-// Semi-join probe with the key bitmap in shared memory.  A bitmap of the whole key
-// domain is up to D/8 bytes (312 KB for 2.5e6 keys): too big for one CTA's shared
-// memory, and read at random from L2 it leaves the probe latency-bound.  So the
-// grid is cut into groups; CTA b belongs to group b % groups, holds that group's
-// slice of the bitmap in shared memory and takes claims b / groups, b / groups +
-// grid / groups, ...  The CTAs of one claim read the same probe data at about the
-// same time (one HBM read, the rest L2 hits), and each marks only the keys of its
-// slice.  With one group the matches and counts are written as in k_mark; with
-// several, the groups OR their matches into a zeroed bitmap and the scan counts
-// the bits.
+// Semi-join probe with the key bitmap in shared memory, for key domains whose
+// bitmap fits one CTA (up to about 1.5 million keys: 2e5 takes 25 KB).  Probing a
+// bitmap in L2 leaves the probe latency-bound on scattered 32-byte sector reads;
+// from shared memory a lookup costs a few bank wavefronts.
 constexpr int kKeyTileBuf = 16384;
 constexpr size_t kKeyTileSmemBytes = sizeof(TileSmem<kKeyTileBuf>);
 
@@ -77,39 +68,24 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_mark_keys(MarkArgs a) {
   const int lane = threadIdx.x & 31;
   auto* sm = reinterpret_cast<TileSmem<kKeyTileBuf>*>(smem_raw);
   uint32_t* kb = reinterpret_cast<uint32_t*>(smem_raw + kKeyTileSmemBytes);
-  const uint32_t G = a.groups, grp = blockIdx.x % G;
-  const uint64_t total_words = (a.domain + 31) / 32;
-  const uint64_t w0 = (uint64_t)grp * a.group_words;
-  const uint32_t nw = (uint32_t)(w0 < total_words ? min((uint64_t)a.group_words, total_words - w0) : 0);
-  for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) kb[i] = __ldg(a.keybits + w0 + i);
+  const uint64_t nw = (a.domain + 31) / 32;
+  for (uint64_t i = threadIdx.x; i < nw; i += blockDim.x) kb[i] = __ldg(a.keybits + i);
   __syncthreads();
-  const uint64_t lo = 32 * w0, span = 32ull * nw;  // keys [lo, lo + span) of the domain
   const ColView c = view_of(a.in);
-  const uint64_t cstride = max(1u, gridDim.x / G);
-  if (blockIdx.x / G >= cstride) return;  // a partial group at the end of the grid
-  uint32_t* bm32 = reinterpret_cast<uint32_t*>(a.bitmap);
-  cta_stream<kKeyTileBuf>(
-      c, sm, a.ctl,
-      [&](uint64_t g, const uint64_t* v, int valid, bool) {
-        uint32_t m16 = 0;
+  cta_stream<kKeyTileBuf>(c, sm, a.ctl, [&](uint64_t g, const uint64_t* v, int valid, bool) {
+    uint32_t m16 = 0;
 #pragma unroll
-        for (int k = 0; k < 16; k++) {
-          const uint64_t r = v[k] - lo;  // keys >= domain lie past every slice
-          const bool hit = r < span && v[k] < a.domain && ((kb[r >> 5] >> (r & 31)) & 1u);
-          m16 |= (uint32_t)hit << k;
-        }
-        const int first = 16 * lane;
-        m16 &= valid >= first + 16 ? 0xffffu : (valid > first ? (1u << (valid - first)) - 1u : 0u);
-        if (G == 1) {
-          a.bitmap[g * 32 + lane] = (uint16_t)m16;
-          const uint32_t cnt = __reduce_add_sync(kFull, (uint32_t)__popc(m16));
-          if (lane == 0) a.counts[g] = cnt;
-        } else {
-          const uint32_t pair = m16 | (__shfl_down_sync(kFull, m16, 1) << 16);
-          if (!(lane & 1) && pair) atomicOr(bm32 + g * 16 + (lane >> 1), pair);
-        }
-      },
-      blockIdx.x / G, cstride);
+    for (int k = 0; k < 16; k++) {
+      const uint64_t x = v[k];
+      const bool hit = x < a.domain && ((kb[x >> 5] >> (x & 31)) & 1u);
+      m16 |= (uint32_t)hit << k;
+    }
+    const int first = 16 * lane;
+    m16 &= valid >= first + 16 ? 0xffffu : (valid > first ? (1u << (valid - first)) - 1u : 0u);
+    a.bitmap[g * 32 + lane] = (uint16_t)m16;
+    const uint32_t cnt = __reduce_add_sync(kFull, (uint32_t)__popc(m16));
+    if (lane == 0) a.counts[g] = cnt;
+  });
 }
 
 // Exclusive scan of the per-chunk match counts (decoupled look-back over tiles of
@@ -137,20 +113,7 @@ __global__ void __launch_bounds__(kThreads) k_scan_counts(ScanArgs a) {
     uint32_t sum = 0;
 #pragma unroll
     for (int k = 0; k < kPer; k++) {
-      if (a.bitmap) {
-        uint32_t c = 0;
-        if (g0 + k < nch) {
-          const uint4* w = reinterpret_cast<const uint4*>(a.bitmap) + 4 * (g0 + k);
-#pragma unroll
-          for (int q = 0; q < 4; q++) {
-            const uint4 u = w[q];
-            c += __popc(u.x) + __popc(u.y) + __popc(u.z) + __popc(u.w);
-          }
-        }
-        cnt[k] = c;
-      } else {
-        cnt[k] = (g0 + k < nch) ? a.counts[g0 + k] : 0;
-      }
+      cnt[k] = (g0 + k < nch) ? a.counts[g0 + k] : 0;
       sum += cnt[k];
     }
     const uint32_t texcl = warp_excl_scan32(sum, lane);
@@ -348,17 +311,15 @@ constexpr size_t kKeySmemBudget = 224 * 1024 - kKeyTileSmemBytes;
 ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max, cudaStream_t s) {
   a.bitmap = w.bitmap;
   a.counts = w.counts;
-  bool bitmap_counts = false;
-  const uint64_t words = a.keybits ? cdiv(a.domain, 32) : 0;
-  const uint64_t groups = a.keybits ? cdiv(4 * words, kKeySmemBudget) : 0;
-  // a key bitmap that fits one CTA's shared memory is probed there; a larger one
-  // through the caches (MS_SEMIJOIN=smem: in slices over CTA groups; =l1: with a
-  // small shared-memory carve-out so that L1 holds more of it)
-  static const int large_mode = [] {
-    const char* e = getenv("MS_SEMIJOIN");
-    return !e ? 0 : (strcmp(e, "smem") == 0 ? 1 : (strcmp(e, "l1") == 0 ? 2 : 0));
-  }();
-  if (a.keybits && groups > 1 && large_mode == 2) {
+  const uint64_t key_bytes = a.keybits ? 4 * cdiv(a.domain, 32) : 0;
+  if (a.keybits && key_bytes <= kKeySmemBudget) {  // key bitmap in shared memory
+    const size_t smem = kKeyTileSmemBytes + key_bytes;
+    const int grid = grid_for(c, k_mark_keys, smem, cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kClaim),
+                              kTileThreads);
+    ProfScope ps(c, MS_K_MARK, s);
+    k_mark_keys<<<grid, kTileThreads, smem, s>>>(a);
+    if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
+  } else if (a.keybits) {  // a larger key bitmap: probed through L1 and L2 (k_mark_l1)
     const size_t smem = sizeof(TileSmem<kMarkL1Buf>);
     cudaFuncSetAttribute(k_mark_l1, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
     const int grid = grid_for(c, k_mark_l1, smem,
@@ -366,37 +327,20 @@ ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max
     ProfScope ps(c, MS_K_MARK, s);
     k_mark_l1<<<grid, kTileThreads, smem, s>>>(a);
     if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
-  } else if (a.keybits && (groups == 1 || large_mode == 1)) {  // key bitmap in shared memory
-    a.groups = (uint32_t)groups;
-    a.group_words = (uint32_t)cdiv(words, groups);
-    const size_t smem = kKeyTileSmemBytes + 4 * (size_t)a.group_words;
-    const uint64_t claims = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kClaim);
-    int grid = grid_for(c, k_mark_keys, smem, claims * groups, kTileThreads);
-    grid = std::max<int>((int)groups, grid - grid % (int)groups);  // whole groups
-    if (groups > 1) {
-      bitmap_counts = true;
-      if (cuda_status(cudaMemsetAsync(w.bitmap, 0, 64 * cdiv(std::max<uint64_t>(n_max, 1), kBlock), s)) != MS_OK)
-        return MS_ERR_CUDA;
-    }
-    ProfScope ps(c, MS_K_MARK, s);
-    k_mark_keys<<<grid, kTileThreads, smem, s>>>(a);
-    if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
-  } else {  // select, or a large key bitmap read through L2
+  } else {  // select
     const int grid = tile_grid(c, k_mark, n_max);
     ProfScope ps(c, MS_K_MARK, s);
     k_mark<<<grid, kTileThreads, kTileSmemBytes, s>>>(a);
     if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
   }
-  return launch_scan(c, a, w, n_max, bitmap_counts, s);
+  return launch_scan(c, a, w, n_max, s);
 }
 
-ms_status launch_scan(ms_ctx* c, const MarkArgs& a, const Work& w, uint64_t n_max, bool bitmap_counts,
-                      cudaStream_t s) {
+ms_status launch_scan(ms_ctx* c, const MarkArgs& a, const Work& w, uint64_t n_max, cudaStream_t s) {
   ScanArgs sa{};
   sa.in = a.in;
   sa.ctl = c->ctl;
   sa.counts = w.counts;
-  sa.bitmap = bitmap_counts ? reinterpret_cast<const uint32_t*>(w.bitmap) : nullptr;
   sa.coff = w.coff;
   sa.bstart = w.bstart;
   sa.status = w.status;

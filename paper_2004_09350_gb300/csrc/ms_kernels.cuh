@@ -279,11 +279,6 @@ struct MarkArgs {
   uint32_t lo32, span32, mode32;
   const uint32_t* keybits;  // semi-join: membership bitmap over the key domain
   uint64_t domain;
-  // semi-join with the key bitmap in shared memory: the grid is cut into `groups`
-  // CTA groups; group r holds bitmap words [r*group_words, (r+1)*group_words) and
-  // marks the matches of keys in that range (OR-ed into a zeroed bitmap when
-  // groups > 1, and then the counts come from the scan)
-  uint32_t groups, group_words;
   uint16_t* bitmap;
   uint32_t* counts;
 };
@@ -295,7 +290,6 @@ struct ScanArgs {
   const DevMeta* in;
   DevCtl* ctl;
   const uint32_t* counts;
-  const uint32_t* bitmap;  // when set, a chunk's count is the population of its 16 bitmap words
   uint64_t* coff;
   uint64_t* bstart;
   uint64_t* status;

@@ -39,9 +39,8 @@ int grid_for(ms_ctx* c, K kernel, size_t smem, uint64_t tiles, int threads = kTh
 
 // consumers (ms_consume.cu)
 ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max, cudaStream_t s);
-// the count scan alone (bitmap_counts: count the bitmap's bits instead of reading counts)
-ms_status launch_scan(ms_ctx* c, const MarkArgs& a, const Work& w, uint64_t n_max, bool bitmap_counts,
-                      cudaStream_t s);
+// the count scan alone
+ms_status launch_scan(ms_ctx* c, const MarkArgs& a, const Work& w, uint64_t n_max, cudaStream_t s);
 // the specialized select on packed block formats (ms_select_packed.cu): mark + scan
 ms_status launch_select_packed(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max, cudaStream_t s);
 ms_status launch_agg_sum(ms_ctx* c, const DevMeta* in, uint64_t* d_result, uint64_t n_max, cudaStream_t s);

@@ -95,12 +95,12 @@ namespace {
 bool owned(ms_ctx* c, const ms_column* col) { return col && col->ctx == c && !col->freed; }
 
 
-// MS_PRODUCER=map selects the staged producers (k_map + placement) instead of the
-// direct-offset ones, for comparison.
+// The staged producers (k_map + placement) are the default; MS_PRODUCER=direct
+// selects the direct-offset ones (k_produce), for comparison.
 bool use_staged_producers() {
   static const bool on = [] {
     const char* e = getenv("MS_PRODUCER");
-    return e && strcmp(e, "map") == 0;
+    return !(e && strcmp(e, "direct") == 0);
   }();
   return on;
 }

@@ -103,11 +103,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_select_packed(MarkArgs a) {
         bounded = (top >> 64) == 0;
         R1 = bounded ? (uint64_t)top : ~0ull;
       } else {
+        // x = ref + r with no wrap (FOR's residual is x minus the block minimum), so
+        // the bound saturates at 2^64 - 1 (FOR blocks of width 64 reach it)
         R1 = ref + rmax;
-        if (R1 < ref) {  // only a corrupt header gets here (ref > 0 with b = 64)
-          bounded = false;
-          R1 = ~0ull;
-        }
+        if (R1 < ref) R1 = ~0ull;
       }
       const bool inside = bounded && iv.A <= R0 && R1 <= iv.B;
       const bool outside = bounded && (R1 < iv.A || R0 > iv.B);
@@ -209,7 +208,7 @@ ms_status launch_select_packed(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n
     k_select_packed<<<grid, kThreads, 0, s>>>(a);
     if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
   }
-  return launch_scan(c, a, w, n_max, false, s);
+  return launch_scan(c, a, w, n_max, s);
 }
 
 }  // namespace ms

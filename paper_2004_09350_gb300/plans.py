@@ -61,16 +61,30 @@ def star_plan(ctx, base, fm, out=None, trace=None):
       gid = year(fk_date) * 15 + D2.c25[fk2]; result[g] = sum of revenue per gid
 
     trace, when a list, receives one record per operator: (op, output name,
-    input columns, output column, key domain or group count).
+    input columns, output column, key domain or group count, CUDA events before
+    and after the operator's launches).
     """
     from .synth import DIM_SIZES
     cols = []
+    ev = [None]
+
+    def mark():  # an event before the next operator's launches (traced runs only)
+        if trace is not None:
+            import torch
+            ev[0] = torch.cuda.Event(enable_timing=True)
+            ev[0].record()
 
     def keep(op, name, ins, c, extra=0):
         cols.append(c)
         if trace is not None:
-            trace.append((op, name, ins, c, extra))
+            import torch
+            e1 = torch.cuda.Event(enable_timing=True)
+            e1.record()
+            trace.append((op, name, ins, c, extra, ev[0], e1))
+        mark()
         return c
+
+    mark()
 
     b = base
     s1 = keep("select", "S1", [b["d1_c5"]], ctx.select(b["d1_c5"], ms.EQ, 0, fmt=fm["S1"]))
@@ -94,7 +108,10 @@ def star_plan(ctx, base, fm, out=None, trace=None):
     rev = keep("project", "REV", [b["revenue"], p4], ctx.project(b["revenue"], p4, fmt=fm["REV"]))
     res = ctx.group_sum(gid, rev, STAR_GROUPS, out=out)
     if trace is not None:
-        trace.append(("group_sum", "RESULT", [gid, rev], None, STAR_GROUPS))
+        import torch
+        e1 = torch.cuda.Event(enable_timing=True)
+        e1.record()
+        trace.append(("group_sum", "RESULT", [gid, rev], None, STAR_GROUPS, ev[0], e1))
     return res, cols
 
 
