@@ -437,11 +437,10 @@ struct ProducePlan {
           typename std::conditional<
               OP == OP_PROJECT_DELTA, SmemProjectDelta,
               typename std::conditional<OP == OP_EMIT, SmemEmit, SmemSingle>::type>::type>::type>::type;
-  static constexpr int kMinBlocks =
-      (OP == OP_PROJECT_DELTA || OP == OP_PROJECT) ? MS_PROJECT_MIN_BLOCKS : (OP == OP_CALC ? 1 : 2);
-  // CTA-shared shared memory behind the per-warp plans
-  using Cta = ProjectCta<OP == OP_PROJECT_DELTA ? MS_PROJECT_DELTA_CTA_BUF : MS_PROJECT_CTA_BUF>;
-  static constexpr size_t kCtaBytes = (OP == OP_PROJECT_DELTA || OP == OP_PROJECT) ? sizeof(Cta) : 0;
+  static constexpr int kMinBlocks = OP == OP_PROJECT ? MS_PROJECT_MIN_BLOCKS : (OP == OP_CALC ? 1 : 2);
+  // CTA-shared shared memory behind the per-warp plans (the CTA span copy of project)
+  using Cta = ProjectCta<MS_PROJECT_CTA_BUF>;
+  static constexpr size_t kCtaBytes = OP == OP_PROJECT ? sizeof(Cta) : 0;
 };
 
 // Output length of the operator (device-side, may depend on previous kernels).
@@ -1090,11 +1089,13 @@ MS_DEV void decode_delta_block(const ColView& d, uint64_t B, uint64_t w0, uint64
   }
 }
 
-// project core, DELTA data: values need their block's prefix sums, so every
-// distinct block the warp's positions touch is decoded once (in ascending order)
-// into `aux` and the positions in it are read from there.  A block of width 0 holds
-// 512 copies of its reference and is not decoded.  The positions wait in `stage`
-// (lane-private slots).  Works for unsorted positions.
+// project core, DELTA data: values need their block's prefix sums.  First every
+// position's block header is read (sixteen independent loads per lane, nearly all
+// hits in L1): a block of width 0 holds 512 copies of its reference, and its
+// positions are answered at once.  Then every other distinct block the warp's
+// positions touch is decoded once (in ascending order) into `aux`, and the positions
+// in it are read from there.  The positions wait in `stage` (lane-private slots).
+// Works for unsorted positions.
 MS_DEV void project_delta(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
                           uint64_t v[16], uint64_t* stage, uint64_t* aux) {
   uint32_t pending = 0;
@@ -1102,9 +1103,17 @@ MS_DEV void project_delta(const ProduceArgs& a, const ColView& d, const uint64_t
   for (int k = 0; k < 16; k++) {
     v[k] = 0;
     stage[swz(16 * lane + k)] = p[k];
-    if (16 * lane + k < valid) {
-      if (p[k] < d.n) pending |= 1u << k;
-      else set_error(a.ctl, MS_ERR_OUT_OF_RANGE, p[k]);
+    const bool in = 16 * lane + k < valid;
+    if (in && p[k] >= d.n) set_error(a.ctl, MS_ERR_OUT_OF_RANGE, p[k]);
+    if (in && p[k] < d.n) {
+      const uint64_t B = p[k] >> 9;
+      bool flat = false;
+      if (B < d.nb && 16 * (B + 1) <= d.size) {
+        const ulonglong2 h = __ldg(reinterpret_cast<const ulonglong2*>(d.p) + B);
+        flat = (h.x & 255) == 0;
+        v[k] = h.y;
+      }
+      pending |= (uint32_t)!flat << k;
     }
   }
   while (__ballot_sync(kFull, pending) != 0) {
@@ -1117,16 +1126,6 @@ MS_DEV void project_delta(const ProduceArgs& a, const ColView& d, const uint64_t
       ulonglong2 h = make_ulonglong2(0, 0);
       if (16 * (B + 1) <= d.size) h = __ldg(reinterpret_cast<const ulonglong2*>(d.p) + B);
       else if (lane == 0) set_error(a.ctl, MS_ERR_FORMAT, B);
-      if ((h.x & 255) == 0) {  // flat block: every value is the reference
-#pragma unroll
-        for (int k = 0; k < 16; k++) {
-          if ((pending & (1u << k)) && (stage[swz(16 * lane + k)] >> 9) == B) {
-            v[k] = h.y;
-            pending &= ~(1u << k);
-          }
-        }
-        continue;
-      }
       uint64_t t[16];
       decode_delta_block(d, B, h.x, h.y, lane, t, a.ctl);
 #pragma unroll
@@ -1504,6 +1503,153 @@ __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produc
   }
 }
 
+// Stores output chunk g (lane-blocked values v, `valid` of them) of a staged
+// producer: a block-format block is encoded into the warp's stage slot in shared
+// memory and copied to its 4 KB global stage slot with its {width, reference} (the
+// placement pass moves it to its final offset); static BP and uncompressed chunks
+// have fixed offsets and are stored in place.
+MS_DEV void store_staged(const ProduceArgs& a, int fmt, int bw, bool blockfmt, uint64_t g, uint64_t v[16], int valid,
+                         uint16_t* out_stage, uint8_t* base, uint64_t avail, uint64_t static_chunks, DevCtl* ctl,
+                         int lane) {
+    if (blockfmt) {
+      uint4* slot = reinterpret_cast<uint4*>(a.stage + 4096 * g);
+      if (valid == kBlock) {
+        uint64_t ref;
+        const int b = encode_block(fmt, v, lane, &ref);
+        write_lane_stream(out_stage, lane, b, v);
+        __syncwarp();
+        const uint4* src = reinterpret_cast<const uint4*>(out_stage);
+        for (int t = lane; t < 4 * b; t += 32) slot[t] = src[t];
+        if (lane == 0) {
+          a.stage_meta[2 * g] = (uint64_t)b;
+          a.stage_meta[2 * g + 1] = ref;
+        }
+      } else if (valid > 0) {  // remainder: raw values, placed behind the payload later
+        uint64_t* dst = reinterpret_cast<uint64_t*>(slot);
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+          if (16 * lane + k < valid) dst[16 * lane + k] = v[k];
+      }
+    } else if (fmt == MS_STATIC_BP) {
+      uint64_t o = 0;
+#pragma unroll
+      for (int k = 0; k < 16; k++) o |= (16 * lane + k < valid) ? v[k] : 0;
+      o = warp_or(o);
+      if (bw64(o) > bw && lane == 0) set_error(ctl, MS_ERR_VALUE_TOO_WIDE, g);
+      const uint64_t mask = lowmask(bw);
+#pragma unroll
+      for (int k = 0; k < 16; k++) v[k] &= mask;
+      if (g < static_chunks) {
+        write_lane_stream(out_stage, lane, bw, v);
+        __syncwarp();
+        const uint64_t pay = 64ull * bw * g;
+        if (pay + 64ull * bw <= avail) {
+          uint4* dst = reinterpret_cast<uint4*>(base + pay);
+          const uint4* src = reinterpret_cast<const uint4*>(out_stage);
+          for (int t = lane; t < 4 * bw; t += 32) dst[t] = src[t];
+        } else if (lane == 0) {
+          set_error(ctl, MS_ERR_NOMEM, g);
+        }
+      } else {  // horizontal tail
+        uint32_t* w32 = reinterpret_cast<uint32_t*>(out_stage);
+        for (int t = lane; t < 1024; t += 32) w32[t] = 0;
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          const int t = 16 * lane + k;
+          if (t < valid && v[k]) {
+            const uint64_t bit = (uint64_t)t * bw;
+            const int sh = (int)(bit & 31);
+            const uint64_t x = v[k];
+            int wi = (int)(bit >> 5);
+            atomicOr(w32 + wi, (uint32_t)(x << sh));
+            uint64_t rest = (sh == 0) ? (x >> 32) : (x >> (32 - sh));
+            int have = 32 - sh;
+            while (have < bw && rest) {
+              atomicOr(w32 + (++wi), (uint32_t)rest);
+              rest >>= 32;
+              have += 32;
+            }
+          }
+        }
+        __syncwarp();
+        const uint64_t pay = 64ull * bw * static_chunks;
+        const int nw = (int)(((uint64_t)valid * bw + 63) / 64);
+        if (pay + 8ull * nw <= avail) {
+          uint64_t* dst = reinterpret_cast<uint64_t*>(base + pay);
+          const uint64_t* src = reinterpret_cast<const uint64_t*>(out_stage);
+          for (int t = lane; t < nw; t += 32) dst[t] = src[t];
+        } else if (lane == 0) {
+          set_error(ctl, MS_ERR_NOMEM, g);
+        }
+      }
+    } else if (valid > 0) {  // uncompressed output (arena column or caller buffer)
+      const uint64_t pay = 8ull * kBlock * g;
+      if (pay + 8ull * valid <= avail) {
+        uint64_t* dst = reinterpret_cast<uint64_t*>(base + pay);
+        if (valid == kBlock) {
+          uint4* stg = reinterpret_cast<uint4*>(out_stage);
+#pragma unroll
+          for (int cc = 0; cc < 8; cc++)
+            stg[lane * 8 + (cc ^ (lane & 7))] = make_uint4((uint32_t)v[2 * cc], (uint32_t)(v[2 * cc] >> 32),
+                                                          (uint32_t)v[2 * cc + 1], (uint32_t)(v[2 * cc + 1] >> 32));
+          __syncwarp();
+#pragma unroll
+          for (int it = 0; it < 8; it++) {
+            const int ci = lane + 32 * it, L = ci >> 3, cc = ci & 7;
+            reinterpret_cast<uint4*>(dst)[ci] = stg[L * 8 + (cc ^ (L & 7))];
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; k++)
+            if (16 * lane + k < valid) dst[16 * lane + k] = v[k];
+        }
+      } else if (lane == 0) {
+        set_error(ctl, MS_ERR_NOMEM, g);
+      }
+    }
+}
+
+// Epilogue of a staged producer: the last CTA to finish records the output column
+// (fixed-offset formats are complete here; block formats are completed by the
+// placement pass).  Every thread of every CTA calls it.
+MS_DEV void publish_staged(const ProduceArgs& a, uint64_t n_out, int fmt, int bw, bool blockfmt, uint8_t* base,
+                           uint64_t top, uint64_t avail) {
+  DevCtl* ctl = a.ctl;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&ctl->done, 1u);
+    if (prev == gridDim.x - 1) {
+      __threadfence();
+      DevMeta* m = a.out_meta;
+      m->n = n_out;
+      m->ptr = reinterpret_cast<uint64_t>(base);
+      m->fmt = (uint32_t)fmt;
+      m->bw = (uint32_t)(fmt == MS_STATIC_BP ? bw : 0);
+      m->nb = blockfmt ? n_out / kBlock : 0;
+      if (!blockfmt) {
+        const uint64_t size = fmt == MS_UNCOMPR ? 8 * n_out : 8 * ((n_out * (uint64_t)bw + 63) / 64);
+        m->size = size;
+        m->pwords = 0;
+        const uint64_t grow = (size + 255) / 256 * 256;
+        if (size > avail) {
+          // the column did not fit: publish it empty so no reader leaves the arena
+          set_error(ctl, MS_ERR_NOMEM, size);
+          m->n = 0;
+          m->size = 0;
+          m->nb = 0;
+        } else {
+          ctl->top = top + grow;
+          if (top + grow > ctl->high) ctl->high = top + grow;
+        }
+      }
+      ctl->done = 0;
+      __threadfence();
+    }
+  }
+}
+
 // Warp-independent producing kernel.  Every warp streams its own chunks (chunk
 // gw, gw + W, ... for warp gw of W), runs the operator and encodes each output
 // block.  Uncompressed and static-BP outputs have fixed offsets and are stored in
@@ -1625,151 +1771,25 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
       } else if constexpr (OP == OP_PROJECT) {  // c0 = data, st0 streams the positions (c1)
         uint64_t p[16];
         valid = st0.decode(i, p, ctl);
+        __syncwarp();
         if (cta_gather) gather_cta<false>(a, c0, p, valid, warp, lane, v, pcta, (uint64_t*)nullptr);
-        else gather_random(a, c0, p, valid, lane, v);
-      } else {  // OP_PROJECT_DELTA
+        else project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
+      } else {  // OP_PROJECT_DELTA: per-warp block decode (no CTA tile)
         uint64_t p[16];
         valid = st0.decode(i, p, ctl);
-        gather_cta<true>(a, c0, p, valid, warp, lane, v, pcta, sm->aux);
+        __syncwarp();
+        project_delta(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage), sm->aux);
       }
       __syncwarp();
     }
-    if (blockfmt) {
-      uint4* slot = reinterpret_cast<uint4*>(a.stage + 4096 * g);
-      if (valid == kBlock) {
-        uint64_t ref;
-        const int b = encode_block(fmt, v, lane, &ref);
-        write_lane_stream(out_stage, lane, b, v);
-        __syncwarp();
-        const uint4* src = reinterpret_cast<const uint4*>(out_stage);
-        for (int t = lane; t < 4 * b; t += 32) slot[t] = src[t];
-        if (lane == 0) {
-          a.stage_meta[2 * g] = (uint64_t)b;
-          a.stage_meta[2 * g + 1] = ref;
-        }
-      } else if (valid > 0) {  // remainder: raw values, placed behind the payload later
-        uint64_t* dst = reinterpret_cast<uint64_t*>(slot);
-#pragma unroll
-        for (int k = 0; k < 16; k++)
-          if (16 * lane + k < valid) dst[16 * lane + k] = v[k];
-      }
-    } else if (fmt == MS_STATIC_BP) {
-      uint64_t o = 0;
-#pragma unroll
-      for (int k = 0; k < 16; k++) o |= (16 * lane + k < valid) ? v[k] : 0;
-      o = warp_or(o);
-      if (bw64(o) > bw && lane == 0) set_error(ctl, MS_ERR_VALUE_TOO_WIDE, g);
-      const uint64_t mask = lowmask(bw);
-#pragma unroll
-      for (int k = 0; k < 16; k++) v[k] &= mask;
-      if (g < static_chunks) {
-        write_lane_stream(out_stage, lane, bw, v);
-        __syncwarp();
-        const uint64_t pay = 64ull * bw * g;
-        if (pay + 64ull * bw <= avail) {
-          uint4* dst = reinterpret_cast<uint4*>(base + pay);
-          const uint4* src = reinterpret_cast<const uint4*>(out_stage);
-          for (int t = lane; t < 4 * bw; t += 32) dst[t] = src[t];
-        } else if (lane == 0) {
-          set_error(ctl, MS_ERR_NOMEM, g);
-        }
-      } else {  // horizontal tail
-        uint32_t* w32 = reinterpret_cast<uint32_t*>(out_stage);
-        for (int t = lane; t < 1024; t += 32) w32[t] = 0;
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < 16; k++) {
-          const int t = 16 * lane + k;
-          if (t < valid && v[k]) {
-            const uint64_t bit = (uint64_t)t * bw;
-            const int sh = (int)(bit & 31);
-            const uint64_t x = v[k];
-            int wi = (int)(bit >> 5);
-            atomicOr(w32 + wi, (uint32_t)(x << sh));
-            uint64_t rest = (sh == 0) ? (x >> 32) : (x >> (32 - sh));
-            int have = 32 - sh;
-            while (have < bw && rest) {
-              atomicOr(w32 + (++wi), (uint32_t)rest);
-              rest >>= 32;
-              have += 32;
-            }
-          }
-        }
-        __syncwarp();
-        const uint64_t pay = 64ull * bw * static_chunks;
-        const int nw = (int)(((uint64_t)valid * bw + 63) / 64);
-        if (pay + 8ull * nw <= avail) {
-          uint64_t* dst = reinterpret_cast<uint64_t*>(base + pay);
-          const uint64_t* src = reinterpret_cast<const uint64_t*>(out_stage);
-          for (int t = lane; t < nw; t += 32) dst[t] = src[t];
-        } else if (lane == 0) {
-          set_error(ctl, MS_ERR_NOMEM, g);
-        }
-      }
-    } else if (valid > 0) {  // uncompressed output (arena column or caller buffer)
-      const uint64_t pay = 8ull * kBlock * g;
-      if (pay + 8ull * valid <= avail) {
-        uint64_t* dst = reinterpret_cast<uint64_t*>(base + pay);
-        if (valid == kBlock) {
-          uint4* stg = reinterpret_cast<uint4*>(out_stage);
-#pragma unroll
-          for (int cc = 0; cc < 8; cc++)
-            stg[lane * 8 + (cc ^ (lane & 7))] = make_uint4((uint32_t)v[2 * cc], (uint32_t)(v[2 * cc] >> 32),
-                                                          (uint32_t)v[2 * cc + 1], (uint32_t)(v[2 * cc + 1] >> 32));
-          __syncwarp();
-#pragma unroll
-          for (int it = 0; it < 8; it++) {
-            const int ci = lane + 32 * it, L = ci >> 3, cc = ci & 7;
-            reinterpret_cast<uint4*>(dst)[ci] = stg[L * 8 + (cc ^ (L & 7))];
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < 16; k++)
-            if (16 * lane + k < valid) dst[16 * lane + k] = v[k];
-        }
-      } else if (lane == 0) {
-        set_error(ctl, MS_ERR_NOMEM, g);
-      }
-    }
+    store_staged(a, fmt, bw, blockfmt, g, v, valid, out_stage, base, avail, static_chunks, ctl, lane);
     __syncwarp();
   }
   cp_async_wait<0>();
 
-  // ---- epilogue: the last CTA to finish records the output length; fixed-offset
-  // formats are complete here, block formats are completed by k_copy_blocks.
+  // ---- epilogue: the last CTA to finish records the output column
   if (raw) return;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned prev = atomicAdd(&ctl->done, 1u);
-    if (prev == gridDim.x - 1) {
-      __threadfence();
-      DevMeta* m = a.out_meta;
-      m->n = n_out;
-      m->ptr = reinterpret_cast<uint64_t>(base);
-      m->fmt = (uint32_t)fmt;
-      m->bw = (uint32_t)(fmt == MS_STATIC_BP ? bw : 0);
-      m->nb = blockfmt ? n_out / kBlock : 0;
-      if (!blockfmt) {
-        const uint64_t size = fmt == MS_UNCOMPR ? 8 * n_out : 8 * ((n_out * (uint64_t)bw + 63) / 64);
-        m->size = size;
-        m->pwords = 0;
-        const uint64_t grow = (size + 255) / 256 * 256;
-        if (size > avail) {
-          // the column did not fit: publish it empty so no reader leaves the arena
-          set_error(ctl, MS_ERR_NOMEM, size);
-          m->n = 0;
-          m->size = 0;
-          m->nb = 0;
-        } else {
-          ctl->top = top + grow;
-          if (top + grow > ctl->high) ctl->high = top + grow;
-        }
-      }
-      ctl->done = 0;
-      __threadfence();
-    }
-  }
+  publish_staged(a, n_out, fmt, bw, blockfmt, base, top, avail);
 }
 
 // Placement of a staged block-format column, step 1: the exclusive scan of the
