@@ -28,7 +28,8 @@ constexpr int kSpanSlots = 2;
 constexpr int kSpanTouch = 1024;                // touched data blocks per tile, at most
 constexpr uint32_t kRemBlock = 0xffu;           // width tag of a block past the packed part
 
-struct SpanCta {
+// 16-byte aligned size: the per-warp buffers behind it take 16-byte accesses
+struct alignas(16) SpanCta {
   uint8_t slot[kSpanSlots][kSpanPiece];
   uint64_t ref[kSpanTouch];         // reference of each touched block (FOR), else 0
   uint32_t info[kSpanTouch];        // (halfword offset of the block in its slot << 8) | width
@@ -54,6 +55,8 @@ struct SpanWarp {
 };
 
 constexpr size_t kSpanSmemBytes = sizeof(SpanCta) + kWarps * sizeof(SpanWarp);
+static_assert(sizeof(SpanCta) % 16 == 0 && sizeof(SpanWarp) % 16 == 0, "16-byte aligned warp buffers");
+static_assert(kSpanSmemBytes + 1024 <= 228 * 1024 / 2, "two CTAs per SM");
 
 // CTA-wide exclusive scan of one value per thread (kThreads threads).  Returns the
 // thread's exclusive prefix; *total receives the sum.
