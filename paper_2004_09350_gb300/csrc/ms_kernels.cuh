@@ -1691,7 +1691,7 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
   // count, since the gather synchronises the CTA.  A project from uncompressed data
   // reads at random: each warp takes a contiguous segment of output chunks so that
   // its reads move forward through the data column.
-  const bool cta_gather = kProject && c0.fmt != MS_UNCOMPR;
+  const bool cta_gather = OP == OP_PROJECT && c0.fmt != MS_UNCOMPR;
   const uint64_t seg = (nch + W - 1) / W;
   const bool segmented = kProject && !cta_gather;
   const uint64_t first = segmented ? gw * seg : gw, stride = segmented ? 1 : W;
@@ -1728,7 +1728,7 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
   }
 
   auto* pcta = reinterpret_cast<typename ProducePlan<OP>::Cta*>(smem_raw + sizeof(Smem) * kWarps);
-  if constexpr (kProject) {
+  if constexpr (OP == OP_PROJECT) {  // the CTA span copy's shared state (only OP_PROJECT has it)
     // piece headers start zeroed: a slot that a corrupt chain skips then reads as an
     // empty block at offset 0, never as an offset outside the buffer
     for (int t = threadIdx.x; t < kCtaHdr; t += blockDim.x) pcta->hdr[t] = make_uint4(0, 0, 0, 0);
@@ -1774,11 +1774,12 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
         __syncwarp();
         if (cta_gather) gather_cta<false>(a, c0, p, valid, warp, lane, v, pcta, (uint64_t*)nullptr);
         else project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
-      } else {  // OP_PROJECT_DELTA: per-warp block decode (no CTA tile)
+      } else {  // OP_PROJECT_DELTA: per-warp gather (no CTA tile), DELTA or uncompressed data
         uint64_t p[16];
         valid = st0.decode(i, p, ctl);
         __syncwarp();
-        project_delta(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage), sm->aux);
+        if (c0.fmt == MS_DELTA_BP) project_delta(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage), sm->aux);
+        else project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
       }
       __syncwarp();
     }

@@ -270,11 +270,12 @@ ms_status ms_project(ms_ctx* c, const ms_column* data, const ms_column* pos, int
   ProduceArgs a{};
   a.in0 = c->metas + data->slot;
   a.in1 = c->metas + pos->slot;
-  // DELTA data needs whole-block decoding (prefix sums); DYN / FOR / static-BP data is
-  // streamed by the span gather (MS_PROJECT_CTA=1: the earlier CTA span copy, for
-  // comparison); uncompressed data is read in place
-  if (data->fmt == MS_DELTA_BP) return produce_column<OP_PROJECT_DELTA>(c, a, w, pos->n_max, fmt, bw, out, s);
-  if (data->fmt != MS_UNCOMPR && use_staged_producers() && !getenv("MS_PROJECT_CTA"))
+  // DELTA data needs whole-block decoding (prefix sums) and uncompressed data is read
+  // in place, both by the per-warp gather; DYN / FOR / static-BP data is streamed by
+  // the span gather (MS_PROJECT_CTA=1: the earlier CTA span copy, for comparison)
+  if (data->fmt == MS_DELTA_BP || (data->fmt == MS_UNCOMPR && use_staged_producers()))
+    return produce_column<OP_PROJECT_DELTA>(c, a, w, pos->n_max, fmt, bw, out, s);
+  if (use_staged_producers() && !getenv("MS_PROJECT_CTA"))
     return produce_project_span(c, a, w, pos->n_max, fmt, bw, out, s);
   return produce_column<OP_PROJECT>(c, a, w, pos->n_max, fmt, bw, out, s);
 }
