@@ -729,10 +729,10 @@ def bench_star(args):
     # the compressed base columns, which stay for the end-to-end runs (12 bytes a row)
     ctx = ms.Ctx(local, arena_bytes=8 * 8 * n + 8 * n + 12 * n + (256 << 20), max_rows=n)
     out = {}
-    for label, base_fm, fm in (("compressed", plans.STAR_BASE_COMPRESSED, plans.STAR_COMPRESSED),
-                               ("uncompressed", plans.STAR_BASE_UNCOMPRESSED, plans.STAR_UNCOMPRESSED)):
-        base = {k: ctx.compress(v, base_fm[k]) for k, v in raw.items()}
-        ctx.check(what="star base")
+
+    def run_variant(label, base, fm):
+        """Warm-up, one traced sizing step (sizes, footprint, per-operator times,
+        algorithmic bytes) and the timed steps of the star plan in formats fm."""
         base_bytes = sum(ctx.info(c)["size_bytes"] for c in base.values())
         res = torch.zeros(plans.STAR_GROUPS, dtype=torch.int64, device=dev)
         for _ in range(args.warmup):
@@ -779,16 +779,34 @@ def bench_star(args):
         ctx.check(what=f"star {label} timed steps")
         ms_step = max_over_ranks(evs[0].elapsed_time(evs[-1]) / args.steps, world, dev)
         best = min(evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps))
-        out[label] = {"ms_per_step": round(ms_step, 4), "ms_per_step_best": round(best, 4),
-                      "rows_per_s": job_rows_per_s(world, n, ms_step),
-                      "base_bytes": int(base_bytes), "intermediate_bytes": int(inter_bytes),
-                      "footprint_bytes": int(base_bytes + inter_bytes),
-                      "arena_peak_intermediates": int(high - use0),
-                      "device_peak_bytes": int(base_bytes + (high - use0) + ctx.work_bytes()),
-                      "sums": ms.to_numpy_u64(res).tolist(), "prof": prof, "kernel_bytes": kb,
-                      "clocks": ck_info, "op_ms_sizing_step": op_ms,
-                      "per_kernel_ms": {k: round(v[1] / args.steps, 4) for k, v in prof.items()}}
-        out[label]["_base"] = base
+        return {"ms_per_step": round(ms_step, 4), "ms_per_step_best": round(best, 4),
+                "rows_per_s": job_rows_per_s(world, n, ms_step),
+                "base_bytes": int(base_bytes), "intermediate_bytes": int(inter_bytes),
+                "footprint_bytes": int(base_bytes + inter_bytes),
+                "arena_peak_intermediates": int(high - use0),
+                "device_peak_bytes": int(base_bytes + (high - use0) + ctx.work_bytes()),
+                "sums": ms.to_numpy_u64(res).tolist(), "prof": prof, "kernel_bytes": kb,
+                "clocks": ck_info, "op_ms_sizing_step": op_ms,
+                "per_kernel_ms": {k: round(v[1] / args.steps, 4) for k, v in prof.items()}}
+
+    base_c = {k: ctx.compress(v, plans.STAR_BASE_COMPRESSED[k]) for k, v in raw.items()}
+    ctx.check(what="star base")
+    out["compressed"] = run_variant("compressed", base_c, plans.STAR_COMPRESSED)
+    out["compressed"]["_base"] = base_c
+    # the plan-level format search (Sec. 5.2): greedy per-intermediate runtime choice
+    # over the compressed base columns
+    t_g = time.perf_counter()
+    fm_g, _, evals = plans.greedy_formats(ctx, lambda fm: plans.star_plan(ctx, base_c, fm), plans.STAR_NAMES,
+                                          plans.STAR_COMPRESSED, "time", reps=2)
+    search_s = time.perf_counter() - t_g
+    out["greedy"] = run_variant("greedy", base_c, fm_g)
+    out["greedy"]["formats"] = {k: ms.FORMAT_NAMES[v] for k, v in fm_g.items()}
+    out["greedy"]["search"] = {"evaluations": evals, "seconds": round(search_s, 1)}
+    base_u = {k: ctx.compress(v, plans.STAR_BASE_UNCOMPRESSED[k]) for k, v in raw.items()}
+    ctx.check(what="star base")
+    out["uncompressed"] = run_variant("uncompressed", base_u, plans.STAR_UNCOMPRESSED)
+    out["uncompressed"]["_base"] = base_u
+    assert out["greedy"]["sums"] == out["compressed"]["sums"], "greedy formats change the result"
     assert out["compressed"]["sums"] == out["uncompressed"]["sums"], "star pipelines disagree"
     comp, unc = out["compressed"], out["uncompressed"]
 
@@ -855,9 +873,12 @@ def bench_star(args):
         return None
     clocks = comp.get("clocks")
     launches = int(sum(p["launches_per_step"] for p in per_kernel.values()) * args.steps)
-    for v in (comp, unc):
+    greedy = out["greedy"]
+    for v in (comp, unc, greedy):
         for k in ("sums", "prof", "kernel_bytes", "clocks"):
             v.pop(k, None)
+    greedy["speedup_vs_uncompressed"] = round(unc["ms_per_step"] / greedy["ms_per_step"], 3)
+    greedy["footprint_ratio"] = round(greedy["footprint_bytes"] / unc["footprint_bytes"], 4)
     return {
         "metric": METRIC, "value": comp["rows_per_s"], "unit": "rows/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": comp["ms_per_step"],
@@ -876,7 +897,7 @@ def bench_star(args):
                      "launches_per_step": lps},
         "per_kernel": per_kernel,
         "plan_alg_GBps": round(plan_bytes / (comp["ms_per_step"] * 1e-3) / 1e9, 1),
-        "compressed": comp, "uncompressed": dict(unc, e2e=e2e_unc),
+        "compressed": comp, "uncompressed": dict(unc, e2e=e2e_unc), "compressed_greedy_formats": greedy,
         "speedup_vs_uncompressed": round(unc["ms_per_step"] / comp["ms_per_step"], 3),
         "footprint_ratio": round(comp["footprint_bytes"] / unc["footprint_bytes"], 4),
         "device_peak_ratio": round(comp["device_peak_bytes"] / unc["device_peak_bytes"], 4),

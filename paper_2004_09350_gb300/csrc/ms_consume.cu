@@ -1,8 +1,6 @@
 // ms_consume.cu -- consuming kernels (no output column): the select / semi-join
 // mark step and its count scan, agg_sum, group_sum and the semi-join build side,
 // plus their launchers.
-#include <stdlib.h>
-
 #include "ms_launch.h"
 
 namespace ms {
@@ -88,66 +86,6 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_mark_keys(MarkArgs a) {
     const uint32_t cnt = __reduce_add_sync(kFull, (uint32_t)__popc(m16));
     if (lane == 0) a.counts[g] = cnt;
   });
-}
-
-// Semi-join probe for key bitmaps of up to twice one CTA's shared memory, on a
-// cluster of two CTAs (two SMs): CTA rank r holds half r of the bitmap in its
-// shared memory, and a key in the other half is looked up in the partner's shared
-// memory through the cluster's distributed shared memory (mapa + ld.shared::cluster).
-// Each CTA streams its own claims of the probe column; the probe is read once.
-// Both CTAs pass a cluster barrier after loading their halves (before any remote
-// read) and again before exiting (no CTA leaves while its partner may still read
-// its shared memory).
-constexpr int kPairTileBuf = 32768;
-constexpr size_t kPairTileSmemBytes = sizeof(TileSmem<kPairTileBuf>);
-
-MS_DEV void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-
-__global__ void __launch_bounds__(kTileThreads, 1) k_mark_pair(MarkArgs a, uint32_t half_words) {
-  extern __shared__ __align__(16) uint8_t smem_raw[];
-  const int lane = threadIdx.x & 31;
-  auto* sm = reinterpret_cast<TileSmem<kPairTileBuf>*>(smem_raw);
-  uint32_t* kb = reinterpret_cast<uint32_t*>(smem_raw + kPairTileSmemBytes);
-  uint32_t rank;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(rank));
-  const uint64_t total_words = (a.domain + 31) / 32;
-  const uint64_t w0 = (uint64_t)rank * half_words;
-  const uint64_t nw = w0 < total_words ? min((uint64_t)half_words, total_words - w0) : 0;
-  for (uint64_t i = threadIdx.x; i < half_words; i += blockDim.x) kb[i] = i < nw ? __ldg(a.keybits + w0 + i) : 0u;
-  __syncthreads();
-  cluster_sync();
-  const uint32_t kb_local = smem_u32(kb);
-  uint32_t kb_peer;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(kb_peer) : "r"(kb_local), "r"(rank ^ 1u));
-  const ColView c = view_of(a.in);
-  cta_stream<kPairTileBuf>(c, sm, a.ctl, [&](uint64_t g, const uint64_t* v, int valid, bool) {
-    uint32_t m16 = 0;
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-      const uint64_t x = v[k];
-      const uint64_t wd = x >> 5;
-      const uint32_t h = wd >= half_words ? 1u : 0u;
-      const uint32_t idx = (uint32_t)(wd - (uint64_t)h * half_words);
-      uint32_t word = 0;
-      if (x < a.domain) {
-        if (h == rank) {
-          word = kb[idx];
-        } else {
-          asm volatile("ld.shared::cluster.u32 %0, [%1];\n" : "=r"(word) : "r"(kb_peer + 4 * idx) : "memory");
-        }
-      }
-      m16 |= ((word >> (x & 31)) & 1u) << k;
-    }
-    const int first = 16 * lane;
-    m16 &= valid >= first + 16 ? 0xffffu : (valid > first ? (1u << (valid - first)) - 1u : 0u);
-    a.bitmap[g * 32 + lane] = (uint16_t)m16;
-    const uint32_t cnt = __reduce_add_sync(kFull, (uint32_t)__popc(m16));
-    if (lane == 0) a.counts[g] = cnt;
-  });
-  __syncthreads();
-  cluster_sync();
 }
 
 // Exclusive scan of the per-chunk match counts (decoupled look-back over tiles of
@@ -369,7 +307,6 @@ ms_status launch_stats(ms_ctx* c, const DevMeta* in, uint64_t* d_stats, uint64_t
 
 // Shared memory the key bitmap of a semi-join probe may take per CTA.
 constexpr size_t kKeySmemBudget = 224 * 1024 - kKeyTileSmemBytes;
-constexpr size_t kPairKeyBudget = 226 * 1024 - kPairTileSmemBytes;
 
 ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max, cudaStream_t s) {
   a.bitmap = w.bitmap;
@@ -382,27 +319,6 @@ ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max
     ProfScope ps(c, MS_K_MARK, s);
     k_mark_keys<<<grid, kTileThreads, smem, s>>>(a);
     if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
-  } else if (a.keybits && getenv("MS_SEMIJOIN_PAIR") && key_bytes <= 2 * kPairKeyBudget) {
-    // a bitmap of up to two CTAs' shared memory: split over a cluster of two CTAs
-    const uint32_t half_words = (uint32_t)cdiv(cdiv(a.domain, 32), 2);
-    const size_t smem = kPairTileSmemBytes + 4 * (size_t)half_words;
-    cudaFuncSetAttribute(k_mark_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const uint64_t claims = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kClaim);
-    const int grid = (int)std::max<uint64_t>(2, std::min<uint64_t>((uint64_t)c->sms, claims + (claims & 1)) & ~1ull);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(kTileThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    ProfScope ps(c, MS_K_MARK, s);
-    if (cuda_status(cudaLaunchKernelEx(&cfg, k_mark_pair, a, half_words)) != MS_OK) return MS_ERR_CUDA;
   } else if (a.keybits) {  // a larger key bitmap: probed through L1 and L2 (k_mark_l1)
     const size_t smem = sizeof(TileSmem<kMarkL1Buf>);
     cudaFuncSetAttribute(k_mark_l1, cudaFuncAttributePreferredSharedMemoryCarveout, 25);

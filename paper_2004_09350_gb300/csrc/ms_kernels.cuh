@@ -457,133 +457,10 @@ MS_DEV uint64_t arith(int op, uint64_t x, uint64_t y) {
   return op == MS_ADD ? x + y : op == MS_SUB ? x - y : x * y;
 }
 
-// project core for DELTA data when the positions are unsorted or spread over
-// more than kSpanMaxBlocks blocks: every distinct touched block is decoded once
-// (prefix sums) into `aux` and the positions in it read from there.
-MS_DEV void gather_delta_blocks(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
-                                uint64_t v[16], uint8_t* span, uint64_t* aux) {
-  uint32_t pending = 0;
-#pragma unroll
-  for (int k = 0; k < 16; k++) {
-    v[k] = 0;
-    if (16 * lane + k < valid) {
-      if (p[k] < d.n) pending |= 1u << k;
-      else set_error(a.ctl, MS_ERR_OUT_OF_RANGE, p[k]);
-    }
-  }
-  while (__ballot_sync(kFull, pending) != 0) {
-    uint64_t mb = ~0ull;
-#pragma unroll
-    for (int k = 0; k < 16; k++)
-      if (pending & (1u << k)) mb = min(mb, p[k] / kBlock);
-    const uint64_t B = warp_min(mb);
-    uint64_t t[16];
-    decode_chunk(d, B, lane, t, reinterpret_cast<uint16_t*>(span), a.ctl);
-#pragma unroll
-    for (int k = 0; k < 16; k++) aux[swz(16 * lane + k)] = t[k];
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-      if ((pending & (1u << k)) && p[k] / kBlock == B) {
-        v[k] = aux[swz((int)(p[k] % kBlock))];
-        pending &= ~(1u << k);
-      }
-    }
-    __syncwarp();
-  }
-}
-
-// project core for non-DELTA data: every position is a random read through the
-// header directory (Sec. 4.2 random access, extended to the dynamic formats).
-// Written without data-dependent branches so that a lane's 16 header loads, and
-// then its payload halfword loads, are all in flight together.
-MS_DEV void gather_random(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
-                          uint64_t v[16]) {
-  uint64_t q[16];
-  uint32_t pending = 0;
-#pragma unroll
-  for (int k = 0; k < 16; k++) {
-    const bool in = 16 * lane + k < valid;
-    if (in && p[k] >= d.n) set_error(a.ctl, MS_ERR_OUT_OF_RANGE, p[k]);
-    const bool ok = in && p[k] < d.n;
-    pending |= (uint32_t)ok << k;
-    q[k] = ok ? p[k] : 0;
-  }
-  if (d.n == 0) {
-#pragma unroll
-    for (int k = 0; k < 16; k++) v[k] = 0;
-    return;
-  }
-  if (d.fmt == MS_UNCOMPR) {
-#pragma unroll
-    for (int k = 0; k < 16; k++) v[k] = ldg64(d.p + 8 * q[k]);
-  } else {
-    const uint64_t nb = d.fmt == MS_STATIC_BP ? d.n / kBlock : d.nb;
-    const uint64_t rem_base = d.fmt == MS_STATIC_BP ? 64ull * d.bw * nb : 16 * nb + 8 * d.pwords;
-    uint64_t w0[16], ref[16];
-#pragma unroll
-    for (int k = 0; k < 16; k++) {  // phase 1: the block headers (or the fixed static width)
-      const uint64_t g = q[k] / kBlock;
-      if (d.fmt == MS_STATIC_BP) {
-        w0[k] = ((64ull * d.bw * g / 8) << 8) | (uint64_t)d.bw;  // payload word offset of chunk g
-        ref[k] = 0;
-      } else {
-        const uint64_t gg = min(g, nb ? nb - 1 : 0);
-        w0[k] = nb ? ldg64(d.p + 16 * gg) : 0;
-        ref[k] = nb ? ldg64(d.p + 16 * gg + 8) : 0;
-      }
-    }
-    const uint64_t pay_base = d.fmt == MS_STATIC_BP ? 0 : 16 * nb;
-#pragma unroll
-    for (int half = 0; half < 2; half++) {  // phase 2: payload halfwords, 8 values at a time
-      uint32_t h[8][5];
-#pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const int k = 8 * half + u;
-        const uint64_t g = q[k] / kBlock;
-        const int r = (int)(q[k] % kBlock);
-        const int b = (int)min((uint64_t)64, w0[k] & 255);
-        const int bit0 = (r & 15) * b, j = r >> 4;
-        const uint64_t pay = pay_base + 8 * (w0[k] >> 8);
-        const bool ok = g < nb && b > 0 && pay + 64ull * b <= d.size;
-        const uint16_t* hw = reinterpret_cast<const uint16_t*>(d.p + (ok ? pay : 0));
-        const int q0 = bit0 >> 4;
-        const int nq = ok ? (((bit0 & 15) + b + 15) >> 4) : 0;
-#pragma unroll
-        for (int t = 0; t < 5; t++) h[u][t] = t < nq ? (uint32_t)__ldg(hw + 32 * (q0 + t) + j) : 0u;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const int k = 8 * half + u;
-        const uint64_t g = q[k] / kBlock;
-        const int r = (int)(q[k] % kBlock);
-        const int b = (int)min((uint64_t)64, w0[k] & 255);
-        const int sh = ((r & 15) * b) & 15;
-        uint64_t lo = (uint64_t)h[u][0] | ((uint64_t)h[u][1] << 16) | ((uint64_t)h[u][2] << 32) |
-                      ((uint64_t)h[u][3] << 48);
-        uint64_t x = (lo >> sh) | (sh ? ((uint64_t)h[u][4] << (64 - sh)) : 0);
-        x = (x & lowmask(b)) + ref[k];
-        if (g >= nb) {  // remainder (or the horizontal static-BP tail)
-          if (d.fmt == MS_STATIC_BP) {
-            const uint64_t bit = (uint64_t)r * d.bw;
-            const int s2 = (int)(bit & 63);
-            const uint64_t at = rem_base + 8 * (bit >> 6);
-            uint64_t y = at + 8 <= d.size ? ldg64(d.p + at) >> s2 : 0;
-            if (s2 + d.bw > 64 && at + 16 <= d.size) y |= ldg64(d.p + at + 8) << (64 - s2);
-            x = y & lowmask(d.bw);
-          } else {
-            const uint64_t at = rem_base + 8 * (uint64_t)r;
-            x = at + 8 <= d.size ? ldg64(d.p + at) : 0;
-          }
-        }
-        v[k] = (pending >> k) & 1u ? x : 0;
-      }
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 16; k++)
-    if (!((pending >> k) & 1u)) v[k] = 0;
-}
+// project core for non-DELTA data read in place (defined with the other project
+// cores below); the CTA span gather falls back to it.
+MS_DEV void project_direct(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
+                           uint64_t v[16], uint64_t* stage);
 
 // emit core: positions of output block g (lane-blocked) from the match bitmap.
 MS_DEV int emit_gather(const ProduceArgs& a, uint64_t n_out, uint64_t g, int lane, uint64_t v[16], SmemEmit* sm) {
@@ -659,9 +536,9 @@ MS_DEV int emit_gather(const ProduceArgs& a, uint64_t n_out, uint64_t g, int lan
 // load.  Unsorted, out-of-range or sparse positions (fewer positions than blocks
 // spanned) and uncompressed data go through the per-warp random path.  Every
 // thread of the CTA calls this once per tile (it synchronises the CTA).
-template <bool kDelta, class Cta>
+template <class Cta>
 MS_DEV void gather_cta(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int warp, int lane,
-                       uint64_t v[16], Cta* cs, uint64_t* aux) {
+                       uint64_t v[16], Cta* cs) {
   constexpr int kCtaBuf = Cta::kBuf;
   const int tid = threadIdx.x;
   const int nv = max(0, min(16, valid - 16 * lane));
@@ -705,12 +582,8 @@ MS_DEV void gather_cta(const ProduceArgs& a, const ColView& d, const uint64_t p[
   const uint64_t B_lo = lo >> 9, B_hi = hi >> 9;
   tile_ok &= any && B_hi - B_lo + 1 <= npos;
   __syncthreads();  // every thread has read the summaries
-  if (!tile_ok) {
-    if constexpr (kDelta) {
-      gather_delta_blocks(a, d, p, valid, lane, v, cs->buf + 4096 * warp, aux);
-    } else {
-      gather_random(a, d, p, valid, lane, v);
-    }
+  if (!tile_ok) {  // gather in place, striped (the warp's 4 KB of the CTA buffer as its stage)
+    project_direct(a, d, p, valid, lane, v, reinterpret_cast<uint64_t*>(cs->buf + 4096 * warp));
     __syncthreads();
     return;
   }
@@ -811,46 +684,7 @@ MS_DEV void gather_cta(const ProduceArgs& a, const ColView& d, const uint64_t p[
     __syncthreads();
 #endif
     const uint32_t lo_r = (uint32_t)(lo_blk - B_lo);  // the piece's first block, tile-relative
-    if constexpr (kDelta) {
-      uint32_t pend = 0;
-#pragma unroll
-      for (int k = 0; k < 16; k++) pend |= (uint32_t)((rel[k] >> 9) - lo_r < (uint32_t)cnt) << k;
-      while (__ballot_sync(kFull, pend) != 0) {
-        uint32_t mb = ~0u;
-#pragma unroll
-        for (int k = 0; k < 16; k++)
-          if (pend & (1u << k)) mb = min(mb, rel[k] >> 9);
-        const uint32_t B = __reduce_min_sync(kFull, mb);
-        const uint4 h = cs->hdr[B - lo_r];
-        const uint64_t rr = cs->ref[B - lo_r];
-        uint64_t t[16];
-        if (2 * h.x + 64 * h.y > bytes) {  // never read past the copy
-          if (lane == 0) set_error(a.ctl, MS_ERR_FORMAT, B_lo + B);
-#pragma unroll
-          for (int k = 0; k < 16; k++) t[k] = 0;
-        } else {
-          read_lane_stream(reinterpret_cast<const uint16_t*>(cs->buf) + h.x, lane, (int)h.y, t);
-        }
-        uint64_t sum = 0;
-#pragma unroll
-        for (int k = 0; k < 16; k++) {
-          sum += t[k];
-          t[k] = sum;
-        }
-        const uint64_t excl = warp_excl_scan(sum, lane) + rr;
-#pragma unroll
-        for (int k = 0; k < 16; k++) aux[swz(16 * lane + k)] = t[k] + excl;
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < 16; k++) {
-          if ((pend & (1u << k)) && (rel[k] >> 9) == B) {
-            v[k] = aux[swz((int)(rel[k] & 511))];
-            pend &= ~(1u << k);
-          }
-        }
-        __syncwarp();
-      }
-    } else {
+    {
       // Value r of a block is bits [kk*b, kk*b + b) of lane stream j = r/16 (kk = r%16),
       // and stream halfword i of lane j is payload halfword 32i + j.  Five halfwords
       // cover a value of up to 64 bits at any of the 16 bit phases; the bits past the
@@ -1772,7 +1606,7 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
         uint64_t p[16];
         valid = st0.decode(i, p, ctl);
         __syncwarp();
-        if (cta_gather) gather_cta<false>(a, c0, p, valid, warp, lane, v, pcta, (uint64_t*)nullptr);
+        if (cta_gather) gather_cta(a, c0, p, valid, warp, lane, v, pcta);
         else project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
       } else {  // OP_PROJECT_DELTA: per-warp gather (no CTA tile), DELTA or uncompressed data
         uint64_t p[16];

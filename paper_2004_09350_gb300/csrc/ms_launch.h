@@ -84,10 +84,6 @@ ms_status launch_direct<OP_EMIT>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cuda
 template <>
 ms_status launch_direct<OP_PROJECT_DELTA>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
 
-// project from DYN / FOR / static-BP data by span streaming (ms_map_project.cu):
-// staged output, placed by launch_place
-ms_status launch_project_span(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
-
 // placement of a staged block-format output (ms_place.cu)
 ms_status launch_place(ms_ctx* c, const Work& w, DevMeta* out, uint64_t n_max, cudaStream_t s);
 

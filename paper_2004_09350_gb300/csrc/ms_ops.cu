@@ -134,28 +134,6 @@ ms_status produce_column(ms_ctx* c, ProduceArgs& a, const Work& w, uint64_t n_ma
   return MS_OK;
 }
 
-// project from DYN / FOR / static-BP data: the span-streaming gather into the stage,
-// then placement.
-ms_status produce_project_span(ms_ctx* c, ProduceArgs& a, const Work& w, uint64_t n_max, int fmt, int bw,
-                               ms_column** out, cudaStream_t s) {
-  ms_column* col = new_arena_column(c, fmt, bw, n_max);
-  if (!col) return MS_ERR_NOMEM;
-  a.ctl = c->ctl;
-  a.out_meta = c->metas + col->slot;
-  a.fmt = fmt;
-  a.bw = fmt == MS_STATIC_BP ? bw : 0;
-  a.stage = w.stage;
-  a.stage_meta = w.stage_meta;
-  ms_status st = launch_project_span(c, a, n_max, s);
-  if (st == MS_OK && fmt >= MS_DYN_BP) st = launch_place(c, w, a.out_meta, n_max, s);
-  if (st != MS_OK) {
-    drop_new_column(c, col);
-    return st;
-  }
-  *out = col;
-  return MS_OK;
-}
-
 // Second step of select / semi-join: match bitmap -> positions column.
 ms_status emit_positions(ms_ctx* c, const Work& w, uint64_t n_max, int fmt, int bw, ms_column** out,
                          cudaStream_t s) {
@@ -271,12 +249,10 @@ ms_status ms_project(ms_ctx* c, const ms_column* data, const ms_column* pos, int
   a.in0 = c->metas + data->slot;
   a.in1 = c->metas + pos->slot;
   // DELTA data needs whole-block decoding (prefix sums) and uncompressed data is read
-  // in place, both by the per-warp gather; DYN / FOR / static-BP data is streamed by
-  // the span gather (MS_PROJECT_CTA=1: the earlier CTA span copy, for comparison)
+  // in place, both by the per-warp gather; DYN / FOR / static-BP data goes through
+  // the CTA span gather (sorted positions) or is read in place
   if (data->fmt == MS_DELTA_BP || (data->fmt == MS_UNCOMPR && use_staged_producers()))
     return produce_column<OP_PROJECT_DELTA>(c, a, w, pos->n_max, fmt, bw, out, s);
-  if (use_staged_producers() && !getenv("MS_PROJECT_CTA"))
-    return produce_project_span(c, a, w, pos->n_max, fmt, bw, out, s);
   return produce_column<OP_PROJECT>(c, a, w, pos->n_max, fmt, bw, out, s);
 }
 
