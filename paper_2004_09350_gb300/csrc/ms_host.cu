@@ -80,7 +80,7 @@ ms_status ensure_work(ms_ctx* c, uint64_t bytes) {
   if (bytes <= c->work_cap) return MS_OK;
   if (cuda_status(cudaDeviceSynchronize()) != MS_OK) return MS_ERR_CUDA;
   dev_free(c, c->work);
-  uint64_t cap = std::max(bytes, c->work_cap * 2);
+  const uint64_t cap = bytes;  // exactly what the longest column asks for: no slack
   c->work = static_cast<uint8_t*>(dev_alloc(c, cap));
   if (!c->work) {
     c->work_cap = 0;

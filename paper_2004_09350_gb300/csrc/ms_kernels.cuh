@@ -339,7 +339,7 @@ MS_DEV void stream_pairs(const ColView& c0, const ColView& c1, uint64_t n, uint6
 
 // ------------------------------------------------------- produce (map) kernel
 
-enum ProduceOp { OP_COMPRESS = 0, OP_DECOMPRESS = 1, OP_PROJECT = 2, OP_CALC = 3, OP_EMIT = 4, OP_PROJECT_DELTA = 5 };
+enum ProduceOp { OP_COMPRESS = 0, OP_DECOMPRESS = 1, OP_PROJECT = 2, OP_CALC = 3, OP_EMIT = 4, OP_PROJECT_WARP = 5 };
 
 struct ProduceArgs {
   DevCtl* ctl;
@@ -435,7 +435,7 @@ struct ProducePlan {
       typename std::conditional<
           OP == OP_PROJECT, SmemProjectRandom,
           typename std::conditional<
-              OP == OP_PROJECT_DELTA, SmemProjectDelta,
+              OP == OP_PROJECT_WARP, SmemProjectDelta,
               typename std::conditional<OP == OP_EMIT, SmemEmit, SmemSingle>::type>::type>::type>::type;
   static constexpr int kMinBlocks = OP == OP_PROJECT ? MS_PROJECT_MIN_BLOCKS : (OP == OP_CALC ? 1 : 2);
   // CTA-shared shared memory behind the per-warp plans (the CTA span copy of project)
@@ -448,7 +448,7 @@ template <int OP>
 MS_DEV uint64_t produce_n(const ProduceArgs& a) {
   if (OP == OP_COMPRESS) return a.raw_n;
   if (OP == OP_DECOMPRESS) return min(a.in0->n, a.raw_cap);
-  if (OP == OP_PROJECT || OP == OP_PROJECT_DELTA) return a.in1->n;
+  if (OP == OP_PROJECT || OP == OP_PROJECT_WARP) return a.in1->n;
   if (OP == OP_CALC) return a.in1 ? min(a.in0->n, a.in1->n) : a.in0->n;
   return *reinterpret_cast<volatile uint64_t*>(&a.ctl->op_n);  // OP_EMIT
 }
@@ -1007,7 +1007,7 @@ struct DirectPlan {
       typename std::conditional<
           OP == OP_PROJECT, DSmemProject,
           typename std::conditional<
-              OP == OP_PROJECT_DELTA, DSmemProjectDelta,
+              OP == OP_PROJECT_WARP, DSmemProjectDelta,
               typename std::conditional<OP == OP_EMIT, SmemEmit, DSmemSingle>::type>::type>::type>::type;
   static constexpr int kMinBlocks = 2;
 };
@@ -1017,7 +1017,7 @@ struct DirectPlan {
 template <int OP>
 __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produce(ProduceArgs a) {
   using Smem = typename DirectPlan<OP>::Smem;
-  constexpr bool kProject = OP == OP_PROJECT || OP == OP_PROJECT_DELTA;
+  constexpr bool kProject = OP == OP_PROJECT || OP == OP_PROJECT_WARP;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ uint64_t s_words[2][kWarps];  // by tile parity: payload words of each warp's block
   __shared__ uint64_t s_agg[2];
@@ -1170,10 +1170,12 @@ __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produc
         valid = st0.decode(i, p, ctl);
         __syncwarp();
         project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
-      } else if constexpr (OP == OP_PROJECT_DELTA) {
+      } else if constexpr (OP == OP_PROJECT_WARP) {
         uint64_t p[16];
         valid = st0.decode(i, p, ctl);
-        project_delta(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage), sm->aux);
+        __syncwarp();
+        if (c0.fmt == MS_DELTA_BP) project_delta(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage), sm->aux);
+        else project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
       }
       __syncwarp();
     }
@@ -1506,7 +1508,7 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
 
   ColView c0{}, c1{};
   if (OP == OP_COMPRESS) c0 = view_raw(a.raw_in, a.raw_n);
-  constexpr bool kProject = OP == OP_PROJECT || OP == OP_PROJECT_DELTA;
+  constexpr bool kProject = OP == OP_PROJECT || OP == OP_PROJECT_WARP;
   if (OP == OP_DECOMPRESS || OP == OP_CALC || kProject) c0 = view_of(a.in0);
   if ((OP == OP_CALC || kProject) && a.in1) c1 = view_of(a.in1);
   const uint64_t n_out = produce_n<OP>(a);
@@ -1608,7 +1610,7 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
         __syncwarp();
         if (cta_gather) gather_cta(a, c0, p, valid, warp, lane, v, pcta);
         else project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
-      } else {  // OP_PROJECT_DELTA: per-warp gather (no CTA tile), DELTA or uncompressed data
+      } else {  // OP_PROJECT_WARP: per-warp gather (no CTA tile): DELTA data by block decode, others in place
         uint64_t p[16];
         valid = st0.decode(i, p, ctl);
         __syncwarp();

@@ -65,7 +65,7 @@ ms_status launch_map<OP_CALC>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStr
 template <>
 ms_status launch_map<OP_EMIT>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
 template <>
-ms_status launch_map<OP_PROJECT_DELTA>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
+ms_status launch_map<OP_PROJECT_WARP>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
 
 // producers with in-kernel placement (ms_map_*.cu): one k_produce<OP> launch that
 // writes every output block at its final offset (decoupled look-back over tiles)
@@ -82,7 +82,7 @@ ms_status launch_direct<OP_CALC>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cuda
 template <>
 ms_status launch_direct<OP_EMIT>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
 template <>
-ms_status launch_direct<OP_PROJECT_DELTA>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
+ms_status launch_direct<OP_PROJECT_WARP>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
 
 // placement of a staged block-format output (ms_place.cu)
 ms_status launch_place(ms_ctx* c, const Work& w, DevMeta* out, uint64_t n_max, cudaStream_t s);

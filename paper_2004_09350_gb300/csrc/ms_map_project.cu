@@ -1,4 +1,4 @@
-// ms_map_project.cu -- k_map instantiation(s): OP_PROJECT (random access) and OP_PROJECT_DELTA (compiled on its own for build parallelism).
+// ms_map_project.cu -- k_map instantiations of project: OP_PROJECT (the CTA span gather) and OP_PROJECT_WARP (the per-warp gather), compiled on their own for build parallelism.
 #include "ms_launch.h"
 
 namespace ms {
@@ -9,8 +9,8 @@ ms_status launch_map<OP_PROJECT>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cuda
 }
 
 template <>
-ms_status launch_map<OP_PROJECT_DELTA>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
-  return launch_map_impl<OP_PROJECT_DELTA>(c, a, n_max, s);
+ms_status launch_map<OP_PROJECT_WARP>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
+  return launch_map_impl<OP_PROJECT_WARP>(c, a, n_max, s);
 }
 
 
@@ -20,7 +20,7 @@ ms_status launch_direct<OP_PROJECT>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, c
 }
 
 template <>
-ms_status launch_direct<OP_PROJECT_DELTA>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
-  return launch_direct_impl<OP_PROJECT_DELTA>(c, a, n_max, s);
+ms_status launch_direct<OP_PROJECT_WARP>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
+  return launch_direct_impl<OP_PROJECT_WARP>(c, a, n_max, s);
 }
 }  // namespace ms

@@ -249,10 +249,13 @@ ms_status ms_project(ms_ctx* c, const ms_column* data, const ms_column* pos, int
   a.in0 = c->metas + data->slot;
   a.in1 = c->metas + pos->slot;
   // DELTA data needs whole-block decoding (prefix sums) and uncompressed data is read
-  // in place, both by the per-warp gather; DYN / FOR / static-BP data goes through
-  // the CTA span gather (sorted positions) or is read in place
-  if (data->fmt == MS_DELTA_BP || (data->fmt == MS_UNCOMPR && use_staged_producers()))
-    return produce_column<OP_PROJECT_DELTA>(c, a, w, pos->n_max, fmt, bw, out, s);
+  // in place, both by the per-warp gather.  DYN / FOR / static-BP data goes through the
+  // CTA span gather when the positions are a DELTA column (sorted position lists are
+  // kept as DELTA); other position columns (values used as keys, in any order) are
+  // read in place by the per-warp gather, which keeps more warps per SM.  Both paths
+  // give the same values for any positions.
+  if (data->fmt == MS_DELTA_BP || (use_staged_producers() && (data->fmt == MS_UNCOMPR || pos->fmt != MS_DELTA_BP)))
+    return produce_column<OP_PROJECT_WARP>(c, a, w, pos->n_max, fmt, bw, out, s);
   return produce_column<OP_PROJECT>(c, a, w, pos->n_max, fmt, bw, out, s);
 }
 
