@@ -60,9 +60,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=2020)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["star", "sweep-plan", "selector", "batch", "kernel"], default="star",
+    ap.add_argument("--workload", choices=["star", "sweep-plan", "sweep-table", "selector", "batch", "kernel"],
+                    default="star",
                     help="star: the star-schema plan on a 6e8-row fact table (default); "
                          "sweep-plan: the 2^28-row select/project/calc/sum plan; "
+                         "sweep-table: every operator of that plan for every input/output format pair; "
                          "selector: train the learned format selector on engine traces and measure its regret; "
                          "batch: 4096 select->project->agg_sum fragments in one persistent launch; "
                          "kernel: one operator of the plan alone (--kernel), the case the ncu summaries use")
@@ -1204,6 +1206,98 @@ def bench_batch(args):
     }
 
 
+# ------------------------------------------------------------ format sweep table
+
+def bench_sweep_table(args):
+    """The format sweep at --rows (default 2^28): every operator of the plain plan for
+    every input/output format pair, timed on its own (CUDA events, mean of --steps
+    after 3 warm-ups): select X < c for X in 5 formats x positions in 5 formats at
+    selectivities 0.1%, 10%, 90%; the specialized select on packed X; project X at
+    the 10% positions (DELTA) for 5 data x 5 output formats, and uncompressed X at
+    positions in 5 formats; calc X' * K' with both inputs in one of 5 formats x 5
+    output formats; agg_sum of X in 5 formats.  Reports ms and logical rows/s
+    (select, agg_sum: X's rows; project, calc: output rows)."""
+    import torch
+    from paper_2004_09350_gb300 import morphstore as ms
+
+    n = args.rows
+    x, k, _ = make_inputs(n, args.seed, 0.1)
+    from paper_2004_09350_gb300 import synth
+    dev = torch.device("cuda", 0)
+    ctx = ms.Ctx(0, arena_bytes=int(14 * 8 * n) + (1 << 30), max_rows=n)
+    bx = max(1, int(x.max()).bit_length())
+    bk = max(1, int(k.max()).bit_length())
+    F = list(range(5))
+    dx, dk = ms.as_device_u64(x, dev), ms.as_device_u64(k, dev)
+    X = {f: ctx.compress(dx, f, bx if f == ms.STATIC_BP else 0) for f in F}
+    K = {f: ctx.compress(dk, f, bk if f == ms.STATIC_BP else 0) for f in F}
+    del dx, dk
+    ctx.check(what="sweep base columns")
+    res = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    name = ms.FORMAT_NAMES
+    out = {"rows": n, "x_bytes": {name[f]: ctx.info(X[f])["size_bytes"] for f in F},
+           "k_bytes": {name[f]: ctx.info(K[f])["size_bytes"] for f in F},
+           "select": {}, "select_packed": {}, "project": {}, "project_positions": {}, "calc": {}, "agg_sum": {}}
+    for sel in (0.001, 0.1, 0.9):
+        c = synth.value_at_rank(x, sel)
+        for fi in F:
+            for fo in F:
+                bwo = 0
+                if fo == ms.STATIC_BP:
+                    bwo = max(1, (n - 1).bit_length())
+                t = timed(lambda: ctx.free(ctx.select(X[fi], ms.LT, c, fmt=fo, bw=bwo)))
+                out["select"][f"{sel}|{name[fi]}|{name[fo]}"] = {"ms": round(t, 4), "rows_per_s": n / (t * 1e-3)}
+            if fi != ms.UNCOMPR:
+                t = timed(lambda: ctx.free(ctx.select_packed(X[fi], ms.LT, c, fmt=ms.DELTA_BP)))
+                out["select_packed"][f"{sel}|{name[fi]}|delta_bp"] = {"ms": round(t, 4), "rows_per_s": n / (t * 1e-3)}
+        ctx.check(what=f"select sweep {sel}")
+    c = synth.value_at_rank(x, 0.1)
+    P = ctx.select(X[ms.DYN_BP], ms.LT, c, fmt=ms.DELTA_BP)
+    m = ctx.info(P)["n"]
+    bxo = bx
+    for fi in F:
+        for fo in F:
+            t = timed(lambda: ctx.free(ctx.project(X[fi], P, fmt=fo, bw=bxo if fo == ms.STATIC_BP else 0)))
+            out["project"][f"{name[fi]}|{name[fo]}"] = {"ms": round(t, 4), "rows_per_s": m / (t * 1e-3)}
+    ctx.check(what="project sweep")
+    Pf = {f: ctx.morph(P, f, max(1, (n - 1).bit_length()) if f == ms.STATIC_BP else 0) for f in F}
+    for fp in F:
+        t = timed(lambda: ctx.free(ctx.project(X[ms.UNCOMPR], Pf[fp], fmt=ms.UNCOMPR)))
+        out["project_positions"][f"{name[fp]}|uncompr"] = {"ms": round(t, 4), "rows_per_s": m / (t * 1e-3)}
+    ctx.check(what="position-format sweep")
+    for fi in F:
+        xp = ctx.project(X[ms.UNCOMPR], P, fmt=fi, bw=bx if fi == ms.STATIC_BP else 0)
+        kp = ctx.project(K[ms.UNCOMPR], P, fmt=fi, bw=bk if fi == ms.STATIC_BP else 0)
+        for fo in F:
+            # static BP output: the products need up to bx + bk bits
+            bwo = min(64, bx + bk) if fo == ms.STATIC_BP else 0
+            t = timed(lambda: ctx.free(ctx.calc(ms.MUL, xp, kp, fmt=fo, bw=bwo)))
+            out["calc"][f"{name[fi]}|{name[fo]}"] = {"ms": round(t, 4), "rows_per_s": m / (t * 1e-3)}
+        ctx.free(kp)
+        ctx.free(xp)
+    ctx.check(what="calc sweep")
+    for fi in F:
+        t = timed(lambda: ctx.agg_sum(X[fi], out=res))
+        out["agg_sum"][name[fi]] = {"ms": round(t, 4), "rows_per_s": n / (t * 1e-3)}
+    ctx.check(what="agg_sum sweep")
+    out["positions"] = m
+    ctx.close()
+    return {"workload": "sweep-table", "metric": METRIC, **out}
+
+
 # ------------------------------------------------------------ one kernel
 
 def bench_kernel(args):
@@ -1279,6 +1373,9 @@ def main():
     args = parse()
     if args.workload == "kernel" and args.impl == "ours":
         print(json.dumps(bench_kernel(args)))
+        return
+    if args.workload == "sweep-table" and args.impl == "ours":
+        print(json.dumps(bench_sweep_table(args)))
         return
     if args.workload == "batch" and args.impl == "ours":
         print(json.dumps(bench_batch(args)))
