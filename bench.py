@@ -77,7 +77,12 @@ def parse():
                     help="kernel workload: every 512-block of X at this bit width (0: the plan's width mix)")
     ap.add_argument("--x-format", choices=["uncompr", "static_bp", "dyn_bp", "delta_bp", "for_bp"], default="dyn_bp",
                     help="kernel workload: the format X is stored in (static BP at X's largest width)")
-    ap.add_argument("--selector-items", type=int, default=3000)
+    ap.add_argument("--selector-items", type=int, default=20000,
+                    help="selector workload: engine traces to train and hold out (80/20), 2^16 rows up to "
+                         "2^--selector-max-log2")
+    ap.add_argument("--selector-max-log2", type=float, default=20.0)
+    ap.add_argument("--selector-large-items", type=int, default=200,
+                    help="selector workload: extra held-out traces of 2^22 .. 2^26 rows")
     ap.add_argument("--fragments", type=int, default=4096)
     ap.add_argument("--batch-max-log2", type=float, default=24.0)
     ap.add_argument("--batch-train-items", type=int, default=400)
@@ -959,12 +964,19 @@ def bench_selector(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    ctx = ms.Ctx(0, arena_bytes=3 << 30, max_rows=1 << 22)
-    # ---- 1. traces: every intermediate compressed into every format
+    ctx = ms.Ctx(0, arena_bytes=4 << 30, max_rows=1 << 26)
+    # ---- 1. traces: every intermediate compressed into every format (items are
+    # generated and labelled one at a time)
     t_h = time.perf_counter()
-    items = list(selector.synthetic_intermediates(args.seed, args.selector_items, lo_log2=14, hi_log2=22))
+    items = selector.synthetic_intermediates(args.seed, args.selector_items, lo_log2=16,
+                                             hi_log2=args.selector_max_log2)
     X, Y, S, T, names = selector.harvest(ctx, items, reps=2)
     harvest_s = time.perf_counter() - t_h
+    # a held-out set of long intermediates (2^22 .. 2^26 rows), never trained on
+    t_l = time.perf_counter()
+    big = selector.synthetic_intermediates(args.seed + 99, args.selector_large_items, lo_log2=22, hi_log2=26)
+    XL, _, SL, TL, _ = selector.harvest(ctx, big, reps=1)
+    large_s = time.perf_counter() - t_l
     ctx.close()
     idx = np.random.default_rng(args.seed).permutation(len(X))
     cut = int(0.8 * len(X))
@@ -976,11 +988,12 @@ def bench_selector(args):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t_t
     held = {}
-    for obj, costs in (("size", S[te]), ("time", T[te])):
-        chosen = sel.choose(X[te], obj)
+    for obj, feats_, costs in (("size", X[te], S[te]), ("time", X[te], T[te]), ("size_long", XL, SL),
+                               ("time_long", XL, TL)):
+        chosen = sel.choose(feats_, obj.split("_")[0])
         held[obj] = {"regret": round(selector.regret(chosen, costs), 4),
-                     "static_bp_for_all_regret": round(selector.regret(np.full(len(te), 1), costs), 4),
-                     "best_fixed_format_regret": round(min(selector.regret(np.full(len(te), f), costs)
+                     "static_bp_for_all_regret": round(selector.regret(np.full(len(costs), 1), costs), 4),
+                     "best_fixed_format_regret": round(min(selector.regret(np.full(len(costs), f), costs)
                                                            for f in range(5)), 4)}
     # ---- 3. the 2^28-row plan with formats picked from a prefix sample
     n = args.rows
@@ -1017,8 +1030,9 @@ def bench_selector(args):
     ctx.check(what="selector plans")
     ctx.close()
     return {"workload": "selector", "metric": "learned format selector: regret vs exhaustive choice",
-            "items": len(X), "train_items": len(tr), "heldout_items": len(te),
-            "harvest_s": round(harvest_s, 1), "train_s": round(train_s, 2),
+            "items": len(X), "train_items": len(tr), "heldout_items": len(te), "long_heldout_items": len(XL),
+            "rows_log2": [16, args.selector_max_log2], "long_rows_log2": [22, 26],
+            "harvest_s": round(harvest_s, 1), "long_harvest_s": round(large_s, 1), "train_s": round(train_s, 2),
             "loss_first_last": [hist[0][1], hist[-1][1]], "heldout": held,
             "plan_2e28": {"rows": n, "selector_formats": fm_sel, "greedy_formats": {k2: fm_g[k2] for k2 in PLAN_INTERMEDIATES},
                           "ms_selector": round(t_sel, 4), "ms_greedy_search": round(t_greedy, 4),

@@ -44,6 +44,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
+    # MS_NVCC_DEFINES: extra -D definitions for a tuning build (space separated)
+    common += [f"-D{d}" for d in os.environ.get("MS_NVCC_DEFINES", "").split() if d]
     if verbose:
         common += ["-Xptxas", "-v"]
 

@@ -214,10 +214,12 @@ def synthetic_intermediates(seed: int, count: int, lo_log2: int = 16, hi_log2: i
         elif kind == "sorted":
             x, op = synth.sorted_gaps(s, n), "base"
         elif kind == "positions":
+            # the positions a select keeps at selectivity sel: gaps between kept rows
+            # are geometric with mean 1/sel (generated in O(n), not by scanning n/sel rows)
             sel = float(rng.choice([0.001, 0.01, 0.1, 0.5, 0.9]))
-            base = synth.splitmix64(s, int(n / sel) + 1)
-            keep = base < np.uint64(int(sel * 2**64))
-            x, op = np.flatnonzero(keep).astype(np.uint64)[:n], "select"
+            u = (synth.splitmix64(s, n) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+            gaps = 1 + np.floor(np.log1p(-u) / np.log1p(-sel)) if sel < 1.0 else np.ones(n)
+            x, op = (np.cumsum(gaps.astype(np.uint64)) - np.uint64(1)), "select"
         elif kind == "product":
             with np.errstate(over="ignore"):
                 x = synth.skewed_widths(s, n, widths=(3, 8, 16)) * synth.sorted_gaps(s + 1, n)
