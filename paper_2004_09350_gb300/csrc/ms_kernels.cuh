@@ -388,8 +388,8 @@ struct SmemProjectDelta {
 };
 // Shared by the CTA of a project kernel: a piece of consecutive data blocks (their
 // payloads are contiguous) and the pieces' block headers.
-// (152 KB beside DYN/FOR/static data so that a typical tile's span is one piece;
-// 96 KB beside DELTA data, whose warps also keep a decoded block each)
+// (36 KB, so that two CTAs fit an SM: one CTA's tile set-up and copy latency
+// overlaps the other's extraction; a wide span takes several pieces)
 constexpr int kCtaHdr = 256;
 template <int kCtaBuf>
 struct ProjectCta {
@@ -413,13 +413,18 @@ struct SmemEmit {
   uint64_t coff[kEmitSpan + 2];
   uint64_t aux[kBlock];
   uint16_t out[2048];
+  uint32_t bits2[kEmitSpan * 16];  // the next block's first span (pipelined emit)
+  uint64_t coff2[kEmitSpan + 2];
 };
 
 #ifndef MS_PROJECT_MIN_BLOCKS
-#define MS_PROJECT_MIN_BLOCKS 1  // resident CTAs per SM the project kernel is compiled for
+#define MS_PROJECT_MIN_BLOCKS 2  // resident CTAs per SM the project kernel is compiled for
 #endif
 #ifndef MS_PROJECT_CTA_BUF
-#define MS_PROJECT_CTA_BUF (152 * 1024)  // staged data blocks per CTA (DYN / FOR / static data)
+#define MS_PROJECT_CTA_BUF (36 * 1024)  // staged data blocks per CTA (DYN / FOR / static data)
+#endif
+#ifndef MS_PROJECT_SPAN_DENSITY
+#define MS_PROJECT_SPAN_DENSITY 16  // a tile is staged when it has this many positions per spanned block
 #endif
 #ifndef MS_PROJECT_BULK
 #define MS_PROJECT_BULK 1  // project copies its data pieces with the bulk-copy engine
@@ -526,16 +531,104 @@ MS_DEV int emit_gather(const ProduceArgs& a, uint64_t n_out, uint64_t g, int lan
   return valid;
 }
 
+// Pipelined emit (the staged producer): while a warp expands output block g, the
+// bitmap words and offsets of its next block are already on their way, and the
+// next block's first input chunk (bstart) was read one block earlier still, so the
+// per-block chain of dependent loads is off the critical path.
+struct EmitPlan {
+  uint64_t lo, cfirst, clast;
+  int valid;
+};
+
+MS_DEV void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// bs0 = bstart[g], bs1 = bstart[g + 1] (or anything when g is the last block).
+MS_DEV EmitPlan emit_plan(const ProduceArgs& a, uint64_t n_out, uint64_t g, uint64_t bs0, uint64_t bs1) {
+  EmitPlan e;
+  e.lo = g * kBlock;
+  e.valid = (int)min((uint64_t)kBlock, n_out - e.lo);
+  const uint64_t hi = e.lo + e.valid;
+  const uint64_t nch_in =
+      max((uint64_t)1, min(a.emit_nch, *reinterpret_cast<volatile const uint64_t*>(&a.ctl->op_nch)));
+  e.cfirst = min(bs0, nch_in - 1);
+  e.clast = max(e.cfirst, min((hi < n_out) ? bs1 : nch_in - 1, nch_in - 1));
+  return e;
+}
+
+// Issues the copies of the bitmap words and offsets of chunks c0 .. c0 + nc - 1 (and
+// the offset behind them) into bits / coff (one commit group).
+MS_DEV void emit_stage(const ProduceArgs& a, uint64_t c0, int nc, uint32_t* bits, uint64_t* coff, int lane) {
+  for (int u = lane; u < nc * 4; u += 32)
+    cp_async16(bits + 4 * u, reinterpret_cast<const uint4*>(a.bitmap + c0 * 32) + u);
+  for (int u = lane; u <= nc; u += 32) cp_async8(coff + u, a.coff + c0 + u);
+  cp_async_commit();
+}
+
+// Positions of output block e (lane-blocked in v) from its staged first span in
+// bits / coff; later spans (blocks spread over more than kEmitSpan chunks) are
+// staged and waited for here.  The caller waited for the first span.
+MS_DEV int emit_expand(const ProduceArgs& a, const EmitPlan& e, int lane, uint64_t v[16], SmemEmit* sm,
+                       uint32_t* bits, uint64_t* coff) {
+  const uint64_t lo = e.lo, hi = e.lo + e.valid;
+  const bool dense = e.clast - e.cfirst < 64;
+  for (uint64_t c0 = e.cfirst; c0 <= e.clast; c0 += kEmitSpan) {
+    const int nc = (int)min((uint64_t)kEmitSpan, e.clast - c0 + 1);
+    if (c0 != e.cfirst) {
+      emit_stage(a, c0, nc, bits, coff, lane);
+      cp_async_wait<0>();
+      __syncwarp();
+    }
+    if (dense) {  // each lane expands its 16 rows of the chunk
+      for (int ci = 0; ci < nc; ci++) {
+        uint32_t hw = (bits[ci * 16 + (lane >> 1)] >> (16 * (lane & 1))) & 0xffffu;
+        uint64_t o = coff[ci] + warp_excl_scan32(__popc(hw), lane);
+        const uint64_t ch = c0 + ci;
+        while (hw) {
+          const int bb = __ffs(hw) - 1;
+          hw &= hw - 1;
+          if (o >= lo && o < hi) sm->aux[swz((int)(o - lo))] = ch * kBlock + 16 * lane + bb;
+          o++;
+        }
+      }
+    } else if (lane < nc) {  // sparse: a lane per chunk
+      uint64_t o = coff[lane];
+      const uint64_t end = coff[lane + 1];
+      const uint64_t ch = c0 + lane;
+      if (end > o && end > lo && o < hi) {
+        for (int w = 0; w < 16 && o < hi; w++) {
+          uint32_t bb32 = bits[lane * 16 + w];
+          while (bb32) {
+            const int bb = __ffs(bb32) - 1;
+            bb32 &= bb32 - 1;
+            if (o >= lo && o < hi) sm->aux[swz((int)(o - lo))] = ch * kBlock + 32 * w + bb;
+            o++;
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    const int t = 16 * lane + k;
+    v[k] = t < e.valid ? sm->aux[swz(t)] : 0;
+  }
+  __syncwarp();
+  return e.valid;
+}
+
 // Sorted positions of a whole CTA tile (8 consecutive output chunks) into DYN /
-// FOR / DELTA / static-BP data.  The data blocks the tile's positions span have
-// contiguous payloads, so the CTA copies them into shared memory in pieces of up
-// to kCtaBuf bytes (one bulk copy per piece, issued by one thread), and each warp
-// then takes its values from there: DYN / FOR / static values are cut out of their
-// blocks, DELTA blocks are decoded whole (prefix sums) into the warp's `aux`.  A
-// random read per position would instead touch up to 32 scattered sectors per warp
-// load.  Unsorted, out-of-range or sparse positions (fewer positions than blocks
-// spanned) and uncompressed data go through the per-warp random path.  Every
-// thread of the CTA calls this once per tile (it synchronises the CTA).
+// FOR / static-BP data.  The data blocks the tile's positions span have contiguous
+// payloads, so the CTA copies them into shared memory in pieces of up to kCtaBuf
+// bytes (one bulk copy per piece, issued by one thread), and each warp then cuts
+// its values out of their blocks there.  A read per position in place would touch
+// two or three scattered 64-byte rows of a block per value.  Unsorted or
+// out-of-range positions, and tiles with fewer than MS_PROJECT_SPAN_DENSITY
+// positions per spanned block, are read in place (project_direct).  Every thread of
+// the CTA calls this once per tile (it synchronises the CTA).
 template <class Cta>
 MS_DEV void gather_cta(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int warp, int lane,
                        uint64_t v[16], Cta* cs) {
@@ -580,7 +673,9 @@ MS_DEV void gather_cta(const ProduceArgs& a, const ColView& d, const uint64_t p[
     }
   }
   const uint64_t B_lo = lo >> 9, B_hi = hi >> 9;
-  tile_ok &= any && B_hi - B_lo + 1 <= npos;
+  // sparser tiles read their values in place: staging whole blocks for a few
+  // positions each costs more than the scattered sector reads
+  tile_ok &= any && (B_hi - B_lo + 1) * (uint64_t)MS_PROJECT_SPAN_DENSITY <= npos;
   __syncthreads();  // every thread has read the summaries
   if (!tile_ok) {  // gather in place, striped (the warp's 4 KB of the CTA buffer as its stage)
     project_direct(a, d, p, valid, lane, v, reinterpret_cast<uint64_t*>(cs->buf + 4096 * warp));
@@ -1575,6 +1670,22 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
     }
     __syncthreads();
   }
+  // pipelined emit: the first block's plan and span, the second block's first chunks
+  EmitPlan eplan{};
+  uint64_t nbs0 = 0, nbs1 = 0;
+  if constexpr (OP == OP_EMIT) {
+    if (loop_n > 0) {
+      const uint64_t g0 = first;
+      eplan = emit_plan(a, n_out, g0, a.bstart[g0], g0 + 1 < nch ? a.bstart[g0 + 1] : 0);
+      emit_stage(a, eplan.cfirst, (int)min((uint64_t)kEmitSpan, eplan.clast - eplan.cfirst + 1), sm->bits,
+                 sm->coff, lane);
+      if (loop_n > 1) {
+        const uint64_t g1 = first + stride;
+        nbs0 = a.bstart[g1];
+        nbs1 = g1 + 1 < nch ? a.bstart[g1 + 1] : 0;
+      }
+    }
+  }
   for (uint64_t i = 0; i < loop_n; i++) {
     const uint64_t g = first + i * stride;
     uint64_t v[16];
@@ -1582,7 +1693,25 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
     uint16_t* out_stage;
     if constexpr (OP == OP_EMIT) {
       out_stage = sm->out;
-      valid = emit_gather(a, n_out, g, lane, v, sm);
+      uint32_t* cbits = (i & 1) ? sm->bits2 : sm->bits;
+      uint64_t* ccoff = (i & 1) ? sm->coff2 : sm->coff;
+      const EmitPlan cur = eplan;
+      if (i + 1 < loop_n) {  // the next block: plan it and start its first span
+        const uint64_t gn = g + stride;
+        eplan = emit_plan(a, n_out, gn, nbs0, nbs1);
+        emit_stage(a, eplan.cfirst, (int)min((uint64_t)kEmitSpan, eplan.clast - eplan.cfirst + 1),
+                   (i & 1) ? sm->bits : sm->bits2, (i & 1) ? sm->coff : sm->coff2, lane);
+        if (i + 2 < loop_n) {  // the block after: its first chunks, for the next plan
+          const uint64_t g2 = gn + stride;
+          nbs0 = a.bstart[g2];
+          nbs1 = g2 + 1 < nch ? a.bstart[g2 + 1] : 0;
+        }
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncwarp();
+      valid = emit_expand(a, cur, lane, v, sm, cbits, ccoff);
     } else {
       cp_async_wait<D - 2>();
       __syncwarp();
