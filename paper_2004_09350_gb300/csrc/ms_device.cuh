@@ -671,13 +671,15 @@ struct ChunkStream {
   }
 
   // Decodes chunk i (already landed) into lane registers; returns its valid count.
+  // kC selects the compact (one loop for every width) lane-stream decoder.
+  template <bool kC = kCompactCodec>
   MS_DEV int decode(uint64_t i, uint64_t v[16], DevCtl* ctl) const {
     if (i >= count) {
 #pragma unroll
       for (int k = 0; k < 16; k++) v[k] = 0;
       return 0;
     }
-    return decode_staged(c, chunk(i), sm->hdr[i % (2 * kDepth)], sm->slot[i % kDepth], lane, v, ctl, 4 * SW);
+    return decode_staged<kC>(c, chunk(i), sm->hdr[i % (2 * kDepth)], sm->slot[i % kDepth], lane, v, ctl, 4 * SW);
   }
 };
 

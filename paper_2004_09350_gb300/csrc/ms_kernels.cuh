@@ -994,7 +994,11 @@ MS_DEV void decode_delta_block(const ColView& d, uint64_t B, uint64_t w0, uint64
     if (lane == 0) set_error(ctl, MS_ERR_FORMAT, B);
     b = 0;
   }
+#ifdef MS_DELTA_COMPACT
+  read_lane_stream_as<true>(reinterpret_cast<const uint16_t*>(d.p + (b ? pay : 0)), lane, b, t);
+#else
   read_lane_stream(reinterpret_cast<const uint16_t*>(d.p + (b ? pay : 0)), lane, b, t);
+#endif
   if (b <= 23) {  // 512 residuals below 2^23 sum below 2^32
     uint32_t sum = 0;
 #pragma unroll
@@ -1741,7 +1745,11 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
         else project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
       } else {  // OP_PROJECT_WARP: per-warp gather (no CTA tile): DELTA data by block decode, others in place
         uint64_t p[16];
+#ifdef MS_PROJECT_WARP_COMPACT
+        valid = st0.template decode<true>(i, p, ctl);
+#else
         valid = st0.decode(i, p, ctl);
+#endif
         __syncwarp();
         if (c0.fmt == MS_DELTA_BP) project_delta(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage), sm->aux);
         else project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
