@@ -13,7 +13,8 @@
 //     block widths into payload offsets with a decoupled look-back and moves the
 //     payloads into place.  Project gathers a CTA tile of sorted positions from
 //     the data blocks they span, staged the same way (gather_cta).
-//   * k_produce is the direct-offset variant of the allocation-free compress path.
+//   * k_produce is the direct-offset compress of the allocation-free path: payload
+//     offsets from a decoupled look-back inside the kernel, no placement pass.
 #pragma once
 #include <type_traits>
 
@@ -466,70 +467,6 @@ MS_DEV uint64_t arith(int op, uint64_t x, uint64_t y) {
 // cores below); the CTA span gather falls back to it.
 MS_DEV void project_direct(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
                            uint64_t v[16], uint64_t* stage);
-
-// emit core: positions of output block g (lane-blocked) from the match bitmap.
-MS_DEV int emit_gather(const ProduceArgs& a, uint64_t n_out, uint64_t g, int lane, uint64_t v[16], SmemEmit* sm) {
-  const uint64_t lo = g * kBlock;
-  const int valid = (int)min((uint64_t)kBlock, n_out - lo);
-  const uint64_t hi = lo + valid;
-  // chunk range holding the block's outputs, within the input's real chunk count
-  // (clamped: scratch is never trusted blindly)
-  const uint64_t nch_in =
-      max((uint64_t)1, min(a.emit_nch, *reinterpret_cast<volatile const uint64_t*>(&a.ctl->op_nch)));
-  const uint64_t cfirst = min(a.bstart[g], nch_in - 1);
-  const uint64_t clast = max(cfirst, min((hi < n_out) ? a.bstart[g + 1] : nch_in - 1, nch_in - 1));
-  // dense blocks (<= 64 chunks): a warp expands one chunk at a time; sparse: a lane per chunk
-  const bool dense = clast - cfirst < 64;
-  for (uint64_t c0 = cfirst; c0 <= clast; c0 += kEmitSpan) {
-    const int nc = (int)min((uint64_t)kEmitSpan, clast - c0 + 1);
-    // stage the bitmap words and offsets of up to kEmitSpan chunks at once
-    for (int u = lane; u < nc * 4; u += 32)
-      cp_async16(sm->bits + 4 * u, reinterpret_cast<const uint4*>(a.bitmap + c0 * 32) + u);
-    // nc + 1 offsets: the sparse path reads the end offset of the span's last chunk
-    for (int u = lane; u <= nc; u += 32) sm->coff[u] = a.coff[c0 + u];
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncwarp();
-    if (dense) {  // each lane expands its 16 rows of the chunk
-      for (int ci = 0; ci < nc; ci++) {
-        uint32_t hw = (sm->bits[ci * 16 + (lane >> 1)] >> (16 * (lane & 1))) & 0xffffu;
-        uint64_t o = sm->coff[ci] + warp_excl_scan32(__popc(hw), lane);
-        const uint64_t ch = c0 + ci;
-        while (hw) {
-          const int bb = __ffs(hw) - 1;
-          hw &= hw - 1;
-          if (o >= lo && o < hi) sm->aux[swz((int)(o - lo))] = ch * kBlock + 16 * lane + bb;
-          o++;
-        }
-      }
-    } else {
-      if (lane < nc) {
-        uint64_t o = sm->coff[lane];
-        const uint64_t e = sm->coff[lane + 1];
-        const uint64_t ch = c0 + lane;
-        if (e > o && e > lo && o < hi) {
-          for (int w = 0; w < 16 && o < hi; w++) {
-            uint32_t bits = sm->bits[lane * 16 + w];
-            while (bits) {
-              const int bb = __ffs(bits) - 1;
-              bits &= bits - 1;
-              if (o >= lo && o < hi) sm->aux[swz((int)(o - lo))] = ch * kBlock + 32 * w + bb;
-              o++;
-            }
-          }
-        }
-      }
-    }
-    __syncwarp();
-  }
-#pragma unroll
-  for (int k = 0; k < 16; k++) {
-    const int t = 16 * lane + k;
-    v[k] = t < valid ? sm->aux[swz(t)] : 0;
-  }
-  __syncwarp();
-  return valid;
-}
 
 // Pipelined emit (the staged producer): while a warp expands output block g, the
 // bitmap words and offsets of its next block are already on their way, and the
@@ -994,11 +931,7 @@ MS_DEV void decode_delta_block(const ColView& d, uint64_t B, uint64_t w0, uint64
     if (lane == 0) set_error(ctl, MS_ERR_FORMAT, B);
     b = 0;
   }
-#ifdef MS_DELTA_COMPACT
-  read_lane_stream_as<true>(reinterpret_cast<const uint16_t*>(d.p + (b ? pay : 0)), lane, b, t);
-#else
   read_lane_stream(reinterpret_cast<const uint16_t*>(d.p + (b ? pay : 0)), lane, b, t);
-#endif
   if (b <= 23) {  // 512 residuals below 2^23 sum below 2^32
     uint32_t sum = 0;
 #pragma unroll
@@ -1086,28 +1019,11 @@ MS_DEV void project_delta(const ProduceArgs& a, const ColView& d, const uint64_t
 }
 
 // Per-warp shared memory and occupancy of the direct-offset producer.
-struct DSmemSingle {
-  StreamSmem<kProdDepth> s0;
-};
-struct DSmemPair {
-  StreamSmem<kProdDepth2> s0, s1;
-};
-struct DSmemProject {
-  StreamSmem<kProdDepth2> s0;  // positions
-};
-struct DSmemProjectDelta {
-  StreamSmem<kProdDepth2> s0;  // positions
-  uint64_t aux[kBlock];        // the data block decoded last
-};
 template <int OP>
 struct DirectPlan {
-  using Smem = typename std::conditional<
-      OP == OP_CALC, DSmemPair,
-      typename std::conditional<
-          OP == OP_PROJECT, DSmemProject,
-          typename std::conditional<
-              OP == OP_PROJECT_WARP, DSmemProjectDelta,
-              typename std::conditional<OP == OP_EMIT, SmemEmit, DSmemSingle>::type>::type>::type>::type;
+  struct Smem {
+    StreamSmem<kProdDepth> s0;
+  };
   static constexpr int kMinBlocks = 2;
 };
 
@@ -1115,8 +1031,8 @@ struct DirectPlan {
 // from a decoupled look-back inside the kernel instead of a placement pass.
 template <int OP>
 __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produce(ProduceArgs a) {
+  static_assert(OP == OP_COMPRESS, "the direct-offset producer serves the allocation-free compress only");
   using Smem = typename DirectPlan<OP>::Smem;
-  constexpr bool kProject = OP == OP_PROJECT || OP == OP_PROJECT_WARP;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ uint64_t s_words[2][kWarps];  // by tile parity: payload words of each warp's block
   __shared__ uint64_t s_agg[2];
@@ -1130,15 +1046,8 @@ __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produc
   const uint64_t avail = raw ? 8 * a.raw_cap : ctl->cap - top;
   uint8_t* base = raw ? reinterpret_cast<uint8_t*>(a.raw_out) : reinterpret_cast<uint8_t*>(ctl->arena + top);
 
-  ColView c0{}, c1{};
-  if (OP == OP_COMPRESS) c0 = view_raw(a.raw_in, a.raw_n);
-  if (OP == OP_DECOMPRESS || OP == OP_CALC || kProject) c0 = view_of(a.in0);
-  if ((OP == OP_CALC || kProject) && a.in1) c1 = view_of(a.in1);
-  const uint64_t n_out = produce_n<OP>(a);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (OP == OP_DECOMPRESS && raw && a.in0->n > a.raw_cap) set_error(ctl, MS_ERR_INVALID_ARG, a.in0->n);
-    if (OP == OP_CALC && a.in1 && a.in0->n != a.in1->n) set_error(ctl, MS_ERR_INVALID_ARG, a.in1->n);
-  }
+  const ColView c0 = view_raw(a.raw_in, a.raw_n);
+  const uint64_t n_out = a.raw_n;
   const int fmt = a.fmt, bw = a.bw;
   const bool blockfmt = is_block_fmt(fmt);
   const uint64_t nch = (n_out + kBlock - 1) / kBlock, ntiles = (nch + kWarps - 1) / kWarps;
@@ -1149,28 +1058,16 @@ __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produc
   const uint64_t first = (uint64_t)blockIdx.x * kWarps + warp, stride = kWarps * G;
 
   // input streams: chunk i of a warp is first + i*stride, for every tile of the CTA
-  constexpr int D = (OP == OP_CALC || kProject) ? kProdDepth2 : kProdDepth;
-  StreamSmem<D>* ring0 = nullptr;
-  StreamSmem<D>* ring1 = nullptr;
-  if constexpr (OP == OP_COMPRESS || OP == OP_DECOMPRESS || kProject) ring0 = &sm->s0;
-  if constexpr (OP == OP_CALC) {
-    ring0 = &sm->s0;
-    ring1 = &sm->s1;
-  }
-  // project streams its positions (c1); the data column (c0) is read in place
-  ChunkStream<D> st0{kProject ? c1 : c0, first, stride, (OP == OP_EMIT) ? 0 : my_tiles, ring0, lane};
-  ChunkStream<D> st1{c1, first, stride, (OP == OP_CALC && a.in1) ? my_tiles : 0, ring1, lane};
-  if (OP != OP_EMIT && my_tiles) {
-    for (int i = 0; i < D; i++) {
-      st0.issue_header(i);
-      st1.issue_header(i);
-    }
+  constexpr int D = kProdDepth;
+  StreamSmem<D>* ring0 = &sm->s0;
+  ChunkStream<D> st0{c0, first, stride, my_tiles, ring0, lane};
+  if (my_tiles) {
+    for (int i = 0; i < D; i++) st0.issue_header(i);
     cp_async_commit();
     cp_async_wait<0>();
     __syncwarp();
     for (int j = 0; j < D - 1; j++) {
       st0.prologue_step(j);
-      st1.prologue_step(j);
       cp_async_commit();
     }
   }
@@ -1234,50 +1131,15 @@ __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produc
     uint64_t v[16];
     int valid = 0;
     uint16_t* out_stage;
-    if constexpr (OP == OP_EMIT) {
-      if (pend) finish();  // its stage (sm->out) is reused below
-      out_stage = sm->out;
-      if (g < nch) valid = emit_gather(a, n_out, g, lane, v, sm);
-      else {
-#pragma unroll
-        for (int k = 0; k < 16; k++) v[k] = 0;
-      }
-    } else {
-      cp_async_wait<D - 2>();
-      __syncwarp();
-      if (pend) finish();  // before step(i) refills the pending tile's slot
-      st0.step(i);
-      st1.step(i);
-      cp_async_commit();
-      out_stage = ring0->slot[i % D];
-      if constexpr (OP == OP_COMPRESS || OP == OP_DECOMPRESS) {
-        valid = st0.decode(i, v, ctl);
-        valid = (int)min((uint64_t)valid, g * kBlock < n_out ? n_out - g * kBlock : 0);
-      } else if constexpr (OP == OP_CALC) {
-        valid = st0.decode(i, v, ctl);
-        if (a.in1) {
-          uint64_t w[16];
-          valid = min(valid, st1.decode(i, w, ctl));
-#pragma unroll
-          for (int k = 0; k < 16; k++) v[k] = arith(a.arith, v[k], w[k]);
-        } else {
-#pragma unroll
-          for (int k = 0; k < 16; k++) v[k] = arith(a.arith, v[k], a.scalar);
-        }
-      } else if constexpr (OP == OP_PROJECT) {
-        uint64_t p[16];
-        valid = st0.decode(i, p, ctl);
-        __syncwarp();
-        project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
-      } else if constexpr (OP == OP_PROJECT_WARP) {
-        uint64_t p[16];
-        valid = st0.decode(i, p, ctl);
-        __syncwarp();
-        if (c0.fmt == MS_DELTA_BP) project_delta(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage), sm->aux);
-        else project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
-      }
-      __syncwarp();
-    }
+    cp_async_wait<D - 2>();
+    __syncwarp();
+    if (pend) finish();  // before step(i) refills the pending tile's slot
+    st0.step(i);
+    cp_async_commit();
+    out_stage = ring0->slot[i % D];
+    valid = st0.decode(i, v, ctl);
+    valid = (int)min((uint64_t)valid, g * kBlock < n_out ? n_out - g * kBlock : 0);
+    __syncwarp();
     if (blockfmt) {
       // ---- encode into the warp's stage (the remainder as raw values) and publish
       // the tile's aggregate; the look-back and the store wait for the next iteration
@@ -1745,11 +1607,7 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
         else project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
       } else {  // OP_PROJECT_WARP: per-warp gather (no CTA tile): DELTA data by block decode, others in place
         uint64_t p[16];
-#ifdef MS_PROJECT_WARP_COMPACT
-        valid = st0.template decode<true>(i, p, ctl);
-#else
         valid = st0.decode(i, p, ctl);
-#endif
         __syncwarp();
         if (c0.fmt == MS_DELTA_BP) project_delta(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage), sm->aux);
         else project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));

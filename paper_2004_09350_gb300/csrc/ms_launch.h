@@ -67,23 +67,6 @@ ms_status launch_map<OP_EMIT>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStr
 template <>
 ms_status launch_map<OP_PROJECT_WARP>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
 
-// producers with in-kernel placement (ms_map_*.cu): one k_produce<OP> launch that
-// writes every output block at its final offset (decoupled look-back over tiles)
-template <int OP>
-ms_status launch_direct(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
-template <>
-ms_status launch_direct<OP_COMPRESS>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
-template <>
-ms_status launch_direct<OP_DECOMPRESS>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
-template <>
-ms_status launch_direct<OP_PROJECT>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
-template <>
-ms_status launch_direct<OP_CALC>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
-template <>
-ms_status launch_direct<OP_EMIT>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
-template <>
-ms_status launch_direct<OP_PROJECT_WARP>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
-
 // placement of a staged block-format output (ms_place.cu)
 ms_status launch_place(ms_ctx* c, const Work& w, DevMeta* out, uint64_t n_max, cudaStream_t s);
 
@@ -100,14 +83,5 @@ ms_status launch_map_impl(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_
   return cuda_status(cudaGetLastError());  // records the failing code
 }
 
-template <int OP>
-ms_status launch_direct_impl(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
-  const size_t smem = sizeof(typename DirectPlan<OP>::Smem) * kWarps;
-  const uint64_t tiles = cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kWarps);
-  const int grid = grid_for(c, k_produce<OP>, smem, tiles);
-  ProfScope ps(c, kMapKernel[OP], s);
-  k_produce<OP><<<grid, kThreads, smem, s>>>(a);
-  return cuda_status(cudaGetLastError());
-}
 
 }  // namespace ms

@@ -7,10 +7,4 @@ template <>
 ms_status launch_map<OP_CALC>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
   return launch_map_impl<OP_CALC>(c, a, n_max, s);
 }
-
-
-template <>
-ms_status launch_direct<OP_CALC>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
-  return launch_direct_impl<OP_CALC>(c, a, n_max, s);
-}
 }  // namespace ms

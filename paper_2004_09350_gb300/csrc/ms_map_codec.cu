@@ -12,15 +12,4 @@ template <>
 ms_status launch_map<OP_DECOMPRESS>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
   return launch_map_impl<OP_DECOMPRESS>(c, a, n_max, s);
 }
-
-
-template <>
-ms_status launch_direct<OP_COMPRESS>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
-  return launch_direct_impl<OP_COMPRESS>(c, a, n_max, s);
-}
-
-template <>
-ms_status launch_direct<OP_DECOMPRESS>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
-  return launch_direct_impl<OP_DECOMPRESS>(c, a, n_max, s);
-}
 }  // namespace ms

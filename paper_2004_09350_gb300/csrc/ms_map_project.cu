@@ -12,15 +12,4 @@ template <>
 ms_status launch_map<OP_PROJECT_WARP>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
   return launch_map_impl<OP_PROJECT_WARP>(c, a, n_max, s);
 }
-
-
-template <>
-ms_status launch_direct<OP_PROJECT>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
-  return launch_direct_impl<OP_PROJECT>(c, a, n_max, s);
-}
-
-template <>
-ms_status launch_direct<OP_PROJECT_WARP>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s) {
-  return launch_direct_impl<OP_PROJECT_WARP>(c, a, n_max, s);
-}
 }  // namespace ms

@@ -1,9 +1,6 @@
 // ms_ops.cu -- operator entry points of libms: argument checks, scratch layout and
 // the launch sequence of each operator.  Every launch is asynchronous on the
 // caller's stream.
-#include <stdlib.h>
-#include <string.h>
-
 #include <algorithm>
 
 #include "ms_launch.h"
@@ -95,18 +92,8 @@ namespace {
 bool owned(ms_ctx* c, const ms_column* col) { return col && col->ctx == c && !col->freed; }
 
 
-// The staged producers (k_map + placement) are the default; MS_PRODUCER=direct
-// selects the direct-offset ones (k_produce), for comparison.
-bool use_staged_producers() {
-  static const bool on = [] {
-    const char* e = getenv("MS_PRODUCER");
-    return !(e && strcmp(e, "direct") == 0);
-  }();
-  return on;
-}
-
-// Launches the producer of OP into a new arena column: k_produce<OP>, which places
-// every output block itself, or k_map<OP> followed by the placement pass.
+// Launches k_map<OP> into a new arena column and, for block formats, places the
+// staged blocks.
 template <int OP>
 ms_status produce_column(ms_ctx* c, ProduceArgs& a, const Work& w, uint64_t n_max, int fmt, int bw,
                          ms_column** out, cudaStream_t s) {
@@ -118,14 +105,8 @@ ms_status produce_column(ms_ctx* c, ProduceArgs& a, const Work& w, uint64_t n_ma
   a.bw = fmt == MS_STATIC_BP ? bw : 0;
   a.stage = w.stage;
   a.stage_meta = w.stage_meta;
-  a.status = w.status2;
-  ms_status st;
-  if (use_staged_producers()) {
-    st = launch_map<OP>(c, a, n_max, s);
-    if (st == MS_OK && fmt >= MS_DYN_BP) st = launch_place(c, w, a.out_meta, n_max, s);
-  } else {
-    st = launch_direct<OP>(c, a, n_max, s);
-  }
+  ms_status st = launch_map<OP>(c, a, n_max, s);
+  if (st == MS_OK && fmt >= MS_DYN_BP) st = launch_place(c, w, a.out_meta, n_max, s);
   if (st != MS_OK) {
     drop_new_column(c, col);
     return st;
@@ -179,8 +160,7 @@ ms_status ms_decompress(ms_ctx* c, const ms_column* col, uint64_t* d_out, uint64
   a.raw_out = d_out;
   a.raw_cap = cap;
   a.fmt = MS_UNCOMPR;
-  if (use_staged_producers()) return launch_map<OP_DECOMPRESS>(c, a, std::min(col->n_max, cap), s);
-  return launch_direct<OP_DECOMPRESS>(c, a, std::min(col->n_max, cap), s);
+  return launch_map<OP_DECOMPRESS>(c, a, std::min(col->n_max, cap), s);
 }
 
 ms_status ms_morph(ms_ctx* c, const ms_column* col, int fmt, int bw, ms_column** out, void* stream) {
@@ -254,7 +234,7 @@ ms_status ms_project(ms_ctx* c, const ms_column* data, const ms_column* pos, int
   // kept as DELTA); other position columns (values used as keys, in any order) are
   // read in place by the per-warp gather, which keeps more warps per SM.  Both paths
   // give the same values for any positions.
-  if (data->fmt == MS_DELTA_BP || (use_staged_producers() && (data->fmt == MS_UNCOMPR || pos->fmt != MS_DELTA_BP)))
+  if (data->fmt == MS_DELTA_BP || data->fmt == MS_UNCOMPR || pos->fmt != MS_DELTA_BP)
     return produce_column<OP_PROJECT_WARP>(c, a, w, pos->n_max, fmt, bw, out, s);
   return produce_column<OP_PROJECT>(c, a, w, pos->n_max, fmt, bw, out, s);
 }
