@@ -1376,7 +1376,7 @@ def bench_kernel(args):
     if args.kernel in ("compress", "decompress"):  # algorithmic bytes: 8n + bytes(col)
         key = "compress" if args.kernel == "compress" else "decompress"
         alg = 8 * n + out["bytes"]["X"]
-        ms_k = sum(v for kk, v in out["ms_per_launch"].items() if kk in (key, "place_scan", "place_copy"))
+        ms_k = sum(v for kk, v in out["ms_per_launch"].items() if kk in (key, "place"))
         out["alg_bytes"] = alg
         out["alg_GBps_with_placement"] = round(alg / (ms_k * 1e-3) / 1e9, 1) if ms_k else None
     ctx.close()

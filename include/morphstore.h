@@ -429,11 +429,11 @@ typedef enum {
   MS_K_BUILD_KEYS = 8, /* semi-join build side */
   MS_K_VALIDATE = 9,   /* header check of imported columns */
   MS_K_SCAN = 10,      /* select / semi-join: exclusive scan of per-chunk match counts */
-  MS_K_PLACE_SCAN = 11, /* block-format outputs: payload offsets and headers */
-  MS_K_PLACE_COPY = 12, /* block-format outputs: payload placement */
-  MS_K_STATS = 13,      /* column statistics for the format selector */
-  MS_K_BATCH = 14,      /* batched select -> project -> agg_sum fragments */
-  MS_K_SELECT_PACKED = 15, /* specialized select on packed codes -> match bitmap */
+  MS_K_PLACE = 11,      /* block-format outputs: payload offsets, headers and payload copy */
+  MS_K_STATS = 12,      /* column statistics for the format selector */
+  MS_K_BATCH = 13,      /* batched select -> project -> agg_sum fragments */
+  MS_K_SELECT_PACKED = 14, /* specialized select on packed codes -> match bitmap */
+  MS_K_ARENA = 15,      /* arena bookkeeping: top reset after ms_column_free, metadata writes */
   MS_K_COUNT = 16
 } ms_kernel;
 

@@ -47,7 +47,8 @@ struct DevCtl {
   uint64_t op_n;      // element count produced by the last mark kernel
   uint64_t op_words;  // payload words published by an op's final tile
   uint64_t op_nch;    // input chunks of the last mark step (its real length, not a bound)
-  uint64_t rsv[7];
+  uint64_t stage;     // bytes of the transient output stage, taken from the arena's end
+  uint64_t rsv[6];
 };
 
 // Read-only view of a column inside a kernel.

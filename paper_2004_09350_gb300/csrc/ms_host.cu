@@ -223,8 +223,11 @@ ms_status ms_get_error(ms_ctx* c, void* stream) {
   uint32_t err = static_cast<uint32_t>(c->pin[0] & 0xffffffffu);
   c->last_err_info = c->pin[1];
   if (err != 0) {
+    // clear the error and release a stage that a failed producer may have left taken
     uint32_t zero = 0;
-    if (cuda_status(cudaMemcpy(&c->ctl->err, &zero, 4, cudaMemcpyHostToDevice)) != MS_OK) return MS_ERR_CUDA;
+    if (cuda_status(cudaMemcpy(&c->ctl->err, &zero, 4, cudaMemcpyHostToDevice)) != MS_OK ||
+        cuda_status(cudaMemset(&c->ctl->stage, 0, 8)) != MS_OK)
+      return MS_ERR_CUDA;
   }
   return static_cast<ms_status>(err);
 }
@@ -277,6 +280,7 @@ ms_status ms_column_import(ms_ctx* c, int fmt, int bw, uint64_t n, const void* s
   m.bw = fmt == MS_STATIC_BP ? static_cast<uint32_t>(bw) : 0;
   m.pwords = 0;  // block formats: set by the validation kernel from the last header
   if (e == cudaSuccess) {
+    ProfScope ps(c, MS_K_ARENA, s);
     k_write_meta<<<1, 1, 0, s>>>(c->metas + slot, m);
     e = cudaGetLastError();
   }
@@ -373,6 +377,7 @@ ms_status ms_column_free(ms_ctx* c, ms_column* col, void* stream) {
   if (lowest >= 0) {
     // the arena top returns to the start of the lowest popped column; the slot's
     // metadata is read by the kernel before any later kernel can reuse the slot
+    ProfScope ps(c, MS_K_ARENA, s);
     k_set_top<<<1, 1, 0, s>>>(c->ctl, c->metas + lowest);
     if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
   }
@@ -408,10 +413,10 @@ ms_status ms_profile_collect(ms_ctx* c, ms_kernel_time* out, int max, int* n_out
 }
 
 const char* ms_kernel_name(int k) {
-  static const char* names[MS_K_COUNT] = {"mark",      "emit",       "compress", "decompress",
-                                          "project",   "calc",       "agg_sum",  "group_sum",
-                                          "build_keys", "validate",  "scan",     "place_scan",
-                                          "place_copy", "stats",      "batch",    "select_packed"};
+  static const char* names[MS_K_COUNT] = {"mark",       "emit",     "compress", "decompress",    "project",
+                                          "calc",       "agg_sum",  "group_sum", "build_keys",   "validate",
+                                          "scan",       "place",    "stats",     "batch",        "select_packed",
+                                          "arena"};
   return (k >= 0 && k < MS_K_COUNT) ? names[k] : "?";
 }
 

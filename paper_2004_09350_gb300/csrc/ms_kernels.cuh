@@ -9,9 +9,9 @@
 //     through the CTA tile stream (cta_stream): runs of consecutive blocks copied
 //     into shared memory with all the CTA's threads, double-buffered.
 //   * Producers (k_map: compress, decompress, project, calc, emit) encode each
-//     output block into a stage slot; a placement pass (ms_place.cu) turns the
-//     block widths into payload offsets with a decoupled look-back and moves the
-//     payloads into place.  Project gathers a CTA tile of sorted positions from
+//     output block into a stage at the arena's free end; a placement pass
+//     (k_place, ms_place.cu) turns the block widths into payload offsets with a
+//     decoupled look-back and moves the payloads into place.  Project gathers a CTA tile of sorted positions from
 //     the data blocks they span, staged the same way (gather_cta).
 //   * k_produce is the direct-offset compress of the allocation-free path: payload
 //     offsets from a decoupled look-back inside the kernel, no placement pass.
@@ -362,9 +362,9 @@ struct ProduceArgs {
   uint64_t raw_cap;
   int fmt, bw;
   uint64_t* status;
-  // staged block-format output (k_map): one 4 KB slot per output block and its
-  // {width, reference} pair; k_scan_widths and k_copy_blocks place them
-  uint8_t* stage;
+  // staged block-format output (k_map): per output block {(stage offset << 8) |
+  // width, reference}; the payloads sit in the stage at the arena's end, and k_place
+  // places them
   uint64_t* stage_meta;
 };
 
@@ -1300,32 +1300,86 @@ __global__ void __launch_bounds__(kThreads, DirectPlan<OP>::kMinBlocks) k_produc
   }
 }
 
+// The output stage of a block-format producer.  Encoded blocks wait there until
+// the placement pass knows their final offsets.  It is taken from the free end of
+// the arena, growing down from (cap & ~255) towards the columns at the arena top, so
+// it holds the output's actual payload bytes (plus each warp's unused tail), not a
+// worst-case slot per block.  A warp takes a piece of up to kStagePiece bytes with
+// one atomic and fills it with its consecutive blocks.
+constexpr uint64_t kStagePiece = 16384;
+
+struct StageCursor {
+  uint64_t at;    // arena offset of the warp's next free stage byte
+  uint64_t left;  // free bytes left in the warp's piece
+};
+
+MS_DEV uint64_t stage_end(const DevCtl* ctl) { return ctl->cap & ~255ull; }
+
+// Reserves `need` bytes (a multiple of 64) of the stage for the calling warp (every
+// lane calls it with the same arguments); `remaining` is the number of output chunks
+// the warp has left, the current one included.  Returns the arena offset, or
+// ~0 when the stage would reach the columns below it (MS_ERR_NOMEM is raised).
+MS_DEV uint64_t stage_take(DevCtl* ctl, uint64_t top, uint64_t need, uint64_t remaining, StageCursor& sc,
+                           uint64_t g, int lane) {
+  if (sc.left < need) {
+    const uint64_t piece = remaining * (uint64_t)2048;
+    const uint64_t want = max(need, piece < kStagePiece ? piece : kStagePiece);
+    unsigned long long old = 0;
+    if (lane == 0) old = atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->stage), (unsigned long long)want);
+    old = __shfl_sync(kFull, old, 0);
+    const uint64_t end = stage_end(ctl);
+    if (old + want > end - top) {
+      if (lane == 0) set_error(ctl, MS_ERR_NOMEM, g);
+      sc.left = 0;
+      return ~0ull;
+    }
+    sc.at = end - (old + want);
+    sc.left = want;
+  }
+  const uint64_t at = sc.at;
+  sc.at += need;
+  sc.left -= need;
+  return at;
+}
+
 // Stores output chunk g (lane-blocked values v, `valid` of them) of a staged
 // producer: a block-format block is encoded into the warp's stage slot in shared
-// memory and copied to its 4 KB global stage slot with its {width, reference} (the
-// placement pass moves it to its final offset); static BP and uncompressed chunks
-// have fixed offsets and are stored in place.
+// memory and copied into the arena's stage with its {stage offset, width,
+// reference} (the placement pass moves it to its final offset); static BP and
+// uncompressed chunks have fixed offsets and are stored in place.  `remaining`
+// counts the warp's output chunks left, this one included.
 MS_DEV void store_staged(const ProduceArgs& a, int fmt, int bw, bool blockfmt, uint64_t g, uint64_t v[16], int valid,
                          uint16_t* out_stage, uint8_t* base, uint64_t avail, uint64_t static_chunks, DevCtl* ctl,
-                         int lane) {
+                         int lane, uint64_t top, StageCursor& sc, uint64_t remaining) {
     if (blockfmt) {
-      uint4* slot = reinterpret_cast<uint4*>(a.stage + 4096 * g);
+      uint8_t* arena = reinterpret_cast<uint8_t*>(ctl->arena);
       if (valid == kBlock) {
         uint64_t ref;
         const int b = encode_block(fmt, v, lane, &ref);
         write_lane_stream(out_stage, lane, b, v);
         __syncwarp();
-        const uint4* src = reinterpret_cast<const uint4*>(out_stage);
-        for (int t = lane; t < 4 * b; t += 32) slot[t] = src[t];
+        uint64_t at = 0;
+        if (b > 0) {
+          at = stage_take(ctl, top, 64ull * b, remaining, sc, g, lane);
+          if (at != ~0ull) {
+            uint4* dst = reinterpret_cast<uint4*>(arena + at);
+            const uint4* src = reinterpret_cast<const uint4*>(out_stage);
+            for (int t = lane; t < 4 * b; t += 32) dst[t] = src[t];
+          }
+        }
         if (lane == 0) {
-          a.stage_meta[2 * g] = (uint64_t)b;
+          a.stage_meta[2 * g] = (at << 8) | (uint64_t)b;
           a.stage_meta[2 * g + 1] = ref;
         }
       } else if (valid > 0) {  // remainder: raw values, placed behind the payload later
-        uint64_t* dst = reinterpret_cast<uint64_t*>(slot);
+        const uint64_t at = stage_take(ctl, top, (8ull * valid + 63) & ~63ull, remaining, sc, g, lane);
+        if (at != ~0ull) {
+          uint64_t* dst = reinterpret_cast<uint64_t*>(arena + at);
 #pragma unroll
-        for (int k = 0; k < 16; k++)
-          if (16 * lane + k < valid) dst[16 * lane + k] = v[k];
+          for (int k = 0; k < 16; k++)
+            if (16 * lane + k < valid) dst[16 * lane + k] = v[k];
+        }
+        if (lane == 0) a.stage_meta[2 * g] = at << 8;
       }
     } else if (fmt == MS_STATIC_BP) {
       uint64_t o = 0;
@@ -1450,9 +1504,9 @@ MS_DEV void publish_staged(const ProduceArgs& a, uint64_t n_out, int fmt, int bw
 // Warp-independent producing kernel.  Every warp streams its own chunks (chunk
 // gw, gw + W, ... for warp gw of W), runs the operator and encodes each output
 // block.  Uncompressed and static-BP outputs have fixed offsets and are stored in
-// place.  A block-format output block goes to its own 4 KB staging slot, and its
-// {width, reference} to stage_meta.  k_scan_widths and k_copy_blocks then compute
-// the payload offsets and move the compressed bytes into place.  No block
+// place.  A block-format output block goes to the output stage at the arena's end,
+// and its {stage offset, width, reference} to stage_meta.  k_place then computes
+// the payload offsets and moves the compressed bytes into place.  No block
 // barrier and no look-back, so no warp waits for another.
 template <int OP>
 __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(ProduceArgs a) {
@@ -1552,6 +1606,7 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
       }
     }
   }
+  StageCursor sc{0, 0};
   for (uint64_t i = 0; i < loop_n; i++) {
     const uint64_t g = first + i * stride;
     uint64_t v[16];
@@ -1614,7 +1669,8 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
       }
       __syncwarp();
     }
-    store_staged(a, fmt, bw, blockfmt, g, v, valid, out_stage, base, avail, static_chunks, ctl, lane);
+    store_staged(a, fmt, bw, blockfmt, g, v, valid, out_stage, base, avail, static_chunks, ctl, lane, top, sc,
+                 loop_n - i);
     __syncwarp();
   }
   cp_async_wait<0>();
@@ -1624,45 +1680,65 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
   publish_staged(a, n_out, fmt, bw, blockfmt, base, top, avail);
 }
 
-// Placement of a staged block-format column, step 1: the exclusive scan of the
-// blocks' payload words (8 * width) over tiles of 4096 blocks with a decoupled
-// look-back.  It writes the final header entries {(offset << 8) | width, ref} at the
-// arena top and the total payload words into ctl->op_words.
+// Placement of a staged block-format column, in one pass over tiles of T
+// consecutive blocks (tile t on CTA t mod grid; the grid never exceeds the CTAs that
+// fit the GPU at once, so a tile's predecessors are always in progress).  T is the
+// output's block count spread over the grid, between 8 and kPlaceTile, so that a
+// small output still reaches every CTA.  Per tile: the blocks' widths come from
+// stage_meta, a CTA scan and a decoupled look-back over the tiles give every
+// block's payload word offset, the final headers {(offset << 8) | width, ref} go to
+// the arena top, and the CTA's warps copy the tile's payloads out of the stage, a
+// block per warp with all its loads in flight at once.  The CTA of the last tile
+// records the total payload words and places the raw remainder behind the payload;
+// the last CTA to finish completes the column record, moves the arena top past the
+// column and releases the stage.
 struct PlaceArgs {
   DevCtl* ctl;
   DevMeta* out_meta;
-  const uint8_t* stage;
   const uint64_t* stage_meta;
-  uint64_t* offsets;  // per-block payload word offset
-  uint64_t* status;
+  uint64_t* status;  // look-back status words, one per tile, zeroed
 };
 
+constexpr int kPlaceTile = kThreads;  // largest tile: a block per thread
+
+// Bytes free for the output column between the arena top and the stage below the
+// arena's end, and the stage's start (an arena offset).
+struct PlaceRoom {
+  uint64_t avail, lo;
+};
+
+MS_DEV PlaceRoom place_room(const DevCtl* ctl, uint64_t top) {
+  const uint64_t end = stage_end(ctl);
+  const uint64_t used = min(*reinterpret_cast<const volatile uint64_t*>(&ctl->stage), end - top);
+  return PlaceRoom{end - used - top, end - used};
+}
+
 template <int kUnused = 0>
-__global__ void __launch_bounds__(kThreads) k_scan_widths(PlaceArgs a) {
+__global__ void __launch_bounds__(kThreads) k_place(PlaceArgs a) {
   __shared__ uint64_t s_warp[kWarps];
   __shared__ uint64_t s_excl;
+  __shared__ uint32_t s_off[kPlaceTile];  // payload words before the block, within its tile
+  __shared__ uint8_t s_b[kPlaceTile];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   DevCtl* ctl = a.ctl;
-  const uint64_t nb = a.out_meta->n / kBlock;
+  const uint64_t n = a.out_meta->n, nb = n / kBlock, r = n % kBlock;
   const uint64_t top = *reinterpret_cast<volatile uint64_t*>(&ctl->top);
-  const uint64_t avail = ctl->cap - top;
-  uint64_t* hdr = reinterpret_cast<uint64_t*>(ctl->arena + top);
-  constexpr int kPer = 16;
-  const uint64_t per_tile = (uint64_t)kThreads * kPer;
-  const uint64_t ntiles = (nb + per_tile - 1) / per_tile;
-  if (nb == 0 && blockIdx.x == 0 && threadIdx.x == 0) ctl->op_words = 0;
+  const PlaceRoom room = place_room(ctl, top);
+  const uint64_t avail = room.avail, send = stage_end(ctl);
+  uint8_t* arena = reinterpret_cast<uint8_t*>(ctl->arena);
+  uint8_t* base = arena + top;
+  uint64_t* hdr = reinterpret_cast<uint64_t*>(base);
+  const uint64_t spread = (nb + gridDim.x - 1) / gridDim.x;
+  const int T = (int)min((uint64_t)kPlaceTile, max((uint64_t)8, (spread + 7) / 8 * 8));
+  const uint64_t ntiles = (nb + T - 1) / T;
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const uint64_t g0 = tile * per_tile + (uint64_t)threadIdx.x * kPer;
-    uint32_t wds[kPer];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < kPer; k++) {
-      const uint64_t b = (g0 + k < nb) ? min((uint64_t)64, a.stage_meta[2 * (g0 + k)]) : 0;
-      wds[k] = (uint32_t)(8 * b);
-      sum += wds[k];
-    }
-    const uint32_t texcl = warp_excl_scan32(sum, lane);
-    if (lane == 31) s_warp[warp] = texcl + sum;
+    const uint64_t t0 = tile * T;
+    const int nt = (int)min((uint64_t)T, nb - t0);
+    const int j = threadIdx.x;
+    const uint64_t g = t0 + j;
+    const uint32_t b = j < nt ? (uint32_t)min((uint64_t)64, a.stage_meta[2 * g] & 255) : 0;
+    const uint32_t texcl = warp_excl_scan32(8 * b, lane);
+    if (lane == 31) s_warp[warp] = texcl + 8 * b;
     __syncthreads();
     if (warp == 0) {
       const uint64_t wt = lane < kWarps ? s_warp[lane] : 0;
@@ -1670,58 +1746,54 @@ __global__ void __launch_bounds__(kThreads) k_scan_widths(PlaceArgs a) {
       const uint64_t agg = warp_sum(wt);
       const uint64_t ex = lookback(a.status, tile, agg, lane, ctl);
       if (lane < kWarps) s_warp[lane] = wex;
-      if (lane == 0) s_excl = ex;
-    }
-    __syncthreads();
-    uint64_t o = s_excl + s_warp[warp] + texcl;
-#pragma unroll
-    for (int k = 0; k < kPer; k++) {
-      const uint64_t g = g0 + k;
-      if (g < nb) {
-        a.offsets[g] = o;
-        if (16 * (g + 1) <= avail) {
-          hdr[2 * g] = (o << 8) | (wds[k] / 8);
-          hdr[2 * g + 1] = a.stage_meta[2 * g + 1];
-        } else {
-          set_error(ctl, MS_ERR_NOMEM, g);
-        }
-        o += wds[k];
-        if (g == nb - 1) ctl->op_words = o;
+      if (lane == 0) {
+        s_excl = ex;
+        if (tile == ntiles - 1) ctl->op_words = ex + agg;
       }
     }
     __syncthreads();
-  }
-}
-
-// Placement, step 2: every warp copies staged block payloads to their final
-// offsets (and the last chunk's raw remainder behind the payload); the last CTA
-// completes the column record and moves the arena top past the column.
-template <int kUnused = 0>
-__global__ void __launch_bounds__(kThreads) k_copy_blocks(PlaceArgs a) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  DevCtl* ctl = a.ctl;
-  const uint64_t n = a.out_meta->n, nb = n / kBlock, r = n % kBlock;
-  const uint64_t top = *reinterpret_cast<volatile uint64_t*>(&ctl->top);
-  const uint64_t avail = ctl->cap - top;
-  uint8_t* base = reinterpret_cast<uint8_t*>(ctl->arena + top);
-  const uint64_t pwords = nb ? *reinterpret_cast<volatile uint64_t*>(&ctl->op_words) : 0;
-  const uint64_t gw = (uint64_t)blockIdx.x * kWarps + warp, W = (uint64_t)gridDim.x * kWarps;
-  for (uint64_t g = gw; g < nb; g += W) {
-    const uint64_t off = a.offsets[g];
-    const int b = (int)min((uint64_t)64, a.stage_meta[2 * g]);
-    const uint64_t pay = 16 * nb + 8 * off;
-    if (pay + 64ull * b <= avail) {
-      const uint4* src = reinterpret_cast<const uint4*>(a.stage + 4096 * g);
-      uint4* dst = reinterpret_cast<uint4*>(base + pay);
-      for (int t = lane; t < 4 * b; t += 32) dst[t] = src[t];
-    } else if (lane == 0) {
-      set_error(ctl, MS_ERR_NOMEM, g);
+    const uint64_t tex = s_excl;
+    if (j < nt) {
+      const uint32_t o = (uint32_t)s_warp[warp] + texcl;  // at most 512 words per block: 32 bits
+      s_off[j] = o;
+      s_b[j] = (uint8_t)b;
+      if (16 * (g + 1) <= avail) {
+        hdr[2 * g] = ((tex + o) << 8) | b;
+        hdr[2 * g + 1] = a.stage_meta[2 * g + 1];
+      } else {
+        set_error(ctl, MS_ERR_NOMEM, g);
+      }
     }
+    __syncthreads();
+    for (int jj = warp; jj < nt; jj += kWarps) {
+      const int bb = s_b[jj];
+      const uint64_t gg = t0 + jj;
+      if (bb == 0 || 16 * (gg + 1) > avail) continue;  // nothing to copy, or no header room (raised above)
+      const uint64_t pay = 16 * nb + 8 * (tex + s_off[jj]), at = a.stage_meta[2 * gg] >> 8;
+      if (pay + 64ull * bb <= avail && at >= room.lo && at + 64ull * bb <= send) {
+        const uint4* src = reinterpret_cast<const uint4*>(arena + at);
+        uint4* dst = reinterpret_cast<uint4*>(base + pay);
+        const int units = 4 * bb;  // at most 256: 8 per lane
+        uint4 q[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+          if (lane + 32 * i < units) q[i] = src[lane + 32 * i];
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+          if (lane + 32 * i < units) dst[lane + 32 * i] = q[i];
+      } else if (lane == 0) {  // no room, or the block never reached the stage
+        set_error(ctl, MS_ERR_NOMEM, gg);
+      }
+    }
+    __syncthreads();  // s_off / s_b are reused by the next tile
   }
-  if (r && gw == (nb % W)) {  // one warp places the remainder
-    const uint64_t rem = 16 * nb + 8 * pwords;
-    if (rem + 8 * r <= avail) {
-      const uint64_t* src = reinterpret_cast<const uint64_t*>(a.stage + 4096 * nb);
+  // the remainder, by the CTA of the last tile (CTA 0 when there is no block): that
+  // CTA's warp 0 wrote the total payload words
+  if (r && warp == 0 && blockIdx.x == (ntiles ? (ntiles - 1) % gridDim.x : 0)) {
+    const uint64_t pwords = nb ? *reinterpret_cast<volatile uint64_t*>(&ctl->op_words) : 0;
+    const uint64_t rem = 16 * nb + 8 * pwords, at = a.stage_meta[2 * nb] >> 8;
+    if (rem + 8 * r <= avail && at >= room.lo && at + 8 * r <= send) {
+      const uint64_t* src = reinterpret_cast<const uint64_t*>(arena + at);
       uint64_t* dst = reinterpret_cast<uint64_t*>(base + rem);
       for (uint64_t t = lane; t < r; t += 32) dst[t] = src[t];
     } else if (lane == 0) {
@@ -1734,6 +1806,7 @@ __global__ void __launch_bounds__(kThreads) k_copy_blocks(PlaceArgs a) {
     const unsigned prev = atomicAdd(&ctl->done, 1u);
     if (prev == gridDim.x - 1) {
       __threadfence();
+      const uint64_t pwords = nb ? *reinterpret_cast<volatile uint64_t*>(&ctl->op_words) : 0;
       const uint64_t size = 16 * nb + 8 * pwords + 8 * r;
       DevMeta* m = a.out_meta;
       m->ptr = reinterpret_cast<uint64_t>(base);
@@ -1750,8 +1823,11 @@ __global__ void __launch_bounds__(kThreads) k_copy_blocks(PlaceArgs a) {
         m->pwords = 0;
       } else {
         ctl->top = top + grow;
-        if (top + grow > ctl->high) ctl->high = top + grow;
+        // the stage below the arena's end was in use beside the new column
+        const uint64_t peak = top + grow + (send - room.lo);
+        if (peak > ctl->high) ctl->high = peak;
       }
+      ctl->stage = 0;
       ctl->done = 0;
       __threadfence();
     }

@@ -17,9 +17,7 @@ struct Work {
   uint64_t* bstart;      // per-output-block first chunk
   uint32_t* counts;      // per-chunk match counts
   uint32_t* keybits;     // semi-join membership bitmap
-  uint8_t* stage;        // one 4 KB slot per output block (block-format outputs)
-  uint64_t* stage_meta;  // {width, reference} per output block
-  uint64_t* offsets;     // payload word offset per output block
+  uint64_t* stage_meta;  // {(stage offset << 8) | width, reference} per output block
 };
 
 ms_status carve(ms_ctx* c, uint64_t n_max, uint64_t key_domain, Work* w, cudaStream_t s);

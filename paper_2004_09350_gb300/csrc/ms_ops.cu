@@ -15,18 +15,15 @@ ms_status carve(ms_ctx* c, uint64_t n_max, uint64_t key_domain, Work* w, cudaStr
   const uint64_t co_b = align_up(8 * (nch + 2), 256);
   const uint64_t kb_b = align_up(4 * cdiv(std::max<uint64_t>(key_domain, 1), 32), 256);
   const uint64_t cn_b = align_up(4 * (nch + 1), 256);
-  const uint64_t sg_b = 4096 * (nch + 1);
   const uint64_t sm_b = align_up(16 * (nch + 1), 256);
-  const uint64_t of_b = align_up(8 * (nch + 1), 256);
-  const uint64_t total = 2 * st_b + bm_b + 2 * co_b + kb_b + cn_b + sg_b + sm_b + of_b;
+  // about 102 bytes per 512 rows; block payloads are staged in the arena
+  const uint64_t total = 2 * st_b + bm_b + 2 * co_b + kb_b + cn_b + sm_b;
   ms_status st = ensure_work(c, total);
   if (st != MS_OK) return st;
   uint8_t* p = c->work;
   w->status = reinterpret_cast<uint64_t*>(p);
   w->status2 = reinterpret_cast<uint64_t*>(p + st_b);
   p += 2 * st_b;
-  w->stage = p;  // 4 KB aligned slots (the work area starts 256-byte aligned)
-  p += sg_b;
   w->bitmap = reinterpret_cast<uint16_t*>(p);
   p += bm_b;
   w->coff = reinterpret_cast<uint64_t*>(p);
@@ -38,8 +35,6 @@ ms_status carve(ms_ctx* c, uint64_t n_max, uint64_t key_domain, Work* w, cudaStr
   w->counts = reinterpret_cast<uint32_t*>(p);
   p += cn_b;
   w->stage_meta = reinterpret_cast<uint64_t*>(p);
-  p += sm_b;
-  w->offsets = reinterpret_cast<uint64_t*>(p);
   return cuda_status(cudaMemsetAsync(c->work, 0, 2 * st_b, s));
 }
 
@@ -103,11 +98,12 @@ ms_status produce_column(ms_ctx* c, ProduceArgs& a, const Work& w, uint64_t n_ma
   a.out_meta = c->metas + col->slot;
   a.fmt = fmt;
   a.bw = fmt == MS_STATIC_BP ? bw : 0;
-  a.stage = w.stage;
   a.stage_meta = w.stage_meta;
   ms_status st = launch_map<OP>(c, a, n_max, s);
   if (st == MS_OK && fmt >= MS_DYN_BP) st = launch_place(c, w, a.out_meta, n_max, s);
   if (st != MS_OK) {
+    // a producer that ran without its placement leaves stage bytes taken
+    cudaMemsetAsync(&c->ctl->stage, 0, 8, s);
     drop_new_column(c, col);
     return st;
   }

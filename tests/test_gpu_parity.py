@@ -430,6 +430,45 @@ def test_arena_is_lifo_and_tracks_high_water(ctx):
     assert ctx.arena_usage()[1] == high
 
 
+@pytest.mark.parametrize("fmt", [ms.DYN_BP, ms.DELTA_BP, ms.FOR_BP])
+def test_block_outputs_stage_at_the_arena_end(fmt):
+    """A block-format output waits in a stage taken from the arena's free end until
+    the placement pass puts it behind its headers.  The high-water mark counts the
+    stage beside the new column, the stage is released after every operator, and
+    a column whose stage does not fit beside it is reported (MS_ERR_NOMEM) and
+    published empty."""
+    n = 500_000 + 37
+    x = synth.skewed_widths(83, n)
+    want = oracle.compress(fmt, x)
+    size = want.nbytes
+    payload = size - 16 * (n // 512) - 8 * (n % 512)
+    with ms.Ctx(0, arena_bytes=4 * size + (1 << 20), max_rows=n) as big:
+        base, _ = big.arena_usage()
+        big.reset_high_water()
+        col = big.compress(ms.as_device_u64(x, big.device), fmt)
+        used, high = big.arena_usage()
+        assert used - base == (size + 255) // 256 * 256
+        assert high - base >= used - base + payload
+        assert big.export_bytes(col).tobytes() == want.tobytes()
+        for _ in range(6):  # each output's stage is released: repeated outputs fit
+            tmp = big.calc(ms.ADD, col, None, 1, fmt=fmt)
+            big.free(tmp)
+        big.check(what="repeated staged outputs")
+        big.free(col)
+    arena = (size + size // 2 + 255) // 256 * 256  # the column alone fits, not beside its stage
+    assert arena < size + payload
+    with ms.Ctx(0, arena_bytes=arena, max_rows=n) as small:
+        col = small.compress(ms.as_device_u64(x, small.device), fmt)
+        assert small.get_error() == ms.MS_ERR_NOMEM
+        assert small.info(col)["n"] == 0 and small.info(col)["size_bytes"] == 0
+        small.free(col)
+        assert small.get_error() == ms.MS_OK
+        tiny = x[: 20_000]
+        t = small.compress(ms.as_device_u64(tiny, small.device), fmt)
+        small.check(what="stage released after a failed output")
+        assert small.export_bytes(t).tobytes() == oracle.compress(fmt, tiny).tobytes()
+
+
 @pytest.mark.parametrize("fmt", [ms.UNCOMPR, ms.DELTA_BP, ms.DYN_BP])
 def test_select_and_semijoin_on_short_intermediates(ctx, fmt):
     """Operators on intermediates whose real length is far below the host-side
