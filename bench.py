@@ -567,11 +567,12 @@ def oracle_star_plan(fact, dims, codec=True):
     from paper_2004_09350_gb300 import plans, synth
     fm = {k: int(v) for k, v in plans.STAR_COMPRESSED.items()}
     fb = {k: int(v) for k, v in plans.STAR_BASE_COMPRESSED.items()}
-    packed = {k: oracle.compress(fb[k], v) for k, v in {**fact, **dims}.items()} if codec else None
+    packed = ({k: oracle.compress(fb[k], v, bw=plans.base_width(k, fb[k])) for k, v in {**fact, **dims}.items()}
+              if codec else None)
     t0 = time.perf_counter()
     if codec:
         src = {**fact, **dims}
-        b = {k: oracle.decompress(fb[k], src[k].size, packed[k]) for k in src}
+        b = {k: oracle.decompress(fb[k], src[k].size, packed[k], bw=plans.base_width(k, fb[k])) for k in src}
     else:
         b = {**fact, **dims}
 
@@ -796,7 +797,7 @@ def bench_star(args):
                 "clocks": ck_info, "op_ms_sizing_step": op_ms,
                 "per_kernel_ms": {k: round(v[1] / args.steps, 4) for k, v in prof.items()}}
 
-    base_c = {k: ctx.compress(v, plans.STAR_BASE_COMPRESSED[k]) for k, v in raw.items()}
+    base_c = plans.compress_base(ctx, raw, plans.STAR_BASE_COMPRESSED)
     ctx.check(what="star base")
     out["compressed"] = run_variant("compressed", base_c, plans.STAR_COMPRESSED)
     out["compressed"]["_base"] = base_c
@@ -809,7 +810,7 @@ def bench_star(args):
     out["greedy"] = run_variant("greedy", base_c, fm_g)
     out["greedy"]["formats"] = {k: ms.FORMAT_NAMES[v] for k, v in fm_g.items()}
     out["greedy"]["search"] = {"evaluations": evals, "seconds": round(search_s, 1)}
-    base_u = {k: ctx.compress(v, plans.STAR_BASE_UNCOMPRESSED[k]) for k, v in raw.items()}
+    base_u = plans.compress_base(ctx, raw, plans.STAR_BASE_UNCOMPRESSED)
     ctx.check(what="star base")
     out["uncompressed"] = run_variant("uncompressed", base_u, plans.STAR_UNCOMPRESSED)
     out["uncompressed"]["_base"] = base_u
@@ -841,7 +842,7 @@ def bench_star(args):
         res = torch.zeros(plans.STAR_GROUPS, dtype=torch.int64, device=dev)
 
         def step():
-            imp = {k: ctx.import_bytes(base_fm[k], rows[k], host[k]) for k in base}
+            imp = {k: ctx.import_bytes(base_fm[k], rows[k], host[k], bw=plans.base_width(k, base_fm[k])) for k in base}
             _, cols = plans.star_plan(ctx, imp, fm, out=res)
             plans.free_lifo(ctx, cols)
             hres.copy_(res, non_blocking=True)
@@ -892,8 +893,8 @@ def bench_star(args):
         "ms_per_step_best": comp["ms_per_step_best"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded SplitMix64, generated on the GPU)",
         "config": {"workload": STAR_WORKLOAD, "fact_rows": n, "dimension_rows": list(synth.DIM_SIZES),
-                   "formats": "base: fk_date DELTA+BP, other columns dynamic BP; positions DELTA+BP, values "
-                              "dynamic BP",
+                   "formats": "base: columns read at positions static BP, fk_date DELTA+BP, scanned columns "
+                              "dynamic BP; positions DELTA+BP, values dynamic BP",
                    "l2": "inputs larger than L2 (compressed fact columns %.2f GB)" % (comp["base_bytes"] / 1e9),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",

@@ -955,6 +955,134 @@ MS_DEV void decode_delta_block(const ColView& d, uint64_t B, uint64_t w0, uint64
   }
 }
 
+// project core, DELTA data, sorted positions (the usual case: the positions come
+// from a select or a semi-join).  The warp's positions span blocks Bf..Bl; taken
+// relative to block Bf they fit 32 bits, and every touched block is visited once,
+// in order: a block of width 0 answers its positions with its reference, any other
+// is decoded straight from global memory into `aux` as prefix sums relative to its
+// reference (32-bit when the block is at most 23 bits wide: 511 residuals below
+// 2^23 sum below 2^32), and its positions are read from there.  Returns false, with
+// v untouched, when the positions are unsorted, out of range or span 2^31 rows or
+// more (project_delta handles those).
+MS_DEV bool project_delta_sorted(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
+                                 uint64_t v[16], uint64_t* aux) {
+  const int nv = max(0, min(16, valid - 16 * lane));
+  bool ok = valid > 0;
+  uint64_t mx = 0;
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    if (k < nv) {
+      ok &= p[k] < d.n;
+      if (k) ok &= p[k - 1] <= p[k];
+      mx = p[k];
+    }
+  }
+  const uint64_t prev_mx = __shfl_up_sync(kFull, mx, 1);
+  if (lane > 0 && nv > 0 && prev_mx > p[0]) ok = false;
+  if (!__all_sync(kFull, ok)) return false;
+  const uint64_t first = __shfl_sync(kFull, p[0], 0);
+  const uint64_t last = __shfl_sync(kFull, mx, (valid - 1) >> 4);
+  if (last - first >= (1ull << 31)) return false;
+  const uint64_t Bf = first >> 9, base = Bf << 9;
+  uint32_t rel[16];
+#pragma unroll
+  for (int k = 0; k < 16; k++) rel[k] = (uint32_t)(p[k] - base);
+  uint32_t pend = nv >= 16 ? 0xffffu : (1u << nv) - 1u;
+  if ((last >> 9) - Bf >= 8) {
+    // sparse positions: those in blocks of width 0 are answered from their headers
+    // first (one load per position, mostly L1 hits), so that the block walk below
+    // visits only blocks that need decoding
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const uint64_t B = Bf + (rel[k] >> 9);
+      if (((pend >> k) & 1u) && B < d.nb && 16 * (B + 1) <= d.size) {
+        const ulonglong2 h = __ldg(reinterpret_cast<const ulonglong2*>(d.p) + B);
+        if ((h.x & 255) == 0) {
+          v[k] = h.y;
+          pend &= ~(1u << k);
+        }
+      }
+    }
+  }
+  uint32_t* aux32 = reinterpret_cast<uint32_t*>(aux);
+  while (__any_sync(kFull, pend != 0)) {
+    // the next touched block: the smallest block among the lanes' pending positions
+    uint32_t m = 0xffffffffu;
+#pragma unroll
+    for (int k = 0; k < 16; k++) m = min(m, ((pend >> k) & 1u) ? rel[k] : 0xffffffffu);
+    const uint32_t blk = __reduce_min_sync(kFull, m >> 9);
+    uint32_t hit = 0;
+#pragma unroll
+    for (int k = 0; k < 16; k++) hit |= (uint32_t)(((pend >> k) & 1u) && (rel[k] >> 9) == blk) << k;
+    const uint64_t B = Bf + blk;
+    if (B >= d.nb) {  // the raw remainder behind the payload
+      const uint64_t at = 16 * d.nb + 8 * d.pwords;
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        const uint64_t o = rel[k] & 511;
+        if ((hit >> k) & 1u) v[k] = at + 8 * (o + 1) <= d.size ? ldg64(d.p + at + 8 * o) : 0;
+      }
+    } else {
+      ulonglong2 h = make_ulonglong2(0, 0);
+      if (16 * (B + 1) <= d.size) h = __ldg(reinterpret_cast<const ulonglong2*>(d.p) + B);
+      else if (lane == 0) set_error(a.ctl, MS_ERR_FORMAT, B);
+      int b = (int)(h.x & 255);
+      const uint64_t pay = 16 * d.nb + 8 * (h.x >> 8);
+      if (b > 64 || pay + 64ull * b > d.size) {
+        if (lane == 0) set_error(a.ctl, MS_ERR_FORMAT, B);
+        b = 0;
+      }
+      if (b == 0) {  // 512 copies of the reference
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+          if ((hit >> k) & 1u) v[k] = h.y;
+      } else {
+        uint64_t t[16];
+        read_lane_stream(reinterpret_cast<const uint16_t*>(d.p + pay), lane, b, t);
+        // value i of the block is ref + (residuals 0..i summed); residual 0 is 0.
+        // Stored transposed (slot 32k + lane for value 16 lane + k): the stores are
+        // conflict-free
+        if (b <= 23) {
+          uint32_t sum = 0;
+#pragma unroll
+          for (int k = 0; k < 16; k++) {
+            sum += (uint32_t)t[k];
+            t[k] = sum;
+          }
+          const uint32_t ex = warp_excl_scan32(sum, lane);
+#pragma unroll
+          for (int k = 0; k < 16; k++) aux32[32 * k + lane] = (uint32_t)t[k] + ex;
+          __syncwarp();
+#pragma unroll
+          for (int k = 0; k < 16; k++) {
+            const uint32_t o = rel[k] & 511;
+            if ((hit >> k) & 1u) v[k] = h.y + aux32[32 * (o & 15) + (o >> 4)];
+          }
+        } else {
+          uint64_t sum = 0;
+#pragma unroll
+          for (int k = 0; k < 16; k++) {
+            sum += t[k];
+            t[k] = sum;
+          }
+          const uint64_t ex = warp_excl_scan(sum, lane);
+#pragma unroll
+          for (int k = 0; k < 16; k++) aux[32 * k + lane] = t[k] + ex;
+          __syncwarp();
+#pragma unroll
+          for (int k = 0; k < 16; k++) {
+            const uint32_t o = rel[k] & 511;
+            if ((hit >> k) & 1u) v[k] = h.y + aux[32 * (o & 15) + (o >> 4)];
+          }
+        }
+        __syncwarp();  // aux is rewritten by the next block
+      }
+    }
+    pend &= ~hit;
+  }
+  return true;
+}
+
 // project core, DELTA data: values need their block's prefix sums.  First every
 // position's block header is read (sixteen independent loads per lane, nearly all
 // hits in L1): a block of width 0 holds 512 copies of its reference, and its
@@ -1664,8 +1792,11 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
         uint64_t p[16];
         valid = st0.decode(i, p, ctl);
         __syncwarp();
-        if (c0.fmt == MS_DELTA_BP) project_delta(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage), sm->aux);
-        else project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
+        if (c0.fmt != MS_DELTA_BP) {
+          project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
+        } else if (!project_delta_sorted(a, c0, p, valid, lane, v, sm->aux)) {
+          project_delta(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage), sm->aux);
+        }
       }
       __syncwarp();
     }

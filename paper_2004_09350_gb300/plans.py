@@ -44,10 +44,28 @@ STAR_COMPRESSED = {
 }
 STAR_UNCOMPRESSED = {k: ms.UNCOMPR for k in STAR_COMPRESSED}
 
-STAR_BASE_COMPRESSED = {"fk1": ms.DYN_BP, "fk2": ms.DYN_BP, "fk3": ms.DYN_BP, "fk_date": ms.DELTA_BP,
-                        "quantity": ms.DYN_BP, "discount": ms.DYN_BP, "revenue": ms.DYN_BP,
-                        "d1_c5": ms.DYN_BP, "d2_c25": ms.DYN_BP, "date_year": ms.DYN_BP}
+# Base columns.  Sec. 4.2 allows random access only into uncompressed and static-BP
+# columns: the columns that the plan projects at positions (fk2, discount, quantity,
+# revenue, d2_c25, date_year) are static BP at the width of their value domain, so a
+# value is read without a block header; the sorted date key is DELTA+BP; the columns
+# that are only scanned are dynamic BP.
+STAR_BASE_COMPRESSED = {"fk1": ms.DYN_BP, "fk2": ms.STATIC_BP, "fk3": ms.DYN_BP, "fk_date": ms.DELTA_BP,
+                        "quantity": ms.STATIC_BP, "discount": ms.STATIC_BP, "revenue": ms.STATIC_BP,
+                        "d1_c5": ms.DYN_BP, "d2_c25": ms.STATIC_BP, "date_year": ms.STATIC_BP}
 STAR_BASE_UNCOMPRESSED = {k: ms.UNCOMPR for k in STAR_BASE_COMPRESSED}
+# static-BP widths: the value domains of the generated columns (fk2 < 2e5, quantity
+# <= 50, discount <= 10, revenue < 2^23, c25 < 25, year < 7)
+STAR_BASE_WIDTHS = {"fk2": 18, "quantity": 6, "discount": 4, "revenue": 23, "d2_c25": 5, "date_year": 3}
+
+
+def base_width(name: str, fmt: int) -> int:
+    """Static-BP width of a star base column in format fmt (0 for other formats)."""
+    return STAR_BASE_WIDTHS[name] if fmt == ms.STATIC_BP else 0
+
+
+def compress_base(ctx, cols, formats):
+    """The star plan's base columns (device tensors by name) compressed in `formats`."""
+    return {k: ctx.compress(v, formats[k], base_width(k, formats[k])) for k, v in cols.items()}
 
 
 def star_plan(ctx, base, fm, out=None, trace=None):

@@ -222,6 +222,40 @@ def test_project_sorted_spans(ctx, data_fmt, step):
     ctx.free(dcol)
 
 
+@pytest.mark.parametrize("kind", ["gaps", "random", "flat", "widths"])
+@pytest.mark.parametrize("step", [0, 1, 3, 70, 2000])
+def test_project_delta_data_sorted_positions(ctx, kind, step):
+    """DELTA data read at sorted positions (repeats allowed) block by block: narrow
+    blocks (32-bit prefix sums), blocks whose differences wrap modulo 2^64 (64-bit
+    sums), blocks of width 0 (answered by their reference), the 22..24-bit switch,
+    spans from one block to hundreds, and positions in the raw remainder."""
+    n = 200 * 512 + 77
+    if kind == "gaps":
+        d = synth.sorted_gaps(51, n)
+    elif kind == "random":
+        d = synth.splitmix64(52, n)
+    elif kind == "flat":
+        d = np.repeat(synth.uniform(53, n // 700 + 1, 0, 1 << 40), 700)[:n]
+    else:
+        d = delta_width_column([22, 23, 24, 0, 1, 40, 64] * 28, tail=77)
+        n = d.size
+    dcol, _ = gpu_col(ctx, d, ms.DELTA_BP)
+    if step == 0:  # sorted random positions with repeats
+        pos = np.sort(synth.uniform(54, 20_000, 0, n))
+    else:
+        pos = np.arange(step // 2, n, step, dtype=np.uint64)
+    pos = np.concatenate([pos, np.arange(n - 30, n, dtype=np.uint64)])
+    pos.sort()
+    pcol, _ = gpu_col(ctx, pos, ms.DELTA_BP)
+    want = oracle.project(d, pos)
+    for out_fmt in (ms.UNCOMPR, ms.DELTA_BP):
+        out = ctx.project(dcol, pcol, fmt=out_fmt)
+        assert_column(ctx, out, want, out_fmt)
+        ctx.free(out)
+    ctx.free(pcol)
+    ctx.free(dcol)
+
+
 @pytest.mark.parametrize("data_fmt", FMTS)
 @pytest.mark.parametrize("pos_fmt", FMTS)
 def test_project_position_formats_and_unsorted(ctx, data_fmt, pos_fmt):

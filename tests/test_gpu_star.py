@@ -39,7 +39,8 @@ def test_star_plan_matches_oracle(base_fm, fm):
     want, matched = oracle_star(fact, dims)
     assert 0.01 < matched / n < 0.022  # 0.2 * 0.6 * 3/11 * 24/50 = 1.57%
     with ms.Ctx(0, arena_bytes=1 << 30, max_rows=1 << 22) as ctx:
-        base = {k: ctx.compress(ms.as_device_u64(v, ctx.device), base_fm[k]) for k, v in {**fact, **dims}.items()}
+        base = plans.compress_base(ctx, {k: ms.as_device_u64(v, ctx.device) for k, v in {**fact, **dims}.items()},
+                                   base_fm)
         res, cols = plans.star_plan(ctx, base, fm)
         got = ms.to_numpy_u64(res)
         ctx.check(what="star plan")
@@ -58,8 +59,8 @@ def test_star_plan_intermediates_match_oracle(base_fm, fm):
     dims = synth.star_dims(6)
     D = synth.DIM_SIZES
     with ms.Ctx(0, arena_bytes=1 << 30, max_rows=1 << 20) as ctx:
-        base = {k: ctx.compress(ms.as_device_u64(v, ctx.device), base_fm[k])
-                for k, v in {**fact, **dims}.items()}
+        base = plans.compress_base(ctx, {k: ms.as_device_u64(v, ctx.device) for k, v in {**fact, **dims}.items()},
+                                   base_fm)
         assert ctx.get_error() == ms.MS_OK
         want, got = {}, {}
         steps = [
@@ -120,8 +121,8 @@ def test_greedy_plan_formats_keep_results_and_meet_their_objective(objective):
     dims = synth.star_dims(10)
     want, _ = oracle_star(fact, dims)
     with ms.Ctx(0, arena_bytes=1 << 30, max_rows=1 << 20) as ctx:
-        base = {k: ctx.compress(ms.as_device_u64(v, ctx.device), plans.STAR_BASE_COMPRESSED[k])
-                for k, v in {**fact, **dims}.items()}
+        base = plans.compress_base(ctx, {k: ms.as_device_u64(v, ctx.device) for k, v in {**fact, **dims}.items()},
+                                   plans.STAR_BASE_COMPRESSED)
         run = lambda fm: plans.star_plan(ctx, base, fm)  # noqa: E731
         start = dict(plans.STAR_COMPRESSED)
         c0 = plans.plan_cost(ctx, run, start, objective, reps=2)
