@@ -963,9 +963,11 @@ MS_DEV void decode_delta_block(const ColView& d, uint64_t B, uint64_t w0, uint64
 // reference (32-bit when the block is at most 23 bits wide: 511 residuals below
 // 2^23 sum below 2^32), and its positions are read from there.  Returns false, with
 // v untouched, when the positions are unsorted, out of range or span 2^31 rows or
-// more (project_delta handles those).
+// more (project_delta handles those).  The values collect in `ob` (lane-private
+// slots 32k + lane, conflict-free) and come back to v at the end, so they do not hold
+// registers during the walk.
 MS_DEV bool project_delta_sorted(const ProduceArgs& a, const ColView& d, const uint64_t p[16], int valid, int lane,
-                                 uint64_t v[16], uint64_t* aux) {
+                                 uint64_t v[16], uint64_t* aux, uint64_t* ob) {
   const int nv = max(0, min(16, valid - 16 * lane));
   bool ok = valid > 0;
   uint64_t mx = 0;
@@ -988,17 +990,17 @@ MS_DEV bool project_delta_sorted(const ProduceArgs& a, const ColView& d, const u
 #pragma unroll
   for (int k = 0; k < 16; k++) rel[k] = (uint32_t)(p[k] - base);
   uint32_t pend = nv >= 16 ? 0xffffu : (1u << nv) - 1u;
-  if ((last >> 9) - Bf >= 8) {
-    // sparse positions: those in blocks of width 0 are answered from their headers
-    // first (one load per position, mostly L1 hits), so that the block walk below
-    // visits only blocks that need decoding
+  if ((last >> 9) - Bf >= 32) {
+    // sparse positions (16 or fewer per spanned block): those in blocks of width 0
+    // are answered from their headers first (one load per position, mostly L1
+    // hits), so that the block walk below visits only blocks that need decoding
 #pragma unroll
     for (int k = 0; k < 16; k++) {
       const uint64_t B = Bf + (rel[k] >> 9);
       if (((pend >> k) & 1u) && B < d.nb && 16 * (B + 1) <= d.size) {
         const ulonglong2 h = __ldg(reinterpret_cast<const ulonglong2*>(d.p) + B);
         if ((h.x & 255) == 0) {
-          v[k] = h.y;
+          ob[32 * k + lane] = h.y;
           pend &= ~(1u << k);
         }
       }
@@ -1020,7 +1022,7 @@ MS_DEV bool project_delta_sorted(const ProduceArgs& a, const ColView& d, const u
 #pragma unroll
       for (int k = 0; k < 16; k++) {
         const uint64_t o = rel[k] & 511;
-        if ((hit >> k) & 1u) v[k] = at + 8 * (o + 1) <= d.size ? ldg64(d.p + at + 8 * o) : 0;
+        if ((hit >> k) & 1u) ob[32 * k + lane] = at + 8 * (o + 1) <= d.size ? ldg64(d.p + at + 8 * o) : 0;
       }
     } else {
       ulonglong2 h = make_ulonglong2(0, 0);
@@ -1035,7 +1037,7 @@ MS_DEV bool project_delta_sorted(const ProduceArgs& a, const ColView& d, const u
       if (b == 0) {  // 512 copies of the reference
 #pragma unroll
         for (int k = 0; k < 16; k++)
-          if ((hit >> k) & 1u) v[k] = h.y;
+          if ((hit >> k) & 1u) ob[32 * k + lane] = h.y;
       } else {
         uint64_t t[16];
         read_lane_stream(reinterpret_cast<const uint16_t*>(d.p + pay), lane, b, t);
@@ -1056,7 +1058,7 @@ MS_DEV bool project_delta_sorted(const ProduceArgs& a, const ColView& d, const u
 #pragma unroll
           for (int k = 0; k < 16; k++) {
             const uint32_t o = rel[k] & 511;
-            if ((hit >> k) & 1u) v[k] = h.y + aux32[32 * (o & 15) + (o >> 4)];
+            if ((hit >> k) & 1u) ob[32 * k + lane] = h.y + aux32[32 * (o & 15) + (o >> 4)];
           }
         } else {
           uint64_t sum = 0;
@@ -1072,7 +1074,7 @@ MS_DEV bool project_delta_sorted(const ProduceArgs& a, const ColView& d, const u
 #pragma unroll
           for (int k = 0; k < 16; k++) {
             const uint32_t o = rel[k] & 511;
-            if ((hit >> k) & 1u) v[k] = h.y + aux[32 * (o & 15) + (o >> 4)];
+            if ((hit >> k) & 1u) ob[32 * k + lane] = h.y + aux[32 * (o & 15) + (o >> 4)];
           }
         }
         __syncwarp();  // aux is rewritten by the next block
@@ -1080,6 +1082,10 @@ MS_DEV bool project_delta_sorted(const ProduceArgs& a, const ColView& d, const u
     }
     pend &= ~hit;
   }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 16; k++) v[k] = k < nv ? ob[32 * k + lane] : 0;
+  __syncwarp();
   return true;
 }
 
@@ -1595,9 +1601,11 @@ MS_DEV void store_staged(const ProduceArgs& a, int fmt, int bw, bool blockfmt, u
 MS_DEV void publish_staged(const ProduceArgs& a, uint64_t n_out, int fmt, int bw, bool blockfmt, uint8_t* base,
                            uint64_t top, uint64_t avail) {
   DevCtl* ctl = a.ctl;
-  __threadfence();
+  // The last CTA reads nothing that another CTA wrote (later kernels see the output
+  // through the kernel boundary), so only the counter needs ordering.
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     const unsigned prev = atomicAdd(&ctl->done, 1u);
     if (prev == gridDim.x - 1) {
       __threadfence();
@@ -1645,7 +1653,8 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
 
   DevCtl* ctl = a.ctl;
   const bool raw = a.out_meta == nullptr;
-  const uint64_t top = raw ? 0 : *reinterpret_cast<volatile uint64_t*>(&ctl->top);
+  // the arena top changes only in the last CTA to finish, after every CTA read it
+  const uint64_t top = raw ? 0 : ldg64(&ctl->top);
   const uint64_t avail = raw ? 8 * a.raw_cap : ctl->cap - top;
   uint8_t* base = raw ? reinterpret_cast<uint8_t*>(a.raw_out) : reinterpret_cast<uint8_t*>(ctl->arena + top);
 
@@ -1794,7 +1803,7 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
         __syncwarp();
         if (c0.fmt != MS_DELTA_BP) {
           project_direct(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage));
-        } else if (!project_delta_sorted(a, c0, p, valid, lane, v, sm->aux)) {
+        } else if (!project_delta_sorted(a, c0, p, valid, lane, v, sm->aux, reinterpret_cast<uint64_t*>(out_stage))) {
           project_delta(a, c0, p, valid, lane, v, reinterpret_cast<uint64_t*>(out_stage), sm->aux);
         }
       }
@@ -1838,9 +1847,12 @@ struct PlaceRoom {
   uint64_t avail, lo;
 };
 
+// (The stage size and the arena top were set by earlier kernels and change only in
+// the last CTA to finish, after every CTA read them: cached loads, so that the CTAs
+// do not all queue on the control block's line in L2.)
 MS_DEV PlaceRoom place_room(const DevCtl* ctl, uint64_t top) {
   const uint64_t end = stage_end(ctl);
-  const uint64_t used = min(*reinterpret_cast<const volatile uint64_t*>(&ctl->stage), end - top);
+  const uint64_t used = min(ldg64(&ctl->stage), end - top);
   return PlaceRoom{end - used - top, end - used};
 }
 
@@ -1852,8 +1864,8 @@ __global__ void __launch_bounds__(kThreads) k_place(PlaceArgs a) {
   __shared__ uint8_t s_b[kPlaceTile];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   DevCtl* ctl = a.ctl;
-  const uint64_t n = a.out_meta->n, nb = n / kBlock, r = n % kBlock;
-  const uint64_t top = *reinterpret_cast<volatile uint64_t*>(&ctl->top);
+  const uint64_t n = ldg64(&a.out_meta->n), nb = n / kBlock, r = n % kBlock;
+  const uint64_t top = ldg64(&ctl->top);
   const PlaceRoom room = place_room(ctl, top);
   const uint64_t avail = room.avail, send = stage_end(ctl);
   uint8_t* arena = reinterpret_cast<uint8_t*>(ctl->arena);
@@ -1931,9 +1943,11 @@ __global__ void __launch_bounds__(kThreads) k_place(PlaceArgs a) {
       set_error(ctl, MS_ERR_NOMEM, nb);
     }
   }
-  __threadfence();
+  // The last CTA reads only the total payload words, which thread 0 of the last
+  // tile's CTA wrote before its fence and increment below.
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     const unsigned prev = atomicAdd(&ctl->done, 1u);
     if (prev == gridDim.x - 1) {
       __threadfence();

@@ -385,6 +385,27 @@ def test_semijoin(ctx, probe_fmt, out_fmt):
     ctx.free(cp)
 
 
+@pytest.mark.parametrize("dom", [1_500_000, 3_000_000, 40_000_000])
+def test_semijoin_large_key_domains(ctx, dom):
+    """Key bitmaps that fit one CTA's shared memory (1.5e6 keys) and larger ones
+    probed through L1 and L2 (3e6 keys, 375 KB; 4e7 keys, 5 MB); probe values span
+    the whole domain, with some at or beyond its end."""
+    n = 9 * 4096 + 313
+    probe = synth.uniform(55, n, 0, dom)
+    probe[:50] = np.uint64(dom - 1)
+    probe[50:60] = np.uint64(dom) + np.arange(10, dtype=np.uint64)
+    keys = np.sort(synth.uniform(56, 40_000, 0, dom))
+    keys[-1] = dom - 1
+    for probe_fmt in (ms.DYN_BP, ms.UNCOMPR):
+        cp, _ = gpu_col(ctx, probe, probe_fmt)
+        ck, _ = gpu_col(ctx, keys, ms.DELTA_BP)
+        out = ctx.semijoin(cp, ck, dom, fmt=ms.DELTA_BP)
+        assert_column(ctx, out, oracle.semijoin(probe, keys, dom), ms.DELTA_BP)
+        ctx.free(out)
+        ctx.free(ck)
+        ctx.free(cp)
+
+
 # ------------------------------------------------------------------ plans
 
 def test_tiny_fragment_plan_bit_exact(ctx):
