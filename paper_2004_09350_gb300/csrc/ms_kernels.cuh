@@ -830,6 +830,47 @@ MS_DEV void gather_values(const ColView& d, uint64_t* stage, uint32_t ok, int la
   const uint64_t nb = stat ? d.n / kBlock : d.nb;
   const uint64_t pay0 = stat ? 0 : 16 * nb;
   const uint64_t rem0 = stat ? 64ull * (uint64_t)d.bw * nb : 16 * nb + 8 * d.pwords;
+  if (stat && d.bw <= 33) {
+    // static BP up to 33 bits: no header, and three halfwords cover a value at any
+    // bit phase, so eight positions' loads are in flight at once
+    const int b = d.bw;
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+      uint32_t h[8][3];
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const int i = 8 * half + u;
+        const uint64_t q = stage[swz(lane + 32 * i)];
+        const uint64_t g = q >> 9;
+        const int r = (int)(q & 511), bit0 = (r & 15) * b;
+        const bool in = ((ok >> i) & 1u) && g < nb && 64ull * b * (g + 1) <= d.size;
+        const int nq = in ? (((bit0 & 15) + b + 15) >> 4) : 0;
+        const uint16_t* hw = reinterpret_cast<const uint16_t*>(d.p + (in ? 64ull * b * g : 0)) + 32 * (bit0 >> 4) +
+                             (r >> 4);
+#pragma unroll
+        for (int t = 0; t < 3; t++) h[u][t] = t < nq ? (uint32_t)__ldg(hw + 32 * t) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const int i = 8 * half + u;
+        const uint64_t q = stage[swz(lane + 32 * i)];  // re-read: fewer live registers
+        const int r = (int)(q & 511);
+        const int sh = ((r & 15) * b) & 15;
+        const uint64_t w = (uint64_t)h[u][0] | ((uint64_t)h[u][1] << 16) | ((uint64_t)h[u][2] << 32);
+        uint64_t v = (w >> sh) & lowmask(b);
+        if ((q >> 9) >= nb) {  // the horizontal tail
+          const uint64_t bit = (uint64_t)r * (uint64_t)b;
+          const int s2 = (int)(bit & 63);
+          const uint64_t at = rem0 + 8 * (bit >> 6);
+          uint64_t y = at + 8 <= d.size ? ldg64(d.p + at) >> s2 : 0;
+          if (s2 + b > 64 && at + 16 <= d.size) y |= ldg64(d.p + at + 8) << (64 - s2);
+          v = y & lowmask(b);
+        }
+        stage[swz(lane + 32 * i)] = ((ok >> i) & 1u) ? v : 0;
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int half = 0; half < 16 / kGatherGroup; half++) {
     uint64_t q[kGatherGroup], w0[kGatherGroup], ref[kGatherGroup];

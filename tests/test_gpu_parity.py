@@ -222,6 +222,27 @@ def test_project_sorted_spans(ctx, data_fmt, step):
     ctx.free(dcol)
 
 
+@pytest.mark.parametrize("bw", [1, 5, 17, 23, 32, 33, 34, 64])
+def test_project_static_data_at_random(ctx, bw):
+    """Static-BP data read in place at sparse sorted and at unsorted positions, at
+    widths on both sides of the 33-bit limit of the three-halfword read, with
+    positions in the horizontal tail."""
+    n = 120 * 512 + 333
+    d = edge_column(n, bw, seed=bw)
+    dcol, _ = gpu_col(ctx, d, ms.STATIC_BP, bw=bw)
+    sparse = np.sort(synth.uniform(57, 1500, 0, n))
+    unsorted = synth.uniform(58, 3000, 0, n)
+    tail = np.arange(n - 333, n, 7, dtype=np.uint64)
+    for pos, pfmt in ((np.concatenate([sparse, tail]), ms.DELTA_BP), (np.concatenate([unsorted, tail]), ms.DYN_BP)):
+        pos_s = np.sort(pos) if pfmt == ms.DELTA_BP else pos
+        pcol, _ = gpu_col(ctx, pos_s, pfmt)
+        out = ctx.project(dcol, pcol, fmt=ms.UNCOMPR)
+        assert_column(ctx, out, oracle.project(d, pos_s), ms.UNCOMPR)
+        ctx.free(out)
+        ctx.free(pcol)
+    ctx.free(dcol)
+
+
 @pytest.mark.parametrize("kind", ["gaps", "random", "flat", "widths"])
 @pytest.mark.parametrize("step", [0, 1, 3, 70, 2000])
 def test_project_delta_data_sorted_positions(ctx, kind, step):
