@@ -1019,8 +1019,7 @@ def bench_selector(args):
     # greedy per-intermediate runtime search (Sec. 5.2) over the plan's intermediates
     # (plans.greedy_formats; static BP is not a candidate: its width must be known
     # before the intermediate exists)
-    run = lambda fm: plans.select_project_calc_sum(  # noqa: E731
-        ctx, cx, ck, c, {k2: fmt_id(v) for k2, v in fm.items()}, out=res)
+    run = lambda fm: plans.select_project_calc_sum(ctx, cx, ck, c, fm, out=res)  # noqa: E731  (format ids)
     names_fm = {k2: v for k2, v in COMPRESSED.items() if k2 in PLAN_INTERMEDIATES}
     g_fm, _, _ = plans.greedy_formats(ctx, run, PLAN_INTERMEDIATES,
                                       {k2: fmt_id(v) for k2, v in names_fm.items()}, "time", reps=3)

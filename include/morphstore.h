@@ -46,9 +46,13 @@
  * ms_column_info() is the one call that copies it to the host, and it
  * synchronises the stream.  Arena columns are released in LIFO order: freeing a
  * column that is not the most recent one only marks it, and its space comes
- * back when every column allocated after it is freed too.  Imported columns are
- * allocated with the context's allocator callbacks (cudaMalloc when none are
- * given).
+ * back when every column allocated after it is freed too.  A block-format
+ * output (dynamic BP, DELTA+BP, FOR+BP) is first encoded into a stage taken
+ * from the arena's free end and then placed behind its block headers at the
+ * top, so while its operator runs it needs room for its payload twice; an output
+ * that does not fit is published empty and MS_ERR_NOMEM is raised.  Imported
+ * columns are allocated with the context's allocator callbacks (cudaMalloc when
+ * none are given).
  *
  * Streams and errors.  Operators are asynchronous on the given stream.
  * `stream` is a cudaStream_t passed as void*; NULL means the legacy default
@@ -145,12 +149,13 @@ const char *ms_cuda_error_string(int code);
 
 /* Arena bytes in use (current) and the high-water mark since the last reset;
    both synchronise `stream`.  The high-water mark is the peak footprint of the
-   operator outputs. */
+   operator outputs, the transient stage of a block-format output included. */
 ms_status ms_arena_usage(ms_ctx *ctx, uint64_t *in_use, uint64_t *high_water,
                          void *stream);
 ms_status ms_arena_reset_high_water(ms_ctx *ctx, void *stream);
 /* Bytes of the context's work area: the scratch its operators carve for
-   look-back status words, match bitmaps, per-chunk offsets and key bitmaps.  It
+   look-back status words, match bitmaps, per-chunk offsets, per-block stage
+   records (about 0.2 bytes per row in all) and key bitmaps.  It
    is allocated on demand and grows with the longest column seen; together with
    the arena's high-water mark it is the device memory a plan needs beyond its
    base columns.  0 for a NULL context.  No synchronisation. */
