@@ -1865,7 +1865,8 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
 // consecutive blocks (tile t on CTA t mod grid; the grid never exceeds the CTAs that
 // fit the GPU at once, so a tile's predecessors are always in progress).  T is the
 // output's block count spread over the grid, between 8 and kPlaceTile, so that a
-// small output still reaches every CTA.  Per tile: the blocks' widths come from
+// small output still reaches every CTA and a large one resolves one look-back per
+// CTA before its warps stream their blocks.  Per tile: the blocks' widths come from
 // stage_meta, a CTA scan and a decoupled look-back over the tiles give every
 // block's payload word offset, the final headers {(offset << 8) | width, ref} go to
 // the arena top, and the CTA's warps copy the tile's payloads out of the stage, a
@@ -1880,7 +1881,8 @@ struct PlaceArgs {
   uint64_t* status;  // look-back status words, one per tile, zeroed
 };
 
-constexpr int kPlaceTile = kThreads;  // largest tile: a block per thread
+constexpr int kPlacePer = 4;                      // blocks per thread in the width scan
+constexpr int kPlaceTile = kThreads * kPlacePer;  // largest tile
 
 // Bytes free for the output column between the arena top and the stage below the
 // arena's end, and the stage's start (an arena offset).
@@ -1902,7 +1904,7 @@ __global__ void __launch_bounds__(kThreads) k_place(PlaceArgs a) {
   __shared__ uint64_t s_warp[kWarps];
   __shared__ uint64_t s_excl;
   __shared__ uint32_t s_off[kPlaceTile];  // payload words before the block, within its tile
-  __shared__ uint8_t s_b[kPlaceTile];
+  __shared__ uint64_t s_at[kPlaceTile];   // the block's stage offset, ~0 if it never reached the stage
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   DevCtl* ctl = a.ctl;
   const uint64_t n = ldg64(&a.out_meta->n), nb = n / kBlock, r = n % kBlock;
@@ -1918,11 +1920,15 @@ __global__ void __launch_bounds__(kThreads) k_place(PlaceArgs a) {
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const uint64_t t0 = tile * T;
     const int nt = (int)min((uint64_t)T, nb - t0);
-    const int j = threadIdx.x;
-    const uint64_t g = t0 + j;
-    const uint32_t b = j < nt ? (uint32_t)min((uint64_t)64, a.stage_meta[2 * g] & 255) : 0;
-    const uint32_t texcl = warp_excl_scan32(8 * b, lane);
-    if (lane == 31) s_warp[warp] = texcl + 8 * b;
+    const int jb = kPlacePer * threadIdx.x;  // this thread's first block of the tile
+    uint32_t b[kPlacePer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPlacePer; k++) {
+      b[k] = jb + k < nt ? (uint32_t)min((uint64_t)64, a.stage_meta[2 * (t0 + jb + k)] & 255) : 0;
+      sum += 8 * b[k];
+    }
+    const uint32_t texcl = warp_excl_scan32(sum, lane);
+    if (lane == 31) s_warp[warp] = texcl + sum;
     __syncthreads();
     if (warp == 0) {
       const uint64_t wt = lane < kWarps ? s_warp[lane] : 0;
@@ -1937,39 +1943,69 @@ __global__ void __launch_bounds__(kThreads) k_place(PlaceArgs a) {
     }
     __syncthreads();
     const uint64_t tex = s_excl;
-    if (j < nt) {
-      const uint32_t o = (uint32_t)s_warp[warp] + texcl;  // at most 512 words per block: 32 bits
-      s_off[j] = o;
-      s_b[j] = (uint8_t)b;
-      if (16 * (g + 1) <= avail) {
-        hdr[2 * g] = ((tex + o) << 8) | b;
-        hdr[2 * g + 1] = a.stage_meta[2 * g + 1];
-      } else {
-        set_error(ctl, MS_ERR_NOMEM, g);
+    uint32_t o = (uint32_t)s_warp[warp] + texcl;  // words before the block within the tile: 32 bits
+#pragma unroll
+    for (int k = 0; k < kPlacePer; k++) {
+      const int j = jb + k;
+      if (j < nt) {
+        const uint64_t g = t0 + j;
+        s_off[j] = o;
+        const uint64_t at = a.stage_meta[2 * g] >> 8;
+        s_at[j] = (b[k] == 0 || (at >= room.lo && at + 64ull * b[k] <= send)) ? at : ~0ull;
+        if (b[k] && s_at[j] == ~0ull) set_error(ctl, MS_ERR_NOMEM, g);  // the block never reached the stage
+        if (16 * (g + 1) <= avail) {
+          hdr[2 * g] = ((tex + o) << 8) | b[k];
+          hdr[2 * g + 1] = a.stage_meta[2 * g + 1];
+        } else {
+          set_error(ctl, MS_ERR_NOMEM, g);
+        }
+        o += 8 * b[k];
       }
     }
     __syncthreads();
-    for (int jj = warp; jj < nt; jj += kWarps) {
-      const int bb = s_b[jj];
-      const uint64_t gg = t0 + jj;
-      if (bb == 0 || 16 * (gg + 1) > avail) continue;  // nothing to copy, or no header room (raised above)
-      const uint64_t pay = 16 * nb + 8 * (tex + s_off[jj]), at = a.stage_meta[2 * gg] >> 8;
-      if (pay + 64ull * bb <= avail && at >= room.lo && at + 64ull * bb <= send) {
-        const uint4* src = reinterpret_cast<const uint4*>(arena + at);
+    // Copy: warp w moves the payloads of the tile's blocks [j0, j1), which are
+    // consecutive in the output, as one run of 16-byte units with eight units per
+    // lane in flight (blocks of a few bits hold only 16-64 units, so a block at a
+    // time would wait one memory round trip per few hundred bytes).  A unit's block
+    // is found by binary search over the blocks' unit offsets.
+    const int per = (nt + kWarps - 1) / kWarps;
+    const int j0 = min(nt, warp * per), j1 = min(nt, j0 + per);
+    if (j0 < j1) {
+      const uint32_t w0 = s_off[j0];
+      const uint32_t total = (s_off[j1 - 1] - w0) / 2 + 4 * (uint32_t)min((uint64_t)64, a.stage_meta[2 * (t0 + j1 - 1)] & 255);
+      const uint64_t pay = 16 * nb + 8 * (tex + w0);
+      if (16 * (t0 + j1) <= avail && pay + 16ull * total <= avail) {
         uint4* dst = reinterpret_cast<uint4*>(base + pay);
-        const int units = 4 * bb;  // at most 256: 8 per lane
-        uint4 q[8];
+        for (uint32_t u0 = 0; u0 < total; u0 += 256) {
+          uint4 q[8];
+          bool ok[8];
 #pragma unroll
-        for (int i = 0; i < 8; i++)
-          if (lane + 32 * i < units) q[i] = src[lane + 32 * i];
+          for (int i = 0; i < 8; i++) {
+            const uint32_t u = u0 + 32 * i + lane;
+            ok[i] = false;
+            if (u < total) {
+              int lo = j0, hi = j1 - 1;  // the last block whose first unit is <= u
+              while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if ((s_off[mid] - w0) / 2 <= u) lo = mid;
+                else hi = mid - 1;
+              }
+              const uint64_t at = s_at[lo];
+              if (at != ~0ull) {
+                q[i] = reinterpret_cast<const uint4*>(arena + at)[u - (s_off[lo] - w0) / 2];
+                ok[i] = true;
+              }
+            }
+          }
 #pragma unroll
-        for (int i = 0; i < 8; i++)
-          if (lane + 32 * i < units) dst[lane + 32 * i] = q[i];
-      } else if (lane == 0) {  // no room, or the block never reached the stage
-        set_error(ctl, MS_ERR_NOMEM, gg);
+          for (int i = 0; i < 8; i++)
+            if (ok[i]) dst[u0 + 32 * i + lane] = q[i];
+        }
+      } else if (lane == 0) {  // no room for the headers or the payload (NOMEM, also raised above)
+        set_error(ctl, MS_ERR_NOMEM, t0 + j0);
       }
     }
-    __syncthreads();  // s_off / s_b are reused by the next tile
+    __syncthreads();  // s_off / s_at are reused by the next tile
   }
   // the remainder, by the CTA of the last tile (CTA 0 when there is no block): that
   // CTA's warp 0 wrote the total payload words
