@@ -37,15 +37,32 @@ def _deps():
     return max(os.path.getmtime(f) for f in files)
 
 
+STAMP = LIB + ".defines"  # the tuning definitions the library was built with
+
+
+def _defines():
+    # MS_NVCC_DEFINES: extra -D definitions for a tuning build (space separated)
+    return [d for d in os.environ.get("MS_NVCC_DEFINES", "").split() if d]
+
+
+def _stamp_matches(defines) -> bool:
+    try:
+        with open(STAMP) as f:
+            return f.read() == " ".join(defines)
+    except OSError:
+        return not defines
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
+    defines = _defines()
+    if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps()
+            and _stamp_matches(defines)):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
-    # MS_NVCC_DEFINES: extra -D definitions for a tuning build (space separated)
-    common += [f"-D{d}" for d in os.environ.get("MS_NVCC_DEFINES", "").split() if d]
+    common += [f"-D{d}" for d in defines]
     if verbose:
         common += ["-Xptxas", "-v"]
 
@@ -68,6 +85,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(defines))
     return LIB
 
 
