@@ -81,6 +81,8 @@ def parse():
                     help="selector workload: engine traces to train and hold out (80/20), 2^16 rows up to "
                          "2^--selector-max-log2")
     ap.add_argument("--selector-max-log2", type=float, default=20.0)
+    ap.add_argument("--selector-mid-items", type=int, default=2000,
+                    help="selector workload: extra training traces of 2^20 .. 2^24 rows")
     ap.add_argument("--selector-large-items", type=int, default=200,
                     help="selector workload: extra held-out traces of 2^22 .. 2^26 rows")
     ap.add_argument("--fragments", type=int, default=4096)
@@ -973,6 +975,12 @@ def bench_selector(args):
                                              hi_log2=args.selector_max_log2)
     X, Y, S, T, names = selector.harvest(ctx, items, reps=2)
     harvest_s = time.perf_counter() - t_h
+    # longer traces (2^20 .. 2^24 rows), all trained on: run times grow with the length
+    # in ways the short traces alone do not show
+    t_m = time.perf_counter()
+    mid = selector.synthetic_intermediates(args.seed + 55, args.selector_mid_items, lo_log2=20, hi_log2=24)
+    XM, YM, _, _, _ = selector.harvest(ctx, mid, reps=1)
+    mid_s = time.perf_counter() - t_m
     # a held-out set of long intermediates (2^22 .. 2^26 rows), never trained on
     t_l = time.perf_counter()
     big = selector.synthetic_intermediates(args.seed + 99, args.selector_large_items, lo_log2=22, hi_log2=26)
@@ -985,7 +993,8 @@ def bench_selector(args):
     # ---- 2. training with the library's kernels
     sel = selector.Selector(dev, seed=args.seed)
     t_t = time.perf_counter()
-    hist = sel.train(X[tr], Y[tr], epochs=800, lr=3e-3)
+    Xtr, Ytr = (np.concatenate([X[tr], XM]), np.concatenate([Y[tr], YM])) if len(XM) else (X[tr], Y[tr])
+    hist = sel.train(Xtr, Ytr, epochs=800, lr=3e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t_t
     held = {}
@@ -1031,8 +1040,10 @@ def bench_selector(args):
     ctx.close()
     return {"workload": "selector", "metric": "learned format selector: regret vs exhaustive choice",
             "items": len(X), "train_items": len(tr), "heldout_items": len(te), "long_heldout_items": len(XL),
-            "rows_log2": [16, args.selector_max_log2], "long_rows_log2": [22, 26],
-            "harvest_s": round(harvest_s, 1), "long_harvest_s": round(large_s, 1), "train_s": round(train_s, 2),
+            "mid_train_items": len(XM), "rows_log2": [16, args.selector_max_log2], "mid_rows_log2": [20, 24],
+            "long_rows_log2": [22, 26],
+            "harvest_s": round(harvest_s, 1), "mid_harvest_s": round(mid_s, 1), "long_harvest_s": round(large_s, 1),
+            "train_s": round(train_s, 2),
             "loss_first_last": [hist[0][1], hist[-1][1]], "heldout": held,
             "plan_2e28": {"rows": n, "selector_formats": fm_sel, "greedy_formats": {k2: fm_g[k2] for k2 in PLAN_INTERMEDIATES},
                           "ms_selector": round(t_sel, 4), "ms_greedy_search": round(t_greedy, 4),

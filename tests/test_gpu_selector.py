@@ -140,3 +140,8 @@ def test_selector_regret_against_exhaustive_choice():
     best_fixed = min(selector.regret(np.full(len(te), f), S[te]) for f in range(5))
     assert r <= 0.05, r
     assert r < static_all and r < best_fixed, (r, static_all, best_fixed)
+    # run-time labels: at 2^14-2^18 rows and one timed repetition the formats' times differ
+    # by a few percent and carry timing noise, so the regret is bounded rather than required
+    # to beat every fixed format (the 2e4-trace bench measures it on longer columns)
+    rt = selector.regret(sel.choose(X[te], "time"), T[te])
+    assert 0.0 <= rt <= 0.05, rt
