@@ -36,13 +36,25 @@ def select_project_calc_sum(ctx, x, k, c, fm, out=None):
 STAR_GROUPS = 105  # year (7 values) * 15 + c25 (< 15 after the filter)
 
 STAR_COMPRESSED = {
-    # positions are sorted: DELTA+BP; values: dynamic BP
-    "S1": ms.DELTA_BP, "S2": ms.DELTA_BP, "P1": ms.DELTA_BP, "F2": ms.DYN_BP, "Q2": ms.DELTA_BP,
-    "P2": ms.DELTA_BP, "DISC": ms.DYN_BP, "Q3": ms.DELTA_BP, "P3": ms.DELTA_BP, "QTY": ms.DYN_BP,
-    "Q4": ms.DELTA_BP, "P4": ms.DELTA_BP, "DATE": ms.DELTA_BP, "YEAR": ms.DYN_BP, "F2B": ms.DYN_BP,
-    "C25": ms.DYN_BP, "G0": ms.DYN_BP, "GID": ms.DYN_BP, "REV": ms.DYN_BP,
+    # positions are sorted: DELTA+BP (so are the projected dates); values: static BP at the
+    # width of their value domain (STAR_VALUE_WIDTHS), which needs no placement pass
+    "S1": ms.DELTA_BP, "S2": ms.DELTA_BP, "P1": ms.DELTA_BP, "F2": ms.STATIC_BP, "Q2": ms.DELTA_BP,
+    "P2": ms.DELTA_BP, "DISC": ms.STATIC_BP, "Q3": ms.DELTA_BP, "P3": ms.DELTA_BP, "QTY": ms.STATIC_BP,
+    "Q4": ms.DELTA_BP, "P4": ms.DELTA_BP, "DATE": ms.DELTA_BP, "YEAR": ms.STATIC_BP, "F2B": ms.STATIC_BP,
+    "C25": ms.STATIC_BP, "G0": ms.STATIC_BP, "GID": ms.STATIC_BP, "REV": ms.STATIC_BP,
 }
 STAR_UNCOMPRESSED = {k: ms.UNCOMPR for k in STAR_COMPRESSED}
+# Value intermediates whose domain the plan knows before they exist: fk2 < 2e5 (F2, F2B),
+# discount <= 10, quantity <= 50, year < 7, c25 < 25, year * 15 <= 90, year * 15 + c25
+# < 105, revenue < 2^23.  Static BP at these widths is a candidate for them; a value
+# beyond its width raises MS_ERR_VALUE_TOO_WIDE.
+STAR_VALUE_WIDTHS = {"F2": 18, "DISC": 4, "QTY": 6, "YEAR": 3, "F2B": 18, "C25": 5, "G0": 7, "GID": 7,
+                     "REV": 23}
+
+
+def star_width(name: str, fmt: int) -> int:
+    """Static-BP width of star intermediate `name` in format fmt (0 for other formats)."""
+    return STAR_VALUE_WIDTHS[name] if fmt == ms.STATIC_BP else 0
 
 # Base columns.  Sec. 4.2 allows random access only into uncompressed and static-BP
 # columns: the columns that the plan projects at positions (fk2, discount, quantity,
@@ -108,22 +120,22 @@ def star_plan(ctx, base, fm, out=None, trace=None):
     s1 = keep("select", "S1", [b["d1_c5"]], ctx.select(b["d1_c5"], ms.EQ, 0, fmt=fm["S1"]))
     s2 = keep("select", "S2", [b["d2_c25"]], ctx.select(b["d2_c25"], ms.LT, 15, fmt=fm["S2"]))
     p1 = keep("semijoin", "P1", [b["fk1"], s1], ctx.semijoin(b["fk1"], s1, DIM_SIZES[0], fmt=fm["P1"]), DIM_SIZES[0])
-    f2 = keep("project", "F2", [b["fk2"], p1], ctx.project(b["fk2"], p1, fmt=fm["F2"]))
+    f2 = keep("project", "F2", [b["fk2"], p1], ctx.project(b["fk2"], p1, fmt=fm["F2"], bw=star_width("F2", fm["F2"])))
     q2 = keep("semijoin", "Q2", [f2, s2], ctx.semijoin(f2, s2, DIM_SIZES[1], fmt=fm["Q2"]), DIM_SIZES[1])
     p2 = keep("project", "P2", [p1, q2], ctx.project(p1, q2, fmt=fm["P2"]))
-    disc = keep("project", "DISC", [b["discount"], p2], ctx.project(b["discount"], p2, fmt=fm["DISC"]))
+    disc = keep("project", "DISC", [b["discount"], p2], ctx.project(b["discount"], p2, fmt=fm["DISC"], bw=star_width("DISC", fm["DISC"])))
     q3 = keep("select", "Q3", [disc], ctx.select(disc, ms.BETWEEN, 1, 3, fmt=fm["Q3"]))
     p3 = keep("project", "P3", [p2, q3], ctx.project(p2, q3, fmt=fm["P3"]))
-    qty = keep("project", "QTY", [b["quantity"], p3], ctx.project(b["quantity"], p3, fmt=fm["QTY"]))
+    qty = keep("project", "QTY", [b["quantity"], p3], ctx.project(b["quantity"], p3, fmt=fm["QTY"], bw=star_width("QTY", fm["QTY"])))
     q4 = keep("select", "Q4", [qty], ctx.select(qty, ms.LT, 25, fmt=fm["Q4"]))
     p4 = keep("project", "P4", [p3, q4], ctx.project(p3, q4, fmt=fm["P4"]))
     date = keep("project", "DATE", [b["fk_date"], p4], ctx.project(b["fk_date"], p4, fmt=fm["DATE"]))
-    year = keep("project", "YEAR", [b["date_year"], date], ctx.project(b["date_year"], date, fmt=fm["YEAR"]))
-    f2b = keep("project", "F2B", [b["fk2"], p4], ctx.project(b["fk2"], p4, fmt=fm["F2B"]))
-    c25 = keep("project", "C25", [b["d2_c25"], f2b], ctx.project(b["d2_c25"], f2b, fmt=fm["C25"]))
-    g0 = keep("calc", "G0", [year], ctx.calc(ms.MUL, year, None, c=15, fmt=fm["G0"]))
-    gid = keep("calc", "GID", [g0, c25], ctx.calc(ms.ADD, g0, c25, fmt=fm["GID"]))
-    rev = keep("project", "REV", [b["revenue"], p4], ctx.project(b["revenue"], p4, fmt=fm["REV"]))
+    year = keep("project", "YEAR", [b["date_year"], date], ctx.project(b["date_year"], date, fmt=fm["YEAR"], bw=star_width("YEAR", fm["YEAR"])))
+    f2b = keep("project", "F2B", [b["fk2"], p4], ctx.project(b["fk2"], p4, fmt=fm["F2B"], bw=star_width("F2B", fm["F2B"])))
+    c25 = keep("project", "C25", [b["d2_c25"], f2b], ctx.project(b["d2_c25"], f2b, fmt=fm["C25"], bw=star_width("C25", fm["C25"])))
+    g0 = keep("calc", "G0", [year], ctx.calc(ms.MUL, year, None, c=15, fmt=fm["G0"], bw=star_width("G0", fm["G0"])))
+    gid = keep("calc", "GID", [g0, c25], ctx.calc(ms.ADD, g0, c25, fmt=fm["GID"], bw=star_width("GID", fm["GID"])))
+    rev = keep("project", "REV", [b["revenue"], p4], ctx.project(b["revenue"], p4, fmt=fm["REV"], bw=star_width("REV", fm["REV"])))
     res = ctx.group_sum(gid, rev, STAR_GROUPS, out=out)
     if trace is not None:
         import torch
@@ -179,7 +191,8 @@ def greedy_formats(ctx, run, names, start, objective="time", candidates=PLAN_CAN
     "Determining a good format combination"): the intermediates are visited once,
     in plan order; for each, every candidate format is tried with all others held
     fixed, and the cheapest is kept before moving on.  Returns (formats, cost of
-    the final combination, number of plan evaluations).  `cost(fm)` overrides the
+    the final combination, number of plan evaluations).  `candidates` is one tuple
+    for every intermediate or a dict of tuples by name; `cost(fm)` overrides the
     measurement (plan_cost by default)."""
     if objective not in PLAN_OBJECTIVES:
         raise ValueError(f"objective must be one of {PLAN_OBJECTIVES}")
@@ -188,7 +201,7 @@ def greedy_formats(ctx, run, names, start, objective="time", candidates=PLAN_CAN
     evals, best_cost = 0, None
     for name in names:
         best = None
-        for f in candidates:
+        for f in (candidates[name] if isinstance(candidates, dict) else candidates):
             trial = dict(fm, **{name: f})
             c = measure(trial)
             evals += 1
@@ -226,3 +239,6 @@ STAR_OPS = {"S1": "select", "S2": "select", "P1": "semijoin", "F2": "project", "
             "REV": "project"}
 # intermediates a later project reads at random (the position lists projected through)
 STAR_RANDOM_READS = ("P1", "P2", "P3")
+# greedy-search candidates of the star plan: static BP too where the value width is known
+STAR_CANDIDATES = {name: PLAN_CANDIDATES + ((ms.STATIC_BP,) if name in STAR_VALUE_WIDTHS else ())
+                   for name in STAR_NAMES}

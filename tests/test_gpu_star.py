@@ -71,19 +71,19 @@ def test_star_plan_intermediates_match_oracle(base_fm, fm):
             ("P1", lambda: oracle.semijoin(fact["fk1"], want["S1"], D[0]),
              lambda: ctx.semijoin(base["fk1"], got["S1"], D[0], fmt=fm["P1"])),
             ("F2", lambda: oracle.project(fact["fk2"], want["P1"]),
-             lambda: ctx.project(base["fk2"], got["P1"], fmt=fm["F2"])),
+             lambda: ctx.project(base["fk2"], got["P1"], fmt=fm["F2"], bw=plans.star_width("F2", fm["F2"]))),
             ("Q2", lambda: oracle.semijoin(want["F2"], want["S2"], D[1]),
              lambda: ctx.semijoin(got["F2"], got["S2"], D[1], fmt=fm["Q2"])),
             ("P2", lambda: oracle.project(want["P1"], want["Q2"]),
              lambda: ctx.project(got["P1"], got["Q2"], fmt=fm["P2"])),
             ("DISC", lambda: oracle.project(fact["discount"], want["P2"]),
-             lambda: ctx.project(base["discount"], got["P2"], fmt=fm["DISC"])),
+             lambda: ctx.project(base["discount"], got["P2"], fmt=fm["DISC"], bw=plans.star_width("DISC", fm["DISC"]))),
             ("Q3", lambda: oracle.select(want["DISC"], oracle.BETWEEN, 1, 3),
              lambda: ctx.select(got["DISC"], ms.BETWEEN, 1, 3, fmt=fm["Q3"])),
             ("P3", lambda: oracle.project(want["P2"], want["Q3"]),
              lambda: ctx.project(got["P2"], got["Q3"], fmt=fm["P3"])),
             ("QTY", lambda: oracle.project(fact["quantity"], want["P3"]),
-             lambda: ctx.project(base["quantity"], got["P3"], fmt=fm["QTY"])),
+             lambda: ctx.project(base["quantity"], got["P3"], fmt=fm["QTY"], bw=plans.star_width("QTY", fm["QTY"]))),
             ("Q4", lambda: oracle.select(want["QTY"], oracle.LT, 25),
              lambda: ctx.select(got["QTY"], ms.LT, 25, fmt=fm["Q4"])),
             ("P4", lambda: oracle.project(want["P3"], want["Q4"]),
@@ -91,17 +91,17 @@ def test_star_plan_intermediates_match_oracle(base_fm, fm):
             ("DATE", lambda: oracle.project(fact["fk_date"], want["P4"]),
              lambda: ctx.project(base["fk_date"], got["P4"], fmt=fm["DATE"])),
             ("YEAR", lambda: oracle.project(dims["date_year"], want["DATE"]),
-             lambda: ctx.project(base["date_year"], got["DATE"], fmt=fm["YEAR"])),
+             lambda: ctx.project(base["date_year"], got["DATE"], fmt=fm["YEAR"], bw=plans.star_width("YEAR", fm["YEAR"]))),
             ("F2B", lambda: oracle.project(fact["fk2"], want["P4"]),
-             lambda: ctx.project(base["fk2"], got["P4"], fmt=fm["F2B"])),
+             lambda: ctx.project(base["fk2"], got["P4"], fmt=fm["F2B"], bw=plans.star_width("F2B", fm["F2B"]))),
             ("C25", lambda: oracle.project(dims["d2_c25"], want["F2B"]),
-             lambda: ctx.project(base["d2_c25"], got["F2B"], fmt=fm["C25"])),
+             lambda: ctx.project(base["d2_c25"], got["F2B"], fmt=fm["C25"], bw=plans.star_width("C25", fm["C25"]))),
             ("G0", lambda: oracle.calc(oracle.MUL, want["YEAR"], c=15),
-             lambda: ctx.calc(ms.MUL, got["YEAR"], None, c=15, fmt=fm["G0"])),
+             lambda: ctx.calc(ms.MUL, got["YEAR"], None, c=15, fmt=fm["G0"], bw=plans.star_width("G0", fm["G0"]))),
             ("GID", lambda: oracle.calc(oracle.ADD, want["G0"], want["C25"]),
-             lambda: ctx.calc(ms.ADD, got["G0"], got["C25"], fmt=fm["GID"])),
+             lambda: ctx.calc(ms.ADD, got["G0"], got["C25"], fmt=fm["GID"], bw=plans.star_width("GID", fm["GID"]))),
             ("REV", lambda: oracle.project(fact["revenue"], want["P4"]),
-             lambda: ctx.project(base["revenue"], got["P4"], fmt=fm["REV"])),
+             lambda: ctx.project(base["revenue"], got["P4"], fmt=fm["REV"], bw=plans.star_width("REV", fm["REV"]))),
         ]
         for name, w, g in steps:
             want[name] = w()
@@ -126,8 +126,9 @@ def test_greedy_plan_formats_keep_results_and_meet_their_objective(objective):
         run = lambda fm: plans.star_plan(ctx, base, fm)  # noqa: E731
         start = dict(plans.STAR_COMPRESSED)
         c0 = plans.plan_cost(ctx, run, start, objective, reps=2)
-        fm, c, evals = plans.greedy_formats(ctx, run, plans.STAR_NAMES, start, objective, reps=2)
-        assert evals == len(plans.STAR_NAMES) * len(plans.PLAN_CANDIDATES)
+        fm, c, evals = plans.greedy_formats(ctx, run, plans.STAR_NAMES, start, objective,
+                                            candidates=plans.STAR_CANDIDATES, reps=2)
+        assert evals == sum(len(plans.STAR_CANDIDATES[name]) for name in plans.STAR_NAMES)
         if objective == "size":  # sizes are deterministic: the search can only improve
             assert c <= c0 and plans.plan_cost(ctx, run, fm, "size") == c
         res, cols = run(fm)
