@@ -1864,9 +1864,9 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
 // Placement of a staged block-format column, in one pass over tiles of T
 // consecutive blocks (tile t on CTA t mod grid; the grid never exceeds the CTAs that
 // fit the GPU at once, so a tile's predecessors are always in progress).  T is the
-// output's block count spread over the grid, between 8 and kPlaceTile, so that a
-// small output still reaches every CTA and a large one resolves one look-back per
-// CTA before its warps stream their blocks.  Per tile: the blocks' widths come from
+// output's block count spread evenly over whole rounds of one tile per CTA, between 8
+// and kPlaceTile, so that a small output still reaches every CTA and a large one
+// resolves few look-backs per CTA, with every CTA copying a like share.  Per tile: the blocks' widths come from
 // stage_meta, a CTA scan and a decoupled look-back over the tiles give every
 // block's payload word offset, the final headers {(offset << 8) | width, ref} go to
 // the arena top, and the CTA's warps copy the tile's payloads out of the stage, a
@@ -1914,7 +1914,9 @@ __global__ void __launch_bounds__(kThreads) k_place(PlaceArgs a) {
   uint8_t* arena = reinterpret_cast<uint8_t*>(ctl->arena);
   uint8_t* base = arena + top;
   uint64_t* hdr = reinterpret_cast<uint64_t*>(base);
-  const uint64_t spread = (nb + gridDim.x - 1) / gridDim.x;
+  // rounds of one tile per CTA, then tiles that fill those rounds evenly
+  const uint64_t G = gridDim.x, rounds = max((uint64_t)1, (nb + (uint64_t)kPlaceTile * G - 1) / ((uint64_t)kPlaceTile * G));
+  const uint64_t spread = (nb + rounds * G - 1) / (rounds * G);
   const int T = (int)min((uint64_t)kPlaceTile, max((uint64_t)8, (spread + 7) / 8 * 8));
   const uint64_t ntiles = (nb + T - 1) / T;
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
