@@ -59,11 +59,13 @@ constexpr auto k_mark_l1 = k_mark_t<kMarkL1Buf>;
 // Semi-join probe with the key bitmap in shared memory, for key domains whose
 // bitmap fits one CTA (up to about 1.5 million keys: 2e5 takes 25 KB).  Probing a
 // bitmap in L2 leaves the probe latency-bound on scattered 32-byte sector reads;
-// from shared memory a lookup costs a few bank wavefronts.
+// from shared memory a lookup costs a few bank wavefronts.  Compiled for the tile
+// stream's three CTAs per SM, which a small bitmap leaves room for (a bitmap that
+// takes most of shared memory runs one).
 constexpr int kKeyTileBuf = 16384;
 constexpr size_t kKeyTileSmemBytes = sizeof(TileSmem<kKeyTileBuf>);
 
-__global__ void __launch_bounds__(kTileThreads, 1) k_mark_keys(MarkArgs a) {
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark_keys(MarkArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31;
   auto* sm = reinterpret_cast<TileSmem<kKeyTileBuf>*>(smem_raw);
