@@ -412,12 +412,14 @@ struct ProjectCta {
 struct SmemEmit {
   uint32_t bits[kEmitSpan * 16];
   uint64_t coff[kEmitSpan + 2];
-  uint64_t aux[kBlock];
-  uint16_t out[2048];
+  uint64_t aux[kBlock];  // the block's positions; then, once they are in registers, its encoding
   uint32_t bits2[kEmitSpan * 16];  // the next block's first span (pipelined emit)
   uint64_t coff2[kEmitSpan + 2];
 };
 
+#ifndef MS_EMIT_MIN_BLOCKS
+#define MS_EMIT_MIN_BLOCKS 3  // resident CTAs per SM the emit kernel is compiled for
+#endif
 #ifndef MS_PROJECT_MIN_BLOCKS
 #define MS_PROJECT_MIN_BLOCKS 2  // resident CTAs per SM the project kernel is compiled for
 #endif
@@ -443,7 +445,8 @@ struct ProducePlan {
           typename std::conditional<
               OP == OP_PROJECT_WARP, SmemProjectDelta,
               typename std::conditional<OP == OP_EMIT, SmemEmit, SmemSingle>::type>::type>::type>::type;
-  static constexpr int kMinBlocks = OP == OP_PROJECT ? MS_PROJECT_MIN_BLOCKS : (OP == OP_CALC ? 1 : 2);
+  static constexpr int kMinBlocks =
+      OP == OP_PROJECT ? MS_PROJECT_MIN_BLOCKS : (OP == OP_CALC ? 1 : (OP == OP_EMIT ? MS_EMIT_MIN_BLOCKS : 2));
   // CTA-shared shared memory behind the per-warp plans (the CTA span copy of project)
   using Cta = ProjectCta<MS_PROJECT_CTA_BUF>;
   static constexpr size_t kCtaBytes = OP == OP_PROJECT ? sizeof(Cta) : 0;
@@ -1791,7 +1794,7 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
     int valid = 0;
     uint16_t* out_stage;
     if constexpr (OP == OP_EMIT) {
-      out_stage = sm->out;
+      out_stage = reinterpret_cast<uint16_t*>(sm->aux);  // free once emit_expand returned
       uint32_t* cbits = (i & 1) ? sm->bits2 : sm->bits;
       uint64_t* ccoff = (i & 1) ? sm->coff2 : sm->coff;
       const EmitPlan cur = eplan;
