@@ -45,6 +45,20 @@
  *              (Sec. 2.1: DELTA = difference to the predecessor; the chain
  *               restarts at every block so that blocks decode independently)
  *     b_k = bw(max residual of block k), 0..64.
+ *  RLE (Sec. 2.1: RLE records each run of equal consecutive values once, with its
+ *                repetition; the repetition is recorded here as the position where
+ *                the run ends, so that a run's length is the difference of two
+ *                consecutive ends):
+ *                R runs, run r = the r-th maximal stretch of equal consecutive
+ *                values; nch = ceil(n / 512).
+ *                values: R uint64, value of run r at byte 8*r
+ *                ends:   R uint64, end_r = index of the first value after run r
+ *                        (exclusive; end_{R-1} = n), at byte 8*R + 8*r
+ *                directory: nch uint64, entry g = index of the run that holds
+ *                        value 512*g, at byte 16*R + 8*g (the block directory of
+ *                        Sec. 4.2's random access: a block's first run without a
+ *                        search)
+ *                size = 16*R + 8*nch; n = 0 gives R = 0 and size 0.
  */
 #include "oracle.h"
 
@@ -141,8 +155,18 @@ void orc_block_widths(int fmt, const uint64_t *x, uint64_t n, uint8_t *widths) {
 
 /* --------------------------------------------------------------- sizes */
 
+/* number of runs of x[0..n): 1 + the number of i >= 1 with x[i] != x[i-1] */
+static uint64_t run_count(const uint64_t *x, uint64_t n) {
+  if (n == 0) return 0;
+  uint64_t R = 1;
+  for (uint64_t i = 1; i < n; i++)
+    if (x[i] != x[i - 1]) R++;
+  return R;
+}
+
 uint64_t orc_size(int fmt, int bw, const uint64_t *x, uint64_t n) {
   if (fmt == ORC_UNCOMPR) return 8 * n;
+  if (fmt == ORC_RLE) return 16 * run_count(x, n) + 8 * ((n + ORC_BLOCK - 1) / ORC_BLOCK);
   if (fmt == ORC_STATIC_BP) {
     if (bw < 1 || bw > 64) return 0;
     uint64_t chunks = n / ORC_BLOCK, r = n % ORC_BLOCK;
@@ -171,12 +195,27 @@ static uint64_t get_u64(const uint8_t *p) {
 
 int orc_compress(int fmt, int bw, const uint64_t *x, uint64_t n, uint8_t *out,
                  uint64_t cap, uint64_t *size_out) {
-  if (fmt < ORC_UNCOMPR || fmt > ORC_FOR_BP) return ORC_BAD_ARG;
+  if (fmt < ORC_UNCOMPR || fmt > ORC_RLE) return ORC_BAD_ARG;
   if (fmt == ORC_STATIC_BP && (bw < 1 || bw > 64)) return ORC_BAD_ARG;
   uint64_t size = orc_size(fmt, bw, x, n);
   if (size > cap) return ORC_BAD_ARG;
   memset(out, 0, size);
   *size_out = size;
+
+  if (fmt == ORC_RLE) {
+    uint64_t R = run_count(x, n), r = 0;
+    uint8_t *vals = out, *ends = out + 8 * R, *dir = out + 16 * R;
+    for (uint64_t i = 0; i < n; i++) {
+      if (i > 0 && x[i] != x[i - 1]) {
+        put_u64(ends + 8 * r, i); /* run r ends where run r+1 starts */
+        r++;
+      }
+      if (i == 0 || x[i] != x[i - 1]) put_u64(vals + 8 * r, x[i]);
+      if (i % ORC_BLOCK == 0) put_u64(dir + 8 * (i / ORC_BLOCK), r);
+    }
+    if (n > 0) put_u64(ends + 8 * r, n);
+    return ORC_OK;
+  }
 
   if (fmt == ORC_UNCOMPR) {
     for (uint64_t i = 0; i < n; i++) put_u64(out + 8 * i, x[i]);
@@ -217,6 +256,25 @@ int orc_compress(int fmt, int bw, const uint64_t *x, uint64_t n, uint8_t *out,
 
 int orc_decompress(int fmt, int bw, uint64_t n, const uint8_t *buf, uint64_t size,
                    uint64_t *out) {
+  if (fmt == ORC_RLE) {
+    uint64_t nch = (n + ORC_BLOCK - 1) / ORC_BLOCK;
+    if (size < 8 * nch || (size - 8 * nch) % 16) return ORC_BAD_FORMAT;
+    uint64_t R = (size - 8 * nch) / 16;
+    if ((n == 0) != (R == 0)) return ORC_BAD_FORMAT;
+    const uint8_t *vals = buf, *ends = buf + 8 * R, *dir = buf + 16 * R;
+    uint64_t start = 0;
+    for (uint64_t r = 0; r < R; r++) {
+      uint64_t end = get_u64(ends + 8 * r), v = get_u64(vals + 8 * r);
+      if (end <= start || end > n) return ORC_BAD_FORMAT;
+      for (uint64_t i = start; i < end; i++) {
+        out[i] = v;
+        if (i % ORC_BLOCK == 0 && get_u64(dir + 8 * (i / ORC_BLOCK)) != r) return ORC_BAD_FORMAT;
+      }
+      start = end;
+    }
+    if (start != n) return ORC_BAD_FORMAT;
+    return ORC_OK;
+  }
   if (fmt == ORC_UNCOMPR) {
     if (size < 8 * n) return ORC_BAD_FORMAT;
     for (uint64_t i = 0; i < n; i++) out[i] = get_u64(buf + 8 * i);

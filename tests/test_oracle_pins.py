@@ -328,3 +328,87 @@ def test_semijoin_matches_isin():
     assert oracle.semijoin(probe, np.zeros(0, np.uint64), 3000).size == 0
     with pytest.raises(oracle.OracleError):
         oracle.semijoin(probe, [3000], 3000)
+
+
+# ------------------------------------------------------------------ RLE pins
+
+def _rle_case_values(case):
+    if "values" in case:
+        return np.array(case["values"], dtype=np.uint64)
+    return np.concatenate([np.full(k, v, dtype=np.uint64) for v, k in case["values_rle"]])
+
+
+@pytest.mark.parametrize("name", ["rle_three_runs", "rle_run_across_a_block_boundary", "rle_run_starting_at_a_block"])
+def test_layout_rle_hand_examples(name):
+    case = {c["name"]: c for c in _gold("layout_examples.json")["cases"]}[name]
+    x = _rle_case_values(case)
+    assert oracle.compress(oracle.RLE, x).tobytes() == _hex(case["bytes_hex"])
+    raw = np.frombuffer(_hex(case["bytes_hex"]), dtype=np.uint8)
+    np.testing.assert_array_equal(oracle.decompress(oracle.RLE, x.size, raw), x)
+
+
+def _rle_parts(buf, n):
+    """Run values, run ends and directory read straight from the bytes."""
+    w = np.frombuffer(buf.tobytes(), dtype="<u8")
+    nch = -(-n // 512)
+    R = (w.size - nch) // 2
+    return w[:R], w[R:2 * R], w[2 * R:]
+
+
+def _runny(seed, n, mean_run):
+    """Values drawn with runs of geometric length (mean `mean_run`)."""
+    rng = np.random.default_rng(seed)
+    lens = rng.geometric(1.0 / mean_run, size=n + 1)
+    vals = rng.integers(0, 6, size=lens.size).astype(np.uint64)  # few values: equal neighbours merge
+    return np.repeat(vals, lens)[:n]
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 511, 512, 513, 1024, 1500, 4097])
+@pytest.mark.parametrize("mean_run", [1, 3, 40, 700])
+def test_rle_bytes_decode_with_numpy_repeat(n, mean_run):
+    """The bytes decode by np.repeat(values, diff(ends)); the size is the closed form
+    16 * (1 + number of changes) + 8 * ceil(n / 512); the directory entry of block g
+    is the run that holds value 512 g (searchsorted over the ends)."""
+    x = _runny(n * 7 + mean_run, n, mean_run)
+    buf = oracle.compress(oracle.RLE, x)
+    runs = 1 + int(np.count_nonzero(np.diff(x))) if n else 0
+    assert buf.size == 16 * runs + 8 * (-(-n // 512)) == oracle.size(oracle.RLE, x)
+    vals, ends, dirs = _rle_parts(buf, n)
+    assert vals.size == runs
+    lens = np.diff(np.concatenate([[0], ends]).astype(np.int64))
+    assert (lens > 0).all()
+    np.testing.assert_array_equal(np.repeat(vals, lens), x)
+    np.testing.assert_array_equal(dirs, np.searchsorted(ends, 512 * np.arange(dirs.size), side="right"))
+    # the run-weighted sum of the values is the column sum (mod 2^64)
+    assert int((vals * lens.astype(np.uint64)).sum(dtype=np.uint64)) == int(x.sum(dtype=np.uint64))
+    np.testing.assert_array_equal(oracle.decompress(oracle.RLE, n, buf), x)
+
+
+def test_rle_special_cases():
+    x = np.full(1000, 42, dtype=np.uint64)  # one run
+    assert oracle.compress(oracle.RLE, x).view("<u8").tolist() == [42, 1000, 0, 0]
+    x = np.arange(600, dtype=np.uint64)  # every value its own run
+    vals, ends, dirs = _rle_parts(oracle.compress(oracle.RLE, x), 600)
+    assert vals.tolist() == list(range(600)) and ends.tolist() == list(range(1, 601)) and dirs.tolist() == [0, 512]
+    assert oracle.compress(oracle.RLE, np.zeros(0, dtype=np.uint64)).size == 0
+
+
+def test_rle_corrupt_columns_are_rejected():
+    x = _runny(3, 1500, 40)
+    buf = oracle.compress(oracle.RLE, x)
+    vals, ends, dirs = _rle_parts(buf, x.size)
+    R = vals.size
+    bad = buf.view("<u8").copy()
+    bad[R + R - 1] = x.size - 1  # the last run must end at n
+    with pytest.raises(oracle.OracleError):
+        oracle.decompress(oracle.RLE, x.size, bad.view(np.uint8))
+    bad = buf.view("<u8").copy()
+    bad[R + 1] = bad[R]  # an empty run
+    with pytest.raises(oracle.OracleError):
+        oracle.decompress(oracle.RLE, x.size, bad.view(np.uint8))
+    bad = buf.view("<u8").copy()
+    bad[2 * R + 1] += 1  # block 1's directory entry names the wrong run
+    with pytest.raises(oracle.OracleError):
+        oracle.decompress(oracle.RLE, x.size, bad.view(np.uint8))
+    with pytest.raises(oracle.OracleError):
+        oracle.decompress(oracle.RLE, x.size, buf[:-8])  # not 16 R + 8 nch bytes
