@@ -36,6 +36,18 @@
  *                difference to the predecessor, restarted at every block.
  *   MS_FOR_BP    as DYN_BP with residual = x - ref, ref = the block minimum.  FOR
  *                is the difference to a reference value.
+ *   MS_RLE       run-length encoding (Sec. 2.1: a run of equal consecutive
+ *                values is stored once, with its repetition).  R runs; the
+ *                repetition is recorded as the position where the run ends:
+ *                R run values (uint64), then R run ends (uint64, exclusive; the
+ *                last is n), then a directory of ceil(n/512) uint64 entries, entry
+ *                g = the run that holds value 512*g, so that a block's runs are
+ *                found without a search (random access, Sec. 4.2).
+ *                size = 16*R + 8*ceil(n/512); n_blocks (ms_column_meta) = R.
+ *                Produced by ms_compress and ms_morph only; read by every
+ *                operator but ms_select_packed and the batched fragments (which
+ *                return MS_ERR_FORMAT for it at once).  Other operators with
+ *                out_fmt MS_RLE return MS_ERR_FORMAT at once: morph their output.
  *   A column buffer starts on a 256-byte boundary.  The header is 16 bytes per
  *   block, so every block payload starts on a 64-byte boundary.
  *
@@ -82,7 +94,8 @@ typedef enum {
   MS_STATIC_BP = 1,
   MS_DYN_BP = 2,
   MS_DELTA_BP = 3,
-  MS_FOR_BP = 4
+  MS_FOR_BP = 4,
+  MS_RLE = 5
 } ms_fmt;
 
 typedef enum {
@@ -439,7 +452,8 @@ typedef enum {
   MS_K_BATCH = 13,      /* batched select -> project -> agg_sum fragments */
   MS_K_SELECT_PACKED = 14, /* specialized select on packed codes -> match bitmap */
   MS_K_ARENA = 15,      /* arena bookkeeping: top reset after ms_column_free, metadata writes */
-  MS_K_COUNT = 16
+  MS_K_RLE = 16,        /* RLE encoding: run heads per block, their scan, run records */
+  MS_K_COUNT = 17
 } ms_kernel;
 
 typedef struct {

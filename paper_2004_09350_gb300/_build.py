@@ -21,7 +21,7 @@ SOURCES = ["ms_host.cu", "ms_ops.cu", "ms_noalloc.cu", "ms_consume.cu", "ms_plac
            "ms_select_packed.cu",
            "ms_map_project.cu", "ms_map_calc.cu", "ms_map_emit.cu", "ms_mlp.cu",
            "ms_batch.cu", "ms_batch_d2.cu", "ms_batch_d3.cu", "ms_batch_d4.cu",
-           "ms_batch_static.cu"]
+           "ms_batch_static.cu", "ms_rle.cu"]
 
 
 def nvcc() -> str:

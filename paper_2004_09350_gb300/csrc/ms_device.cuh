@@ -302,6 +302,80 @@ MS_DEV void write_lane_stream(uint16_t* s, int lane, int b, const uint64_t r[16]
   }
 }
 
+// ------------------------------------------------------------ RLE (Sec. 2.1)
+// An RLE column holds R run values, R exclusive run ends (the last is n) and a
+// directory of ceil(n/512) entries, entry g = the run that holds value 512*g
+// (ColView.nb = R).
+
+// True when the column's size holds its R runs and its directory.
+MS_DEV bool rle_sound(const ColView& c) {
+  const uint64_t nch = (c.n + kBlock - 1) / kBlock;
+  return (c.n == 0 || c.nb > 0) && c.nb <= c.size / 16 && 16 * c.nb + 8 * nch <= c.size;
+}
+
+// The run that holds value i: the least r with ends[r] > i.  `lo` is a run known
+// to start at or before i (ends[lo-1] <= i; 0 always is).  The search gallops
+// forward from lo and then bisects, so a run near lo is found in a few loads.
+// Every index read stays in [0, R) whatever the ends hold.
+MS_DEV uint64_t rle_run_of(const uint64_t* ends, uint64_t R, uint64_t i, uint64_t lo) {
+  if (lo >= R) lo = 0;
+  uint64_t hi = lo, step = 1;
+  while (hi < R - 1 && ldg64(ends + hi) <= i) {
+    lo = hi + 1;
+    hi = min(R - 1, hi + step);
+    step <<= 1;
+  }
+  while (lo < hi) {
+    const uint64_t mid = lo + (hi - lo) / 2;
+    if (ldg64(ends + mid) > i) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Values of block g of an RLE column into lane registers (value 16*lane + k of the
+// block in v[k], zero past `valid`): the directory gives the block's first run,
+// each lane finds the run of its first value from there and walks its 16 values
+// forward through the runs.
+MS_DEV void rle_expand(const ColView& c, uint64_t g, int lane, int valid, uint64_t v[16], DevCtl* ctl) {
+  const uint64_t R = c.nb;
+  const uint64_t* val = reinterpret_cast<const uint64_t*>(c.p);
+  const uint64_t* ends = val + R;
+  const uint64_t* dir = ends + R;
+  if (!rle_sound(c) || valid <= 0) {
+    if (lane == 0 && valid > 0) set_error(ctl, MS_ERR_FORMAT, g);
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = 0;
+    return;
+  }
+  const uint64_t row0 = g * kBlock + 16 * (uint64_t)lane;
+  uint64_t r = rle_run_of(ends, R, row0, ldg64(dir + g));
+  uint64_t e = ldg64(ends + r), x = ldg64(val + r);
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    if (16 * lane + k < valid) {
+      while (row0 + k >= e && r + 1 < R) {
+        r++;
+        e = ldg64(ends + r);
+        x = ldg64(val + r);
+      }
+      v[k] = x;
+    } else {
+      v[k] = 0;
+    }
+  }
+}
+
+// Value i (< n) of an RLE column; 0 for a column whose size cannot hold its runs.
+MS_DEV uint64_t rle_read_at(const ColView& c, uint64_t i) {
+  if (!rle_sound(c) || c.nb == 0) return 0;
+  const uint64_t R = c.nb;
+  const uint64_t* val = reinterpret_cast<const uint64_t*>(c.p);
+  const uint64_t* ends = val + R;
+  const uint64_t* dir = ends + R;
+  return ldg64(val + rle_run_of(ends, R, i, ldg64(dir + i / kBlock)));
+}
+
 // ------------------------------------------------------------- chunk decode
 
 // Decodes chunk g (values 512g .. 512g+511) of column c into lane registers.  Returns
@@ -316,6 +390,10 @@ MS_DEV int decode_chunk(const ColView& c, uint64_t g, int lane, uint64_t v[16], 
     return 0;
   }
   const int valid = (int)min((uint64_t)kBlock, c.n - base);
+  if (c.fmt == MS_RLE) {
+    rle_expand(c, g, lane, valid, v, ctl);
+    return valid;
+  }
   if (c.fmt == MS_UNCOMPR) {
     const uint64_t* src = reinterpret_cast<const uint64_t*>(c.p) + base;
     if (valid == kBlock) {
@@ -497,6 +575,7 @@ MS_DEV void stage_header(const ColView& c, uint64_t g, uint64_t* hdr, int lane) 
 // the same max_units then reads it in place from global memory.
 MS_DEV void stage_payload(const ColView& c, uint64_t g, const uint64_t* hdr, uint16_t* slot, int lane,
                           int max_units = 256) {
+  if (c.fmt == MS_RLE) return;  // read from global memory by rle_expand
   const uint8_t* src = nullptr;
   int units = 0;
   bool swizzle = false;
@@ -540,6 +619,10 @@ MS_DEV int decode_staged(const ColView& c, uint64_t g, const uint64_t* hdr, cons
     return 0;
   }
   const int valid = (int)min((uint64_t)kBlock, c.n - base);
+  if (c.fmt == MS_RLE) {
+    rle_expand(c, g, lane, valid, v, ctl);
+    return valid;
+  }
   if (c.fmt == MS_UNCOMPR) {
     if (valid == kBlock && max_units >= 256) {
       const uint4* st = reinterpret_cast<const uint4*>(slot);
@@ -687,6 +770,7 @@ struct ChunkStream {
 // Random read of value i (< c.n) of a non-DELTA column (Sec. 4.2 random access).
 MS_DEV uint64_t read_at(const ColView& c, uint64_t i) {
   if (c.fmt == MS_UNCOMPR) return ldg64(c.p + 8 * i);
+  if (c.fmt == MS_RLE) return rle_read_at(c, i);
   const uint64_t g = i / kBlock;
   const int r = (int)(i % kBlock);
   int b;

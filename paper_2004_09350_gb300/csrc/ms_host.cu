@@ -35,7 +35,7 @@ void dev_free(ms_ctx* c, void* p) {
 }
 
 bool valid_format(int fmt, int bw) {
-  if (fmt < MS_UNCOMPR || fmt > MS_FOR_BP) return false;
+  if (fmt < MS_UNCOMPR || fmt > MS_RLE) return false;
   if (fmt == MS_STATIC_BP && (bw < 1 || bw > 64)) return false;
   return true;
 }
@@ -258,10 +258,17 @@ ms_status ms_column_import(ms_ctx* c, int fmt, int bw, uint64_t n, const void* s
   if (!c || !out || (!src && size)) return MS_ERR_INVALID_ARG;
   *out = nullptr;
   if (!valid_format(fmt, bw)) return MS_ERR_INVALID_ARG;
-  const uint64_t nb = (fmt >= MS_DYN_BP) ? n / kBlock : 0;
+  const bool blockfmt = fmt >= MS_DYN_BP && fmt <= MS_FOR_BP;
+  uint64_t nb = blockfmt ? n / kBlock : 0;
   if (fmt == MS_UNCOMPR && size < 8 * n) return MS_ERR_FORMAT;
   if (fmt == MS_STATIC_BP && size < 8 * cdiv(n * (uint64_t)bw, 64)) return MS_ERR_FORMAT;
-  if (fmt >= MS_DYN_BP && size < 16 * nb + 8 * (n % kBlock)) return MS_ERR_FORMAT;
+  if (blockfmt && size < 16 * nb + 8 * (n % kBlock)) return MS_ERR_FORMAT;
+  if (fmt == MS_RLE) {  // R runs and the directory: size = 16 R + 8 ceil(n / 512)
+    const uint64_t dir = 8 * cdiv(n, kBlock);
+    if (size < dir || (size - dir) % 16) return MS_ERR_FORMAT;
+    nb = (size - dir) / 16;
+    if ((n == 0) != (nb == 0) || nb > n) return MS_ERR_FORMAT;
+  }
   int slot = take_slot(c);
   if (slot < 0) return MS_ERR_NOMEM;
   void* buf = dev_alloc(c, align_up(size + 64, 256));
@@ -284,7 +291,7 @@ ms_status ms_column_import(ms_ctx* c, int fmt, int bw, uint64_t n, const void* s
     k_write_meta<<<1, 1, 0, s>>>(c->metas + slot, m);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess && fmt >= MS_DYN_BP) {
+  if (e == cudaSuccess && blockfmt) {
     ProfScope ps(c, MS_K_VALIDATE, s);
     k_validate<<<(unsigned)std::min<uint64_t>(cdiv(std::max<uint64_t>(nb, 1), 256), 1024), 256, 0, s>>>(
         c->metas + slot, c->ctl);
@@ -416,7 +423,7 @@ const char* ms_kernel_name(int k) {
   static const char* names[MS_K_COUNT] = {"mark",       "emit",     "compress", "decompress",    "project",
                                           "calc",       "agg_sum",  "group_sum", "build_keys",   "validate",
                                           "scan",       "place",    "stats",     "batch",        "select_packed",
-                                          "arena"};
+                                          "arena",      "rle"};
   return (k >= 0 && k < MS_K_COUNT) ? names[k] : "?";
 }
 

@@ -72,6 +72,24 @@ MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body bo
   const uint32_t fixed = c.fmt == MS_UNCOMPR ? 4096u : (c.fmt == MS_STATIC_BP ? 64u * (uint32_t)c.bw : 0u);
   const uint64_t pay0 = 16 * c.nb;  // byte offset of the block payloads (block formats)
 
+  if (c.fmt == MS_RLE) {  // runs are read from global memory by rle_expand: nothing to stage
+    if (claim0 == ~0ull) {
+      claim0 = blockIdx.x;
+      cstride = gridDim.x;
+    }
+    for (uint64_t cl = claim0; cl < nclaims; cl += cstride) {
+      const uint64_t e = min(nch, (cl + 1) * kClaim);
+      for (uint64_t k = cl * kClaim + warp; k < e; k += nwarps) {
+        const int valid = (int)min((uint64_t)kBlock, c.n - k * kBlock);
+        uint64_t v[16];
+        rle_expand(c, k, lane, valid, v, ctl);
+        body(k, v, valid, false);
+      }
+      __syncthreads();
+    }
+    return;
+  }
+
   auto load_hdr = [&](uint64_t claim, int hb) {
     if (!blockfmt || claim >= nclaims) return;
     for (int k = tid; k < kClaim; k += nthr) {
@@ -814,6 +832,14 @@ MS_DEV int encode_block(int fmt, uint64_t v[16], int lane, uint64_t* ref_out) {
 #endif
 constexpr int kGatherGroup = MS_GATHER_GROUP;
 MS_DEV void gather_values(const ColView& d, uint64_t* stage, uint32_t ok, int lane) {
+  if (d.fmt == MS_RLE) {  // the run of each position: directory, then a short search
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      const uint64_t q = stage[swz(lane + 32 * i)];
+      stage[swz(lane + 32 * i)] = ((ok >> i) & 1u) ? rle_read_at(d, q) : 0;
+    }
+    return;
+  }
   if (d.fmt == MS_UNCOMPR) {
 #pragma unroll
     for (int half = 0; half < 2; half++) {

@@ -65,6 +65,10 @@ ms_status launch_map<OP_EMIT>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStr
 template <>
 ms_status launch_map<OP_PROJECT_WARP>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
 
+// run-length encoding of a column (ms_rle.cu); `in` null: raw uint64 input (raw, n_max)
+ms_status rle_encode(ms_ctx* c, const DevMeta* in, const uint64_t* raw, uint64_t n_max, const Work& w,
+                     ms_column** out, cudaStream_t s);
+
 // placement of a staged block-format output (ms_place.cu)
 ms_status launch_place(ms_ctx* c, const Work& w, DevMeta* out, uint64_t n_max, cudaStream_t s);
 

@@ -100,7 +100,7 @@ ms_status produce_column(ms_ctx* c, ProduceArgs& a, const Work& w, uint64_t n_ma
   a.bw = fmt == MS_STATIC_BP ? bw : 0;
   a.stage_meta = w.stage_meta;
   ms_status st = launch_map<OP>(c, a, n_max, s);
-  if (st == MS_OK && fmt >= MS_DYN_BP) st = launch_place(c, w, a.out_meta, n_max, s);
+  if (st == MS_OK && fmt >= MS_DYN_BP && fmt <= MS_FOR_BP) st = launch_place(c, w, a.out_meta, n_max, s);
   if (st != MS_OK) {
     // a producer that ran without its placement leaves stage bytes taken
     cudaMemsetAsync(&c->ctl->stage, 0, 8, s);
@@ -139,6 +139,7 @@ ms_status ms_compress(ms_ctx* c, const uint64_t* d_in, uint64_t n, int fmt, int 
   Work w;
   ms_status st = carve(c, n, 0, &w, s);
   if (st != MS_OK) return st;
+  if (fmt == MS_RLE) return rle_encode(c, nullptr, d_in, n, w, out, s);
   ProduceArgs a{};
   a.raw_in = d_in;
   a.raw_n = n;
@@ -167,6 +168,7 @@ ms_status ms_morph(ms_ctx* c, const ms_column* col, int fmt, int bw, ms_column**
   Work w;
   ms_status st = carve(c, col->n_max, 0, &w, s);
   if (st != MS_OK) return st;
+  if (fmt == MS_RLE) return rle_encode(c, c->metas + col->slot, nullptr, col->n_max, w, out, s);
   ProduceArgs a{};
   a.in0 = c->metas + col->slot;
   a.raw_cap = ~0ull;
@@ -179,6 +181,7 @@ ms_status ms_select(ms_ctx* c, const ms_column* in, int cmp, uint64_t c1, uint64
   if (!c || !out || !owned(c, in) || !valid_format(fmt, bw) || cmp < MS_EQ || cmp > MS_BETWEEN)
     return MS_ERR_INVALID_ARG;
   *out = nullptr;
+  if (fmt == MS_RLE) return MS_ERR_FORMAT;  // RLE comes from ms_compress / ms_morph
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Work w;
   ms_status st = carve(c, in->n_max, 0, &w, s);
@@ -198,7 +201,8 @@ ms_status ms_select_packed(ms_ctx* c, const ms_column* in, int cmp, uint64_t c1,
   if (!c || !out || !owned(c, in) || !valid_format(fmt, bw) || cmp < MS_EQ || cmp > MS_BETWEEN)
     return MS_ERR_INVALID_ARG;
   *out = nullptr;
-  if (in->fmt == MS_UNCOMPR) return MS_ERR_FORMAT;  // nothing packed to work on
+  if (fmt == MS_RLE) return MS_ERR_FORMAT;  // RLE comes from ms_compress / ms_morph
+  if (in->fmt == MS_UNCOMPR || in->fmt == MS_RLE) return MS_ERR_FORMAT;  // no bit-packed codes to work on
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Work w;
   ms_status st = carve(c, in->n_max, 0, &w, s);
@@ -217,6 +221,7 @@ ms_status ms_project(ms_ctx* c, const ms_column* data, const ms_column* pos, int
   MS_TRACE();
   if (!c || !out || !owned(c, data) || !owned(c, pos) || !valid_format(fmt, bw)) return MS_ERR_INVALID_ARG;
   *out = nullptr;
+  if (fmt == MS_RLE) return MS_ERR_FORMAT;  // RLE comes from ms_compress / ms_morph
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Work w;
   ms_status st = carve(c, pos->n_max, 0, &w, s);
@@ -228,9 +233,10 @@ ms_status ms_project(ms_ctx* c, const ms_column* data, const ms_column* pos, int
   // in place, both by the per-warp gather.  DYN / FOR / static-BP data goes through the
   // CTA span gather when the positions are a DELTA column (sorted position lists are
   // kept as DELTA); other position columns (values used as keys, in any order) are
-  // read in place by the per-warp gather, which keeps more warps per SM.  Both paths
-  // give the same values for any positions.
-  if (data->fmt == MS_DELTA_BP || data->fmt == MS_UNCOMPR || pos->fmt != MS_DELTA_BP)
+  // read in place by the per-warp gather, which keeps more warps per SM.  RLE data is
+  // read by the per-warp gather too (directory, then a short search per position).
+  // Both paths give the same values for any positions.
+  if (data->fmt == MS_DELTA_BP || data->fmt == MS_UNCOMPR || data->fmt == MS_RLE || pos->fmt != MS_DELTA_BP)
     return produce_column<OP_PROJECT_WARP>(c, a, w, pos->n_max, fmt, bw, out, s);
   return produce_column<OP_PROJECT>(c, a, w, pos->n_max, fmt, bw, out, s);
 }
@@ -242,6 +248,7 @@ ms_status ms_calc(ms_ctx* c, int op, const ms_column* x, const ms_column* y, uin
       op > MS_MUL)
     return MS_ERR_INVALID_ARG;
   *out = nullptr;
+  if (fmt == MS_RLE) return MS_ERR_FORMAT;  // RLE comes from ms_compress / ms_morph
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const uint64_t n_max = y ? std::min(x->n_max, y->n_max) : x->n_max;
   Work w;
@@ -279,6 +286,7 @@ ms_status ms_semijoin(ms_ctx* c, const ms_column* probe, const ms_column* keys, 
   if (!c || !out || !owned(c, probe) || !owned(c, keys) || !valid_format(fmt, bw) || domain == 0)
     return MS_ERR_INVALID_ARG;
   *out = nullptr;
+  if (fmt == MS_RLE) return MS_ERR_FORMAT;  // RLE comes from ms_compress / ms_morph
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Work w;
   ms_status st = carve(c, std::max(probe->n_max, keys->n_max), domain, &w, s);

@@ -108,6 +108,22 @@ def geometric_gaps(seed: int, n: int) -> np.ndarray:
     return gap.astype(np.uint64)
 
 
+def runs(seed: int, n: int, mean_run: int, distinct: int = 6) -> np.ndarray:
+    """A column of runs: run lengths uniform in [1, 2*mean_run - 1] (mean `mean_run`),
+    run values uniform in [0, distinct), so that neighbouring runs of equal value merge
+    into longer ones as in real low-cardinality columns."""
+    if n == 0:
+        return np.zeros(0, dtype=np.uint64)
+    k = n // max(mean_run, 1) + 2
+    while True:
+        lens = uniform(seed, k, 1, 2 * mean_run)
+        if int(lens.sum()) >= n:
+            break
+        k *= 2
+    vals = uniform(seed + 1, k, 0, distinct)
+    return np.repeat(vals, lens.astype(np.int64))[:n].copy()
+
+
 # --------------------------------------------------------------- Table 1 columns
 
 def table1_column(which: str, n: int, seed: int = 1) -> np.ndarray:
