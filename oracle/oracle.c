@@ -59,6 +59,12 @@
  *                        Sec. 4.2's random access: a block's first run without a
  *                        search)
  *                size = 16*R + 8*nch; n = 0 gives R = 0 and size 0.
+ *  FOR_STATIC_BP / DELTA_STATIC_BP b (Sec. 2.1: FOR and DELTA cascaded with the
+ *                NS algorithm static BP, "one block and fixed bit width" for the
+ *                residuals): the layout of FOR_BP / DELTA_BP (same residuals,
+ *                references, headers and remainder) with b_k = b for every block,
+ *                b given by the caller (1..64); a residual wider than b is an error.
+ *                size = 16*nb + 64*b*nb + 8*r
  */
 #include "oracle.h"
 
@@ -115,15 +121,19 @@ static void unpack_block(const uint8_t *blk, int b, uint64_t *res) {
 /* ------------------------------------------------------- block transforms */
 
 static int is_block_fmt(int fmt) {
-  return fmt == ORC_DYN_BP || fmt == ORC_DELTA_BP || fmt == ORC_FOR_BP;
+  return fmt == ORC_DYN_BP || fmt == ORC_DELTA_BP || fmt == ORC_FOR_BP || fmt == ORC_FOR_STATIC_BP ||
+         fmt == ORC_DELTA_STATIC_BP;
 }
+
+/* the cascades with static BP: every block at the caller's width */
+static int is_static_cascade(int fmt) { return fmt == ORC_FOR_STATIC_BP || fmt == ORC_DELTA_STATIC_BP; }
 
 /* residuals and reference of one block per the format definitions */
 static void block_residuals(int fmt, const uint64_t *x, uint64_t *res, uint64_t *ref) {
   if (fmt == ORC_DYN_BP) {
     for (unsigned i = 0; i < ORC_BLOCK; i++) res[i] = x[i];
     *ref = 0;
-  } else if (fmt == ORC_FOR_BP) {
+  } else if (fmt == ORC_FOR_BP || fmt == ORC_FOR_STATIC_BP) {
     uint64_t mn = x[0];
     for (unsigned i = 1; i < ORC_BLOCK; i++)
       if (x[i] < mn) mn = x[i];
@@ -174,6 +184,7 @@ uint64_t orc_size(int fmt, int bw, const uint64_t *x, uint64_t n) {
   }
   if (!is_block_fmt(fmt)) return 0;
   uint64_t nb = n / ORC_BLOCK, r = n % ORC_BLOCK, words = 0;
+  if (is_static_cascade(fmt)) return (bw < 1 || bw > 64) ? 0 : 16 * nb + 64 * (uint64_t)bw * nb + 8 * r;
   uint64_t res[ORC_BLOCK], ref;
   for (uint64_t k = 0; k < nb; k++) {
     block_residuals(fmt, x + k * ORC_BLOCK, res, &ref);
@@ -195,8 +206,8 @@ static uint64_t get_u64(const uint8_t *p) {
 
 int orc_compress(int fmt, int bw, const uint64_t *x, uint64_t n, uint8_t *out,
                  uint64_t cap, uint64_t *size_out) {
-  if (fmt < ORC_UNCOMPR || fmt > ORC_RLE) return ORC_BAD_ARG;
-  if (fmt == ORC_STATIC_BP && (bw < 1 || bw > 64)) return ORC_BAD_ARG;
+  if (fmt < ORC_UNCOMPR || fmt > ORC_DELTA_STATIC_BP) return ORC_BAD_ARG;
+  if ((fmt == ORC_STATIC_BP || is_static_cascade(fmt)) && (bw < 1 || bw > 64)) return ORC_BAD_ARG;
   uint64_t size = orc_size(fmt, bw, x, n);
   if (size > cap) return ORC_BAD_ARG;
   memset(out, 0, size);
@@ -242,6 +253,10 @@ int orc_compress(int fmt, int bw, const uint64_t *x, uint64_t n, uint8_t *out,
   for (uint64_t k = 0; k < nb; k++) {
     block_residuals(fmt, x + k * ORC_BLOCK, res, &ref);
     int b = max_width(res, ORC_BLOCK);
+    if (is_static_cascade(fmt)) {
+      if (b > bw) return ORC_TOO_WIDE;
+      b = bw;
+    }
     put_u64(out + 16 * k, (off << 8) | (uint64_t)b);
     put_u64(out + 16 * k + 8, ref);
     pack_block(res, b, payload + 8 * off);
@@ -297,6 +312,7 @@ int orc_decompress(int fmt, int bw, uint64_t n, const uint8_t *buf, uint64_t siz
     return ORC_OK;
   }
   if (!is_block_fmt(fmt)) return ORC_BAD_ARG;
+  if (is_static_cascade(fmt) && (bw < 1 || bw > 64)) return ORC_BAD_ARG;
   uint64_t nb = n / ORC_BLOCK, r = n % ORC_BLOCK;
   if (size < 16 * nb) return ORC_BAD_FORMAT;
   const uint8_t *payload = buf + 16 * nb;
@@ -306,12 +322,13 @@ int orc_decompress(int fmt, int bw, uint64_t n, const uint8_t *buf, uint64_t siz
     int b = (int)(w0 & 0xff);
     uint64_t off = w0 >> 8;
     if (b > 64 || off != expect_off) return ORC_BAD_FORMAT;
+    if (is_static_cascade(fmt) && b != bw) return ORC_BAD_FORMAT;
     if (16 * nb + 8 * (off + 8 * (uint64_t)b) > size) return ORC_BAD_FORMAT;
     unpack_block(payload + 8 * off, b, res);
     uint64_t *x = out + k * ORC_BLOCK;
     if (fmt == ORC_DYN_BP) {
       for (unsigned i = 0; i < ORC_BLOCK; i++) x[i] = res[i];
-    } else if (fmt == ORC_FOR_BP) {
+    } else if (fmt == ORC_FOR_BP || fmt == ORC_FOR_STATIC_BP) {
       for (unsigned i = 0; i < ORC_BLOCK; i++) x[i] = ref + res[i];
     } else { /* DELTA: x_0 = ref, x_i = x_{i-1} + residual_i */
       x[0] = ref + res[0];

@@ -20,6 +20,9 @@
  *   4 FOR_BP    FOR (difference to a reference value) cascaded with DYN_BP.
  *   5 RLE       run-length encoding: every run of equal consecutive values is
  *               recorded once, with the position where it ends.
+ *   6 FOR_STATIC_BP    FOR cascaded with static BP: FOR_BP's layout with every
+ *               block's residuals packed at the one caller-chosen width b.
+ *   7 DELTA_STATIC_BP  DELTA cascaded with static BP, likewise.
  * The bit layout is not printed in the paper; the reading used here is spelled
  * out in oracle.c's header comment and is the one the CUDA library implements.
  */
@@ -37,7 +40,7 @@ enum { ORC_OK = 0, ORC_BAD_ARG = 1, ORC_BAD_FORMAT = 2, ORC_TOO_WIDE = 3,
        ORC_OUT_OF_RANGE = 4 };
 
 enum { ORC_UNCOMPR = 0, ORC_STATIC_BP = 1, ORC_DYN_BP = 2, ORC_DELTA_BP = 3,
-       ORC_FOR_BP = 4, ORC_RLE = 5 };
+       ORC_FOR_BP = 4, ORC_RLE = 5, ORC_FOR_STATIC_BP = 6, ORC_DELTA_STATIC_BP = 7 };
 
 enum { ORC_EQ = 0, ORC_NE = 1, ORC_LT = 2, ORC_LE = 3, ORC_GT = 4, ORC_GE = 5,
        ORC_BETWEEN = 6 };

@@ -24,6 +24,7 @@ _lib = None
 UNCOMPR, STATIC_BP, DYN_BP, DELTA_BP, FOR_BP = range(5)
 FORMAT_NAMES = ("uncompr", "static_bp", "dyn_bp", "delta_bp", "for_bp")
 RLE = 5  # run-length encoding (values, run ends, block directory); not among the five above
+FOR_STATIC_BP, DELTA_STATIC_BP = 6, 7  # FOR / DELTA cascaded with static BP (every block at width bw)
 EQ, NE, LT, LE, GT, GE, BETWEEN = range(7)
 ADD, SUB, MUL = range(3)
 OK, BAD_ARG, BAD_FORMAT, TOO_WIDE, OUT_OF_RANGE = range(5)

@@ -412,3 +412,57 @@ def test_rle_corrupt_columns_are_rejected():
         oracle.decompress(oracle.RLE, x.size, bad.view(np.uint8))
     with pytest.raises(oracle.OracleError):
         oracle.decompress(oracle.RLE, x.size, buf[:-8])  # not 16 R + 8 nch bytes
+
+
+# ----------------------------------------------- FOR / DELTA cascaded with static BP
+
+@pytest.mark.parametrize("fmt,base", [(oracle.FOR_STATIC_BP, oracle.FOR_BP), (oracle.DELTA_STATIC_BP, oracle.DELTA_BP)])
+def test_static_cascade_equals_block_format_at_its_natural_width(fmt, base):
+    """When every block's residuals need exactly b bits, the cascade with static BP at
+    width b writes the same bytes as the cascade with dynamic BP."""
+    x = (1000 + np.arange(3 * 512 + 100, dtype=np.uint64) % 4) if base == oracle.FOR_BP else \
+        (5 + 3 * np.arange(3 * 512 + 100, dtype=np.uint64))
+    b = int(oracle.block_widths(base, x).max())
+    assert (oracle.block_widths(base, x) == b).all()
+    assert oracle.compress(fmt, x, bw=b).tobytes() == oracle.compress(base, x).tobytes()
+
+
+@pytest.mark.parametrize("fmt", [oracle.FOR_STATIC_BP, oracle.DELTA_STATIC_BP])
+@pytest.mark.parametrize("n", [0, 1, 511, 512, 513, 1500, 4097])
+def test_static_cascade_bytes_size_and_residuals(fmt, n):
+    """Every header carries width bw at offset 8*bw*k; the residuals read from the bytes
+    with numpy bit operations give the values back (reference + residual for FOR, the
+    prefix sum from the reference for DELTA); size 16 nb + 64 bw nb + 8 r."""
+    x = synth.sorted_gaps(91, n) if fmt == oracle.DELTA_STATIC_BP else synth.table1_column("C3", n)
+    need = int(oracle.block_widths(oracle.DELTA_BP if fmt == oracle.DELTA_STATIC_BP else oracle.FOR_BP, x).max()) \
+        if n >= 512 else 1
+    bw = need + 3
+    buf = oracle.compress(fmt, x, bw=bw)
+    nb, r = n // 512, n % 512
+    assert buf.size == 16 * nb + 64 * bw * nb + 8 * r == oracle.size(fmt, x, bw=bw)
+    hdr = np.frombuffer(buf[: 16 * nb].tobytes(), dtype="<u8").reshape(nb, 2) if nb else np.zeros((0, 2), np.uint64)
+    assert [int(w) & 0xFF for w in hdr[:, 0]] == [bw] * nb
+    assert [int(w) >> 8 for w in hdr[:, 0]] == [8 * bw * k for k in range(nb)]
+    res, refs = _payload_residuals(buf, n)
+    for k in range(nb):
+        blk = [int(v) for v in x[512 * k: 512 * (k + 1)]]
+        if fmt == oracle.FOR_STATIC_BP:
+            assert refs[k] == min(blk) and [refs[k] + q for q in res[k]] == blk
+        else:
+            assert refs[k] == blk[0] and res[k][0] == 0
+            assert list(np.cumsum([refs[k]] + res[k][1:], dtype=object)) == blk
+    np.testing.assert_array_equal(oracle.decompress(fmt, n, buf, bw=bw), x)
+
+
+def test_static_cascade_width_limits():
+    x = synth.sorted_gaps(92, 2048)
+    need = int(oracle.block_widths(oracle.DELTA_BP, x).max())
+    oracle.compress(oracle.DELTA_STATIC_BP, x, bw=need)
+    with pytest.raises(oracle.OracleError):
+        oracle.compress(oracle.DELTA_STATIC_BP, x, bw=need - 1)
+    y = synth.table1_column("C3", 2048)  # FOR residuals below 2^6
+    with pytest.raises(oracle.OracleError):
+        oracle.compress(oracle.FOR_STATIC_BP, y, bw=5)
+    buf = oracle.compress(oracle.FOR_STATIC_BP, y, bw=6)
+    with pytest.raises(oracle.OracleError):  # read back at another width: headers disagree
+        oracle.decompress(oracle.FOR_STATIC_BP, y.size, buf, bw=7)
