@@ -51,6 +51,8 @@ BLOCK = 512
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--render-sweep-table", default="",
+                    help="print the markdown table of a saved sweep-table JSON line and exit")
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -1321,8 +1323,170 @@ def bench_sweep_table(args):
         out["agg_sum"][name[fi]] = {"ms": round(t, 4), "rows_per_s": n / (t * 1e-3)}
     ctx.check(what="agg_sum sweep")
     out["positions"] = m
+
+    # direct morphs (Sec. 3.2, on-the-fly morphing) of X for every ordered format pair,
+    # against the round trip through uint64 (decompress into a buffer, compress again);
+    # algorithmic bytes: bytes(input) + bytes(output)
+    xb = out["x_bytes"]
+    buf = torch.empty(n, dtype=torch.int64, device=dev)
+    out["morph"], out["morph_staged"] = {}, {}
+    for fi in F:
+        for fo in F:
+            bwo = bx if fo == ms.STATIC_BP else 0
+            t = timed(lambda: ctx.free(ctx.morph(X[fi], fo, bwo)))
+            gbps = (xb[name[fi]] + xb[name[fo]]) / (t * 1e6)
+            out["morph"][f"{name[fi]}|{name[fo]}"] = {"ms": round(t, 4), "rows_per_s": n / (t * 1e-3),
+                                                      "alg_GBps": round(gbps, 1)}
+            t = timed(lambda: (ctx.decompress(X[fi], out=buf), ctx.free(ctx.compress(buf, fo, bwo))))
+            out["morph_staged"][f"{name[fi]}|{name[fo]}"] = {"ms": round(t, 4), "rows_per_s": n / (t * 1e-3)}
+    ctx.check(what="morph sweep")
+
+    # RLE (Sec. 2.1) against uncompressed, dynamic BP and DELTA+BP on a column of long
+    # runs (run lengths uniform in [1, 7999], 6 distinct values: a sorted low-cardinality
+    # column's shape), every operator that reads it, and the encoders
+    r = synth.runs(args.seed + 5, n, 4000)
+    dr = ms.as_device_u64(r, dev)
+    RF = [ms.UNCOMPR, ms.DYN_BP, ms.DELTA_BP, ms.RLE]
+    Rc = {f: ctx.compress(dr, f) for f in RF}
+    rb = {name[f]: ctx.info(Rc[f])["size_bytes"] for f in RF}
+    rle = {"runs": ctx.info(Rc[ms.RLE])["n_blocks"], "bytes": rb, "compress": {}, "decompress": {},
+           "morph_from_dyn_bp": {}, "select": {}, "agg_sum": {}, "project": {}}
+    for f in RF:
+        fn = name[f]
+        t = timed(lambda: ctx.free(ctx.compress(dr, f)))
+        rle["compress"][fn] = {"ms": round(t, 4), "alg_GBps": round((8 * n + rb[fn]) / (t * 1e6), 1)}
+        t = timed(lambda: ctx.decompress(Rc[f], out=buf))
+        rle["decompress"][fn] = {"ms": round(t, 4), "alg_GBps": round((8 * n + rb[fn]) / (t * 1e6), 1)}
+        t = timed(lambda: ctx.free(ctx.morph(Rc[ms.DYN_BP], f)))
+        rle["morph_from_dyn_bp"][fn] = {"ms": round(t, 4),
+                                       "alg_GBps": round((rb["dyn_bp"] + rb[fn]) / (t * 1e6), 1)}
+        t = timed(lambda: ctx.free(ctx.select(Rc[f], ms.LT, 1, fmt=ms.DELTA_BP)))
+        rle["select"][fn] = {"ms": round(t, 4), "rows_per_s": n / (t * 1e-3)}
+        t = timed(lambda: ctx.agg_sum(Rc[f], out=res))
+        rle["agg_sum"][fn] = {"ms": round(t, 4), "rows_per_s": n / (t * 1e-3),
+                             "alg_GBps": round(rb[fn] / (t * 1e6), 1)}
+        t = timed(lambda: ctx.free(ctx.project(Rc[f], P, fmt=ms.UNCOMPR)))
+        rle["project"][fn] = {"ms": round(t, 4), "rows_per_s": m / (t * 1e-3)}
+    ctx.check(what="rle sweep")
+    rle["select_selectivity"] = float(np.count_nonzero(r < 1)) / n
+    out["rle"] = rle
+    for f in reversed(RF):
+        ctx.free(Rc[f])
+    del dr
+
+    # FOR / DELTA cascaded with static BP against the dynamic cascades: K (sorted) as
+    # DELTA, X as FOR, the static width the column's widest block needs
+    cas = {}
+    for col, dyn, stat in (("K", K[ms.DELTA_BP], ms.DELTA_STATIC_BP), ("X", X[ms.FOR_BP], ms.FOR_STATIC_BP)):
+        src = k if col == "K" else x
+        bws = max(1, int(oracle_free_block_width(src, stat == ms.DELTA_STATIC_BP)))
+        dsrc = ms.as_device_u64(src, dev)
+        sc = ctx.compress(dsrc, stat, bws)
+        e = {"static_bw": bws, "bytes": {name[ctx.info(dyn)["fmt"]]: ctx.info(dyn)["size_bytes"],
+                                          name[stat]: ctx.info(sc)["size_bytes"]}}
+        for key, cc, fm, bw_ in (("dyn", dyn, ctx.info(dyn)["fmt"], 0), ("static", sc, stat, bws)):
+            e[key] = {
+                "compress_ms": round(timed(lambda: ctx.free(ctx.compress(dsrc, fm, bw_))), 4),
+                "decompress_ms": round(timed(lambda: ctx.decompress(cc, out=buf)), 4),
+                "agg_sum_ms": round(timed(lambda: ctx.agg_sum(cc, out=res)), 4),
+                "project_ms": round(timed(lambda: ctx.free(ctx.project(cc, P, fmt=ms.UNCOMPR))), 4)}
+        cas[col] = e
+        ctx.free(sc)
+        del dsrc
+    ctx.check(what="cascade sweep")
+    out["static_cascades"] = cas
     ctx.close()
     return {"workload": "sweep-table", "metric": METRIC, **out}
+
+
+def oracle_free_block_width(x: np.ndarray, delta: bool) -> int:
+    """The widest 512-value block's residual width (DELTA: differences to the
+    predecessor within the block; FOR: distance to the block minimum), from numpy."""
+    nb = x.size // BLOCK
+    if nb == 0:
+        return 1
+    b = x[: nb * BLOCK].reshape(nb, BLOCK)
+    if delta:
+        r = np.diff(b, axis=1)  # sorted input: no wrap-around
+    else:
+        r = b - b.min(axis=1, keepdims=True)
+    return int(r.max()).bit_length()
+
+
+def render_sweep_table(t: dict) -> str:
+    """Markdown of a sweep-table line (--render-sweep-table FILE)."""
+    F = ["uncompr", "static_bp", "dyn_bp", "delta_bp", "for_bp"]
+    L = ["# Format sweep at 2^28 rows: every operator for every input/output format pair\n",
+         "Columns: X with per-512-block widths in {3, 8, 16, 27, 40} (values below 2^b), K sorted with gaps",
+         "Geometric(1/4); select X < c at three selectivities; project X and K at the positions of the 10%",
+         f"select ({t['positions']:,} positions, DELTA+BP); calc X' * K'; agg_sum; morph X between every pair",
+         "of formats; RLE on a column of long runs.  Milliseconds per call (CUDA events, mean of the timed",
+         "calls after 3 warm-ups, every kernel of the call included: mark, scan, emit and placement for",
+         "select).  One GB300.\n",
+         "Command (committed files only): `python bench.py --workload sweep-table --steps 5`, rendered by",
+         "`python bench.py --render-sweep-table <its JSON line>`.\n",
+         "Column sizes (bytes): " + ", ".join(f"X {k} {v / 1e6:.0f} MB" for k, v in t["x_bytes"].items()) + "; "
+         + ", ".join(f"K {k} {v / 1e6:.0f} MB" for k, v in t["k_bytes"].items()) + ".\n"]
+
+    def grid(title, key, fmt_key, rows=F, cols=F, head="in \\ out"):
+        L.append(title + "\n")
+        L.append(f"| {head} | " + " | ".join(cols) + " |")
+        L.append("|---|" + "---|" * len(cols))
+        for a in rows:
+            L.append(f"| {a} | " + " | ".join(f"{t[key][fmt_key(a, b)]['ms']:.3f}" for b in cols) + " |")
+        L.append("")
+
+    for sel in ("0.001", "0.1", "0.9"):
+        grid(f"## select X < c, selectivity {float(sel) * 100:g}% (rows: X format; columns: positions format)",
+             "select", lambda a, b, s=sel: f"{s}|{a}|{b}", head="X \\ out")
+        sp = t["select_packed"]
+        L.append("Specialized select on the packed codes (`ms_select_packed`, DELTA+BP positions): "
+                 + ", ".join(f"{a} {sp[f'{sel}|{a}|delta_bp']['ms']:.3f}" for a in F if f"{sel}|{a}|delta_bp" in sp)
+                 + " (general select with the same output: "
+                 + ", ".join(f"{a} {t['select'][f'{sel}|{a}|delta_bp']['ms']:.3f}" for a in F if a != "uncompr")
+                 + ").\n")
+    grid("## project (rows: data format; columns: output format), 10% positions", "project",
+         lambda a, b: f"{a}|{b}", head="data \\ out")
+    L.append("Positions column format (X uncompressed, uncompressed output): "
+             + ", ".join(f"{k.split('|')[0]} {v['ms']:.3f}" for k, v in t["project_positions"].items()) + ".\n")
+    grid("## calc X' * K' (rows: X' format; columns: output format)", "calc", lambda a, b: f"{a}|{b}",
+         head="X' \\ out")
+    L.append("## agg_sum of X\n")
+    L.append(" | ".join(f"{k} {v['ms']:.3f} ms ({v['rows_per_s'] / 1e9:.0f} G rows/s)"
+                        for k, v in t["agg_sum"].items()) + "\n")
+    if "morph" in t:
+        grid("## morph X (Sec. 3.2 direct morphing; rows: from; columns: to)", "morph", lambda a, b: f"{a}|{b}",
+             head="from \\ to")
+        grid("The same through uint64 (ms_decompress into a buffer, then ms_compress):", "morph_staged",
+             lambda a, b: f"{a}|{b}", head="from \\ to")
+        L.append("Algorithmic GB/s of the direct morphs (bytes in + bytes out): "
+                 + ", ".join(f"{k} {v['alg_GBps']:.0f}" for k, v in t["morph"].items()) + ".\n")
+    if "rle" in t:
+        r = t["rle"]
+        RF = list(r["bytes"])
+        L.append(f"## RLE on a column of long runs ({r['runs']:,} runs; run lengths uniform in [1, 7999], 6 values)\n")
+        L.append("| operation | " + " | ".join(RF) + " |")
+        L.append("|---|" + "---|" * len(RF))
+        L.append("| bytes | " + " | ".join(f"{r['bytes'][f] / 1e6:.1f} MB" for f in RF) + " |")
+        for op, what in (("compress", "compress from uint64"), ("decompress", "decompress to uint64"),
+                         ("morph_from_dyn_bp", "morph from dynamic BP"),
+                         ("select", f"select x < 1 ({100 * r['select_selectivity']:.1f}%), DELTA+BP positions"),
+                         ("agg_sum", "agg_sum"), ("project", "project at the 10% positions of X")):
+            L.append(f"| {what} | " + " | ".join(f"{r[op][f]['ms']:.3f}" for f in RF) + " |")
+        L.append("")
+    if "static_cascades" in t:
+        L.append("## FOR / DELTA cascaded with static BP against the dynamic cascades (ms)\n")
+        L.append("| column | format | bytes | compress | decompress | agg_sum | project at the 10% positions |")
+        L.append("|---|---|---|---|---|---|---|")
+        for col, e in t["static_cascades"].items():
+            names = list(e["bytes"])
+            for key, nm in (("dyn", names[0]), ("static", names[1])):
+                d = e[key]
+                label = nm + (f" (b = {e['static_bw']})" if key == "static" else "")
+                L.append(f"| {col} | {label} | {e['bytes'][nm] / 1e6:.0f} MB | {d['compress_ms']:.3f} | "
+                         f"{d['decompress_ms']:.3f} | {d['agg_sum_ms']:.3f} | {d['project_ms']:.3f} |")
+        L.append("")
+    return "\n".join(L)
 
 
 # ------------------------------------------------------------ one kernel
@@ -1398,6 +1562,10 @@ def bench_kernel(args):
 
 def main():
     args = parse()
+    if args.render_sweep_table:
+        with open(args.render_sweep_table) as f:
+            print(render_sweep_table(json.loads(f.read().strip().splitlines()[-1])))
+        return
     if args.workload == "kernel" and args.impl == "ours":
         print(json.dumps(bench_kernel(args)))
         return

@@ -48,6 +48,14 @@
  *                operator but ms_select_packed and the batched fragments (which
  *                return MS_ERR_FORMAT for it at once).  Other operators with
  *                out_fmt MS_RLE return MS_ERR_FORMAT at once: morph their output.
+ *   MS_FOR_STATIC_BP, MS_DELTA_STATIC_BP
+ *                FOR and DELTA cascaded with static BP (Sec. 2.1 cascades; static
+ *                BP's "one fixed bit width" for the residuals): the byte layout of
+ *                MS_FOR_BP / MS_DELTA_BP with every block packed at the caller's
+ *                static_bw (1..64), so block k's payload sits at word 8*b*k.  A
+ *                residual wider than static_bw raises MS_ERR_VALUE_TOO_WIDE
+ *                (device).  Every operator reads them as it reads MS_FOR_BP /
+ *                MS_DELTA_BP; ms_compress_noalloc does not write them.
  *   A column buffer starts on a 256-byte boundary.  The header is 16 bytes per
  *   block, so every block payload starts on a 64-byte boundary.
  *
@@ -95,7 +103,9 @@ typedef enum {
   MS_DYN_BP = 2,
   MS_DELTA_BP = 3,
   MS_FOR_BP = 4,
-  MS_RLE = 5
+  MS_RLE = 5,
+  MS_FOR_STATIC_BP = 6,
+  MS_DELTA_STATIC_BP = 7
 } ms_fmt;
 
 typedef enum {

@@ -153,6 +153,27 @@ __global__ void __launch_bounds__(kThreads) k_scan_counts(ScanArgs a) {
 
 // ----------------------------------------------------------------- aggregates
 
+// agg_sum of an RLE column on its runs (Sec. 3.2, an operator on the compressed
+// form): the sum of run value x (run length) over the runs, modulo 2^64 as the sum
+// of the values is.
+__global__ void __launch_bounds__(256) k_agg_sum_rle(const DevMeta* in, uint64_t* result, DevCtl* ctl) {
+  const ColView c = view_of(in);
+  if (!rle_sound(c)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_error(ctl, MS_ERR_FORMAT, c.size);
+    return;
+  }
+  const uint64_t R = c.nb;
+  const uint64_t* val = reinterpret_cast<const uint64_t*>(c.p);
+  const uint64_t* ends = val + R;
+  uint64_t s = 0;
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t start = r ? ldg64(ends + r - 1) : 0;
+    s += ldg64(val + r) * (ldg64(ends + r) - start);
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(reinterpret_cast<unsigned long long*>(result), (unsigned long long)s);
+}
+
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_agg_sum(const DevMeta* in, uint64_t* result,
                                                                           DevCtl* ctl) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -353,7 +374,14 @@ ms_status launch_scan(ms_ctx* c, const MarkArgs& a, const Work& w, uint64_t n_ma
   return cuda_status(cudaGetLastError());
 }
 
-ms_status launch_agg_sum(ms_ctx* c, const DevMeta* in, uint64_t* d_result, uint64_t n_max, cudaStream_t s) {
+ms_status launch_agg_sum(ms_ctx* c, const DevMeta* in, uint64_t* d_result, uint64_t n_max, cudaStream_t s,
+                         bool rle) {
+  if (rle) {  // runs at most n_max
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(cdiv(n_max, 256), 4ull * c->sms));
+    ProfScope ps(c, MS_K_AGG_SUM, s);
+    k_agg_sum_rle<<<grid, 256, 0, s>>>(in, d_result, c->ctl);
+    return cuda_status(cudaGetLastError());
+  }
   const int grid = tile_grid(c, k_agg_sum, n_max);
   ProfScope ps(c, MS_K_AGG_SUM, s);
   k_agg_sum<<<grid, kTileThreads, kTileSmemBytes, s>>>(in, d_result, c->ctl);

@@ -58,6 +58,11 @@ struct ColView {
   int fmt, bw;
 };
 
+// FOR / DELTA cascaded with static BP are stored in the FOR+BP / DELTA+BP layout
+// (every block at one width), so readers see them as those formats.
+MS_DEV int layout_fmt(int f) { return f == MS_FOR_STATIC_BP ? MS_FOR_BP : (f == MS_DELTA_STATIC_BP ? MS_DELTA_BP : f); }
+MS_DEV bool is_static_cascade(int f) { return f == MS_FOR_STATIC_BP || f == MS_DELTA_STATIC_BP; }
+
 MS_DEV ColView view_of(const DevMeta* m) {
   ColView c;
   c.p = reinterpret_cast<const uint8_t*>(m->ptr);
@@ -65,8 +70,8 @@ MS_DEV ColView view_of(const DevMeta* m) {
   c.nb = m->nb;
   c.pwords = m->pwords;
   c.size = m->size;
-  c.fmt = (int)m->fmt;
-  c.bw = (int)m->bw;
+  c.fmt = layout_fmt((int)m->fmt);
+  c.bw = is_static_cascade((int)m->fmt) ? 0 : (int)m->bw;
   return c;
 }
 
@@ -82,7 +87,9 @@ MS_DEV ColView view_raw(const uint64_t* p, uint64_t n) {
   return c;
 }
 
-MS_DEV bool is_block_fmt(int f) { return f == MS_DYN_BP || f == MS_DELTA_BP || f == MS_FOR_BP; }
+MS_DEV bool is_block_fmt(int f) {
+  return f == MS_DYN_BP || f == MS_DELTA_BP || f == MS_FOR_BP || f == MS_FOR_STATIC_BP || f == MS_DELTA_STATIC_BP;
+}
 
 MS_DEV int bw64(uint64_t x) { return x ? 64 - __clzll((long long)x) : 0; }
 MS_DEV uint64_t lowmask(int b) { return b >= 64 ? ~0ull : ((1ull << b) - 1ull); }
@@ -334,11 +341,14 @@ MS_DEV uint64_t rle_run_of(const uint64_t* ends, uint64_t R, uint64_t i, uint64_
 }
 
 // Values of block g of an RLE column into lane registers (value 16*lane + k of the
-// block in v[k], zero past `valid`): the directory gives the block's first run,
-// each lane finds the run of its first value from there and walks its 16 values
-// forward through the runs.
+// block in v[k], zero past `valid`).  The directory entries of blocks g and g+1
+// bound the runs that cover the block.  When there are at most 32 of them (runs
+// longer than 16 values on average), lane i loads run r0 + i and every lane takes
+// the run of each of its values from the warp's registers: the run of value t is
+// r0 + the number of these runs that end at or before t.  Otherwise each lane finds
+// the run of its first value by a search from r0 and walks forward.
 MS_DEV void rle_expand(const ColView& c, uint64_t g, int lane, int valid, uint64_t v[16], DevCtl* ctl) {
-  const uint64_t R = c.nb;
+  const uint64_t R = c.nb, nch = (c.n + kBlock - 1) / kBlock;
   const uint64_t* val = reinterpret_cast<const uint64_t*>(c.p);
   const uint64_t* ends = val + R;
   const uint64_t* dir = ends + R;
@@ -348,8 +358,35 @@ MS_DEV void rle_expand(const ColView& c, uint64_t g, int lane, int valid, uint64
     for (int k = 0; k < 16; k++) v[k] = 0;
     return;
   }
+  uint64_t d = 0;
+  if (lane < 2) d = g + lane < nch ? ldg64(dir + g + lane) : R - 1;
+  uint64_t r0 = __shfl_sync(kFull, d, 0);
+  const uint64_t r1 = __shfl_sync(kFull, d, 1);
+  if (r0 >= R) r0 = 0;
   const uint64_t row0 = g * kBlock + 16 * (uint64_t)lane;
-  uint64_t r = rle_run_of(ends, R, row0, ldg64(dir + g));
+  if (r1 < R && r1 >= r0 && r1 - r0 < 32) {
+    const int m = (int)(r1 - r0) + 1;
+    uint64_t e = 0, x = 0;
+    if (lane < m) {
+      e = ldg64(ends + r0 + lane);
+      x = ldg64(val + r0 + lane);
+    }
+    int j[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) j[k] = 0;
+    for (int i = 0; i < m; i++) {
+      const uint64_t ei = __shfl_sync(kFull, e, i);
+#pragma unroll
+      for (int k = 0; k < 16; k++) j[k] += ei <= row0 + k;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const uint64_t xk = __shfl_sync(kFull, x, min(j[k], m - 1));
+      v[k] = 16 * lane + k < valid ? xk : 0;
+    }
+    return;
+  }
+  uint64_t r = rle_run_of(ends, R, row0, r0);
   uint64_t e = ldg64(ends + r), x = ldg64(val + r);
 #pragma unroll
   for (int k = 0; k < 16; k++) {

@@ -35,8 +35,8 @@ void dev_free(ms_ctx* c, void* p) {
 }
 
 bool valid_format(int fmt, int bw) {
-  if (fmt < MS_UNCOMPR || fmt > MS_RLE) return false;
-  if (fmt == MS_STATIC_BP && (bw < 1 || bw > 64)) return false;
+  if (fmt < MS_UNCOMPR || fmt > MS_DELTA_STATIC_BP) return false;
+  if (has_static_bw(fmt) && (bw < 1 || bw > 64)) return false;
   return true;
 }
 
@@ -58,7 +58,7 @@ ms_column* new_arena_column(ms_ctx* c, int fmt, int bw, uint64_t n_max) {
   col->ctx = c;
   col->slot = slot;
   col->fmt = fmt;
-  col->bw = fmt == MS_STATIC_BP ? bw : 0;
+  col->bw = has_static_bw(fmt) ? bw : 0;
   col->n_max = n_max;
   col->arena = true;
   col->freed = false;
@@ -258,7 +258,7 @@ ms_status ms_column_import(ms_ctx* c, int fmt, int bw, uint64_t n, const void* s
   if (!c || !out || (!src && size)) return MS_ERR_INVALID_ARG;
   *out = nullptr;
   if (!valid_format(fmt, bw)) return MS_ERR_INVALID_ARG;
-  const bool blockfmt = fmt >= MS_DYN_BP && fmt <= MS_FOR_BP;
+  const bool blockfmt = host_block_fmt(fmt);
   uint64_t nb = blockfmt ? n / kBlock : 0;
   if (fmt == MS_UNCOMPR && size < 8 * n) return MS_ERR_FORMAT;
   if (fmt == MS_STATIC_BP && size < 8 * cdiv(n * (uint64_t)bw, 64)) return MS_ERR_FORMAT;
@@ -284,7 +284,7 @@ ms_status ms_column_import(ms_ctx* c, int fmt, int bw, uint64_t n, const void* s
   m.size = size;
   m.nb = nb;
   m.fmt = static_cast<uint32_t>(fmt);
-  m.bw = fmt == MS_STATIC_BP ? static_cast<uint32_t>(bw) : 0;
+  m.bw = has_static_bw(fmt) ? static_cast<uint32_t>(bw) : 0;
   m.pwords = 0;  // block formats: set by the validation kernel from the last header
   if (e == cudaSuccess) {
     ProfScope ps(c, MS_K_ARENA, s);
@@ -312,7 +312,7 @@ ms_status ms_column_import(ms_ctx* c, int fmt, int bw, uint64_t n, const void* s
   col->ctx = c;
   col->slot = slot;
   col->fmt = fmt;
-  col->bw = fmt == MS_STATIC_BP ? bw : 0;
+  col->bw = has_static_bw(fmt) ? bw : 0;
   col->n_max = n;
   col->arena = false;
   col->freed = false;

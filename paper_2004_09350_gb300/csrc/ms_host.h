@@ -55,6 +55,16 @@ void* dev_alloc(ms_ctx* c, size_t bytes);
 void dev_free(ms_ctx* c, void* p);
 ms_status cuda_status(cudaError_t e);
 bool valid_format(int fmt, int bw);
+// Block-format outputs (headers + payloads; placed after staging), and the layout a
+// format is read as (FOR / DELTA cascaded with static BP use the FOR+BP / DELTA+BP layout).
+inline bool host_block_fmt(int f) {
+  return f == MS_DYN_BP || f == MS_DELTA_BP || f == MS_FOR_BP || f == MS_FOR_STATIC_BP || f == MS_DELTA_STATIC_BP;
+}
+inline int host_layout_fmt(int f) {
+  return f == MS_FOR_STATIC_BP ? MS_FOR_BP : (f == MS_DELTA_STATIC_BP ? MS_DELTA_BP : f);
+}
+// formats with a caller-chosen width (static_bw in 1..64)
+inline bool has_static_bw(int f) { return f == MS_STATIC_BP || f == MS_FOR_STATIC_BP || f == MS_DELTA_STATIC_BP; }
 int take_slot(ms_ctx* c);
 ms_column* new_arena_column(ms_ctx* c, int fmt, int bw, uint64_t n_max);
 void drop_new_column(ms_ctx* c, ms_column* col);

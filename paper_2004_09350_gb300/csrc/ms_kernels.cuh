@@ -1559,7 +1559,16 @@ MS_DEV void store_staged(const ProduceArgs& a, int fmt, int bw, bool blockfmt, u
       uint8_t* arena = reinterpret_cast<uint8_t*>(ctl->arena);
       if (valid == kBlock) {
         uint64_t ref;
-        const int b = encode_block(fmt, v, lane, &ref);
+        int b = encode_block(layout_fmt(fmt), v, lane, &ref);
+        if (is_static_cascade(fmt)) {  // every block at the column's width
+          if (b > bw) {
+            if (lane == 0) set_error(ctl, MS_ERR_VALUE_TOO_WIDE, g);
+            const uint64_t mask = lowmask(bw);
+#pragma unroll
+            for (int k = 0; k < 16; k++) v[k] &= mask;
+          }
+          b = bw;
+        }
         write_lane_stream(out_stage, lane, b, v);
         __syncwarp();
         uint64_t at = 0;
@@ -1683,7 +1692,7 @@ MS_DEV void publish_staged(const ProduceArgs& a, uint64_t n_out, int fmt, int bw
       m->n = n_out;
       m->ptr = reinterpret_cast<uint64_t>(base);
       m->fmt = (uint32_t)fmt;
-      m->bw = (uint32_t)(fmt == MS_STATIC_BP ? bw : 0);
+      m->bw = (uint32_t)((fmt == MS_STATIC_BP || is_static_cascade(fmt)) ? bw : 0);
       m->nb = blockfmt ? n_out / kBlock : 0;
       if (!blockfmt) {
         const uint64_t size = fmt == MS_UNCOMPR ? 8 * n_out : 8 * ((n_out * (uint64_t)bw + 63) / 64);

@@ -41,7 +41,9 @@ ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max
 ms_status launch_scan(ms_ctx* c, const MarkArgs& a, const Work& w, uint64_t n_max, cudaStream_t s);
 // the specialized select on packed block formats (ms_select_packed.cu): mark + scan
 ms_status launch_select_packed(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max, cudaStream_t s);
-ms_status launch_agg_sum(ms_ctx* c, const DevMeta* in, uint64_t* d_result, uint64_t n_max, cudaStream_t s);
+// rle: the column is RLE (summed on its runs)
+ms_status launch_agg_sum(ms_ctx* c, const DevMeta* in, uint64_t* d_result, uint64_t n_max, cudaStream_t s,
+                         bool rle = false);
 ms_status launch_group_sum(ms_ctx* c, const DevMeta* gid, const DevMeta* val, uint64_t G, uint64_t* d_sums,
                            uint64_t n_max, cudaStream_t s);
 ms_status launch_build_keys(ms_ctx* c, const DevMeta* keys, uint64_t domain, uint32_t* bits, uint64_t n_max,

@@ -97,10 +97,10 @@ ms_status produce_column(ms_ctx* c, ProduceArgs& a, const Work& w, uint64_t n_ma
   a.ctl = c->ctl;
   a.out_meta = c->metas + col->slot;
   a.fmt = fmt;
-  a.bw = fmt == MS_STATIC_BP ? bw : 0;
+  a.bw = has_static_bw(fmt) ? bw : 0;
   a.stage_meta = w.stage_meta;
   ms_status st = launch_map<OP>(c, a, n_max, s);
-  if (st == MS_OK && fmt >= MS_DYN_BP && fmt <= MS_FOR_BP) st = launch_place(c, w, a.out_meta, n_max, s);
+  if (st == MS_OK && host_block_fmt(fmt)) st = launch_place(c, w, a.out_meta, n_max, s);
   if (st != MS_OK) {
     // a producer that ran without its placement leaves stage bytes taken
     cudaMemsetAsync(&c->ctl->stage, 0, 8, s);
@@ -236,7 +236,8 @@ ms_status ms_project(ms_ctx* c, const ms_column* data, const ms_column* pos, int
   // read in place by the per-warp gather, which keeps more warps per SM.  RLE data is
   // read by the per-warp gather too (directory, then a short search per position).
   // Both paths give the same values for any positions.
-  if (data->fmt == MS_DELTA_BP || data->fmt == MS_UNCOMPR || data->fmt == MS_RLE || pos->fmt != MS_DELTA_BP)
+  const int dl = host_layout_fmt(data->fmt), pl = host_layout_fmt(pos->fmt);
+  if (dl == MS_DELTA_BP || dl == MS_UNCOMPR || dl == MS_RLE || pl != MS_DELTA_BP)
     return produce_column<OP_PROJECT_WARP>(c, a, w, pos->n_max, fmt, bw, out, s);
   return produce_column<OP_PROJECT>(c, a, w, pos->n_max, fmt, bw, out, s);
 }
@@ -267,7 +268,7 @@ ms_status ms_agg_sum(ms_ctx* c, const ms_column* in, uint64_t* d_result, void* s
   if (!c || !owned(c, in) || !d_result) return MS_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cuda_status(cudaMemsetAsync(d_result, 0, 8, s)) != MS_OK) return MS_ERR_CUDA;
-  return launch_agg_sum(c, c->metas + in->slot, d_result, in->n_max, s);
+  return launch_agg_sum(c, c->metas + in->slot, d_result, in->n_max, s, in->fmt == MS_RLE);
 }
 
 ms_status ms_group_sum(ms_ctx* c, const ms_column* gid, const ms_column* val, uint64_t G, uint64_t* d_sums,

@@ -20,8 +20,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "libms.so")
 _HEADER = os.path.join(os.path.dirname(_PKG), "include", "morphstore.h")
 
-UNCOMPR, STATIC_BP, DYN_BP, DELTA_BP, FOR_BP, RLE = range(6)
-FORMAT_NAMES = ("uncompr", "static_bp", "dyn_bp", "delta_bp", "for_bp", "rle")
+UNCOMPR, STATIC_BP, DYN_BP, DELTA_BP, FOR_BP, RLE, FOR_STATIC_BP, DELTA_STATIC_BP = range(8)
+FORMAT_NAMES = ("uncompr", "static_bp", "dyn_bp", "delta_bp", "for_bp", "rle", "for_static_bp", "delta_static_bp")
 EQ, NE, LT, LE, GT, GE, BETWEEN = range(7)
 ADD, SUB, MUL = range(3)
 STATUS = ("MS_OK", "MS_ERR_INVALID_ARG", "MS_ERR_FORMAT", "MS_ERR_VALUE_TOO_WIDE",

@@ -1,4 +1,5 @@
-"""GPU parity of the RLE format (Sec. 2.1 RLE) through the C ABI, against the oracle.
+"""GPU parity of the RLE format and of FOR / DELTA cascaded with static BP (Sec. 2.1)
+through the C ABI, against the oracle.
 
 Encoding (ms_compress, ms_morph from every format) must give exactly the oracle's
 bytes: run values, exclusive run ends and the per-block run directory.  Decoding
@@ -183,3 +184,85 @@ def test_full_size_rle_sampled():
         pc = _col(c, pos, ms.DELTA_BP)
         out = c.project(col, pc, fmt=ms.UNCOMPR)
         np.testing.assert_array_equal(_values(c, out), x[pos.astype(np.int64)])
+
+
+# ----------------------------------------------- FOR / DELTA cascaded with static BP
+
+CASCADES = [ms.FOR_STATIC_BP, ms.DELTA_STATIC_BP]
+
+
+def _cascade_data(fmt, n, seed):
+    return synth.sorted_gaps(seed, n) if fmt == ms.DELTA_STATIC_BP else synth.table1_column("C3", n, seed)
+
+
+def _cascade_width(fmt, x):
+    base = oracle.DELTA_BP if fmt == ms.DELTA_STATIC_BP else oracle.FOR_BP
+    return int(oracle.block_widths(base, x).max()) if x.size >= 512 else 1
+
+
+@pytest.mark.parametrize("fmt", CASCADES)
+@pytest.mark.parametrize("n", [0, 1, 511, 512, 513, 5 * 4096 + 300, 3 * 65536 + 777])
+@pytest.mark.parametrize("extra", [0, 5])
+def test_compress_static_cascade_matches_oracle_bytes(ctx, fmt, n, extra):
+    x = _cascade_data(fmt, n, 81 + n)
+    bw = _cascade_width(fmt, x) + extra
+    col = ctx.compress(ms.as_device_u64(x, ctx.device), fmt, bw)
+    ctx.check(what="compress static cascade")
+    assert ctx.export_bytes(col).tobytes() == oracle.compress(fmt, x, bw=bw).tobytes()
+    info = ctx.info(col)
+    assert info["fmt"] == fmt and info["static_bw"] == bw
+    np.testing.assert_array_equal(_values(ctx, col), x)
+    ctx.free(col)
+
+
+@pytest.mark.parametrize("fmt", CASCADES)
+def test_static_cascade_too_wide(ctx, fmt):
+    x = _cascade_data(fmt, 3000, 83)
+    col = ctx.compress(ms.as_device_u64(x, ctx.device), fmt, _cascade_width(fmt, x) - 1)
+    assert ctx.get_error() == ms.MS_ERR_VALUE_TOO_WIDE
+    ctx.free(col)
+
+
+@pytest.mark.parametrize("fmt", CASCADES)
+@pytest.mark.parametrize("other", FMTS + [ms.RLE])
+def test_morph_static_cascade_pairs(ctx, fmt, other):
+    n = 5 * 4096 + 300
+    x = _cascade_data(fmt, n, 84)
+    bw = _cascade_width(fmt, x) + 2
+    bwx = _bw(x)
+    src = _col(ctx, x, other)
+    c = ctx.morph(src, fmt, bw)
+    ctx.check(what="morph to cascade")
+    assert ctx.export_bytes(c).tobytes() == oracle.compress(fmt, x, bw=bw).tobytes()
+    back = ctx.morph(c, other, bwx if other == ms.STATIC_BP else 0)
+    ctx.check(what="morph from cascade")
+    assert ctx.export_bytes(back).tobytes() == oracle.compress(other, x, bwx if other == ms.STATIC_BP else 0).tobytes()
+    ctx.free(back)
+    ctx.free(c)
+    ctx.free(src)
+
+
+@pytest.mark.parametrize("fmt", CASCADES)
+def test_operators_read_static_cascades(ctx, fmt):
+    """select (general and on the packed codes), agg_sum, project (as data and as the
+    position list) and calc on the cascades, against the oracle."""
+    n = 3 * 65536 + 777
+    x = _cascade_data(fmt, n, 85)
+    bw = _cascade_width(fmt, x) + 1
+    col = ctx.compress(ms.as_device_u64(x, ctx.device), fmt, bw)
+    c = synth.value_at_rank(x, 0.3)
+    for sel in (ctx.select, ctx.select_packed):
+        out = sel(col, ms.LT, c, fmt=ms.DELTA_BP)
+        np.testing.assert_array_equal(_values(ctx, out), oracle.select(x, oracle.LT, c))
+        ctx.free(out)
+    assert int(ctx.agg_sum(col).item()) & ((1 << 64) - 1) == oracle.agg_sum(x)
+    pos = np.sort(synth.uniform(86, 30_000, 0, n))
+    pc = ctx.compress(ms.as_device_u64(pos, ctx.device), ms.DELTA_STATIC_BP, _cascade_width(ms.DELTA_STATIC_BP, pos))
+    out = ctx.project(col, pc, fmt=fmt, bw=_bw(x))
+    np.testing.assert_array_equal(_values(ctx, out), oracle.project(x, pos))
+    ctx.free(out)
+    out = ctx.calc(ms.ADD, col, None, 7, fmt=fmt, bw=bw)
+    np.testing.assert_array_equal(_values(ctx, out), oracle.calc(oracle.ADD, x, None, 7))
+    ctx.free(out)
+    ctx.free(pc)
+    ctx.free(col)
