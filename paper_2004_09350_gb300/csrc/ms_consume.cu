@@ -10,7 +10,7 @@ namespace ms {
 // and the chunk's match count.
 
 
-template <int BUF>
+template <int BUF, bool kRle>
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark_t(MarkArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31;
@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark_t(MarkArg
   const ColView c = view_of(a.in);
   const uint64_t lo = a.lo, span = a.span;
   const uint32_t negate = a.negate ? 0xffffu : 0u, live = a.empty ? 0u : 0xffffu;
-  cta_stream<BUF>(c, sm, a.ctl, [&](uint64_t g, const uint64_t* v, int valid, bool narrow) {
+  cta_stream<BUF, kRle>(c, sm, a.ctl, [&](uint64_t g, const uint64_t* v, int valid, bool narrow) {
     uint32_t m16 = 0;
     if (a.keybits) {  // semi-join probe against a key bitmap read through the caches
 #pragma unroll
@@ -52,9 +52,11 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark_t(MarkArg
 // k_mark: the tile stream's usual 2 x 32 KB buffers.  k_mark_l1: 2 x 8 KB buffers
 // and a small shared-memory carve-out, so that most of the SM's unified L1 caches
 // the key bitmap of a semi-join probe.
-constexpr auto k_mark = k_mark_t<kTileBuf>;
+template <bool kRle>
+constexpr auto k_mark = k_mark_t<kTileBuf, kRle>;
 constexpr int kMarkL1Buf = 8192;
-constexpr auto k_mark_l1 = k_mark_t<kMarkL1Buf>;
+template <bool kRle>
+constexpr auto k_mark_l1 = k_mark_t<kMarkL1Buf, kRle>;
 
 // Semi-join probe with the key bitmap in shared memory, for key domains whose
 // bitmap fits one CTA (up to about 1.5 million keys: 2e5 takes 25 KB).  Probing a
@@ -65,6 +67,7 @@ constexpr auto k_mark_l1 = k_mark_t<kMarkL1Buf>;
 constexpr int kKeyTileBuf = 16384;
 constexpr size_t kKeyTileSmemBytes = sizeof(TileSmem<kKeyTileBuf>);
 
+template <bool kRle>
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark_keys(MarkArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31;
@@ -74,7 +77,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark_keys(Mark
   for (uint64_t i = threadIdx.x; i < nw; i += blockDim.x) kb[i] = __ldg(a.keybits + i);
   __syncthreads();
   const ColView c = view_of(a.in);
-  cta_stream<kKeyTileBuf>(c, sm, a.ctl, [&](uint64_t g, const uint64_t* v, int valid, bool) {
+  cta_stream<kKeyTileBuf, kRle>(c, sm, a.ctl, [&](uint64_t g, const uint64_t* v, int valid, bool) {
     uint32_t m16 = 0;
 #pragma unroll
     for (int k = 0; k < 16; k++) {
@@ -238,13 +241,14 @@ ms_status launch_selftest_wait(ms_ctx* c, cudaStream_t s) {
 }
 
 // Semi-join build side: set bit key for every key of the build column.
+template <bool kRle>
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_build_keys(const DevMeta* keys, uint64_t domain,
                                                                              uint32_t* bits, DevCtl* ctl) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31;
   auto* sm = reinterpret_cast<TileSmem<kTileBuf>*>(smem_raw);
   const ColView c = view_of(keys);
-  cta_stream<kTileBuf>(c, sm, ctl, [&](uint64_t, const uint64_t* v, int valid, bool) {
+  cta_stream<kTileBuf, kRle>(c, sm, ctl, [&](uint64_t, const uint64_t* v, int valid, bool) {
 #pragma unroll
     for (int k = 0; k < 16; k++) {
       if (16 * lane + k < valid) {
@@ -259,6 +263,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_build_keys(con
 // Column statistics for the format selector (see ms_column_stats): one decoding
 // pass, per chunk reductions, block-level accumulation in shared memory, one
 // global atomic per statistic per CTA.
+template <bool kRle>
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_stats(const DevMeta* in, uint64_t* stats,
                                                                         DevCtl* ctl) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -268,7 +273,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_stats(const De
   __syncthreads();
   auto* sm = reinterpret_cast<TileSmem<kTileBuf>*>(smem_raw);
   const ColView c = view_of(in);
-  cta_stream<kTileBuf>(c, sm, ctl, [&](uint64_t, const uint64_t* v, int valid, bool) {
+  cta_stream<kTileBuf, kRle>(c, sm, ctl, [&](uint64_t, const uint64_t* v, int valid, bool) {
     uint64_t mx = 0, mn = ~0ull, dmax = 0;
     uint32_t sorted = 0, runs = 0;
     const uint64_t prev_last = __shfl_up_sync(kFull, v[15], 1);
@@ -321,10 +326,11 @@ int tile_grid(ms_ctx* c, K kernel, uint64_t n_max) {
   return grid_for(c, kernel, kTileSmemBytes, cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kClaim), kTileThreads);
 }
 
-ms_status launch_stats(ms_ctx* c, const DevMeta* in, uint64_t* d_stats, uint64_t n_max, cudaStream_t s) {
-  const int grid = tile_grid(c, k_stats, n_max);
+ms_status launch_stats(ms_ctx* c, const DevMeta* in, uint64_t* d_stats, uint64_t n_max, cudaStream_t s, bool rle) {
+  auto kernel = rle ? k_stats<true> : k_stats<false>;
+  const int grid = tile_grid(c, kernel, n_max);
   ProfScope ps(c, MS_K_STATS, s);
-  k_stats<<<grid, kTileThreads, kTileSmemBytes, s>>>(in, d_stats, c->ctl);
+  kernel<<<grid, kTileThreads, kTileSmemBytes, s>>>(in, d_stats, c->ctl);
   return cuda_status(cudaGetLastError());
 }
 
@@ -336,24 +342,27 @@ ms_status launch_mark_scan(ms_ctx* c, MarkArgs& a, const Work& w, uint64_t n_max
   a.counts = w.counts;
   const uint64_t key_bytes = a.keybits ? 4 * cdiv(a.domain, 32) : 0;
   if (a.keybits && key_bytes <= kKeySmemBudget) {  // key bitmap in shared memory
+    auto kernel = a.rle ? k_mark_keys<true> : k_mark_keys<false>;
     const size_t smem = kKeyTileSmemBytes + key_bytes;
-    const int grid = grid_for(c, k_mark_keys, smem, cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kClaim),
+    const int grid = grid_for(c, kernel, smem, cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kClaim),
                               kTileThreads);
     ProfScope ps(c, MS_K_MARK, s);
-    k_mark_keys<<<grid, kTileThreads, smem, s>>>(a);
+    kernel<<<grid, kTileThreads, smem, s>>>(a);
     if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
   } else if (a.keybits) {  // a larger key bitmap: probed through L1 and L2 (k_mark_l1)
+    auto kernel = a.rle ? k_mark_l1<true> : k_mark_l1<false>;
     const size_t smem = sizeof(TileSmem<kMarkL1Buf>);
-    cudaFuncSetAttribute(k_mark_l1, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
-    const int grid = grid_for(c, k_mark_l1, smem,
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
+    const int grid = grid_for(c, kernel, smem,
                               cdiv(cdiv(std::max<uint64_t>(n_max, 1), kBlock), kClaim), kTileThreads);
     ProfScope ps(c, MS_K_MARK, s);
-    k_mark_l1<<<grid, kTileThreads, smem, s>>>(a);
+    kernel<<<grid, kTileThreads, smem, s>>>(a);
     if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
   } else {  // select
-    const int grid = tile_grid(c, k_mark, n_max);
+    auto kernel = a.rle ? k_mark<true> : k_mark<false>;
+    const int grid = tile_grid(c, kernel, n_max);
     ProfScope ps(c, MS_K_MARK, s);
-    k_mark<<<grid, kTileThreads, kTileSmemBytes, s>>>(a);
+    kernel<<<grid, kTileThreads, kTileSmemBytes, s>>>(a);
     if (cuda_status(cudaGetLastError()) != MS_OK) return MS_ERR_CUDA;
   }
   return launch_scan(c, a, w, n_max, s);
@@ -400,10 +409,11 @@ ms_status launch_group_sum(ms_ctx* c, const DevMeta* gid, const DevMeta* val, ui
 }
 
 ms_status launch_build_keys(ms_ctx* c, const DevMeta* keys, uint64_t domain, uint32_t* bits, uint64_t n_max,
-                            cudaStream_t s) {
-  const int grid = tile_grid(c, k_build_keys, n_max);
+                            cudaStream_t s, bool rle) {
+  auto kernel = rle ? k_build_keys<true> : k_build_keys<false>;
+  const int grid = tile_grid(c, kernel, n_max);
   ProfScope ps(c, MS_K_BUILD_KEYS, s);
-  k_build_keys<<<grid, kTileThreads, kTileSmemBytes, s>>>(keys, domain, bits, c->ctl);
+  kernel<<<grid, kTileThreads, kTileSmemBytes, s>>>(keys, domain, bits, c->ctl);
   return cuda_status(cudaGetLastError());
 }
 

@@ -340,26 +340,52 @@ MS_DEV uint64_t rle_run_of(const uint64_t* ends, uint64_t R, uint64_t i, uint64_
   return lo;
 }
 
-// Values of block g of an RLE column into lane registers (value 16*lane + k of the
-// block in v[k], zero past `valid`).  The directory entries of blocks g and g+1
-// bound the runs that cover the block.  When there are at most 32 of them (runs
-// longer than 16 values on average), lane i loads run r0 + i and every lane takes
-// the run of each of its values from the warp's registers: the run of value t is
-// r0 + the number of these runs that end at or before t.  Otherwise each lane finds
-// the run of its first value by a search from r0 and walks forward.
-MS_DEV void rle_expand(const ColView& c, uint64_t g, int lane, int valid, uint64_t v[16], DevCtl* ctl) {
+// The directory entries that bound block g's runs, on lanes 0 and 1: the run that
+// holds the block's first value and the one that holds the next block's first value
+// (the last run past the last block).  Other lanes get 0.
+MS_DEV uint64_t rle_dir_load(const ColView& c, uint64_t g, int lane) {
   const uint64_t R = c.nb, nch = (c.n + kBlock - 1) / kBlock;
+  if (lane >= 2 || !rle_sound(c) || R == 0 || g >= nch) return 0;
+  const uint64_t* dir = reinterpret_cast<const uint64_t*>(c.p) + 2 * R;
+  return g + lane < nch ? ldg64(dir + g + lane) : R - 1;
+}
+
+// Values of the block from its m <= 32 runs r0 .. r0+m-1 held one per lane (lane i:
+// end e and value x of run r0 + i): the run of value t is r0 + the number of these
+// runs that end at or before t.
+MS_DEV void rle_values_from_runs(uint64_t row0, int lane, int valid, int m, uint64_t e, uint64_t x, uint64_t v[16]) {
+  int j[16];
+#pragma unroll
+  for (int k = 0; k < 16; k++) j[k] = 0;
+  for (int i = 0; i < m; i++) {
+    const uint64_t ei = __shfl_sync(kFull, e, i);
+#pragma unroll
+    for (int k = 0; k < 16; k++) j[k] += ei <= row0 + k;
+  }
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    const uint64_t xk = __shfl_sync(kFull, x, min(j[k], m - 1));
+    v[k] = 16 * lane + k < valid ? xk : 0;
+  }
+}
+
+// Values of block g of an RLE column into lane registers (value 16*lane + k of the
+// block in v[k], zero past `valid`); d is this lane's rle_dir_load(c, g, lane).  When
+// at most 32 runs cover the block (runs longer than 16 values on average), lane i
+// loads run r0 + i and every value takes its run from the warp's registers.
+// Otherwise each lane finds the run of its first value by a search from r0 and walks
+// forward.
+MS_DEV void rle_expand_at(const ColView& c, uint64_t g, int lane, int valid, uint64_t d, uint64_t v[16],
+                          DevCtl* ctl) {
+  const uint64_t R = c.nb;
   const uint64_t* val = reinterpret_cast<const uint64_t*>(c.p);
   const uint64_t* ends = val + R;
-  const uint64_t* dir = ends + R;
   if (!rle_sound(c) || valid <= 0) {
     if (lane == 0 && valid > 0) set_error(ctl, MS_ERR_FORMAT, g);
 #pragma unroll
     for (int k = 0; k < 16; k++) v[k] = 0;
     return;
   }
-  uint64_t d = 0;
-  if (lane < 2) d = g + lane < nch ? ldg64(dir + g + lane) : R - 1;
   uint64_t r0 = __shfl_sync(kFull, d, 0);
   const uint64_t r1 = __shfl_sync(kFull, d, 1);
   if (r0 >= R) r0 = 0;
@@ -371,19 +397,7 @@ MS_DEV void rle_expand(const ColView& c, uint64_t g, int lane, int valid, uint64
       e = ldg64(ends + r0 + lane);
       x = ldg64(val + r0 + lane);
     }
-    int j[16];
-#pragma unroll
-    for (int k = 0; k < 16; k++) j[k] = 0;
-    for (int i = 0; i < m; i++) {
-      const uint64_t ei = __shfl_sync(kFull, e, i);
-#pragma unroll
-      for (int k = 0; k < 16; k++) j[k] += ei <= row0 + k;
-    }
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-      const uint64_t xk = __shfl_sync(kFull, x, min(j[k], m - 1));
-      v[k] = 16 * lane + k < valid ? xk : 0;
-    }
+    rle_values_from_runs(row0, lane, valid, m, e, x, v);
     return;
   }
   uint64_t r = rle_run_of(ends, R, row0, r0);
@@ -401,6 +415,10 @@ MS_DEV void rle_expand(const ColView& c, uint64_t g, int lane, int valid, uint64
       v[k] = 0;
     }
   }
+}
+
+MS_DEV void rle_expand(const ColView& c, uint64_t g, int lane, int valid, uint64_t v[16], DevCtl* ctl) {
+  rle_expand_at(c, g, lane, valid, rle_dir_load(c, g, lane), v, ctl);
 }
 
 // Value i (< n) of an RLE column; 0 for a column whose size cannot hold its runs.
@@ -603,7 +621,64 @@ struct StreamSmem {
 // Staging of one chunk g of column c (used by the streams below): the block header
 // (16 bytes, one lane) and the chunk's packed payload (16-byte cp.async units,
 // swizzled for uncompressed chunks so that blocked reads are conflict-free).
+MS_DEV void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// RLE: the "header" of block g is its two directory entries (rle_dir_load); the
+// "payload" is the block's runs when at most 32 cover it: ends in slot words 0..31,
+// values in words 32..63.
+static __device__ __noinline__ void stage_rle_header(const ColView c, uint64_t g, uint64_t* hdr, int lane) {
+  const uint64_t R = c.nb, nch = (c.n + kBlock - 1) / kBlock;
+  if (lane >= 2 || !rle_sound(c) || R == 0 || g >= nch) return;
+  const uint64_t* dir = reinterpret_cast<const uint64_t*>(c.p) + 2 * R;
+  if (g + lane < nch) cp_async8(hdr + lane, dir + g + lane);
+  else hdr[lane] = R - 1;
+}
+MS_DEV bool rle_window(const ColView& c, const uint64_t* hdr, uint64_t* r0, int* m) {
+  const uint64_t R = c.nb, a = hdr[0], b = hdr[1];
+  if (!rle_sound(c) || a >= R || b >= R || b < a || b - a >= 32) return false;
+  *r0 = a;
+  *m = (int)(b - a) + 1;
+  return true;
+}
+static __device__ __noinline__ void stage_rle_payload(const ColView c, uint64_t g, const uint64_t* hdr, uint16_t* slot,
+                                                      int lane) {
+  uint64_t r0;
+  int m;
+  if (g >= (c.n + kBlock - 1) / kBlock || !rle_window(c, hdr, &r0, &m) || lane >= m) return;
+  const uint64_t* val = reinterpret_cast<const uint64_t*>(c.p);
+  uint64_t* w = reinterpret_cast<uint64_t*>(slot);
+  cp_async8(w + lane, val + c.nb + r0 + lane);
+  cp_async8(w + 32 + lane, val + r0 + lane);
+}
+
+// Block g of an RLE column from its staged runs (at most 32 cover it), else read in
+// place; returned by value so that the caller's registers stay its own.
+struct Values16 {
+  uint64_t v[16];
+};
+static __device__ __noinline__ Values16 rle_decode_staged(const ColView c, uint64_t g, const uint64_t* hdr,
+                                                  const uint16_t* slot, int lane, int valid, DevCtl* ctl) {
+  Values16 r;
+  uint64_t r0;
+  int m;
+  if (rle_window(c, hdr, &r0, &m)) {
+    const uint64_t* w = reinterpret_cast<const uint64_t*>(slot);
+    rle_values_from_runs(g * kBlock + 16 * (uint64_t)lane, lane, valid, m, lane < m ? w[lane] : 0,
+                         lane < m ? w[32 + lane] : 0, r.v);
+  } else {
+    rle_expand(c, g, lane, valid, r.v, ctl);
+  }
+  return r;
+}
+
 MS_DEV void stage_header(const ColView& c, uint64_t g, uint64_t* hdr, int lane) {
+  if (c.fmt == MS_RLE) {
+    stage_rle_header(c, g, hdr, lane);
+    return;
+  }
   if (lane != 0 || !is_block_fmt(c.fmt)) return;
   if (g < c.nb && 16 * (g + 1) <= c.size) cp_async16(hdr, c.p + 16 * g);
 }
@@ -612,7 +687,10 @@ MS_DEV void stage_header(const ColView& c, uint64_t g, uint64_t* hdr, int lane) 
 // the same max_units then reads it in place from global memory.
 MS_DEV void stage_payload(const ColView& c, uint64_t g, const uint64_t* hdr, uint16_t* slot, int lane,
                           int max_units = 256) {
-  if (c.fmt == MS_RLE) return;  // read from global memory by rle_expand
+  if (c.fmt == MS_RLE) {
+    stage_rle_payload(c, g, hdr, slot, lane);
+    return;
+  }
   const uint8_t* src = nullptr;
   int units = 0;
   bool swizzle = false;
@@ -656,8 +734,10 @@ MS_DEV int decode_staged(const ColView& c, uint64_t g, const uint64_t* hdr, cons
     return 0;
   }
   const int valid = (int)min((uint64_t)kBlock, c.n - base);
-  if (c.fmt == MS_RLE) {
-    rle_expand(c, g, lane, valid, v, ctl);
+  if (c.fmt == MS_RLE) {  // out of line: the other formats' decoders keep their registers
+    const Values16 r = rle_decode_staged(c, g, hdr, slot, lane, valid, ctl);
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = r.v[k];
     return valid;
   }
   if (c.fmt == MS_UNCOMPR) {

@@ -59,7 +59,34 @@ struct TileSmem {
 // synchronises the CTA).
 // The CTA takes claims claim0, claim0 + cstride, ... (by default blockIdx.x and
 // gridDim.x).
-template <int BUF, class Body>
+// The tile stream of an RLE column: the CTA's warps expand its claims' blocks from
+// the runs (rle_expand_at), each warp loading the directory entries of its next block
+// one ahead.  Kernels instantiate it in place of cta_stream for RLE inputs (cta_stream's
+// kRle), so that the other formats' kernels keep their registers.
+template <class Body>
+MS_DEV void rle_stream(const ColView& c, DevCtl* ctl, Body& body, uint64_t claim0, uint64_t cstride) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const uint64_t nch = (c.n + kBlock - 1) / kBlock;
+  const uint64_t nclaims = (nch + kClaim - 1) / kClaim;
+  for (uint64_t cl = claim0; cl < nclaims; cl += cstride) {
+    const uint64_t e = min(nch, (cl + 1) * kClaim);
+    uint64_t k = cl * kClaim + warp;
+    uint64_t dn = k < e ? rle_dir_load(c, k, lane) : 0;
+    for (; k < e; k += nwarps) {
+      const uint64_t d = dn;
+      if (k + nwarps < e) dn = rle_dir_load(c, k + nwarps, lane);
+      const int valid = (int)min((uint64_t)kBlock, c.n - k * kBlock);
+      uint64_t v[16];
+      rle_expand_at(c, k, lane, valid, d, v, ctl);
+      body(k, v, valid, false);
+    }
+    __syncthreads();
+  }
+}
+
+// kRle: the kernel's instantiation for RLE inputs (rle_stream); the other one reports
+// an RLE input as a format error.
+template <int BUF, bool kRle = false, class Body>
 MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body body, uint64_t claim0 = ~0ull,
                        uint64_t cstride = 0) {
   static_assert(BUF >= 4096 && BUF % 4096 == 0, "buffer size");
@@ -72,20 +99,15 @@ MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body bo
   const uint32_t fixed = c.fmt == MS_UNCOMPR ? 4096u : (c.fmt == MS_STATIC_BP ? 64u * (uint32_t)c.bw : 0u);
   const uint64_t pay0 = 16 * c.nb;  // byte offset of the block payloads (block formats)
 
-  if (c.fmt == MS_RLE) {  // runs are read from global memory by rle_expand: nothing to stage
-    if (claim0 == ~0ull) {
-      claim0 = blockIdx.x;
-      cstride = gridDim.x;
-    }
-    for (uint64_t cl = claim0; cl < nclaims; cl += cstride) {
-      const uint64_t e = min(nch, (cl + 1) * kClaim);
-      for (uint64_t k = cl * kClaim + warp; k < e; k += nwarps) {
-        const int valid = (int)min((uint64_t)kBlock, c.n - k * kBlock);
-        uint64_t v[16];
-        rle_expand(c, k, lane, valid, v, ctl);
-        body(k, v, valid, false);
+  if (kRle || c.fmt == MS_RLE) {  // runs are read from global memory: nothing to stage
+    if constexpr (kRle) {
+      if (claim0 == ~0ull) {
+        claim0 = blockIdx.x;
+        cstride = gridDim.x;
       }
-      __syncthreads();
+      rle_stream(c, ctl, body, claim0, cstride);
+    } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+      set_error(ctl, MS_ERR_FORMAT, c.n);
     }
     return;
   }
@@ -289,6 +311,7 @@ MS_DEV void cta_stream(const ColView& c, TileSmem<BUF>* sm, DevCtl* ctl, Body bo
 struct MarkArgs {
   const DevMeta* in;
   DevCtl* ctl;
+  int rle;  // the input is RLE (selects the kernels' RLE instantiation on the host)
   // the predicate as one range test: hit = ((x - lo) <= span) != negate, never if empty
   uint64_t lo, span;
   uint32_t negate, empty;
@@ -498,10 +521,6 @@ struct EmitPlan {
   int valid;
 };
 
-MS_DEV void cp_async8(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
 
 // bs0 = bstart[g], bs1 = bstart[g + 1] (or anything when g is the last block).
 MS_DEV EmitPlan emit_plan(const ProduceArgs& a, uint64_t n_out, uint64_t g, uint64_t bs0, uint64_t bs1) {

@@ -46,9 +46,10 @@ ms_status launch_agg_sum(ms_ctx* c, const DevMeta* in, uint64_t* d_result, uint6
                          bool rle = false);
 ms_status launch_group_sum(ms_ctx* c, const DevMeta* gid, const DevMeta* val, uint64_t G, uint64_t* d_sums,
                            uint64_t n_max, cudaStream_t s);
+// rle: the input column is RLE (the kernels' RLE instantiation)
 ms_status launch_build_keys(ms_ctx* c, const DevMeta* keys, uint64_t domain, uint32_t* bits, uint64_t n_max,
-                            cudaStream_t s);
-ms_status launch_stats(ms_ctx* c, const DevMeta* in, uint64_t* d_stats, uint64_t n_max, cudaStream_t s);
+                            cudaStream_t s, bool rle);
+ms_status launch_stats(ms_ctx* c, const DevMeta* in, uint64_t* d_stats, uint64_t n_max, cudaStream_t s, bool rle);
 ms_status launch_selftest_wait(ms_ctx* c, cudaStream_t s);
 
 // producers (ms_map_*.cu): one warp-independent k_map<OP> launch
@@ -67,9 +68,10 @@ ms_status launch_map<OP_EMIT>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStr
 template <>
 ms_status launch_map<OP_PROJECT_WARP>(ms_ctx* c, ProduceArgs& a, uint64_t n_max, cudaStream_t s);
 
-// run-length encoding of a column (ms_rle.cu); `in` null: raw uint64 input (raw, n_max)
+// run-length encoding of a column (ms_rle.cu); `in` null: raw uint64 input (raw, n_max);
+// in_rle: the input is itself RLE
 ms_status rle_encode(ms_ctx* c, const DevMeta* in, const uint64_t* raw, uint64_t n_max, const Work& w,
-                     ms_column** out, cudaStream_t s);
+                     ms_column** out, cudaStream_t s, bool in_rle = false);
 
 // placement of a staged block-format output (ms_place.cu)
 ms_status launch_place(ms_ctx* c, const Work& w, DevMeta* out, uint64_t n_max, cudaStream_t s);

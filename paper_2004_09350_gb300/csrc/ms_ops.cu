@@ -168,7 +168,7 @@ ms_status ms_morph(ms_ctx* c, const ms_column* col, int fmt, int bw, ms_column**
   Work w;
   ms_status st = carve(c, col->n_max, 0, &w, s);
   if (st != MS_OK) return st;
-  if (fmt == MS_RLE) return rle_encode(c, c->metas + col->slot, nullptr, col->n_max, w, out, s);
+  if (fmt == MS_RLE) return rle_encode(c, c->metas + col->slot, nullptr, col->n_max, w, out, s, col->fmt == MS_RLE);
   ProduceArgs a{};
   a.in0 = c->metas + col->slot;
   a.raw_cap = ~0ull;
@@ -189,6 +189,7 @@ ms_status ms_select(ms_ctx* c, const ms_column* in, int cmp, uint64_t c1, uint64
   MarkArgs m{};
   m.in = c->metas + in->slot;
   m.ctl = c->ctl;
+  m.rle = in->fmt == MS_RLE;
   predicate_as_range(cmp, c1, c2, &m);
   st = launch_mark_scan(c, m, w, in->n_max, s);
   if (st != MS_OK) return st;
@@ -293,13 +294,14 @@ ms_status ms_semijoin(ms_ctx* c, const ms_column* probe, const ms_column* keys, 
   ms_status st = carve(c, std::max(probe->n_max, keys->n_max), domain, &w, s);
   if (st != MS_OK) return st;
   if (cuda_status(cudaMemsetAsync(w.keybits, 0, 4 * cdiv(domain, 32), s)) != MS_OK) return MS_ERR_CUDA;
-  st = launch_build_keys(c, c->metas + keys->slot, domain, w.keybits, keys->n_max, s);
+  st = launch_build_keys(c, c->metas + keys->slot, domain, w.keybits, keys->n_max, s, keys->fmt == MS_RLE);
   if (st != MS_OK) return st;
   MarkArgs m{};
   m.in = c->metas + probe->slot;
   m.ctl = c->ctl;
   m.keybits = w.keybits;
   m.domain = domain;
+  m.rle = probe->fmt == MS_RLE;
   st = launch_mark_scan(c, m, w, probe->n_max, s);
   if (st != MS_OK) return st;
   return emit_positions(c, w, probe->n_max, fmt, bw, out, s);
@@ -310,7 +312,7 @@ ms_status ms_column_stats(ms_ctx* c, const ms_column* col, uint64_t* d_stats, vo
   if (!c || !owned(c, col) || !d_stats) return MS_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cuda_status(cudaMemsetAsync(d_stats, 0, 8 * MS_STATS_WORDS, s)) != MS_OK) return MS_ERR_CUDA;
-  return launch_stats(c, c->metas + col->slot, d_stats, col->n_max, s);
+  return launch_stats(c, c->metas + col->slot, d_stats, col->n_max, s, col->fmt == MS_RLE);
 }
 
 ms_status ms_selftest_wait_timeout(ms_ctx* c, void* stream) {

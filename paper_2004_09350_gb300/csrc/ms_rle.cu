@@ -53,12 +53,13 @@ MS_DEV uint64_t rle_last_value(const uint64_t* v, int valid) {
   return __shfl_sync(kFull, (i & 1) ? w2[1] : w2[0], t >> 4);
 }
 
+template <bool kRle>
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_rle_count(RleArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   auto* sm = reinterpret_cast<TileSmem<kTileBuf>*>(smem_raw);
   const int lane = threadIdx.x & 31;
   const ColView c = view_of(a.in);
-  cta_stream<kTileBuf>(c, sm, a.ctl, [&](uint64_t g, const uint64_t* v, int valid, bool) {
+  cta_stream<kTileBuf, kRle>(c, sm, a.ctl, [&](uint64_t g, const uint64_t* v, int valid, bool) {
     const uint32_t heads = __reduce_add_sync(kFull, (unsigned)__popc(rle_inner_heads(v, valid, lane)));
     const uint64_t first = __shfl_sync(kFull, v[0], 0);
     const uint64_t last = rle_last_value(v, valid);
@@ -77,6 +78,7 @@ __global__ void k_rle_bounds(RleArgs a) {
     if (g == 0 || a.fl[2 * g] != a.fl[2 * g - 1]) a.counts[g] += 1;
 }
 
+template <bool kRle>
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_rle_write(RleArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   auto* sm = reinterpret_cast<TileSmem<kTileBuf>*>(smem_raw);
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_rle_write(RleA
   uint64_t* ends = vals + R;
   uint64_t* dir = ends + R;
   if (fits) {
-    cta_stream<kTileBuf>(c, sm, ctl, [&](uint64_t g, const uint64_t* v, int valid, bool) {
+    cta_stream<kTileBuf, kRle>(c, sm, ctl, [&](uint64_t g, const uint64_t* v, int valid, bool) {
       const uint64_t first = __shfl_sync(kFull, v[0], 0);
       const bool h0 = g == 0 || first != ldg64(a.fl + 2 * g - 1);
       uint32_t m = rle_inner_heads(v, valid, lane);
@@ -167,7 +169,9 @@ int rle_grid(ms_ctx* c, K kernel, uint64_t n_max) {
 
 // `in` may be null for raw uint64 input (raw, n); the scratch comes from w.
 ms_status rle_encode(ms_ctx* c, const DevMeta* in, const uint64_t* raw, uint64_t n_max, const Work& w,
-                     ms_column** out, cudaStream_t s) {
+                     ms_column** out, cudaStream_t s, bool in_rle) {
+  auto count = in_rle ? k_rle_count<true> : k_rle_count<false>;
+  auto write = in_rle ? k_rle_write<true> : k_rle_write<false>;
   if (!in) {  // a column record for the raw input, in scratch the encoder does not use
     DevMeta* m = reinterpret_cast<DevMeta*>(w.status2);
     k_rle_raw_meta<<<1, 1, 0, s>>>(m, raw, n_max);
@@ -180,7 +184,7 @@ ms_status rle_encode(ms_ctx* c, const DevMeta* in, const uint64_t* raw, uint64_t
   ms_status st = MS_OK;
   {
     ProfScope ps(c, MS_K_RLE, s);
-    k_rle_count<<<rle_grid(c, k_rle_count, n_max), kTileThreads, kRleSmem, s>>>(a);
+    count<<<rle_grid(c, count, n_max), kTileThreads, kRleSmem, s>>>(a);
     st = cuda_status(cudaGetLastError());
     if (st == MS_OK) {
       const uint64_t nch = cdiv(n_max, kBlock);
@@ -197,7 +201,7 @@ ms_status rle_encode(ms_ctx* c, const DevMeta* in, const uint64_t* raw, uint64_t
   }
   if (st == MS_OK) {
     ProfScope ps(c, MS_K_RLE, s);
-    k_rle_write<<<rle_grid(c, k_rle_write, n_max), kTileThreads, kRleSmem, s>>>(a);
+    write<<<rle_grid(c, write, n_max), kTileThreads, kRleSmem, s>>>(a);
     st = cuda_status(cudaGetLastError());
   }
   if (st != MS_OK) {
