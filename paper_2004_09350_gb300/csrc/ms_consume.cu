@@ -11,7 +11,7 @@ namespace ms {
 
 
 template <int BUF, bool kRle>
-__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark_t(MarkArgs a) {
+__global__ void __launch_bounds__(kTileThreads, kRle ? 2 : kTileMinBlocks) k_mark_t(MarkArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31;
   auto* sm = reinterpret_cast<TileSmem<BUF>*>(smem_raw);
@@ -68,7 +68,7 @@ constexpr int kKeyTileBuf = 16384;
 constexpr size_t kKeyTileSmemBytes = sizeof(TileSmem<kKeyTileBuf>);
 
 template <bool kRle>
-__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_mark_keys(MarkArgs a) {
+__global__ void __launch_bounds__(kTileThreads, kRle ? 2 : kTileMinBlocks) k_mark_keys(MarkArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31;
   auto* sm = reinterpret_cast<TileSmem<kKeyTileBuf>*>(smem_raw);
@@ -242,7 +242,7 @@ ms_status launch_selftest_wait(ms_ctx* c, cudaStream_t s) {
 
 // Semi-join build side: set bit key for every key of the build column.
 template <bool kRle>
-__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_build_keys(const DevMeta* keys, uint64_t domain,
+__global__ void __launch_bounds__(kTileThreads, kRle ? 2 : kTileMinBlocks) k_build_keys(const DevMeta* keys, uint64_t domain,
                                                                              uint32_t* bits, DevCtl* ctl) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31;
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_build_keys(con
 // pass, per chunk reductions, block-level accumulation in shared memory, one
 // global atomic per statistic per CTA.
 template <bool kRle>
-__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_stats(const DevMeta* in, uint64_t* stats,
+__global__ void __launch_bounds__(kTileThreads, kRle ? 2 : kTileMinBlocks) k_stats(const DevMeta* in, uint64_t* stats,
                                                                         DevCtl* ctl) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ unsigned long long s_acc[MS_STATS_WORDS];

@@ -724,7 +724,9 @@ MS_DEV void stage_payload(const ColView& c, uint64_t g, const uint64_t* hdr, uin
 
 // Decodes staged chunk g of column c into lane registers; returns its valid count.
 // Payloads above max_units 16-byte units (not staged) are read from global memory.
-template <bool kCompact = kCompactCodec>
+// kRleInline: RLE blocks decoded in line (the decompress / morph producer, where RLE
+// input is the common case); elsewhere out of line, so that the kernel keeps its registers.
+template <bool kCompact = kCompactCodec, bool kRleInline = false>
 MS_DEV int decode_staged(const ColView& c, uint64_t g, const uint64_t* hdr, const uint16_t* slot, int lane,
                          uint64_t v[16], DevCtl* ctl, int max_units = 256) {
   const uint64_t base = g * kBlock;
@@ -734,10 +736,22 @@ MS_DEV int decode_staged(const ColView& c, uint64_t g, const uint64_t* hdr, cons
     return 0;
   }
   const int valid = (int)min((uint64_t)kBlock, c.n - base);
-  if (c.fmt == MS_RLE) {  // out of line: the other formats' decoders keep their registers
-    const Values16 r = rle_decode_staged(c, g, hdr, slot, lane, valid, ctl);
+  if (c.fmt == MS_RLE) {
+    if constexpr (kRleInline) {
+      uint64_t r0;
+      int m;
+      if (rle_window(c, hdr, &r0, &m)) {
+        const uint64_t* w = reinterpret_cast<const uint64_t*>(slot);
+        rle_values_from_runs(base + 16 * (uint64_t)lane, lane, valid, m, lane < m ? w[lane] : 0,
+                             lane < m ? w[32 + lane] : 0, v);
+      } else {
+        rle_expand(c, g, lane, valid, v, ctl);
+      }
+    } else {
+      const Values16 r = rle_decode_staged(c, g, hdr, slot, lane, valid, ctl);
 #pragma unroll
-    for (int k = 0; k < 16; k++) v[k] = r.v[k];
+      for (int k = 0; k < 16; k++) v[k] = r.v[k];
+    }
     return valid;
   }
   if (c.fmt == MS_UNCOMPR) {
@@ -873,14 +887,15 @@ struct ChunkStream {
 
   // Decodes chunk i (already landed) into lane registers; returns its valid count.
   // kC selects the compact (one loop for every width) lane-stream decoder.
-  template <bool kC = kCompactCodec>
+  template <bool kC = kCompactCodec, bool kRleInline = false>
   MS_DEV int decode(uint64_t i, uint64_t v[16], DevCtl* ctl) const {
     if (i >= count) {
 #pragma unroll
       for (int k = 0; k < 16; k++) v[k] = 0;
       return 0;
     }
-    return decode_staged<kC>(c, chunk(i), sm->hdr[i % (2 * kDepth)], sm->slot[i % kDepth], lane, v, ctl, 4 * SW);
+    return decode_staged<kC, kRleInline>(c, chunk(i), sm->hdr[i % (2 * kDepth)], sm->slot[i % kDepth], lane, v,
+                                         ctl, 4 * SW);
   }
 };
 

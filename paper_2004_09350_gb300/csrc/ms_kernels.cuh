@@ -68,17 +68,43 @@ MS_DEV void rle_stream(const ColView& c, DevCtl* ctl, Body& body, uint64_t claim
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const uint64_t nch = (c.n + kBlock - 1) / kBlock;
   const uint64_t nclaims = (nch + kClaim - 1) / kClaim;
+  const uint64_t R = c.nb;
+  const uint64_t* val = reinterpret_cast<const uint64_t*>(c.p);
+  // the runs of a block when at most 32 cover it (lane i: end and value of run r0 + i);
+  // returns their count, or 0 when the block is expanded by a search instead
+  auto load_runs = [&](uint64_t d, uint64_t& e, uint64_t& x) -> int {
+    const uint64_t r0 = __shfl_sync(kFull, d, 0), r1 = __shfl_sync(kFull, d, 1);
+    if (!rle_sound(c) || r0 >= R || r1 >= R || r1 < r0 || r1 - r0 >= 32) return 0;
+    const int m = (int)(r1 - r0) + 1;
+    if (lane < m) {
+      e = ldg64(val + R + r0 + lane);
+      x = ldg64(val + r0 + lane);
+    }
+    return m;
+  };
   for (uint64_t cl = claim0; cl < nclaims; cl += cstride) {
-    const uint64_t e = min(nch, (cl + 1) * kClaim);
+    const uint64_t end = min(nch, (cl + 1) * kClaim);
     uint64_t k = cl * kClaim + warp;
-    uint64_t dn = k < e ? rle_dir_load(c, k, lane) : 0;
-    for (; k < e; k += nwarps) {
-      const uint64_t d = dn;
-      if (k + nwarps < e) dn = rle_dir_load(c, k + nwarps, lane);
+    // block k: directory entries d0 and runs (m0, e0, x0); block k + nwarps: d1, its
+    // runs loaded while block k is expanded; block k + 2 nwarps: d2
+    uint64_t d0 = k < end ? rle_dir_load(c, k, lane) : 0;
+    uint64_t d1 = k + nwarps < end ? rle_dir_load(c, k + nwarps, lane) : 0;
+    uint64_t e0 = 0, x0 = 0;
+    int m0 = k < end ? load_runs(d0, e0, x0) : 0;
+    for (; k < end; k += nwarps) {
+      const uint64_t d2 = k + 2 * nwarps < end ? rle_dir_load(c, k + 2 * nwarps, lane) : 0;
+      uint64_t e1 = 0, x1 = 0;
+      const int m1 = k + nwarps < end ? load_runs(d1, e1, x1) : 0;
       const int valid = (int)min((uint64_t)kBlock, c.n - k * kBlock);
       uint64_t v[16];
-      rle_expand_at(c, k, lane, valid, d, v, ctl);
+      if (m0 > 0) rle_values_from_runs(k * kBlock + 16 * (uint64_t)lane, lane, valid, m0, e0, x0, v);
+      else rle_expand_at(c, k, lane, valid, d0, v, ctl);
       body(k, v, valid, false);
+      d0 = d1;
+      d1 = d2;
+      e0 = e1;
+      x0 = x1;
+      m0 = m1;
     }
     __syncthreads();
   }
@@ -1876,7 +1902,7 @@ __global__ void __launch_bounds__(kThreads, ProducePlan<OP>::kMinBlocks) k_map(P
       cp_async_commit();
       out_stage = ring0->slot[i % D];
       if constexpr (OP == OP_COMPRESS || OP == OP_DECOMPRESS) {
-        valid = st0.decode(i, v, ctl);
+        valid = st0.template decode<kCompactCodec, OP == OP_DECOMPRESS>(i, v, ctl);
         valid = (int)min((uint64_t)valid, n_out - g * kBlock);
       } else if constexpr (OP == OP_CALC) {
         valid = st0.decode(i, v, ctl);

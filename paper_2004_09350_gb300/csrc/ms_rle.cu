@@ -54,7 +54,7 @@ MS_DEV uint64_t rle_last_value(const uint64_t* v, int valid) {
 }
 
 template <bool kRle>
-__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_rle_count(RleArgs a) {
+__global__ void __launch_bounds__(kTileThreads, kRle ? 2 : kTileMinBlocks) k_rle_count(RleArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   auto* sm = reinterpret_cast<TileSmem<kTileBuf>*>(smem_raw);
   const int lane = threadIdx.x & 31;
@@ -79,7 +79,7 @@ __global__ void k_rle_bounds(RleArgs a) {
 }
 
 template <bool kRle>
-__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_rle_write(RleArgs a) {
+__global__ void __launch_bounds__(kTileThreads, kRle ? 2 : kTileMinBlocks) k_rle_write(RleArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   auto* sm = reinterpret_cast<TileSmem<kTileBuf>*>(smem_raw);
   const int lane = threadIdx.x & 31;
