@@ -85,3 +85,19 @@ def test_entry_points_reject_missing_arguments_before_touching_the_device(lib):
     }
     got = {name: call() for name, call in calls.items()}
     assert all(v == bad for v in got.values()), {k: v for k, v in got.items() if v != bad}
+
+
+def _header_enum(name_prefix):
+    """name -> value of the header's enumerators with the given prefix."""
+    import re
+    text = open(morphstore._HEADER).read()
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(" + name_prefix + r"[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+
+
+def test_binding_format_and_kernel_ids_match_the_header():
+    fm = _header_enum("MS_")
+    for name in ("UNCOMPR", "STATIC_BP", "DYN_BP", "DELTA_BP", "FOR_BP", "RLE", "FOR_STATIC_BP", "DELTA_STATIC_BP"):
+        assert getattr(morphstore, name) == fm["MS_" + name], name
+        assert morphstore.FORMAT_NAMES[fm["MS_" + name]] == name.lower()
+    ks = _header_enum("MS_K_")
+    assert ks["MS_K_RLE"] == ks["MS_K_COUNT"] - 1
