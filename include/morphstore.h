@@ -208,8 +208,9 @@ ms_status ms_column_free(ms_ctx *ctx, ms_column *col, void *stream);
 /* -------------------------------------------------------------- operators */
 
 /* compress (Sec. 4.1): n uncompressed values at device address d_in (16-byte
-   aligned) -> new column in `fmt`.  MS_ERR_VALUE_TOO_WIDE (device) if a value
-   needs more than static_bw bits under MS_STATIC_BP. */
+   aligned) -> new column in `fmt` (any format, MS_RLE included).
+   MS_ERR_VALUE_TOO_WIDE (device) if a value needs more than static_bw bits under
+   MS_STATIC_BP, or a residual under MS_FOR_STATIC_BP / MS_DELTA_STATIC_BP. */
 ms_status ms_compress(ms_ctx *ctx, const uint64_t *d_in, uint64_t n, int fmt,
                       int static_bw, ms_column **out, void *stream);
 
@@ -234,9 +235,12 @@ ms_status ms_select_packed(ms_ctx *ctx, const ms_column *in, int cmp, uint64_t c
 /* morph (Sec. 3.2, "On-the-Fly Morphing"): the column's values as a new column in
    out_fmt, with no uncompressed intermediate in device memory.  Each 512-value
    block is decoded into registers and re-encoded in out_fmt by the same warp (a
-   direct morphing algorithm for every ordered pair of formats: n^2 - n = 20 of
-   them, and the identity).  MS_ERR_VALUE_TOO_WIDE (device) for a value wider than
-   out_static_bw under MS_STATIC_BP. */
+   direct morphing algorithm for every ordered pair of the five block and
+   fixed-width formats: n^2 - n = 20 of them, and the identity; the static
+   cascades likewise).  Into MS_RLE the column is decoded twice, block by block:
+   once to count the runs of every block, once to write them (sizes from a scan of
+   the counts).  MS_ERR_VALUE_TOO_WIDE (device) for a value or residual wider than
+   out_static_bw under MS_STATIC_BP, MS_FOR_STATIC_BP or MS_DELTA_STATIC_BP. */
 ms_status ms_morph(ms_ctx *ctx, const ms_column *col, int out_fmt, int out_static_bw,
                    ms_column **out, void *stream);
 
@@ -261,7 +265,8 @@ ms_status ms_calc(ms_ctx *ctx, int op, const ms_column *a, const ms_column *b,
                   void *stream);
 
 /* sum (Sec. 5.1 "Simple Query"): *d_result = sum of all values modulo 2^64
-   (0 for an empty column).  d_result is caller-owned device memory. */
+   (0 for an empty column).  d_result is caller-owned device memory.  An MS_RLE
+   column is summed on its runs (value x run length), without expanding them. */
 ms_status ms_agg_sum(ms_ctx *ctx, const ms_column *in, uint64_t *d_result,
                      void *stream);
 
