@@ -412,7 +412,8 @@ typedef struct {
    The columns must outlive the batch and must not be freed before it.
    Errors: MS_ERR_INVALID_ARG (NULL pointers, n_frags == 0, a foreign or freed
    column, an unknown cmp, x and y of unequal length, 2^31 chunks or more),
-   MS_ERR_NOMEM, MS_ERR_CUDA. */
+   MS_ERR_FORMAT (a column in MS_RLE or a static cascade: the batch kernels take
+   the five base formats), MS_ERR_NOMEM, MS_ERR_CUDA. */
 ms_status ms_batch_create(ms_ctx *ctx, uint32_t n_frags, ms_column *const *x,
                           ms_column *const *y, const int32_t *cmp, const uint64_t *c1,
                           const uint64_t *c2, ms_batch **out, void *stream);

@@ -150,7 +150,7 @@ ms_status ms_batch_create(ms_ctx* c, uint32_t n, ms_column* const* x, ms_column*
   for (uint32_t f = 0; f < n; f++) {
     if (!owned_column(c, x[f]) || !owned_column(c, y[f]) || cmp[f] < MS_EQ || cmp[f] > MS_BETWEEN)
       return MS_ERR_INVALID_ARG;
-    if (x[f]->fmt == MS_RLE || y[f]->fmt == MS_RLE) return MS_ERR_FORMAT;  // block and fixed-width formats only
+    if (x[f]->fmt > MS_FOR_BP || y[f]->fmt > MS_FOR_BP) return MS_ERR_FORMAT;  // the five base formats only
     MarkArgs m{};
     predicate_as_range(cmp[f], c1[f], c2 ? c2[f] : 0, &m);
     init[f] = BatchInit{x[f]->slot, y[f]->slot, m.lo, m.span, m.negate, m.empty};
