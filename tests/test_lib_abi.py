@@ -101,3 +101,12 @@ def test_binding_format_and_kernel_ids_match_the_header():
         assert morphstore.FORMAT_NAMES[fm["MS_" + name]] == name.lower()
     ks = _header_enum("MS_K_")
     assert ks["MS_K_RLE"] == ks["MS_K_COUNT"] - 1
+
+
+def test_oracle_and_binding_share_the_format_numbering():
+    """The oracle numbers the formats from the same written definitions (it imports
+    nothing from the library); both sides must agree so that the parity tests compare
+    like with like."""
+    import oracle
+    for name in ("UNCOMPR", "STATIC_BP", "DYN_BP", "DELTA_BP", "FOR_BP", "RLE", "FOR_STATIC_BP", "DELTA_STATIC_BP"):
+        assert getattr(oracle, name) == getattr(morphstore, name), name
